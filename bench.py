@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput of the Hessian-preconditioned HMC hot path of arXiv:2504.07090 on one GB300.
+
+One step = one HMC iteration on the 37-antenna HERA-like workload (cfg1: 64 channels
+140-160 MHz, 60 LSTs, 128x192 pixels, 128x128 sky modes per channel + 4 complex gain
+modes per antenna, 1,048,872 parameters): draw the momentum p = L z through the
+preconditioner's Cholesky factor, then one 20-step leapfrog trajectory through
+fm_leapfrog (21 chi^2+gradient evaluations: mode->pixel, beam, in-kernel fringe
+phasors, tensor-core contraction, gains, chi^2, tensor-core adjoint, pixel->mode,
+gain gradient, kicks, block-triangular drift, FP64 Hamiltonian, Metropolis test).
+
+Prints one JSON line (rank 0).  value = chi^2+grad evaluations/s of the whole job.
+`--impl reference` times the FP64 CPU oracle instead (bounded samples, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "χ²+grad evals/s & vis-pixel terms/s at stated err vs FP64; leapfrog steps/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+N_PRODUCTS = {"bf16x1": 1, "fp16x1": 1, "bf16x3": 3, "fp16x3": 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg1")
+    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--traj", type=int, default=20, help="leapfrog steps per trajectory")
+    ap.add_argument("--eps", type=float, default=0.1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle timing sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}, "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def workload_desc(prob, traj):
+    return (f"{prob.name}: {prob.n_ant}-antenna hexagon ({prob.n_bl} baselines), {prob.n_freq} ch "
+            f"{prob.freq_hz[0] / 1e6:.0f}-{prob.freq_hz[-1] / 1e6:.0f} MHz, {prob.n_lst} LSTs, "
+            f"{prob.n_dec}x{prob.n_ra} px, {prob.n_mode_ra}x{prob.n_mode_dec} modes/ch, "
+            f"{prob.n_params} params; one HMC iteration = p = L z + {traj}-step leapfrog ({traj + 1} chi2+grad evals)")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample_rate(prob, theta, d, budget_s: float):
+    """chi^2+grad evals/s of the FP64 oracle, from a bounded sample: the pixel<->mode
+    transforms of one channel and the fringe sum + adjoint of k (channel, LST) pairs,
+    extrapolated linearly to all channels and pairs (the work is exactly linear in both)."""
+    import oracle
+    o = oracle.Oracle(prob)
+    o.sigma = prob.sigma
+    a, gam = o.split(theta)
+    t0 = time.perf_counter()
+    x0 = o.sky_f(a[0])
+    abar = o.sky_adjoint_f(x0)
+    t_chan = time.perf_counter() - t0
+    g = o.gains(gam)
+    k, t_pairs = 0, 0.0
+    while True:
+        t = k % prob.n_lst
+        t1 = time.perf_counter()
+        V = o.vis_ft(0, t, x0)
+        r = g[0, o.bl_i] * np.conj(g[0, o.bl_j]) * V - d[0, t]
+        omega = np.conj(g[0, o.bl_i]) * g[0, o.bl_j] * r / o.sigma ** 2
+        xbar = np.zeros(o.npix)
+        o.adjoint_ft(0, t, omega, xbar)
+        t_pairs += time.perf_counter() - t1
+        k += 1
+        if t_pairs + t_chan > budget_s or k >= prob.n_lst:
+            break
+    per_eval = prob.n_freq * t_chan + prob.n_freq * prob.n_lst * (t_pairs / k)
+    sample = (f"1 channel of pixel<->mode transforms ({t_chan:.2f} s) + {k} (channel, LST) pairs of fringe sum "
+              f"and adjoint ({t_pairs:.2f} s), extrapolated to {prob.n_freq} channels x {prob.n_lst} LSTs")
+    return 1.0 / per_eval, oracle.num_threads(), sample, t_chan + t_pairs
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2504_07090_gb300 import synth
+    prob = synth.config(args.config)
+    tr = synth.draw_truth(prob)
+    rng = np.random.default_rng(1)
+    prob.sigma = 1.0
+    d = rng.standard_normal((prob.n_freq, prob.n_lst, prob.n_bl)) * 10 + 0j
+    budget = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    cores = 1
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        r, cores, sample, _ = oracle_sample_rate(prob, tr.theta, d, budget)
+        if i >= args.warmup:
+            rates.append(r)
+    v = float(np.mean(rates))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "chi2+grad evals/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(prob, args.traj).split(";")[0] + "; one chi2+grad evaluation"},
+        "cpu_baseline": {"value": v, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "chi2+grad evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2504_07090_gb300 import build, fm, synth
+    build.build()
+
+    prob = synth.config(args.config)
+    tr = synth.draw_truth(prob)
+    dev = "cuda"
+    # mock data: model at the truth plus noise of 1 % of the mean |V| per real component
+    h0 = fm.ForwardModel(prob, args.precision, sigma=1.0)
+    th_true = torch.tensor(tr.theta, dtype=torch.float32, device=dev)
+    m = h0.forward(th_true)
+    sigma = 0.01 * float(torch.linalg.norm(m, dim=-1).mean())
+    h0.close()
+    prob.sigma = sigma
+    h = fm.ForwardModel(prob, args.precision, sigma=sigma)
+    d = (m + sigma * torch.tensor(tr.noise, dtype=torch.float32, device=dev)).contiguous()
+    h.set_data(d)
+    mu, lam = synth.prior_for(prob, tr.theta)
+    h.set_prior(torch.tensor(mu, dtype=torch.float32, device=dev), torch.tensor(lam, dtype=torch.float32, device=dev))
+    q = th_true.clone()
+    h.build_precond(q, 64)
+    torch.cuda.synchronize()
+
+    K, W = args.steps, args.warmup
+    zs = torch.tensor(synth.random_vectors(h.n_params, K + W, 20250420 + rank), dtype=torch.float32, device=dev)
+    us = np.random.default_rng(20250421 + rank).random(K + W)
+    p = torch.empty_like(q)
+    h_out = torch.empty(2, dtype=torch.float64, device=dev)
+    acc = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
+    st = torch.cuda.current_stream()
+
+    def step(i):
+        h.precond_apply(0, zs[i], out=p)
+        h.leapfrog(q, p, args.eps, args.traj, float(us[i]), h_out, acc)
+
+    for i in range(W):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    h.sync_status()
+
+    clocks = ClockSampler(local)
+    h.get_profile()
+    h.set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = fm.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    n_acc = 0
+    torch.cuda.nvtx.range_push("bench_timed")
+    for i in range(K):
+        flush.zero_()
+        evs[i][0].record(st)
+        step(W + i)
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    launches = fm.kernel_launches() - launches0
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    h.set_profiling(False)
+    (fwd_ms, adj_ms), (fwd_n, adj_n) = h.get_profile()
+    h.sync_status()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    n_acc = int(acc.item())
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals_per_step = args.traj + 1
+    value = world * K * evals_per_step / (total_ms / 1000.0)
+
+    # roofline of the dominant contraction kernel (live CUDA events around each launch)
+    flops_launch = 8.0 * prob.n_ant ** 2 * prob.n_pix * prob.n_freq * prob.n_lst
+    dom = "forward contraction (k_vis_tc)" if fwd_ms >= adj_ms else "adjoint contraction (k_adj_tc)"
+    dom_ms, dom_n = (fwd_ms, fwd_n) if fwd_ms >= adj_ms else (adj_ms, adj_n)
+    pk, pk_src = peaks()
+    nprod = N_PRODUCTS.get(args.precision, 1)
+    peak = pk["bf16_tflops_sustained"] / nprod
+    achieved = flops_launch / (dom_ms / max(dom_n, 1) / 1000.0) / 1e12 if dom_n else None
+    roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
+                               f"(FP32-equivalent rate of the {args.precision} split); algorithmic flops per launch "
+                               f"= 8 n_ant^2 n_pix n_freq n_lst = {flops_launch:.4g}",
+                "forward_ms_per_launch": fwd_ms / max(fwd_n, 1), "adjoint_ms_per_launch": adj_ms / max(adj_n, 1),
+                "launches": {"forward": fwd_n, "adjoint": adj_n}}
+
+    # end to end through the C ABI with host buffers: H2D (q, z) -> step -> D2H (q, H, accepted)
+    e2e = None
+    if not args.no_e2e:
+        qh = q.detach().cpu().pin_memory()
+        zh = zs[:K].detach().cpu().pin_memory()
+        q_back = torch.empty_like(qh).pin_memory()
+        hh = torch.empty(2, dtype=torch.float64).pin_memory()
+        ah = torch.empty(1, dtype=torch.int32).pin_memory()
+        zdev = torch.empty_like(q)
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        for i in range(K):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            q.copy_(qh, non_blocking=True)
+            zdev.copy_(zh[i], non_blocking=True)
+            h.precond_apply(0, zdev, out=p)
+            h.leapfrog(q, p, args.eps, args.traj, float(us[W + i]), h_out, acc)
+            q_back.copy_(q, non_blocking=True)
+            hh.copy_(h_out, non_blocking=True)
+            ah.copy_(acc, non_blocking=True)
+            b.record(st)
+            torch.cuda.synchronize()
+            e_ms += a.elapsed_time(b)
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * K * evals_per_step / (e_ms / 1000.0), "unit": "chi2+grad evals/s",
+               "h2d_bytes_per_step": 2 * 4 * h.n_params, "d2h_bytes_per_step": 4 * h.n_params + 16 + 4}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dn = d.double().cpu().numpy()
+        r, cores, sample, _ = oracle_sample_rate(prob, tr.theta, dn[..., 0] + 1j * dn[..., 1], args.cpu_seconds)
+        cpu = {"value": r, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "chi2+grad evals/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "precision": args.precision, "data": "synthetic",
+            "config": {"workload": workload_desc(prob, args.traj), "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "terms_per_s": value * prob.terms_per_forward(),
+            "leapfrog_steps_per_s": world * K * args.traj / (total_ms / 1000.0),
+            "accepted_last": n_acc,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * fm.h -- C ABI of libfm: the visibility forward model, chi^2 gradient, Hessian-vector
+ * products, Gauss-Newton preconditioner and Hessian-preconditioned leapfrog of
+ * arXiv:2504.07090 (Kern, "A Differentiable, End-to-End Forward Model for 21 cm
+ * Cosmology"), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions (every entry point):
+ *  - Pointers named dev_* / documented "device" are caller-owned device memory,
+ *    contiguous, and must stay valid until the call's stream work completes.  Host
+ *    arrays (fm_config) are copied during fm_create.
+ *  - Real arrays are float (4 bytes) unless the handle was created with
+ *    FM_PREC_FP64_SIMT, in which case they are double.  Complex arrays interleave
+ *    (re, im) in that real type.
+ *  - Visibility layout: [n_freq][n_lst][n_bl] complex, baseline b enumerates the
+ *    antenna pairs (p, q), p < q, row-major (0,1), (0,2), ..., (1,2), ...
+ *  - Parameter vector theta (n_params reals): sky modes a[freq][m_ra][n_dec] first,
+ *    then gain coefficients gamma[ant][k][re/im].
+ *  - All work is enqueued on `stream` (NULL = legacy default stream) and is
+ *    asynchronous; outputs are valid once the stream reaches that point.
+ *  - A handle owns its device workspace and is not thread-safe: one host thread
+ *    and one stream at a time per handle.
+ *  - Errors: every call returns an fm_status; the message of the last failure on
+ *    the calling thread is available from fm_last_error().  Invalid arguments are
+ *    rejected before any work is enqueued.  Conditions only the device can see
+ *    (non-finite energy, a wait that timed out) are written to a device status word
+ *    and returned by the next fm_sync_status().
+ */
+#ifndef FM_H
+#define FM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FM_API __attribute__((visibility("default")))
+#else
+#define FM_API
+#endif
+
+typedef struct CUstream_st *fm_stream;   /* identical to cudaStream_t */
+typedef struct fm_ctx *fm_handle;
+
+typedef enum {
+    FM_OK = 0,
+    FM_ERR_INVALID_ARG = 1,   /* null pointer, bad size, unsupported combination */
+    FM_ERR_ALLOC = 2,         /* device allocation failed */
+    FM_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    FM_ERR_NONFINITE = 4,     /* chi^2 or the Hamiltonian was NaN/Inf (trajectory rejected) */
+    FM_ERR_TIMEOUT = 5,       /* a device-side wait exceeded its iteration limit */
+    FM_ERR_NOT_SPD = 6,       /* a preconditioner block stayed indefinite after inflation */
+    FM_ERR_UNSUPPORTED = 7,   /* shape or precision not supported by this build */
+    FM_ERR_STATE = 8          /* call order: e.g. leapfrog before data were set */
+} fm_status;
+
+typedef enum {
+    FM_PREC_FP64_SIMT = 0,    /* complex128 throughout, FP64 CUDA-core contraction */
+    FM_PREC_FP32_SIMT = 1,    /* FP32 storage and FP32 CUDA-core contraction */
+    FM_PREC_BF16X1 = 2,       /* FP32 storage, tcgen05 BF16 contraction, one product */
+    FM_PREC_BF16X3 = 3,       /* FP32 storage, tcgen05 BF16 hi/lo split, three products */
+    FM_PREC_FP16X1 = 4,       /* FP32 storage, tcgen05 FP16 contraction (power-of-two scaled), one product */
+    FM_PREC_FP16X3 = 5        /* FP32 storage, tcgen05 FP16 hi/lo split (scaled), three products */
+} fm_precision;
+
+/* Problem description (Sec. 2.1 discretised RIME; Sec. 3 parameterisation).
+ * All arrays are host memory and are copied by fm_create. */
+typedef struct {
+    int n_ant;                   /* antennas, >= 2 (baselines: all pairs p < q) */
+    const double *ant_enu_m;     /* [n_ant][3] east, north, up positions in metres */
+    int n_freq;                  /* channels, >= 1 */
+    const double *freq_hz;       /* [n_freq] channel frequencies in Hz */
+    int n_lst;                   /* local sidereal times, >= 1 */
+    const double *lst_rad;       /* [n_lst] in radians */
+    double latitude_rad;         /* array latitude */
+    int n_ra, n_dec;             /* pixel grid: n_dec rows of n_ra cells, pixel = dec*n_ra + ra */
+    double ra_min, ra_max;       /* RA cell edges (radians); cells are uniform */
+    double dec_min, dec_max;     /* Dec cell edges (radians); cells are uniform */
+    int n_mode_ra;               /* RA functions: 1, cos k a, sin k a (k < M/2), cos(M/2 a) */
+    int n_mode_dec;              /* Legendre polynomials P_0 .. P_{N-1} in normalised Dec */
+    int n_gain_modes;            /* complex Legendre-in-frequency coefficients per antenna */
+    double beam_fwhm_ref_rad;    /* Gaussian beam FWHM at beam_ref_hz (scales as 1/nu) */
+    double beam_ref_hz;
+    double sigma_noise;          /* noise standard deviation per real component (Jy) */
+    int precision;               /* fm_precision */
+} fm_config;
+
+/* Create a handle: validates the configuration, allocates the device workspace and
+ * runs the once-per-handle precompute on the device ("cached mode" of Sec. 6):
+ * topocentric pixel directions for every LST, cell solid angles, basis tables and
+ * the gain frequency basis.  Synchronous.  On failure *out is NULL. */
+FM_API fm_status fm_create(const fm_config *cfg, fm_handle *out);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+FM_API fm_status fm_destroy(fm_handle h);
+
+FM_API int64_t fm_num_params(fm_handle h);     /* n_freq*n_mode_ra*n_mode_dec + 2*n_ant*n_gain_modes */
+FM_API int64_t fm_num_vis(fm_handle h);        /* n_freq*n_lst*n_bl complex visibilities */
+
+/* Data visibilities d (device, [n_freq][n_lst][n_bl] complex) used by the chi^2 of
+ * Eq. likelihood with Sigma = sigma_noise^2 I.  Copied into the handle. */
+FM_API fm_status fm_set_data(fm_handle h, const void *dev_vis, fm_stream stream);
+
+/* Gaussian prior of Eq. posterior: U gains sum_k inv_var_k (theta_k - mu_k)^2 / 2.
+ * dev_mu, dev_inv_var: device [n_params]; copied.  Without a call the prior is zero. */
+FM_API fm_status fm_set_prior(fm_handle h, const void *dev_mu, const void *dev_inv_var, fm_stream stream);
+
+/* Model visibilities m_pq = g_p conj(g_q) V_pq(theta) (Eq. rime_discrete with the gain
+ * terms of Sec. 2.1), written to dev_vis_out ([n_freq][n_lst][n_bl] complex). */
+FM_API fm_status fm_forward(fm_handle h, const void *dev_theta, void *dev_vis_out, fm_stream stream);
+
+/* Unit-gain visibilities V(nu,t) of pixel values dev_x ([n_freq][n_pix] reals, the sky
+ * brightness per pixel in Jy/sr) -- Eq. rime_discrete alone, for tests. */
+FM_API fm_status fm_forward_pixels(fm_handle h, const void *dev_x, void *dev_vis_out, fm_stream stream);
+
+/* chi^2 = sum |m - d|^2 / sigma^2 (Eq. likelihood) and the gradient of
+ * U = chi^2/2 + prior (the negative log posterior of Eq. posterior up to a constant).
+ * dev_chi2_out, dev_u_out: device double[1] (dev_u_out may be NULL).
+ * dev_grad_out: device [n_params]. */
+FM_API fm_status fm_chi2_grad(fm_handle h, const void *dev_theta, double *dev_chi2_out, double *dev_u_out,
+                       void *dev_grad_out, fm_stream stream);
+
+/* Hessian-vector product of U at theta along v: full = 1 gives the full Hessian
+ * (equal to a finite difference of the gradient), full = 0 the Gauss-Newton matrix
+ * Re(J^H J)/sigma^2 + prior (the mass matrix of Sec. 4.2 / App. B). */
+FM_API fm_status fm_hvp(fm_handle h, const void *dev_theta, const void *dev_v, void *dev_hv_out, int full,
+                 fm_stream stream);
+
+/* Build the HMC mass matrix at theta (Sec. 4.2, App. B): the Gauss-Newton Hessian of U
+ * on a block diagonal -- `block` consecutive sky modes within a channel (block = 64,
+ * or 1 for the diagonal; n_mode_ra*n_mode_dec must be a multiple of it) plus one dense
+ * block for all gain coefficients (diagonal when block = 1) -- accumulated in FP64,
+ * then Cholesky-factored block by block, inflating the prior part by 1.1x per retry
+ * until positive definite.  Returns FM_ERR_NOT_SPD after 200 retries. */
+FM_API fm_status fm_build_precond(fm_handle h, const void *dev_theta, int block, fm_stream stream);
+
+/* Copy the preconditioner's FP64 Gauss-Newton blocks (before factorisation) to
+ * dev_out: sky blocks [n_sky/block][block][block] then the gain block [ng][ng]
+ * (ng = 2*n_ant*n_gain_modes; only its diagonal when block = 1, as [ng]). */
+FM_API fm_status fm_get_precond_blocks(fm_handle h, double *dev_out, fm_stream stream);
+FM_API int64_t fm_precond_size(fm_handle h);   /* doubles written by fm_get_precond_blocks */
+
+/* One Hessian-preconditioned HMC trajectory (App. B; leapfrog of Neal 2011):
+ * H0 = U(q) + z.z/2 with L z = p; n_steps of kick(eps/2) - drift(eps L^-T L^-1 p) -
+ * kick(eps/2); H1 likewise; accepted iff u_accept < exp(H0 - H1).
+ * dev_q (in: q0; out: final q if accepted, q0 otherwise), dev_p (in: initial momentum,
+ * already L times a unit normal; out: final momentum): device [n_params].
+ * dev_h_out: device double[2] = {H0, H1}; dev_accepted_out: device int[1].
+ * Needs fm_set_data and fm_build_precond first (FM_ERR_STATE otherwise). */
+FM_API fm_status fm_leapfrog(fm_handle h, void *dev_q, void *dev_p, double eps, int n_steps, double u_accept,
+                      double *dev_h_out, int *dev_accepted_out, fm_stream stream);
+
+/* Apply the preconditioner's block Cholesky factor L (M = L L^T, App. B) to a device
+ * vector [n_params]: op 0: out = L in (momentum draw p = L p0);  op 1: out = L^-1 in
+ * (z of the kinetic energy);  op 2: out = L^-T in (Laplace-approximation draw from
+ * L^T v = v0);  op 3: out = M^-1 in = L^-T L^-1 in (the drift direction).
+ * Needs fm_build_precond first (FM_ERR_STATE otherwise).  in and out may not alias. */
+FM_API fm_status fm_precond_apply(fm_handle h, int op, const void *dev_in, void *dev_out, fm_stream stream);
+
+/* Event timing of the two contraction kernels (forward fringe sum, pixel adjoint) on
+ * the stream each call uses: fm_set_profiling(h, 1) starts recording, fm_get_profile
+ * synchronises, writes total milliseconds and launch counts per class
+ * (out_ms[2], out_count[2]: 0 = forward contraction, 1 = adjoint contraction) and
+ * clears the record.  Off by default; recording adds two events per contraction. */
+FM_API fm_status fm_set_profiling(fm_handle h, int on);
+FM_API fm_status fm_get_profile(fm_handle h, double *out_ms, int64_t *out_count);
+
+/* Kernels launched by this library in this process so far (all handles). */
+FM_API int64_t fm_kernel_launches(void);
+
+/* Synchronise the stream and return (then clear) the handle's device status word:
+ * FM_ERR_NONFINITE or FM_ERR_TIMEOUT if a kernel raised one, else FM_OK. */
+FM_API fm_status fm_sync_status(fm_handle h, fm_stream stream);
+
+/* Message of the last non-OK status returned on this thread ("" if none). */
+FM_API const char *fm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FM_H */

@@ -1,0 +1,184 @@
+// Internal declarations of libfm: the handle, the device parameter block passed to
+// every kernel, launch helpers and error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fm.h"
+
+namespace fm {
+
+constexpr double kCLight = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+
+// Everything a kernel needs to know about the problem, by value.
+struct DevGeom {
+    int A, F, T, R, D, M, N, NG, npix, nk, B;
+    int apad;                 // antennas padded to a multiple of 4
+    double inv_sigma2;        // 1 / sigma^2
+    // FP64 precompute
+    const double *s64;        // [T][npix][3] topocentric east, north, up
+    const double *za2_64;     // [T][npix] squared zenith angle, < 0 below the horizon
+    const double *domega64;   // [D]
+    const double *phi64;      // [R][M]
+    const double *leg64;      // [D][N]
+    const double *gleg64;     // [F][NG]
+    const double *kap64;      // [F][A][3]   nu r_i / c (turns per unit direction cosine)
+    const double *bcoef64;    // [F]  beam exponent: A = exp(bcoef * za^2)
+    // FP32 precompute
+    const float *s32;         // [T][npix][6] two-float (hi, lo) east, north, up
+    const float *za2_32;      // [T][npix]
+    const float *domega32;    // [D]
+    const float *phi32;       // [R][M]
+    const float *leg32;       // [D][N]
+    const float *gleg32;      // [F][NG]
+    const float *kap32;       // [F][A][6] two-float
+    const float *bcoef32;     // [F]
+    const float *dkap32;      // [A][3] channel step dnu * r_i / c (turns per unit direction cosine)
+    int uniform_freq;         // channels equally spaced: E(nu + dnu) = E(nu) exp(-2 pi i dkap . s)
+    const int *bl_i, *bl_j;   // [B]
+    int *status;              // device status word (fm_status codes)
+};
+
+template <typename R> struct Tab;
+template <> struct Tab<double> {
+    static __device__ __forceinline__ const double *domega(const DevGeom &g) { return g.domega64; }
+    static __device__ __forceinline__ const double *za2(const DevGeom &g) { return g.za2_64; }
+    static __device__ __forceinline__ const double *gleg(const DevGeom &g) { return g.gleg64; }
+    static __device__ __forceinline__ const double *bcoef(const DevGeom &g) { return g.bcoef64; }
+};
+template <> struct Tab<float> {
+    static __device__ __forceinline__ const float *domega(const DevGeom &g) { return g.domega32; }
+    static __device__ __forceinline__ const float *za2(const DevGeom &g) { return g.za2_32; }
+    static __device__ __forceinline__ const float *gleg(const DevGeom &g) { return g.gleg32; }
+    static __device__ __forceinline__ const float *bcoef(const DevGeom &g) { return g.bcoef32; }
+};
+
+// Device workspace and state of one handle.
+struct Ctx {
+    fm_config cfg;
+    std::vector<double> ant, freq, lst;
+    int A, F, T, R, D, M, N, NG, npix, nk, B, prec;
+    int64_t n_sky, n_par, n_vis;
+    size_t rsz;                       // bytes per real (4 or 8)
+    DevGeom g;
+    // owned device buffers
+    std::vector<void *> allocs;
+    void *data = nullptr, *mu = nullptr, *lam = nullptr;
+    bool have_data = false, have_prior = false;
+    void *x = nullptr, *xv = nullptr, *xbar = nullptr, *tmp = nullptr;
+    void *vis = nullptr, *dvis = nullptr, *omega = nullptr, *zpart = nullptr;
+    void *gains = nullptr, *dgains = nullptr, *work_par = nullptr;
+    double *chi2p = nullptr, *scal = nullptr, *red = nullptr;
+    int *status = nullptr;
+    // preconditioner
+    int pc_block = 0;
+    double *pc_blocks = nullptr;      // FP64 GN blocks (sky then gain)
+    void *pc_chol = nullptr;          // factors in the working real type
+    int64_t pc_size = 0;
+    // tensor-core path: per-channel power-of-two operand scale (FP16 modes), max cell solid angle
+    float *tc_scale = nullptr;
+    float domega_max = 0.f;
+    // monopole split (FP32 storage paths): U[f][t][b] = visibility of a unit uniform sky,
+    // computed once in FP64; the contraction kernels see x - a_00 only
+    bool dc_split = false;
+    float *dc_u = nullptr;
+    void *dc_mean = nullptr;          // [F] channel means for fm_forward_pixels
+    // profiling: event pairs around the contraction kernels
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_rec;
+    size_t prof_next = 0;
+    // leapfrog scratch
+    void *lf_q0 = nullptr, *lf_g = nullptr, *lf_z = nullptr;
+    double *lf_scal = nullptr;
+};
+
+// --------------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+fm_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define FM_CK(call)                                                         \
+    do {                                                                    \
+        cudaError_t _e = (call);                                            \
+        if (_e != cudaSuccess) return ::fm::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+extern long long g_launches;     // kernels launched by the library (relaxed counter)
+#define FM_CK_LAUNCH()                                                      \
+    do {                                                                    \
+        __atomic_fetch_add(&::fm::g_launches, 1LL, __ATOMIC_RELAXED);       \
+        FM_CK(cudaGetLastError());                                          \
+    } while (0)
+
+#define FM_TRY(expr)                                                        \
+    do {                                                                    \
+        fm_status _s = (expr);                                              \
+        if (_s != FM_OK) return _s;                                         \
+    } while (0)
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ stage launchers
+// (each defined in the .cu file that owns the kernels; all enqueue on `st`)
+fm_status launch_precompute(Ctx &c, cudaStream_t st);
+
+template <typename R>
+fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc = 0);   // a -> x
+template <typename R>
+fm_status launch_modes_adjoint(Ctx &c, const R *xbar, R *abar, cudaStream_t st);  // xbar -> abar
+template <typename R>
+fm_status launch_gains(Ctx &c, const R *gamma, R *g, cudaStream_t st);       // theta gain part -> g[F][A]
+template <typename R>
+fm_status launch_vis(Ctx &c, const R *x, R *vis, cudaStream_t st);           // x -> V (unit gains)
+template <typename R>
+fm_status launch_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st);  // omega -> xbar
+template <typename R>
+fm_status launch_apply_gains(Ctx &c, const R *vis, const R *g, R *out, cudaStream_t st);
+template <typename R>
+fm_status launch_chi2_mid(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p,
+                          cudaStream_t st);
+template <typename R>
+fm_status launch_hvp_mid(Ctx &c, const R *vis, const R *dvis, const R *g, const R *dg, int full, R *omega,
+                         R *zpart, cudaStream_t st);
+template <typename R>
+fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
+template <typename R>
+fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, double *chi2_out,
+                                 double *u_out, cudaStream_t st);
+template <typename R>
+fm_status launch_prior_hvp(Ctx &c, const R *v, R *hv, cudaStream_t st);
+template <typename R>
+fm_status launch_add_dc(Ctx &c, const R *src, long long stride, R *vis, cudaStream_t st);
+template <typename R>
+fm_status launch_center(Ctx &c, const R *x, R *xc, R *mean, cudaStream_t st);
+// visibilities of the sky of mode coefficients a (the sky part of theta): V = V(x - a_00) + a_00 U
+// on the FP32 paths, V(x) directly on the FP64 path; x is left in `xbuf`
+fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st);
+template <typename R>
+fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st);
+
+// tensor-core contraction (sm_103a tcgen05); returns FM_ERR_UNSUPPORTED when the
+// shape does not fit its tiles
+fm_status launch_vis_tc(Ctx &c, const float *x, float *vis, cudaStream_t st);
+fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_t st);
+
+// preconditioner and leapfrog
+template <typename R>
+fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st);
+template <typename R>
+fm_status run_precond_apply(Ctx &c, int op, const R *in, R *out, cudaStream_t st);
+template <typename R>
+fm_status run_leapfrog(Ctx &c, R *q, R *p, double eps, int n_steps, double u, double *h_out, int *acc_out,
+                       cudaStream_t st);
+
+// gradient / hvp drivers (fm_api.cu)
+template <typename R>
+fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out, R *grad, cudaStream_t st);
+
+}  // namespace fm

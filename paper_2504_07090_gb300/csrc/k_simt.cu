@@ -1,0 +1,801 @@
+// CUDA-core kernels of the forward model and its adjoint, templated on the real type
+// (double for the complex128 path, float for the plain FP32 path):
+//   - separable mode <-> pixel transforms (Eq. fg_separable) as strided batched GEMMs;
+//   - antenna phasors E_ip = exp(-2 pi i nu r_i . s_p / c) generated in-kernel, never
+//     stored (b_pq = r_p - r_q makes K_pq = E_p conj(E_q), Eq. rime_discrete);
+//   - the fringe contraction V_pq = sum_p w_p E_p conj(E_q), w = dOmega A x;
+//   - gains, residual, chi^2 partials in FP64 and the adjoint weights (Eq. likelihood);
+//   - the pixel adjoint xbar_p = dOmega A sum_{p<q} Re[conj(omega_pq) K_pq];
+//   - deterministic reductions (fixed order, no floating-point atomics).
+#include "fm_internal.cuh"
+
+namespace fm {
+
+template <typename R> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+// ---------------------------------------------------------------- phasors
+// FP32: phase in turns from two-float products so its fractional part keeps ~2^-24
+// absolute accuracy even at 60 turns; every product and sum of the error-free
+// transformations is explicitly rounded (no contraction into FMAs).
+__device__ __forceinline__ float phase_frac_2f(const float *__restrict__ kap, const float *__restrict__ s)
+{
+    float accf = 0.f, acce = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float kh = kap[2 * c], kl = kap[2 * c + 1], sh = s[2 * c], sl = s[2 * c + 1];
+        float p = __fmul_rn(kh, sh);
+        float e = __fmaf_rn(kh, sh, -p);                 // exact rounding error of p
+        float f = __fsub_rn(p, rintf(p));                // exact: p minus its nearest integer
+        accf = __fadd_rn(accf, f);
+        acce = __fadd_rn(acce, __fadd_rn(e, __fmaf_rn(kh, sl, __fmul_rn(kl, sh))));
+    }
+    float t = __fadd_rn(accf, acce);
+    return __fsub_rn(t, rintf(t));
+}
+
+template <typename R> struct Phasor;
+template <> struct Phasor<float> {
+    static __device__ __forceinline__ void eval(const DevGeom &g, int f, int i, int t, int p, float &re, float &im)
+    {
+        float fr = phase_frac_2f(g.kap32 + ((size_t)f * g.A + i) * 6, g.s32 + ((size_t)t * g.npix + p) * 6);
+        float sn, cs;
+        sincospif(2.0f * fr, &sn, &cs);
+        re = cs;
+        im = -sn;
+    }
+};
+template <> struct Phasor<double> {
+    static __device__ __forceinline__ void eval(const DevGeom &g, int f, int i, int t, int p, double &re, double &im)
+    {
+        const double *k = g.kap64 + ((size_t)f * g.A + i) * 3;
+        const double *s = g.s64 + ((size_t)t * g.npix + p) * 3;
+        double ph = k[0] * s[0] + k[1] * s[1] + k[2] * s[2];
+        ph -= rint(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        re = cs;
+        im = -sn;
+    }
+};
+
+// Beam-weighted solid angle dOmega_d A(za; nu) of pixel p at LST t.
+template <typename R>
+__device__ __forceinline__ R pixel_weight(const DevGeom &g, int f, int t, int p)
+{
+    R z2 = Tab<R>::za2(g)[(size_t)t * g.npix + p];
+    if (z2 < R(0)) return R(0);
+    return Tab<R>::domega(g)[p / g.R] * exp(Tab<R>::bcoef(g)[f] * z2);
+}
+template <>
+__device__ __forceinline__ float pixel_weight<float>(const DevGeom &g, int f, int t, int p)
+{
+    float z2 = g.za2_32[(size_t)t * g.npix + p];
+    if (z2 < 0.f) return 0.f;
+    return g.domega32[p / g.R] * __expf(g.bcoef32[f] * z2);
+}
+
+__host__ __device__ __forceinline__ int pair_index(int i, int j, int A)
+{
+    return i * A - (i * (i + 1)) / 2 + (j - i - 1);
+}
+
+// ---------------------------------------------------------------- GEMM
+struct GemmArgs {
+    int M, N, K;
+    long long sAb, sAi, sAk, sBb, sBk, sBj, sCb, sCi, sCj;
+    int zero_b00;      // read B[0][0] of every batch as zero (drops the monopole mode a_00)
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs a, const R *__restrict__ A, const R *__restrict__ B,
+                                              R *__restrict__ C)
+{
+    __shared__ R sA[16][65];
+    __shared__ R sB[16][65];
+    const int b = blockIdx.z, i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    R acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = R(0);
+    const R *Ab = A + b * a.sAb;
+    const R *Bb = B + b * a.sBb;
+    for (int k0 = 0; k0 < a.K; k0 += 16) {
+        for (int e = tid; e < 1024; e += 256) {
+            int ii = e / 16, kk = e % 16;
+            int gi = i0 + ii, gk = k0 + kk;
+            sA[kk][ii] = (gi < a.M && gk < a.K) ? Ab[gi * a.sAi + gk * a.sAk] : R(0);
+            int kb = e / 64, jj = e % 64;
+            int gj = j0 + jj, gk2 = k0 + kb;
+            sB[kb][jj] = (gj < a.N && gk2 < a.K && !(a.zero_b00 && gj == 0 && gk2 == 0)) ? Bb[gk2 * a.sBk + gj * a.sBj]
+                                                                                          : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            R av[4], bv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { av[q] = sA[kk][ty * 4 + q]; bv[q] = sB[kk][tx * 4 + q]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+        }
+        __syncthreads();
+    }
+    R *Cb = C + b * a.sCb;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int gi = i0 + ty * 4 + u, gj = j0 + tx * 4 + v;
+            if (gi < a.M && gj < a.N) Cb[gi * a.sCi + gj * a.sCj] = acc[u][v];
+        }
+}
+
+template <typename R>
+static fm_status gemm(const GemmArgs &a, int batch, const R *A, const R *B, R *C, cudaStream_t st)
+{
+    dim3 grid(cdiv(a.N, 64), cdiv(a.M, 64), batch);
+    k_gemm<R><<<grid, 256, 0, st>>>(a, A, B, C);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+template <typename R> static const R *tab_phi(const Ctx &c);
+template <> const double *tab_phi<double>(const Ctx &c) { return c.g.phi64; }
+template <> const float *tab_phi<float>(const Ctx &c) { return c.g.phi32; }
+template <typename R> static const R *tab_leg(const Ctx &c);
+template <> const double *tab_leg<double>(const Ctx &c) { return c.g.leg64; }
+template <> const float *tab_leg<float>(const Ctx &c) { return c.g.leg32; }
+
+// x[f][d][r] = sum_n P[d][n] sum_m Phi[r][m] a[f][m][n]   (Eq. fg_separable)
+template <typename R>
+fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc)
+{
+    R *t1 = (R *)c.tmp;
+    GemmArgs s1{c.R, c.N, c.M, 0, c.M, 1, c.nk, c.N, 1, (long long)c.R * c.N, c.N, 1, skip_dc};
+    FM_TRY(gemm<R>(s1, c.F, tab_phi<R>(c), a, t1, st));
+    GemmArgs s2{c.D, c.R, c.N, 0, c.N, 1, (long long)c.R * c.N, 1, c.N, c.npix, c.R, 1, 0};
+    return gemm<R>(s2, c.F, tab_leg<R>(c), t1, x, st);
+}
+
+// abar[f][m][n] = sum_r Phi[r][m] sum_d xbar[f][d][r] P[d][n]   (transpose of the above)
+template <typename R>
+fm_status launch_modes_adjoint(Ctx &c, const R *xbar, R *abar, cudaStream_t st)
+{
+    R *t2 = (R *)c.tmp;
+    GemmArgs s1{c.R, c.N, c.D, c.npix, 1, c.R, 0, c.N, 1, (long long)c.R * c.N, c.N, 1, 0};
+    FM_TRY(gemm<R>(s1, c.F, xbar, tab_leg<R>(c), t2, st));
+    GemmArgs s2{c.M, c.N, c.R, 0, 1, c.M, (long long)c.R * c.N, c.N, 1, c.nk, c.N, 1, 0};
+    return gemm<R>(s2, c.F, tab_phi<R>(c), t2, abar, st);
+}
+
+// ---------------------------------------------------------------- gains
+template <typename R>
+__global__ void k_gains(DevGeom g, const R *__restrict__ gamma, R *__restrict__ out)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.F * g.A) return;
+    int f = e / g.A, i = e % g.A;
+    const R *X = Tab<R>::gleg(g) + (size_t)f * g.NG;
+    R re = 0, im = 0;
+    for (int k = 0; k < g.NG; ++k) {
+        re += X[k] * gamma[(i * g.NG + k) * 2];
+        im += X[k] * gamma[(i * g.NG + k) * 2 + 1];
+    }
+    out[2 * e] = re;
+    out[2 * e + 1] = im;
+}
+
+template <typename R>
+fm_status launch_gains(Ctx &c, const R *gamma, R *g, cudaStream_t st)
+{
+    k_gains<R><<<cdiv(c.F * c.A, 128), 128, 0, st>>>(c.g, gamma, g);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// m_pq = g_p conj(g_q) V_pq
+template <typename R>
+__global__ void k_apply_gains(DevGeom g, const R *__restrict__ vis, const R *__restrict__ gains, R *__restrict__ out)
+{
+    long long n = (long long)g.F * g.T * g.B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % g.B);
+        int f = (int)(e / ((long long)g.T * g.B));
+        int i = g.bl_i[b], j = g.bl_j[b];
+        R gir = gains[2 * (f * g.A + i)], gii = gains[2 * (f * g.A + i) + 1];
+        R gjr = gains[2 * (f * g.A + j)], gji = gains[2 * (f * g.A + j) + 1];
+        R ggr = gir * gjr + gii * gji, ggi = gii * gjr - gir * gji;   // g_i conj(g_j)
+        R vr = vis[2 * e], vi = vis[2 * e + 1];
+        out[2 * e] = ggr * vr - ggi * vi;
+        out[2 * e + 1] = ggr * vi + ggi * vr;
+    }
+}
+
+template <typename R>
+fm_status launch_apply_gains(Ctx &c, const R *vis, const R *g, R *out, cudaStream_t st)
+{
+    k_apply_gains<R><<<1024, 256, 0, st>>>(c.g, vis, g, out);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// ---------------------------------------------------------------- forward contraction
+// One CTA per (channel, LST).  Pixels stream through shared memory in chunks of PC:
+// E and w E are generated there, then each thread accumulates 4x4 antenna tiles
+// (p-block <= q-block) of sum_p (w E_p) conj(E_q).  Threads are split into pixel
+// groups whose partial sums are added in a fixed order at the end.
+template <typename R, int TPT>
+__global__ void __launch_bounds__(256) k_vis_simt(DevGeom g, const R *__restrict__ x, R *__restrict__ vis, int nbk,
+                                                  int ntile, int tpg, int ngrp, int pc)
+{
+    using C2 = typename V2<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *sEw = reinterpret_cast<C2 *>(smem_raw);
+    C2 *sE = sEw + (size_t)pc * g.apad;
+    const int ft = blockIdx.x, f = ft / g.T, t = ft % g.T;
+    const int tid = threadIdx.x, grp = tid / tpg, lane = tid % tpg;
+    int tbi[TPT], tbj[TPT];
+    bool tact[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        int tile = lane + k * tpg;
+        tact[k] = (grp < ngrp) && (tile < ntile);
+        int bi = 0, off = 0;
+        if (tact[k]) {
+            while (off + (nbk - bi) <= tile) { off += nbk - bi; ++bi; }
+        }
+        tbi[k] = bi;
+        tbj[k] = bi + (tile - off);
+    }
+    R acc[TPT][4][4][2];
+#pragma unroll
+    for (int k = 0; k < TPT; ++k)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[k][u][v][0] = acc[k][u][v][1] = R(0);
+
+    const R *xf = x + (size_t)f * g.npix;
+    R *sW = reinterpret_cast<R *>(sE + (size_t)pc * g.apad);       // [pc]
+    for (int p0 = 0; p0 < g.npix; p0 += pc) {
+        __syncthreads();
+        for (int pl = tid; pl < pc; pl += blockDim.x) {
+            int p = p0 + pl;
+            sW[pl] = (p < g.npix) ? pixel_weight<R>(g, f, t, p) * xf[p] : R(0);
+        }
+        __syncthreads();
+        for (int e = tid; e < pc * g.apad; e += blockDim.x) {
+            int pl = e / g.apad, i = e % g.apad, p = p0 + pl;
+            C2 ev, ew;
+            ev.x = ev.y = ew.x = ew.y = R(0);
+            if (i < g.A && p < g.npix) {
+                R w = sW[pl];
+                R er, ei;
+                Phasor<R>::eval(g, f, i, t, p, er, ei);
+                ev.x = er; ev.y = ei;
+                ew.x = w * er; ew.y = w * ei;
+            }
+            sE[e] = ev;
+            sEw[e] = ew;
+        }
+        __syncthreads();
+        if (grp < ngrp) {
+            // chunk partial sums first, then one add into the running total: the
+            // rounding error grows with pc/ngrp + npix/pc terms instead of npix/ngrp
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (!tact[k]) continue;
+                R part[4][4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) part[u][v][0] = part[u][v][1] = R(0);
+                for (int pl = grp; pl < pc; pl += ngrp) {
+                    const C2 *rw = sEw + (size_t)pl * g.apad;
+                    const C2 *rv = sE + (size_t)pl * g.apad;
+                    C2 av[4], bv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { av[q] = rw[4 * tbi[k] + q]; bv[q] = rv[4 * tbj[k] + q]; }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            part[u][v][0] += av[u].x * bv[v].x + av[u].y * bv[v].y;
+                            part[u][v][1] += av[u].y * bv[v].x - av[u].x * bv[v].y;
+                        }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        acc[k][u][v][0] += part[u][v][0];
+                        acc[k][u][v][1] += part[u][v][1];
+                    }
+            }
+        }
+    }
+    __syncthreads();
+    R *red = reinterpret_cast<R *>(smem_raw);       // [ngrp][ntile][16][2]
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        if (!tact[k]) continue;
+        int tile = lane + k * tpg;
+        R *dst = red + ((size_t)grp * ntile + tile) * 32;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                dst[(u * 4 + v) * 2] = acc[k][u][v][0];
+                dst[(u * 4 + v) * 2 + 1] = acc[k][u][v][1];
+            }
+    }
+    __syncthreads();
+    for (int e = tid; e < ntile * 16; e += blockDim.x) {
+        int tile = e / 16, q = e % 16, u = q / 4, v = q % 4;
+        int bi = 0, off = 0;
+        while (off + (nbk - bi) <= tile) { off += nbk - bi; ++bi; }
+        int bj = bi + (tile - off);
+        int i = 4 * bi + u, j = 4 * bj + v;
+        if (i < j && j < g.A) {
+            R re = 0, im = 0;
+            for (int gq = 0; gq < ngrp; ++gq) {
+                re += red[((size_t)gq * ntile + tile) * 32 + 2 * q];
+                im += red[((size_t)gq * ntile + tile) * 32 + 2 * q + 1];
+            }
+            size_t o = ((size_t)ft * g.B + pair_index(i, j, g.A)) * 2;
+            vis[o] = re;
+            vis[o + 1] = im;
+        }
+    }
+}
+
+template <typename R, int TPT>
+static fm_status vis_simt_launch(Ctx &c, const R *x, R *vis, cudaStream_t st)
+{
+    int nbk = (c.A + 3) / 4, ntile = nbk * (nbk + 1) / 2;
+    int tpg = ((cdiv(ntile, TPT) + 31) / 32) * 32;
+    if (tpg > 256) return FM_ERR_UNSUPPORTED;
+    int ngrp = 256 / tpg;
+    int pc = 64;
+    size_t sm_e = 2 * (size_t)pc * c.g.apad * 2 * sizeof(R) + pc * sizeof(R);
+    size_t sm_r = (size_t)ngrp * ntile * 32 * sizeof(R);
+    size_t smem = sm_e > sm_r ? sm_e : sm_r;
+    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    FM_CK(cudaFuncSetAttribute(k_vis_simt<R, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_vis_simt<R, TPT><<<c.F * c.T, 256, smem, st>>>(c.g, x, vis, nbk, ntile, tpg, ngrp, pc);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+template <typename R>
+fm_status launch_vis(Ctx &c, const R *x, R *vis, cudaStream_t st)
+{
+    int nbk = (c.A + 3) / 4, ntile = nbk * (nbk + 1) / 2;
+    if (ntile <= 256) return vis_simt_launch<R, 1>(c, x, vis, st);
+    if (ntile <= 512) return vis_simt_launch<R, 2>(c, x, vis, st);
+    if (ntile <= 1024) return vis_simt_launch<R, 4>(c, x, vis, st);
+    return vis_simt_launch<R, 8>(c, x, vis, st);
+}
+
+// ---------------------------------------------------------------- chi^2 epilogue
+template <typename R>
+__device__ void block_sum_double(double v, double *out, double *sred)
+{
+    sred[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sred[threadIdx.x] += sred[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sred[0];
+}
+
+// One CTA per (channel, LST): model, residual, chi^2 partial (FP64), the adjoint
+// weights omega_pq = conj(g_p) g_q r_pq / sigma^2 and the per-antenna gain-gradient
+// partials Z_a (gradient w.r.t. gamma_ak is X_k(nu) (Re Z_a, Im Z_a)).
+template <typename R>
+__global__ void __launch_bounds__(256) k_chi2_mid(DevGeom g, const R *__restrict__ vis, const R *__restrict__ data,
+                                                  const R *__restrict__ gains, R *__restrict__ omega,
+                                                  R *__restrict__ zpart, double *__restrict__ chi2p)
+{
+    using C2 = typename V2<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *sred = reinterpret_cast<double *>(smem_raw);            // [256]
+    C2 *sG = reinterpret_cast<C2 *>(sred + 256);                      // [A]
+    C2 *sV = sG + g.A;                                                // [B]
+    C2 *sRr = sV + g.B;                                               // [B]
+    const int ft = blockIdx.x, f = ft / g.T;
+    for (int i = threadIdx.x; i < g.A; i += blockDim.x) {
+        sG[i].x = gains[2 * (f * g.A + i)];
+        sG[i].y = gains[2 * (f * g.A + i) + 1];
+    }
+    __syncthreads();
+    const R is2 = (R)g.inv_sigma2;
+    double c2 = 0.0;
+    for (int b = threadIdx.x; b < g.B; b += blockDim.x) {
+        int i = g.bl_i[b], j = g.bl_j[b];
+        size_t o = ((size_t)ft * g.B + b) * 2;
+        C2 V, gi = sG[i], gj = sG[j];
+        V.x = vis[o]; V.y = vis[o + 1];
+        R ggr = gi.x * gj.x + gi.y * gj.y, ggi = gi.y * gj.x - gi.x * gj.y;     // g_i conj(g_j)
+        R rr = ggr * V.x - ggi * V.y - data[o];
+        R ri = ggr * V.y + ggi * V.x - data[o + 1];
+        c2 += (double)rr * (double)rr + (double)ri * (double)ri;
+        // omega = conj(g_i) g_j r / sigma^2 = conj(g_i conj(g_j)) r / sigma^2
+        omega[o] = (ggr * rr + ggi * ri) * is2;
+        omega[o + 1] = (ggr * ri - ggi * rr) * is2;
+        sV[b] = V;
+        sRr[b].x = rr; sRr[b].y = ri;
+    }
+    block_sum_double<R>(c2, chi2p + ft, sred);
+    if (threadIdx.x == 0) chi2p[ft] *= g.inv_sigma2;
+    __syncthreads();
+    for (int a = threadIdx.x; a < g.A; a += blockDim.x) {
+        R zr = 0, zi = 0;
+        for (int j = 0; j < g.A; ++j) {
+            if (j == a) continue;
+            if (j > a) {   // pair (a, j): t = conj(r) conj(g_j) V; Z += conj(t)
+                int b = pair_index(a, j, g.A);
+                C2 r = sRr[b], V = sV[b], gj = sG[j];
+                R cr = r.x * gj.x - r.y * gj.y, ci = -(r.x * gj.y + r.y * gj.x);   // conj(r) conj(g_j)
+                R tr = cr * V.x - ci * V.y, ti = cr * V.y + ci * V.x;
+                zr += tr; zi -= ti;
+            } else {       // pair (j, a): t = conj(r) g_j V; Z += t
+                int b = pair_index(j, a, g.A);
+                C2 r = sRr[b], V = sV[b], gj = sG[j];
+                R cr = r.x * gj.x + r.y * gj.y, ci = r.x * gj.y - r.y * gj.x;      // conj(r) g_j
+                zr += cr * V.x - ci * V.y;
+                zi += cr * V.y + ci * V.x;
+            }
+        }
+        zpart[((size_t)ft * g.A + a) * 2] = zr * is2;
+        zpart[((size_t)ft * g.A + a) * 2 + 1] = zi * is2;
+    }
+}
+
+template <typename R>
+fm_status launch_chi2_mid(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p, cudaStream_t st)
+{
+    size_t smem = 256 * sizeof(double) + (c.A + 2 * (size_t)c.B) * 2 * sizeof(R);
+    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    FM_CK(cudaFuncSetAttribute(k_chi2_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_chi2_mid<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// Tangent of the epilogue for Hessian-vector products.  With dm = dg_p conj(g_q) V +
+// g_p conj(dg_q) V + g_p conj(g_q) dV (JVP), the adjoint weights become
+// omega' = [dm conj(g_p) g_q + full * r (conj(dg_p) g_q + conj(g_p) dg_q)] / sigma^2 and
+// the gain partials follow the same pattern (full = 0 keeps only the dm terms: GN).
+template <typename R>
+__global__ void __launch_bounds__(256) k_hvp_mid(DevGeom g, const R *__restrict__ vis, const R *__restrict__ dvis,
+                                                 const R *__restrict__ data, const R *__restrict__ gains,
+                                                 const R *__restrict__ dgains, int full, R *__restrict__ omega,
+                                                 R *__restrict__ zpart)
+{
+    using C2 = typename V2<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *sG = reinterpret_cast<C2 *>(smem_raw);
+    C2 *sD = sG + g.A;
+    C2 *sV = sD + g.A;
+    C2 *sdV = sV + g.B;
+    C2 *sRr = sdV + g.B;
+    C2 *sdM = sRr + g.B;
+    const int ft = blockIdx.x, f = ft / g.T;
+    for (int i = threadIdx.x; i < g.A; i += blockDim.x) {
+        sG[i].x = gains[2 * (f * g.A + i)];
+        sG[i].y = gains[2 * (f * g.A + i) + 1];
+        sD[i].x = dgains[2 * (f * g.A + i)];
+        sD[i].y = dgains[2 * (f * g.A + i) + 1];
+    }
+    __syncthreads();
+    const R is2 = (R)g.inv_sigma2;
+    auto mul = [](C2 a, C2 b) { C2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; };
+    auto cj = [](C2 a) { a.y = -a.y; return a; };
+    auto add = [](C2 a, C2 b) { a.x += b.x; a.y += b.y; return a; };
+    for (int b = threadIdx.x; b < g.B; b += blockDim.x) {
+        int i = g.bl_i[b], j = g.bl_j[b];
+        size_t o = ((size_t)ft * g.B + b) * 2;
+        C2 V, dV, gi = sG[i], gj = sG[j], di = sD[i], dj = sD[j];
+        V.x = vis[o]; V.y = vis[o + 1];
+        dV.x = dvis[o]; dV.y = dvis[o + 1];
+        C2 gg = mul(gi, cj(gj));
+        C2 r = mul(gg, V);
+        r.x -= data[o]; r.y -= data[o + 1];
+        C2 dm = add(add(mul(mul(di, cj(gj)), V), mul(mul(gi, cj(dj)), V)), mul(gg, dV));
+        C2 w = mul(dm, cj(gg));
+        if (full) w = add(w, mul(r, add(mul(cj(di), gj), mul(cj(gi), dj))));
+        omega[o] = w.x * is2;
+        omega[o + 1] = w.y * is2;
+        sV[b] = V; sdV[b] = dV; sRr[b] = r; sdM[b] = dm;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < g.A; a += blockDim.x) {
+        C2 z;
+        z.x = z.y = R(0);
+        for (int j = 0; j < g.A; ++j) {
+            if (j == a) continue;
+            if (j > a) {       // pair (a, j): c = conj(dm) conj(g_j) V + full conj(r)(conj(dg_j) V + conj(g_j) dV)
+                int b = pair_index(a, j, g.A);
+                C2 c = mul(mul(cj(sdM[b]), cj(sG[j])), sV[b]);
+                if (full) c = add(c, mul(cj(sRr[b]), add(mul(cj(sD[j]), sV[b]), mul(cj(sG[j]), sdV[b]))));
+                z = add(z, cj(c));
+            } else {           // pair (j, a): c = conj(dm) g_j V + full conj(r)(dg_j V + g_j dV)
+                int b = pair_index(j, a, g.A);
+                C2 c = mul(mul(cj(sdM[b]), sG[j]), sV[b]);
+                if (full) c = add(c, mul(cj(sRr[b]), add(mul(sD[j], sV[b]), mul(sG[j], sdV[b]))));
+                z = add(z, c);
+            }
+        }
+        zpart[((size_t)ft * g.A + a) * 2] = z.x * is2;
+        zpart[((size_t)ft * g.A + a) * 2 + 1] = z.y * is2;
+    }
+}
+
+template <typename R>
+fm_status launch_hvp_mid(Ctx &c, const R *vis, const R *dvis, const R *g, const R *dg, int full, R *omega, R *zpart,
+                         cudaStream_t st)
+{
+    size_t smem = (2 * (size_t)c.A + 4 * (size_t)c.B) * 2 * sizeof(R);
+    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    FM_CK(cudaFuncSetAttribute(k_hvp_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_hvp_mid<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, dvis, (const R *)c.data, g, dg, full, omega, zpart);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// ---------------------------------------------------------------- adjoint contraction
+// One CTA per (channel, tile of PT pixels), looping over LSTs so xbar accumulates in
+// registers without atomics.  For each LST the tile's phasors go to shared memory and
+// each thread forms, for its pixel, sum_p Re[E_p conj(Y_p)] with
+// Y_p = sum_{q>p} omega_pq E_q  (= sum_{p<q} Re[conj(omega_pq) E_p conj(E_q)]).
+template <typename R>
+__global__ void __launch_bounds__(128) k_adj_simt(DevGeom g, const R *__restrict__ omega, R *__restrict__ xbar)
+{
+    using C2 = typename V2<R>::t;
+    constexpr int PT = 128;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *sE = reinterpret_cast<C2 *>(smem_raw);        // [A][PT]
+    C2 *sC = sE + (size_t)g.A * PT;                   // [B]
+    const int f = blockIdx.y, p0 = blockIdx.x * PT, tid = threadIdx.x;
+    const int p = p0 + tid;
+    R accx = R(0);
+    for (int t = 0; t < g.T; ++t) {
+        __syncthreads();
+        for (int e = tid; e < g.A * PT; e += blockDim.x) {
+            int i = e / PT, pl = e % PT, pp = p0 + pl;
+            C2 ev;
+            ev.x = ev.y = R(0);
+            if (pp < g.npix) Phasor<R>::eval(g, f, i, t, pp, ev.x, ev.y);
+            sE[e] = ev;
+        }
+        const R *om = omega + ((size_t)(f * g.T + t) * g.B) * 2;
+        for (int b = tid; b < g.B; b += blockDim.x) {
+            sC[b].x = om[2 * b];
+            sC[b].y = om[2 * b + 1];
+        }
+        __syncthreads();
+        if (p < g.npix) {
+            R w = pixel_weight<R>(g, f, t, p);
+            if (w != R(0)) {
+                R acc = R(0);
+                for (int i = 0; i + 1 < g.A; ++i) {
+                    R yr = 0, yi = 0;
+                    int b0 = pair_index(i, i + 1, g.A) - (i + 1);
+                    for (int j = i + 1; j < g.A; ++j) {
+                        C2 cc = sC[b0 + j], ej = sE[(size_t)j * PT + tid];
+                        yr += cc.x * ej.x - cc.y * ej.y;
+                        yi += cc.x * ej.y + cc.y * ej.x;
+                    }
+                    C2 ei = sE[(size_t)i * PT + tid];
+                    acc += ei.x * yr + ei.y * yi;
+                }
+                accx += w * acc;
+            }
+        }
+    }
+    if (p < g.npix) xbar[(size_t)f * g.npix + p] = accx;
+}
+
+template <typename R>
+fm_status launch_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st)
+{
+    size_t smem = ((size_t)c.A * 128 + c.B) * 2 * sizeof(R);
+    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    FM_CK(cudaFuncSetAttribute(k_adj_simt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(cdiv(c.npix, 128), c.F);
+    k_adj_simt<R><<<grid, 128, smem, st>>>(c.g, omega, xbar);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// ---------------------------------------------------------------- reductions
+// grad_gamma[a][k][re, im] = sum_{f,t} X_k(nu_f) Z[f][t][a]   (FP64, fixed order)
+template <typename R>
+__global__ void __launch_bounds__(256) k_gain_reduce(DevGeom g, const R *__restrict__ zpart, R *__restrict__ out)
+{
+    __shared__ double sred[256];
+    const int a = blockIdx.x, k = blockIdx.y;
+    double sr = 0.0, si = 0.0;
+    for (int ft = threadIdx.x; ft < g.F * g.T; ft += blockDim.x) {
+        int f = ft / g.T;
+        double X = (double)Tab<R>::gleg(g)[(size_t)f * g.NG + k];
+        sr += X * (double)zpart[((size_t)ft * g.A + a) * 2];
+        si += X * (double)zpart[((size_t)ft * g.A + a) * 2 + 1];
+    }
+    double tot;
+    block_sum_double<R>(sr, &tot, sred);
+    __syncthreads();
+    if (threadIdx.x == 0) out[(a * g.NG + k) * 2] = (R)tot;
+    __syncthreads();
+    block_sum_double<R>(si, &tot, sred);
+    if (threadIdx.x == 0) out[(a * g.NG + k) * 2 + 1] = (R)tot;
+}
+
+template <typename R>
+fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st)
+{
+    dim3 grid(c.A, c.NG);
+    k_gain_reduce<R><<<grid, 256, 0, st>>>(c.g, zpart, grad_gain);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// grad += lam (theta - mu); per-block partial sums of lam (theta - mu)^2 / 2
+template <typename R>
+__global__ void __launch_bounds__(256) k_prior(long long n, const R *__restrict__ theta, const R *__restrict__ mu,
+                                               const R *__restrict__ lam, R *__restrict__ grad, double *__restrict__ part)
+{
+    __shared__ double sred[256];
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        if (lam) {
+            R dv = theta[k] - mu[k];
+            grad[k] += lam[k] * dv;
+            acc += 0.5 * (double)lam[k] * (double)dv * (double)dv;
+        }
+    }
+    block_sum_double<R>(acc, part + blockIdx.x, sred);
+}
+
+// chi2 = sum of per-(f,t) partials; U = chi2/2 + prior (both in fixed order)
+__global__ void __launch_bounds__(256) k_total(int nft, const double *__restrict__ chi2p, int npart,
+                                               const double *__restrict__ part, double *chi2_out, double *u_out,
+                                               int *status)
+{
+    __shared__ double sred[256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nft; i += blockDim.x) a += chi2p[i];
+    for (int i = threadIdx.x; i < npart; i += blockDim.x) b += part[i];
+    double ta, tb;
+    block_sum_double<float>(a, &ta, sred);
+    __syncthreads();
+    block_sum_double<float>(b, &tb, sred);
+    if (threadIdx.x == 0) {
+        if (chi2_out) *chi2_out = ta;
+        if (u_out) *u_out = 0.5 * ta + tb;
+        if (!isfinite(ta) || !isfinite(tb)) atomicExch(status, (int)FM_ERR_NONFINITE);
+    }
+}
+
+template <typename R>
+fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, double *chi2_out,
+                                 double *u_out, cudaStream_t st)
+{
+    const int nblk = 296;
+    k_prior<R><<<nblk, 256, 0, st>>>(c.n_par, theta, (const R *)c.mu, c.have_prior ? (const R *)c.lam : nullptr,
+                                     grad, c.red);
+    FM_CK_LAUNCH();
+    k_total<<<1, 256, 0, st>>>(c.F * c.T, chi2p, nblk, c.red, chi2_out, u_out, c.status);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+template <typename R>
+__global__ void k_prior_hvp(long long n, const R *__restrict__ v, const R *__restrict__ lam, R *__restrict__ hv)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        hv[k] += lam[k] * v[k];
+}
+
+template <typename R>
+fm_status launch_prior_hvp(Ctx &c, const R *v, R *hv, cudaStream_t st)
+{
+    if (!c.have_prior) return FM_OK;
+    k_prior_hvp<R><<<296, 256, 0, st>>>(c.n_par, v, (const R *)c.lam, hv);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// ---------------------------------------------------------------- monopole split
+// vis[f][t][b] += c_f U[f][t][b] with c_f = src[f * stride]: puts back the visibility of
+// the uniform part of the sky that the contraction kernels did not see.
+template <typename R>
+__global__ void k_add_dc(DevGeom g, const R *__restrict__ src, long long stride, const float *__restrict__ U,
+                         R *__restrict__ vis)
+{
+    long long n = (long long)g.F * g.T * g.B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(e / ((long long)g.T * g.B));
+        R cf = src[(long long)f * stride];
+        vis[2 * e] += cf * (R)U[2 * e];
+        vis[2 * e + 1] += cf * (R)U[2 * e + 1];
+    }
+}
+
+template <typename R>
+fm_status launch_add_dc(Ctx &c, const R *src, long long stride, R *vis, cudaStream_t st)
+{
+    k_add_dc<R><<<1024, 256, 0, st>>>(c.g, src, stride, c.dc_u, vis);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+// per-channel mean of x (fixed-order tree) and x' = x - mean
+template <typename R>
+__global__ void __launch_bounds__(256) k_center(int npix, const R *__restrict__ x, R *__restrict__ xc,
+                                                R *__restrict__ mean)
+{
+    __shared__ double red[256];
+    const int f = blockIdx.x;
+    double s = 0.0;
+    for (int p = threadIdx.x; p < npix; p += blockDim.x) s += (double)x[(size_t)f * npix + p];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const R m = (R)(red[0] / npix);
+    if (threadIdx.x == 0) mean[f] = m;
+    for (int p = threadIdx.x; p < npix; p += blockDim.x) xc[(size_t)f * npix + p] = x[(size_t)f * npix + p] - m;
+}
+
+template <typename R>
+fm_status launch_center(Ctx &c, const R *x, R *xc, R *mean, cudaStream_t st)
+{
+    k_center<R><<<c.F, 256, 0, st>>>(c.npix, x, xc, mean);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+__global__ void k_d2f(long long n, const double *__restrict__ a, float *__restrict__ b)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
+{
+    k_d2f<<<1024, 256, 0, st>>>(n, a, b);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+#define FM_INST(R)                                                                                       \
+    template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int);                \
+    template fm_status launch_modes_adjoint<R>(Ctx &, const R *, R *, cudaStream_t);                     \
+    template fm_status launch_gains<R>(Ctx &, const R *, R *, cudaStream_t);                             \
+    template fm_status launch_vis<R>(Ctx &, const R *, R *, cudaStream_t);                               \
+    template fm_status launch_adjoint<R>(Ctx &, const R *, R *, cudaStream_t);                           \
+    template fm_status launch_apply_gains<R>(Ctx &, const R *, const R *, R *, cudaStream_t);            \
+    template fm_status launch_chi2_mid<R>(Ctx &, const R *, const R *, R *, R *, double *, cudaStream_t); \
+    template fm_status launch_hvp_mid<R>(Ctx &, const R *, const R *, const R *, const R *, int, R *, R *, \
+                                         cudaStream_t);                                                  \
+    template fm_status launch_gain_reduce<R>(Ctx &, const R *, R *, cudaStream_t);                       \
+    template fm_status launch_prior_and_total<R>(Ctx &, const R *, R *, const double *, double *, double *, \
+                                                 cudaStream_t);                                          \
+    template fm_status launch_prior_hvp<R>(Ctx &, const R *, R *, cudaStream_t);                         \
+    template fm_status launch_add_dc<R>(Ctx &, const R *, long long, R *, cudaStream_t);                \
+    template fm_status launch_center<R>(Ctx &, const R *, R *, R *, cudaStream_t);
+FM_INST(float)
+FM_INST(double)
+
+}  // namespace fm

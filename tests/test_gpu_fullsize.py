@@ -1,0 +1,73 @@
+"""Parity at the full benchmark size (cfg1: 37 antennas, 64 channels, 60 LSTs, 24,576
+pixels, 16,384 modes per channel) in the launch configuration bench.py times: sampled
+visibilities computed one by one by the oracle, and the complete sky gradient of one
+channel (all LSTs) against the oracle's per-baseline adjoint."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_cases import as_complex, quant, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_VIS = {"fp32": 1e-5, "fp16x3": 1e-5, "bf16x3": 2e-5}
+TOL_GRAD = {"fp32": 1e-4, "fp16x3": 3e-4, "bf16x3": 3e-4}
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    from paper_2504_07090_gb300 import build, synth
+    build.build()
+    p = synth.config("cfg1")
+    tr = synth.draw_truth(p)
+    o = oracle.Oracle(p)
+    return p, o, tr
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "fp32"])
+def test_cfg1_sampled_visibilities(cfg1, prec):
+    import torch
+    from paper_2504_07090_gb300 import fm
+    p, o, tr = cfg1
+    th = quant(prec, tr.theta)
+    h = fm.ForwardModel(p, prec, sigma=1.0)
+    V = as_complex(h.forward(torch.tensor(th, dtype=torch.float32, device="cuda")))
+    rng = np.random.default_rng(3)
+    a, gam = o.split(th)
+    g = o.gains(gam)
+    got, want = [], []
+    for f in rng.choice(p.n_freq, 3, replace=False):
+        x_f = o.sky_f(a[f])
+        for _ in range(8):
+            t, b = int(rng.integers(p.n_lst)), int(rng.integers(p.n_bl))
+            v = o.vis_one(int(f), t, b, x_f) * g[f, o.bl_i[b]] * np.conj(g[f, o.bl_j[b]])
+            got.append(V[f, t, b])
+            want.append(v)
+    assert rel_l2(np.array(got), np.array(want)) < TOL_VIS[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp16x3"])
+def test_cfg1_one_channel_gradient(cfg1, prec):
+    import torch
+    from paper_2504_07090_gb300 import fm
+    p, o, tr = cfg1
+    th = quant(prec, tr.theta)
+    h0 = fm.ForwardModel(p, prec, sigma=1.0)
+    m = as_complex(h0.forward(torch.tensor(th, dtype=torch.float32, device="cuda")))
+    h0.close()
+    sigma = 0.01 * float(np.mean(np.abs(m)))
+    p.sigma = sigma
+    o.sigma = sigma
+    # data: oracle-independent seeded noise around a perturbed model (no oracle input from the GPU)
+    d = quant(prec, sigma * (tr.noise[..., 0] + 1j * tr.noise[..., 1]) + 0.0)
+    rng = np.random.default_rng(5)
+    f0 = int(rng.integers(p.n_freq))
+    d_full = np.zeros((p.n_freq, p.n_lst, p.n_bl), dtype=np.complex128)
+    d_full[f0] = o.model(th, fts=[(f0, t) for t in range(p.n_lst)])[f0] + d[f0]
+    d_full = quant(prec, d_full)
+    h = fm.ForwardModel(p, prec, sigma=sigma)
+    h.set_data(torch.tensor(np.stack([d_full.real, d_full.imag], -1), dtype=torch.float32, device="cuda").contiguous())
+    _, grad = h.chi2_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    chi2, U, g = o.chi2_grad(th, d_full, fts=[(f0, t) for t in range(p.n_lst)])
+    sl = slice(f0 * o.nk, (f0 + 1) * o.nk)
+    assert rel_l2(grad.cpu().numpy()[sl], g[sl]) < TOL_GRAD[prec]

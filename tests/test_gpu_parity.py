@@ -1,0 +1,113 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs that span several
+tiles with ragged tails.  Errors are relative l2 over the whole output vector.
+
+Tolerances (visibilities / gradients and HVPs):
+  fp64    1e-10 / 1e-10
+  fp32    1e-5  / 1e-4          (the FP32 targets)
+  fp16x3  1e-5  / 3e-4
+  bf16x3  2e-5  / 3e-4
+  fp16x1  2e-3  / 5e-3
+  bf16x1  1e-2  / 2e-2
+The split-precision operand rounding (2^-9 BF16, 2^-12 FP16 per product; about 2^-17 and
+2^-22 after the hi/lo split) is amplified by the cancellation of the fringe sum, and the
+gradient amplifies visibility errors by |m| / |m - d| (about 100 at a noise level of 1 % of
+|V|); the measured errors behind these bounds are recorded in the design doc.  The chi^2 check
+uses the bound implied by the visibility tolerance."""
+import numpy as np
+import pytest
+
+from gpu_cases import as_complex, handle, make_case, perturbed, quant, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_VIS = {"fp64": 1e-10, "fp32": 1e-5, "bf16x1": 1e-2, "bf16x3": 2e-5, "fp16x1": 2e-3, "fp16x3": 1e-5}
+TOL_GRAD = {"fp64": 1e-10, "fp32": 1e-4, "bf16x1": 2e-2, "bf16x3": 3e-4, "fp16x1": 5e-3, "fp16x3": 3e-4}
+CASES = ["tiny", "small", "mid"]
+PRECS = ["fp64", "fp32", "bf16x1", "bf16x3", "fp16x1", "fp16x3"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2504_07090_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _t(a, h):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=h.dtype, device="cuda").contiguous()
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("prec", PRECS)
+def test_forward_pixels_matches_oracle(name, prec):
+    p, o, th, d, mu, lam = make_case(name)
+    h = handle(p, prec)
+    a, _ = o.split(th)
+    x = quant(prec, o.sky(a))
+    got = as_complex(h.forward_pixels(_t(x, h)))
+    want = o.vis(x)
+    assert rel_l2(got, want) < TOL_VIS[prec]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("prec", PRECS)
+def test_forward_model_matches_oracle(name, prec):
+    p, o, th, d, mu, lam = make_case(name)
+    h = handle(p, prec)
+    th = quant(prec, perturbed(o, th, 0.02, 1))
+    got = as_complex(h.forward(_t(th, h)))
+    assert rel_l2(got, o.model(th)) < TOL_VIS[prec]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("prec", PRECS)
+def test_chi2_and_gradient_match_oracle(name, prec):
+    p, o, th, d, mu, lam = make_case(name)
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 2))
+    chi2, U, g = o.chi2_grad(th, d, mu, lam)
+    scal, grad = h.chi2_grad(_t(th, h))
+    scal = scal.cpu().numpy()
+    # |chi2' - chi2| <= 2 sqrt(chi2) |dm| / sigma + |dm|^2 / sigma^2 with |dm| <= tol_V |m| (x2 margin)
+    dm = TOL_VIS[prec] * np.linalg.norm(o.model(th)) / o.sigma
+    bound = 2.0 * (2.0 * np.sqrt(chi2) * dm + dm * dm) + 1e-12 * chi2
+    assert abs(scal[0] - chi2) < bound
+    assert abs(scal[1] - U) < 0.5 * bound + 1e-12 * U
+    assert rel_l2(grad.cpu().numpy(), g) < TOL_GRAD[prec]
+    h.sync_status()
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("full", [True, False])
+def test_hvp_matches_oracle(name, prec, full):
+    p, o, th, d, mu, lam = make_case(name)
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 3))
+    v = quant(prec, perturbed(o, np.zeros_like(th), 1.0, 4))
+    want = o.hvp(th, d, v, lam, full=full)
+    got = h.hvp(_t(th, h), _t(v, h), full=full).cpu().numpy()
+    assert rel_l2(got, want) < TOL_GRAD[prec]
+
+
+def test_gradient_without_data_is_a_state_error():
+    from paper_2504_07090_gb300 import fm
+    p, o, th, d, mu, lam = make_case("tiny")
+    h = handle(p, "fp32")
+    with pytest.raises(fm.FmError) as e:
+        h.chi2_grad(_t(th, h))
+    assert e.value.status == fm.FM_ERR_STATE
+
+
+def test_repeat_runs_are_bitwise_identical():
+    p, o, th, d, mu, lam = make_case("mid")
+    h = handle(p, "fp32", d, mu, lam)
+    t = _t(th, h)
+    s1, g1 = h.chi2_grad(t)
+    s1, g1 = s1.clone(), g1.clone()
+    s2, g2 = h.chi2_grad(t)
+    assert bool((s1 == s2).all()) and bool((g1 == g2).all())

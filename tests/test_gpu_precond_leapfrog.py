@@ -1,0 +1,131 @@
+"""Preconditioner blocks and the leapfrog trajectory vs the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_cases import handle, make_case, perturbed, quant, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2504_07090_gb300 import build
+    build.build()
+
+
+def _t(a, h):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=h.dtype, device="cuda").contiguous()
+
+
+def _oracle_blocks(o, th, lam, bs):
+    if bs == 1:
+        # diagonal of the GN Hessian from explicit Jacobian columns
+        J = o.jacobian(th)
+        diag = np.sum(np.abs(J) ** 2, axis=0) / o.sigma ** 2 + lam
+        return diag[: o.n_sky], diag[o.n_sky:]
+    blocks, Hg = o.gn_blocks(th, lam, bs)
+    return np.stack([blocks[k] for k in sorted(blocks)]), Hg
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,bs", [("tiny", 1), ("small", 64)])
+def test_gn_blocks_match_oracle(prec, name, bs):
+    p, o, th, d, mu, lam = make_case(name)
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 5))
+    h.build_precond(_t(th, h), bs)
+    got = h.precond_blocks().cpu().numpy()
+    sky, gain = _oracle_blocks(o, th, lam, bs)
+    n_sky = sky.size
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert rel_l2(got[:n_sky], sky.reshape(-1)) < tol
+    assert rel_l2(got[n_sky:], gain.reshape(-1)) < tol
+
+
+def _oracle_mass(o, th, lam, bs):
+    blocks, Hg = o.gn_blocks(th, lam, bs)
+    out = []
+    for blk in sorted(blocks):
+        f, j0 = divmod(blk, o.nk // bs)
+        s = f * o.nk + j0 * bs
+        L, _ = oracle.cholesky_with_inflation(blocks[blk] - np.diag(lam[s:s + bs]), lam[s:s + bs])
+        out.append((s, L))
+    L, _ = oracle.cholesky_with_inflation(Hg - np.diag(lam[o.n_sky:]), lam[o.n_sky:])
+    out.append((o.n_sky, L))
+    return oracle.BlockCholesky(out)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_leapfrog_trajectory_matches_oracle(prec):
+    p, o, th, d, mu, lam = make_case("small")
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    q0 = quant(prec, perturbed(o, th, 0.005, 6))
+    mass = _oracle_mass(o, q0, lam, 64)
+    p0 = quant(prec, mass.mul_lower(np.random.default_rng(7).standard_normal(o.n_par)))
+    eps, n, u = 0.1, 20, 0.5
+
+    def fn(q):
+        _, U, g = o.chi2_grad(q, d, mu, lam)
+        return U, g
+
+    qw, pw, H0, H1, acc = oracle.leapfrog(fn, q0, p0, eps, n, 0.0, mass)
+    tq, tp = _t(q0, h), _t(p0, h)
+    h.build_precond(tq, 64)
+    hout, aout = h.leapfrog(tq, tp, eps, n, 0.0)
+    hh = hout.cpu().numpy()
+    tol_h = 1e-9 if prec == "fp64" else 2e-3
+    assert abs(hh[0] - H0) < tol_h * abs(H0) + (1e-9 if prec == "fp64" else 0.05)
+    assert abs((hh[1] - hh[0]) - (H1 - H0)) < (1e-6 if prec == "fp64" else 0.05) * max(1.0, abs(H1 - H0)) + \
+        (0.0 if prec == "fp64" else 0.05)
+    assert int(aout.item()) == 1
+    tol_q = 1e-9 if prec == "fp64" else 1e-4
+    assert rel_l2(tq.cpu().numpy() - q0, qw - q0) < tol_q
+    assert rel_l2(tp.cpu().numpy(), pw) < tol_q
+    # rejection restores q0: u just above the acceptance probability
+    a = math.exp(min(0.0, H0 - H1))
+    if a < 0.999:
+        tq2, tp2 = _t(q0, h), _t(p0, h)
+        hout, aout = h.leapfrog(tq2, tp2, eps, n, min(0.999999, a * 1.5 + 1e-3))
+        assert int(aout.item()) == 0
+        assert np.array_equal(tq2.cpu().numpy(), _t(q0, h).cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_precond_apply_ops_match_oracle_factor(prec):
+    p, o, th, d, mu, lam = make_case("small")
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 8))
+    h.build_precond(_t(th, h), 64)
+    mass = _oracle_mass(o, th, lam, 64)
+    z = quant(prec, np.random.default_rng(9).standard_normal(o.n_par))
+    tol = 1e-9 if prec == "fp64" else 2e-4
+    got = {op: h.precond_apply(op, _t(z, h)).cpu().numpy() for op in range(4)}
+    assert rel_l2(got[0], mass.mul_lower(z)) < tol
+    assert rel_l2(got[1], mass.solve_lower(z)) < tol
+    assert rel_l2(got[2], mass.solve_upper_t(z)) < tol
+    assert rel_l2(got[3], mass.solve_upper_t(mass.solve_lower(z))) < tol
+
+
+def test_profiling_counts_contraction_launches():
+    from paper_2504_07090_gb300 import fm
+    p, o, th, d, mu, lam = make_case("tiny")
+    d, mu, lam = quant("fp32", d, mu, lam)
+    h = handle(p, "fp32", d, mu, lam)
+    t = _t(quant("fp32", th), h)
+    n0 = fm.kernel_launches()
+    h.set_profiling(True)
+    h.chi2_grad(t)
+    h.chi2_grad(t)
+    (fms, ams), (fn, an) = h.get_profile()
+    assert (fn, an) == (2, 2) and fms > 0 and ams > 0
+    assert fm.kernel_launches() - n0 >= 2 * 8
+    h.set_profiling(False)
+    h.chi2_grad(t)
+    assert h.get_profile()[1] == (0, 0)
