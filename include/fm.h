@@ -88,7 +88,7 @@ typedef struct {
 } fm_config;
 
 /* Create a handle: validates the configuration, allocates the device workspace and
- * runs the once-per-handle precompute on the device ("cached mode" of Sec. 6):
+ * runs the once-per-handle precompute on the device ("cached mode" of App. C):
  * topocentric pixel directions for every LST, cell solid angles, basis tables and
  * the gain frequency basis.  Synchronous.  On failure *out is NULL. */
 FM_API fm_status fm_create(const fm_config *cfg, fm_handle *out);
@@ -114,6 +114,11 @@ FM_API fm_status fm_forward(fm_handle h, const void *dev_theta, void *dev_vis_ou
 /* Unit-gain visibilities V(nu,t) of pixel values dev_x ([n_freq][n_pix] reals, the sky
  * brightness per pixel in Jy/sr) -- Eq. rime_discrete alone, for tests. */
 FM_API fm_status fm_forward_pixels(fm_handle h, const void *dev_x, void *dev_vis_out, fm_stream stream);
+
+/* Sky maps of the parameters: x[f][dec][ra] = sum_{m,n} Phi_m(ra) P_n(dec) a[f][m][n]
+ * (the separable mode -> pixel transform of Eq. fg_separable / Eq. eor_model) in Jy/sr,
+ * dev_x_out: device [n_freq][n_dec*n_ra] reals.  Uses the handle's workspace. */
+FM_API fm_status fm_sky_pixels(fm_handle h, const void *dev_theta, void *dev_x_out, fm_stream stream);
 
 /* chi^2 = sum |m - d|^2 / sigma^2 (Eq. likelihood) and the gradient of
  * U = chi^2/2 + prior (the negative log posterior of Eq. posterior up to a constant).

@@ -12,7 +12,7 @@
  *   - pixel centres, exact cell solid angles and topocentric directions of a regular
  *     RA x Dec grid (Sec. 2.1, discretised RIME, Eq. rime_discrete; grid of Sec. 3.2);
  *   - the separable cos/sin(RA) x Legendre(Dec) mode basis evaluated pixel by pixel
- *     (Eq. fg_separable, Eq. eor_model; azimuthal periodicity of App. A.3);
+ *     (Eq. fg_separable, Eq. eor_model; azimuthal periodicity of App. A.2);
  *   - the Gaussian primary beam (total-power response A of Eq. rime_integral);
  *   - V_pq(nu,t) = sum_j dOmega_j A_j K_jpq B_j with K = exp(-2 pi i b_pq . s nu / c),
  *     b_pq = r_p - r_q, one baseline at a time (Eq. rime_integral, Eq. rime_discrete);
@@ -65,7 +65,7 @@ static void orc_legendre(double x, int n, double *out)
 static double orc_ra_function(int m, int n_mode_ra, double ahat)
 {
     /* 1, cos(k a), sin(k a) for k = 1 .. M/2-1, and cos(M/2 a) last: M functions that
-     * are periodic over the RA span (azimuthal condition of App. A.3). */
+     * are periodic over the RA span (azimuthal condition of App. A.2). */
     if (m == 0) return 1.0;
     if (m == n_mode_ra - 1 && n_mode_ra >= 2) return cos(0.5 * n_mode_ra * ahat);
     int k = (m + 1) / 2;

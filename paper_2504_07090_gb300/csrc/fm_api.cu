@@ -413,6 +413,16 @@ fm_status fm_forward_pixels(fm_handle h, const void *dev_x, void *dev_vis_out, f
     return run_vis<float>(c, (const float *)dev_x, (float *)dev_vis_out, stream);
 }
 
+fm_status fm_sky_pixels(fm_handle h, const void *dev_theta, void *dev_x_out, fm_stream stream)
+{
+    FM_HANDLE_OK(h);
+    if (!dev_theta || !dev_x_out) return invalid("NULL device pointer");
+    Ctx &c = *reinterpret_cast<Ctx *>(h);
+    if (c.prec == FM_PREC_FP64_SIMT)
+        return launch_modes_forward<double>(c, (const double *)dev_theta, (double *)dev_x_out, stream, 0);
+    return launch_modes_forward<float>(c, (const float *)dev_theta, (float *)dev_x_out, stream, 0);
+}
+
 fm_status fm_chi2_grad(fm_handle h, const void *dev_theta, double *dev_chi2_out, double *dev_u_out,
                        void *dev_grad_out, fm_stream stream)
 {

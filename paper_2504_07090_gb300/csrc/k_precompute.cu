@@ -1,4 +1,4 @@
-// Once-per-handle precompute on the device, in FP64 ("cached mode" of Sec. 6):
+// Once-per-handle precompute on the device, in FP64 ("cached mode" of App. C):
 // topocentric directions of every pixel at every LST, squared zenith angles for the
 // beam, exact cell solid angles, the separable mode basis, the gain frequency basis,
 // per-channel antenna phase slopes and the beam exponent per channel.  The FP32

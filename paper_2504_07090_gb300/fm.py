@@ -28,7 +28,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x1": 2, "bf16x3": 3, "fp16x1": 4, "fp16
 
 # every entry point declared in include/fm.h
 EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_data", "fm_set_prior", "fm_forward",
-           "fm_forward_pixels", "fm_chi2_grad", "fm_hvp", "fm_build_precond", "fm_get_precond_blocks",
+           "fm_forward_pixels", "fm_sky_pixels", "fm_chi2_grad", "fm_hvp", "fm_build_precond", "fm_get_precond_blocks",
            "fm_precond_size", "fm_leapfrog", "fm_precond_apply", "fm_set_profiling", "fm_get_profile",
            "fm_kernel_launches", "fm_sync_status", "fm_last_error"]
 
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
     L.fm_set_prior.argtypes = [vp, vp, vp, vp]
     L.fm_forward.argtypes = [vp, vp, vp, vp]
     L.fm_forward_pixels.argtypes = [vp, vp, vp, vp]
+    L.fm_sky_pixels.argtypes = [vp, vp, vp, vp]
     L.fm_chi2_grad.argtypes = [vp, vp, vp, vp, vp, vp]
     L.fm_hvp.argtypes = [vp, vp, vp, vp, c_int, vp]
     L.fm_build_precond.argtypes = [vp, vp, c_int, vp]
@@ -146,6 +147,7 @@ class ForwardModel:
         self.n_vis = int(self.lib.fm_num_vis(h))
         self.vis_shape = (prob.n_freq, prob.n_lst, prob.n_bl, 2)
         self.n_sky = prob.n_freq * prob.n_mode_ra * prob.n_mode_dec
+        self.n_pix_total = prob.n_freq * prob.n_ra * prob.n_dec
 
     def close(self):
         if getattr(self, "h", None):
@@ -183,6 +185,13 @@ class ForwardModel:
         out = self.empty_vis() if out is None else out
         _check(self.lib.fm_forward_pixels(self.h, _ptr(x), self._t(out, 2 * self.n_vis, "out"), _stream()),
                "fm_forward_pixels")
+        return out
+
+    def sky_pixels(self, theta: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Pixel maps x[f][dec*n_ra + ra] of the sky modes in theta."""
+        out = torch.empty(self.n_pix_total, dtype=self.dtype, device="cuda") if out is None else out
+        _check(self.lib.fm_sky_pixels(self.h, self._t(theta, self.n_params, "theta"),
+                                      self._t(out, self.n_pix_total, "out"), _stream()), "fm_sky_pixels")
         return out
 
     def chi2_grad(self, theta: torch.Tensor, grad: torch.Tensor | None = None, scal: torch.Tensor | None = None):

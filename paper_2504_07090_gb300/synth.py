@@ -188,7 +188,7 @@ def batch_problems(n: int = 64, seed: int = 20250411) -> list[Problem]:
 # ----------------------------------------------------------------------------- draws
 
 def rayleigh_jeans_jy_per_sr(temp_k: float | np.ndarray, nu_hz: float | np.ndarray):
-    """Specific intensity of a brightness temperature (footnote of Sec. 5.2 uses the same law)."""
+    """Specific intensity of a brightness temperature (footnote of Sec. 4.3 uses the same law)."""
     return 2.0 * K_BOLTZMANN * np.asarray(nu_hz) ** 2 * np.asarray(temp_k) / C_LIGHT ** 2 * 1e26
 
 

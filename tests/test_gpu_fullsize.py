@@ -52,18 +52,15 @@ def test_cfg1_one_channel_gradient(cfg1, prec):
     from paper_2504_07090_gb300 import fm
     p, o, tr = cfg1
     th = quant(prec, tr.theta)
-    h0 = fm.ForwardModel(p, prec, sigma=1.0)
-    m = as_complex(h0.forward(torch.tensor(th, dtype=torch.float32, device="cuda")))
-    h0.close()
-    sigma = 0.01 * float(np.mean(np.abs(m)))
-    p.sigma = sigma
-    o.sigma = sigma
-    # data: oracle-independent seeded noise around a perturbed model (no oracle input from the GPU)
-    d = quant(prec, sigma * (tr.noise[..., 0] + 1j * tr.noise[..., 1]) + 0.0)
     rng = np.random.default_rng(5)
     f0 = int(rng.integers(p.n_freq))
+    # data of channel f0: oracle model plus seeded noise of 1 % of its mean |V| (other channels 0)
+    m0 = o.model(th, fts=[(f0, t) for t in range(p.n_lst)])[f0]
+    sigma = 0.01 * float(np.mean(np.abs(m0)))
+    p.sigma = sigma
+    o.sigma = sigma
     d_full = np.zeros((p.n_freq, p.n_lst, p.n_bl), dtype=np.complex128)
-    d_full[f0] = o.model(th, fts=[(f0, t) for t in range(p.n_lst)])[f0] + d[f0]
+    d_full[f0] = m0 + sigma * (tr.noise[f0, ..., 0] + 1j * tr.noise[f0, ..., 1])
     d_full = quant(prec, d_full)
     h = fm.ForwardModel(p, prec, sigma=sigma)
     h.set_data(torch.tensor(np.stack([d_full.real, d_full.imag], -1), dtype=torch.float32, device="cuda").contiguous())

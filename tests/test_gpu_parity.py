@@ -111,3 +111,13 @@ def test_repeat_runs_are_bitwise_identical():
     s1, g1 = s1.clone(), g1.clone()
     s2, g2 = h.chi2_grad(t)
     assert bool((s1 == s2).all()) and bool((g1 == g2).all())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sky_pixels_match_oracle(prec):
+    p, o, th, d, mu, lam = make_case("small")
+    h = handle(p, prec)
+    th = quant(prec, th)
+    a, _ = o.split(th)
+    got = h.sky_pixels(_t(th, h)).cpu().numpy().reshape(p.n_freq, -1)
+    assert rel_l2(got, o.sky(a)) < (1e-12 if prec == "fp64" else 1e-6)

@@ -88,7 +88,7 @@ def test_dec_basis_is_numpy_legendre():
 
 def test_ra_basis_orthogonal_and_at_its_wavenumber():
     # cos/sin periodic over the span: discrete orthogonality on the uniform grid and the
-    # FFT puts each function's power at its own wavenumber (App. A.3 azimuthal condition)
+    # FFT puts each function's power at its own wavenumber (App. A.2 azimuthal condition)
     M, R = 16, 24
     p = _problem(n_ra=R, n_dec=2, n_mode_ra=M, n_mode_dec=1)
     o = oracle.Oracle(p)
