@@ -172,6 +172,26 @@ FM_API fm_status fm_precond_apply(fm_handle h, int op, const void *dev_in, void 
 FM_API fm_status fm_set_profiling(fm_handle h, int on);
 FM_API fm_status fm_get_profile(fm_handle h, double *out_ms, int64_t *out_count);
 
+/* No-allocation variant of fm_sky_pixels (the paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc at call time, such as code running
+ * under an allocator it does not own or inside a region where a new device allocation
+ * is not allowed).  It takes no handle: the caller passes the basis tables
+ * dev_phi [n_ra][n_mode_ra] (RA functions at the cell centres), dev_leg
+ * [n_dec][n_mode_dec] (Legendre polynomials at the cell centres), the modes dev_a
+ * [n_freq][n_mode_ra][n_mode_dec] and the output dev_x [n_freq][n_dec][n_ra], all float
+ * device memory, and the call computes x[f][d][r] = sum_n leg[d][n] sum_m phi[r][m]
+ * a[f][m][n] without allocating anything.  The intermediate sum over m lives in a
+ * file-scope device array of 2^21 floats (8 MiB) that every GPU loading the library
+ * holds until the process exits; n_freq*n_ra*n_mode_dec above 2^21 is rejected with
+ * FM_ERR_INVALID_ARG.  The first call on each device looks up the array's device
+ * address with that device current (make that first call before any stream capture).
+ * Every call shares the array, which keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, or a second call before the first finished on a
+ * different stream) race on it. */
+FM_API fm_status fm_sky_pixels_noalloc(int n_freq, int n_ra, int n_dec, int n_mode_ra, int n_mode_dec,
+                                       const float *dev_phi, const float *dev_leg, const float *dev_a, float *dev_x,
+                                       fm_stream stream);
+
 /* Kernels launched by this library in this process so far (all handles). */
 FM_API int64_t fm_kernel_launches(void);
 

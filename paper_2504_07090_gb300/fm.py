@@ -30,7 +30,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x1": 2, "bf16x3": 3, "fp16x1": 4, "fp16
 EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_data", "fm_set_prior", "fm_forward",
            "fm_forward_pixels", "fm_sky_pixels", "fm_chi2_grad", "fm_hvp", "fm_build_precond", "fm_get_precond_blocks",
            "fm_precond_size", "fm_leapfrog", "fm_precond_apply", "fm_set_profiling", "fm_get_profile",
-           "fm_kernel_launches", "fm_sync_status", "fm_last_error"]
+           "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status", "fm_last_error"]
 
 
 class FmError(RuntimeError):
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
     L.fm_precond_apply.argtypes = [vp, c_int, vp, vp, vp]
     L.fm_set_profiling.argtypes = [vp, c_int]
     L.fm_get_profile.argtypes = [vp, POINTER(c_double), POINTER(c_int64)]
+    L.fm_sky_pixels_noalloc.argtypes = [c_int, c_int, c_int, c_int, c_int, vp, vp, vp, vp, vp]
     L.fm_kernel_launches.argtypes = []
     L.fm_kernel_launches.restype = c_int64
     L.fm_last_error.restype = ctypes.c_char_p
