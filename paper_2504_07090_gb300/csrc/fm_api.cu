@@ -166,6 +166,7 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
     FM_TRY(dalloc(*c, &d32, (size_t)c->F * c->A * 6)); g.kap32 = d32;
     FM_TRY(dalloc(*c, &d64, c->F)); g.bcoef64 = d64;
     FM_TRY(dalloc(*c, &d32, c->F)); g.bcoef32 = d32;
+    FM_TRY(dalloc(*c, &d32, (size_t)c->npix)); g.dompix32 = d32;
     int *bl;
     FM_TRY(dalloc(*c, &bl, 2 * (size_t)c->B));
     std::vector<int> hb(2 * (size_t)c->B);

@@ -39,6 +39,7 @@ struct DevGeom {
     const float *gleg32;      // [F][NG]
     const float *kap32;       // [F][A][6] two-float
     const float *bcoef32;     // [F]
+    const float *dompix32;    // [npix] cell solid angle of each pixel
     const float *dkap32;      // [A][3] channel step dnu * r_i / c (turns per unit direction cosine)
     int uniform_freq;         // channels equally spaced: E(nu + dnu) = E(nu) exp(-2 pi i dkap . s)
     const int *bl_i, *bl_j;   // [B]
@@ -83,6 +84,7 @@ struct Ctx {
     int64_t pc_size = 0;
     // tensor-core path: per-channel power-of-two operand scale (FP16 modes), max cell solid angle
     float *tc_scale = nullptr;
+    float *tc_wbar = nullptr;         // [F][T][npix] beam-weighted pixel adjoint per LST
     float domega_max = 0.f;
     // monopole split (FP32 storage paths): U[f][t][b] = visibility of a unit uniform sky,
     // computed once in FP64; the contraction kernels see x - a_00 only

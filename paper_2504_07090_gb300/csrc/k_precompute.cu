@@ -127,6 +127,11 @@ __global__ void k_tables(PreArgs a, double *domega64, float *domega32, double *p
     }
 }
 
+__global__ void k_dompix(int npix, int R, const float *__restrict__ domega32, float *__restrict__ dompix)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) dompix[p] = domega32[p / R];
+}
+
 }  // namespace
 
 fm_status launch_precompute(Ctx &c, cudaStream_t st)
@@ -155,6 +160,8 @@ fm_status launch_precompute(Ctx &c, cudaStream_t st)
                                  const_cast<double *>(c.g.gleg64), const_cast<float *>(c.g.gleg32),
                                  const_cast<double *>(c.g.kap64), const_cast<float *>(c.g.kap32),
                                  const_cast<double *>(c.g.bcoef64), const_cast<float *>(c.g.bcoef32));
+    FM_CK_LAUNCH();
+    k_dompix<<<cdiv(c.npix, 256), 256, 0, st>>>(c.npix, c.R, c.g.domega32, const_cast<float *>(c.g.dompix32));
     FM_CK_LAUNCH();
     return FM_OK;
 }

@@ -19,6 +19,8 @@
 // Synchronisation: one mbarrier per stage, completed by tcgen05.commit after the MMAs
 // reading that stage; every wait is bounded by a clock limit, after which the kernel
 // records FM_ERR_TIMEOUT, drains its own MMAs (bounded), frees TMEM and returns.
+#include <cstdlib>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -53,6 +55,38 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
         if (ok) return true;
         if (clock64() - t0 > WAIT_CYCLES) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
+}
+
+// bounded wait that also gives up when another warp raised the CTA's abort flag
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -263,223 +297,312 @@ __global__ void __launch_bounds__(256) k_chan_scale(int npix, const float *__res
 // Producers: lane l of every warp owns pixels 2l, 2l+1 of the 64-pixel stage; warp w
 // generates antennas w, w+8, ...  Each thread writes 32-bit words (2 pixels) of rows
 // 2i (Re) and 2i+1 (Im) of A_op = W Ahat and B_op = Ahat, hi and (x3) lo parts.
+// Warp-specialised forward: warps 0-7 produce operand stages, warp 12 (one lane) issues
+// the MMAs, warps 8-11 drain the TMEM accumulators.  Hand-offs use mbarriers only:
+//   full[s]     8 producer-warp arrivals -> stage s holds operands
+//   empty[s]    tcgen05.commit after the MMAs that read stage s
+//   accfull[q]  tcgen05.commit after the last MMA of a pixel sub-range into set q
+//   accempty[q] 4 epilogue-warp arrivals after set q was read
+// Stage order (all roles enumerate it identically): task -> 64-pixel chunk j -> channel r
+// of the task's frequency-recurrence group.  Accumulator set q = sub-range parity, so
+// the epilogue of one sub-range overlaps the MMAs of the next; partial visibilities
+// are summed in FP32 in shared memory and written once per task.
+constexpr int FWD_PROD_WARPS = 8;
+constexpr int FWD_EPI_WARP0 = 8;
+constexpr int FWD_MMA_WARP = 12;
+constexpr int FWD_THREADS = 13 * 32;
+
 template <int ET, bool X3, int KMAX>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-k_vis_tc(DevGeom g, FwdLayout L, int rch, const float *__restrict__ x, const float *__restrict__ chan_scale,
+__global__ void __launch_bounds__(FWD_THREADS, 1)
+k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, const float *__restrict__ chan_scale,
          float *__restrict__ vis)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;                 // 1024-aligned for the swizzle atoms
+    const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t bar0 = base + L.nstage * L.stage_bytes;        // nstage mbarriers (8 B each)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + L.nstage * L.stage_bytes + 8 * L.nstage);
+    const uint32_t stages_bytes = (uint32_t)L.nstage * L.stage_bytes;
+    float *vpart = reinterpret_cast<float *>(gbase + stages_bytes);            // [rch][B][2]
+    const uint32_t bar_off = stages_bytes + (uint32_t)(rch * g.B * 2 * 4 + 15) / 16 * 16;
+    const uint32_t full0 = base + bar_off, empty0 = full0 + 8 * L.nstage;
+    const uint32_t accf0 = empty0 + 8 * L.nstage, acce0 = accf0 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + bar_off + 16 * L.nstage + 32);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + bar_off + 16 * L.nstage + 36);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rows_used = 2 * g.A;
     const int ntl = X3 ? 2 : 1;
-
     for (int s = 0; s < L.nstage; ++s) {            // zero the padding rows once
         uint8_t *st = gbase + (size_t)s * L.stage_bytes;
         for (int tl = 0; tl < ntl; ++tl) {
             uint8_t *ta = st + tl * L.a_bytes;
-            for (int e = tid; e < (128 - rows_used) * 8; e += TC_THREADS)
+            for (int e = tid; e < (128 - rows_used) * 8; e += FWD_THREADS)
                 reinterpret_cast<uint4 *>(ta + (size_t)(rows_used + e / 8) * 128)[e % 8] = make_uint4(0, 0, 0, 0);
             uint8_t *tb = st + ntl * L.a_bytes + tl * L.b_bytes;
-            for (int e = tid; e < (L.npad - rows_used) * 8; e += TC_THREADS)
+            for (int e = tid; e < (L.npad - rows_used) * 8; e += FWD_THREADS)
                 reinterpret_cast<uint4 *>(tb + (size_t)(rows_used + e / 8) * 128)[e % 8] = make_uint4(0, 0, 0, 0);
         }
     }
     if (tid == 0) {
-        for (int s = 0; s < L.nstage; ++s) mbar_init(bar0 + 8 * s, 1);
+        for (int s = 0; s < L.nstage; ++s) {
+            mbar_init(full0 + 8 * s, FWD_PROD_WARPS);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(accf0 + 8 * q, 1);
+            mbar_init(acce0 + 8 * q, 4);
+        }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
+    if (warp == FWD_MMA_WARP) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_d = *tmem_slot;
-    const uint32_t idesc = idesc_f16(128, L.npad, Elem<ET>::kFmt);
-    const uint32_t wsub = (uint32_t)(lane & 3) * 4u;               // byte offset of this lane's word in a chunk
-    const int wchunk = lane >> 2;                                   // 16-byte chunk holding pixels 2l, 2l+1
-
     const int nst = (g.npix + KST - 1) / KST;
     const int ngrp = (g.F + rch - 1) / rch;
     const int ntask = ngrp * g.T;
-    long long gs = 0;
-    int last_s = -1;
-    long long last_use = 0;
-    bool aborted = false;
+    const int set_cols = rch * L.npad;
 
-    for (int task = blockIdx.x; task < ntask && !aborted; task += gridDim.x) {
-        const int t = task % g.T, f0 = (task / g.T) * rch;
-        const int nr = min(rch, g.F - f0);
-        for (int j = 0; j < nst && !aborted; ++j) {
-            const int pa = j * KST + 2 * lane, pb = pa + 1;
-            const bool va = pa < g.npix, vb = pb < g.npix;
-            float sa[6], sb[6];
-            if (va) load_s6(g, t, pa, sa);
-            if (vb) load_s6(g, t, pb, sb);
-            // phasor state of this thread's antennas at its two pixels, advanced by D per channel
-            float er[KMAX][2], ei[KMAX][2], dr[KMAX][2], di[KMAX][2];
-            for (int r = 0; r < nr; ++r, ++gs) {
-                const int f = f0 + r;
-                const int s = (int)(gs % L.nstage);
-                const long long use = gs / L.nstage;
-                const float scale = ET == 1 ? chan_scale[f] : 1.f;
-                const float wa = va ? pixel_w(g, f, t, pa) * x[(size_t)f * g.npix + pa] * scale : 0.f;
-                const float wb = vb ? pixel_w(g, f, t, pb) * x[(size_t)f * g.npix + pb] * scale : 0.f;
+    if (warp < FWD_PROD_WARPS) {
+        // ------------------------------------------------------------ producers
+        const uint32_t wsub = (uint32_t)(lane & 3) * 4u;
+        const int wchunk = lane >> 2;
+        long long gs = 0;
+        for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+            const int t = task % g.T, f0 = (task / g.T) * rch;
+            const int nr = min(rch, g.F - f0);
+            for (int j = 0; j < nst; ++j) {
+                const int pa = j * KST + 2 * lane, pb = pa + 1;
+                const bool va = pa < g.npix, vb = pb < g.npix;
+                float sa[6], sb[6], za = -1.f, zb = -1.f, da = 0.f, db = 0.f;
+                if (va) { load_s6(g, t, pa, sa); za = g.za2_32[(size_t)t * g.npix + pa]; da = g.dompix32[pa]; }
+                if (vb) { load_s6(g, t, pb, sb); zb = g.za2_32[(size_t)t * g.npix + pb]; db = g.dompix32[pb]; }
+                float er[KMAX][2], ei[KMAX][2], dr[KMAX][2], di[KMAX][2];
+                for (int r = 0; r < nr; ++r, ++gs) {
+                    const int f = f0 + r;
+                    const int s = (int)(gs % L.nstage);
+                    const long long use = gs / L.nstage;
+                    const float scale = ET == 1 ? chan_scale[f] : 1.f;
+                    const float bc = g.bcoef32[f];
+                    const float wa = (za >= 0.f) ? da * __expf(bc * za) * x[(size_t)f * g.npix + pa] * scale : 0.f;
+                    const float wb = (zb >= 0.f) ? db * __expf(bc * zb) * x[(size_t)f * g.npix + pb] * scale : 0.f;
 #pragma unroll
-                for (int k = 0; k < KMAX; ++k) {
-                    const int i = warp + 8 * k;
-                    if (i >= g.A) continue;
-                    if (r == 0) {
-                        float k6[6];
+                    for (int k = 0; k < KMAX; ++k) {
+                        const int i = warp + FWD_PROD_WARPS * k;
+                        if (i >= g.A) continue;
+                        if (r == 0) {
+                            float k6[6];
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) k6[q] = g.kap32[((size_t)f * g.A + i) * 6 + q];
-                        er[k][0] = ei[k][0] = er[k][1] = ei[k][1] = 0.f;
-                        if (va) phasor_of(phase_frac(k6, sa), er[k][0], ei[k][0]);
-                        if (vb) phasor_of(phase_frac(k6, sb), er[k][1], ei[k][1]);
-                        if (nr > 1) {
-                            const float d0 = g.dkap32[3 * i], d1 = g.dkap32[3 * i + 1], d2 = g.dkap32[3 * i + 2];
-                            phasor_of(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]) + d2 * (sa[4] + sa[5]), dr[k][0], di[k][0]);
-                            phasor_of(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]) + d2 * (sb[4] + sb[5]), dr[k][1], di[k][1]);
-                        }
-                    } else {
+                            for (int q = 0; q < 6; ++q) k6[q] = g.kap32[((size_t)f * g.A + i) * 6 + q];
+                            er[k][0] = ei[k][0] = er[k][1] = ei[k][1] = 0.f;
+                            if (va) phasor_of(phase_frac(k6, sa), er[k][0], ei[k][0]);
+                            if (vb) phasor_of(phase_frac(k6, sb), er[k][1], ei[k][1]);
+                            if (nr > 1) {
+                                const float d0 = g.dkap32[3 * i], d1 = g.dkap32[3 * i + 1], d2 = g.dkap32[3 * i + 2];
+                                phasor_of(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]) + d2 * (sa[4] + sa[5]), dr[k][0], di[k][0]);
+                                phasor_of(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]) + d2 * (sb[4] + sb[5]), dr[k][1], di[k][1]);
+                            }
+                        } else {
 #pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const float a = er[k][u], b = ei[k][u];
-                            er[k][u] = a * dr[k][u] - b * di[k][u];
-                            ei[k][u] = a * di[k][u] + b * dr[k][u];
-                        }
-                    }
-                }
-                bool bad = false;
-                if (tid == 0 && use >= 1) bad = !mbar_wait(bar0 + 8 * s, (uint32_t)((use - 1) & 1));
-                if (__syncthreads_or(bad)) { aborted = true; break; }
-                uint8_t *st = gbase + (size_t)s * L.stage_bytes;
-                uint8_t *a_hi = st, *a_lo = st + L.a_bytes;
-                uint8_t *b_hi = st + ntl * L.a_bytes, *b_lo = b_hi + L.b_bytes;
-#pragma unroll
-                for (int k = 0; k < KMAX; ++k) {
-                    const int i = warp + 8 * k;
-                    if (i >= g.A) continue;
-                    uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-                    Elem<ET>::split(wa * er[k][0], wb * er[k][1], h0, l0);
-                    Elem<ET>::split(wa * ei[k][0], wb * ei[k][1], h1, l1);
-                    Elem<ET>::split(er[k][0], er[k][1], h2, l2);
-                    Elem<ET>::split(ei[k][0], ei[k][1], h3, l3);
-                    const uint32_t ore = sw128_off(2 * i, wchunk) + wsub, oim = sw128_off(2 * i + 1, wchunk) + wsub;
-                    *reinterpret_cast<uint32_t *>(a_hi + ore) = h0;
-                    *reinterpret_cast<uint32_t *>(a_hi + oim) = h1;
-                    *reinterpret_cast<uint32_t *>(b_hi + ore) = h2;
-                    *reinterpret_cast<uint32_t *>(b_hi + oim) = h3;
-                    if (X3) {
-                        *reinterpret_cast<uint32_t *>(a_lo + ore) = l0;
-                        *reinterpret_cast<uint32_t *>(a_lo + oim) = l1;
-                        *reinterpret_cast<uint32_t *>(b_lo + ore) = l2;
-                        *reinterpret_cast<uint32_t *>(b_lo + oim) = l3;
-                    }
-                }
-                fence_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    tc_fence_after();
-                    const uint32_t sa_hi = base + (uint32_t)s * L.stage_bytes;
-                    const uint32_t sa_lo = sa_hi + L.a_bytes;
-                    const uint32_t sb_hi = sa_hi + (uint32_t)ntl * L.a_bytes;
-                    const uint32_t sb_lo = sb_hi + L.b_bytes;
-                    const uint32_t dacc = tmem_d + (uint32_t)(r * L.npad);
-#pragma unroll
-                    for (int kk = 0; kk < KST / 16; ++kk) {
-                        const uint32_t off = 32u * kk;
-                        const uint64_t dah = sdesc_sw128(sa_hi + off), dbh = sdesc_sw128(sb_hi + off);
-                        mma_bf16(dacc, dah, dbh, idesc, (j > 0 || kk > 0) ? 1u : 0u);
-                        if (X3) {
-                            mma_bf16(dacc, dah, sdesc_sw128(sb_lo + off), idesc, 1u);
-                            mma_bf16(dacc, sdesc_sw128(sa_lo + off), dbh, idesc, 1u);
+                            for (int u = 0; u < 2; ++u) {
+                                const float a = er[k][u], b = ei[k][u];
+                                er[k][u] = a * dr[k][u] - b * di[k][u];
+                                ei[k][u] = a * di[k][u] + b * dr[k][u];
+                            }
                         }
                     }
-                    mma_commit(bar0 + 8 * s);
+                    bool ok = true;
+                    if (lane == 0 && use >= 1) ok = mbar_wait_ab(empty0 + 8 * s, (uint32_t)((use - 1) & 1), abort_flag);
+                    __syncwarp();
+                    if (*abort_flag || !ok) goto done;
+                    {
+                        uint8_t *st = gbase + (size_t)s * L.stage_bytes;
+                        uint8_t *a_hi = st, *a_lo = st + L.a_bytes;
+                        uint8_t *b_hi = st + ntl * L.a_bytes, *b_lo = b_hi + L.b_bytes;
+#pragma unroll
+                        for (int k = 0; k < KMAX; ++k) {
+                            const int i = warp + FWD_PROD_WARPS * k;
+                            if (i >= g.A) continue;
+                            uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+                            Elem<ET>::split(wa * er[k][0], wb * er[k][1], h0, l0);
+                            Elem<ET>::split(wa * ei[k][0], wb * ei[k][1], h1, l1);
+                            Elem<ET>::split(er[k][0], er[k][1], h2, l2);
+                            Elem<ET>::split(ei[k][0], ei[k][1], h3, l3);
+                            const uint32_t ore = sw128_off(2 * i, wchunk) + wsub, oim = sw128_off(2 * i + 1, wchunk) + wsub;
+                            *reinterpret_cast<uint32_t *>(a_hi + ore) = h0;
+                            *reinterpret_cast<uint32_t *>(a_hi + oim) = h1;
+                            *reinterpret_cast<uint32_t *>(b_hi + ore) = h2;
+                            *reinterpret_cast<uint32_t *>(b_hi + oim) = h3;
+                            if (X3) {
+                                *reinterpret_cast<uint32_t *>(a_lo + ore) = l0;
+                                *reinterpret_cast<uint32_t *>(a_lo + oim) = l1;
+                                *reinterpret_cast<uint32_t *>(b_lo + ore) = l2;
+                                *reinterpret_cast<uint32_t *>(b_lo + oim) = l3;
+                            }
+                        }
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(full0 + 8 * s);
                 }
-                last_s = s;
-                last_use = use;
             }
         }
-        if (aborted) break;
-        bool bad = false;
-        if (tid == 0) bad = !mbar_wait(bar0 + 8 * last_s, (uint32_t)(last_use & 1));
-        if (__syncthreads_or(bad)) { aborted = true; break; }
-        if (warp < 4) {
-            tc_fence_after();
-            const int row = 32 * warp + lane;
-            const int i = row >> 1;
-            const bool even = (row & 1) == 0;
-            for (int r = 0; r < nr; ++r) {
-                const int f = f0 + r;
-                const float inv = ET == 1 ? 1.f / chan_scale[f] : 1.f;
-                const size_t ft = (size_t)f * g.T + t;
-                for (int c0 = 0; c0 < L.npad; c0 += 16) {
-                    float v[16], pv[16];
-                    tmem_ld16(tmem_d + ((uint32_t)(32 * warp) << 16) + (uint32_t)(r * L.npad + c0), v);
+    } else if (warp == FWD_MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, L.npad, Elem<ET>::kFmt);
+            long long gs = 0, sr = 0, last = -1;
+            for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+                const int f0 = (task / g.T) * rch;
+                const int nr = min(rch, g.F - f0);
+                for (int j = 0; j < nst; ++j) {
+                    const int q = (int)(sr & 1);
+                    if (j % sub == 0 && (sr >> 1) >= 1) {
+                        if (!mbar_wait_ab(acce0 + 8 * q, (uint32_t)(((sr >> 1) - 1) & 1), abort_flag)) goto mma_done;
+                    }
+                    for (int r = 0; r < nr; ++r, ++gs) {
+                        const int s = (int)(gs % L.nstage);
+                        if (!mbar_wait_ab(full0 + 8 * s, (uint32_t)((gs / L.nstage) & 1), abort_flag)) goto mma_done;
+                        tc_fence_after();
+                        const uint32_t sa_hi = base + (uint32_t)s * L.stage_bytes;
+                        const uint32_t sa_lo = sa_hi + L.a_bytes;
+                        const uint32_t sb_hi = sa_hi + (uint32_t)ntl * L.a_bytes;
+                        const uint32_t sb_lo = sb_hi + L.b_bytes;
+                        const uint32_t dacc = tmem_d + (uint32_t)(q * set_cols + r * L.npad);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) pv[q] = __shfl_xor_sync(0xffffffffu, v[q], 1);
-                    if (even && i < g.A) {
+                        for (int kk = 0; kk < KST / 16; ++kk) {
+                            const uint32_t off = 32u * kk;
+                            const uint64_t dah = sdesc_sw128(sa_hi + off), dbh = sdesc_sw128(sb_hi + off);
+                            mma_bf16(dacc, dah, dbh, idesc, ((j % sub) > 0 || kk > 0) ? 1u : 0u);
+                            if (X3) {
+                                mma_bf16(dacc, dah, sdesc_sw128(sb_lo + off), idesc, 1u);
+                                mma_bf16(dacc, sdesc_sw128(sa_lo + off), dbh, idesc, 1u);
+                            }
+                        }
+                        mma_commit(empty0 + 8 * s);
+                        last = gs;
+                    }
+                    if ((j % sub) == sub - 1 || j == nst - 1) {
+                        mma_commit(accf0 + 8 * q);
+                        ++sr;
+                    }
+                }
+            }
+        mma_done:
+            if (*abort_flag && last >= 0) {
+                // drain this CTA's MMAs before TMEM is freed (bounded)
+                const int s = (int)(last % L.nstage);
+                long long t0 = clock64();
+                while (clock64() - t0 < WAIT_CYCLES) {
+                    uint32_t ok;
+                    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                                 : "=r"(ok) : "r"(empty0 + 8 * s), "r"((uint32_t)((last / L.nstage) & 1)) : "memory");
+                    if (ok) break;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 8-11)
+        const int quarter = warp & 3;                   // TMEM lanes 32*quarter .. +31
+        const int row = 32 * quarter + lane, i = row >> 1;
+        const bool even = (row & 1) == 0;
+        long long sr = 0;
+        for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+            const int t = task % g.T, f0 = (task / g.T) * rch;
+            const int nr = min(rch, g.F - f0);
+            for (int j = 0; j < nst; ++j) {
+                if (!((j % sub) == sub - 1 || j == nst - 1)) continue;
+                const int q = (int)(sr & 1);
+                const bool first = j < sub, last_sub = j == nst - 1;
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_ab(accf0 + 8 * q, (uint32_t)((sr >> 1) & 1), abort_flag);
+                __syncwarp();
+                if (*abort_flag || !ok) goto done;
+                tc_fence_after();
+                for (int r = 0; r < nr; ++r) {
+                    for (int c0 = 0; c0 < L.npad; c0 += 16) {
+                        float v[16], pv[16];
+                        tmem_ld16(tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(q * set_cols + r * L.npad + c0), v);
 #pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            const int jn = c0 / 2 + jj;
-                            if (jn > i && jn < g.A) {
-                                const size_t o = (ft * g.B + pair_idx(i, jn, g.A)) * 2;
-                                vis[o] = (v[2 * jj] + pv[2 * jj + 1]) * inv;
-                                vis[o + 1] = (pv[2 * jj] - v[2 * jj + 1]) * inv;
+                        for (int qq = 0; qq < 16; ++qq) pv[qq] = __shfl_xor_sync(0xffffffffu, v[qq], 1);
+                        if (even && i < g.A) {
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                const int jn = c0 / 2 + jj;
+                                if (jn > i && jn < g.A) {
+                                    // each (channel, pair) has one owner thread: no synchronisation
+                                    const int b = pair_idx(i, jn, g.A);
+                                    float *o = vpart + ((size_t)r * g.B + b) * 2;
+                                    float re = v[2 * jj] + pv[2 * jj + 1];
+                                    float im = pv[2 * jj] - v[2 * jj + 1];
+                                    if (!first) { re += o[0]; im += o[1]; }
+                                    if (last_sub) {
+                                        const float inv = ET == 1 ? 1.f / chan_scale[f0 + r] : 1.f;
+                                        const size_t go = (((size_t)(f0 + r) * g.T + t) * g.B + b) * 2;
+                                        vis[go] = re * inv;
+                                        vis[go + 1] = im * inv;
+                                    } else {
+                                        o[0] = re;
+                                        o[1] = im;
+                                    }
+                                }
                             }
                         }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * q);
+                ++sr;
             }
         }
-        tc_fence_before();
-        __syncthreads();
     }
-    if (aborted) {
-        if (tid == 0) {
-            atomicExch(g.status, (int)FM_ERR_TIMEOUT);
-            if (last_s >= 0) mbar_wait(bar0 + 8 * last_s, (uint32_t)(last_use & 1));   // drain own MMAs (bounded)
-        }
-        __syncthreads();
-    }
-    if (warp == 0) {
+done:
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicExch(g.status, (int)FM_ERR_TIMEOUT);
+    if (warp == FWD_MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tmem_d, (uint32_t)L.ncols);
     }
 }
 
 // ------------------------------------------------------------------ adjoint kernel
+// One task per (channel, LST): the residual-weight tile B = Chat (built once) stays in
+// shared memory while 128-pixel chunks stream through a double-buffered A tile (rows =
+// pixels, K = interleaved Re/Im phasors of the antennas); D = A B^T lands in a TMEM
+// double buffer and the epilogue of chunk c-1 (wbar_p = A_p dOmega sum_i Re(conj(E_i) Y_i)/2)
+// overlaps the MMAs of chunk c.  wbar[f][t][p] is summed over t by k_wbar_reduce.
 struct AdjLayout {
     int npad, katoms, ksteps, ncols;
-    uint32_t a_bytes, b_bytes, buf_bytes;     // per hi (or lo) tile; buffer = [A_hi A_lo B_hi B_lo]
+    uint32_t a_bytes, b_bytes;        // one hi (or lo) tile
+    uint32_t abuf_bytes;              // A buffer (hi + lo)
+    uint32_t b_off;                   // offset of the B tiles (after the two A buffers)
+    uint32_t tail_off;                // barriers, TMEM slot, scale, omega
 };
 
 template <int ET, bool X3>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restrict__ xbar)
+k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restrict__ wbar)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t bar0 = base + 2 * L.buf_bytes;                 // 2 mbarriers
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 2 * L.buf_bytes + 16);
-    float *sscale = reinterpret_cast<float *>(gbase + 2 * L.buf_bytes + 32);   // [2] B-operand scale per buffer
-    float *sred = sscale + 2;                                                     // [8] warp maxima
-    float *som = reinterpret_cast<float *>(gbase + 2 * L.buf_bytes + 128);       // [2B] omega of this (f, t)
+    const uint32_t bar0 = base + L.tail_off;                      // 2 mbarriers
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + L.tail_off + 16);
+    float *sscale = reinterpret_cast<float *>(gbase + L.tail_off + 32);
+    float *sred = sscale + 2;                                       // [8]
+    float *som = reinterpret_cast<float *>(gbase + L.tail_off + 128);   // [2B]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int kused = 2 * g.A;
-    const int ntl = X3 ? 2 : 1;
     const uint32_t a_atom = 128u * 128u, b_atom = (uint32_t)L.npad * 128u;
+    uint8_t *bt_hi = gbase + L.b_off, *bt_lo = bt_hi + L.b_bytes;
 
-    for (uint32_t e = tid; e < 2 * L.buf_bytes / 16; e += TC_THREADS)
+    for (uint32_t e = tid; e < L.tail_off / 16; e += TC_THREADS)
         reinterpret_cast<uint4 *>(gbase)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         mbar_init(bar0, 1);
@@ -493,24 +616,25 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
     tc_fence_after();
     const uint32_t tmem0 = *tmem_slot;
     const uint32_t idesc = idesc_f16(128, L.npad, Elem<ET>::kFmt);
-    const int ntile = (g.npix + 127) / 128;
-    const int ntask = g.F * ntile;
+    const int nchk = (g.npix + 127) / 128;
+    const int ntask = g.F * g.T;
     const int nchunk = (kused + 7) / 8;            // 16-byte chunks of K actually used
     const int half = (nchunk + 1) / 2;             // A-tile chunks per thread (two threads per pixel row)
+    const int row = tid & 127, hsel = tid >> 7;
     long long gi = 0;
     bool aborted = false;
-    long long pending = -1;
     long long last_issued = -1;
 
-    auto epilogue = [&](long long it, int f, int t, int p0, float &xacc) -> bool {
+    // epilogue of chunk iteration `it`: wbar for its 128 pixels
+    auto epilogue = [&](long long it, int ft, int f, int t, int p0) -> bool {
         const int b = (int)(it & 1);
         bool bad = false;
         if (tid == 0) bad = !mbar_wait(bar0 + 8 * b, (uint32_t)((it >> 1) & 1));
         if (__syncthreads_or(bad)) return false;
         if (warp < 4) {
             tc_fence_after();
-            const int row = 32 * warp + lane, p = p0 + row;
-            const uint8_t *ahi = gbase + (size_t)b * L.buf_bytes, *alo = ahi + L.a_bytes;
+            const int r = 32 * warp + lane, p = p0 + r;
+            const uint8_t *ahi = gbase + (size_t)b * L.abuf_bytes, *alo = ahi + L.a_bytes;
             float acc = 0.f;
             for (int c0 = 0; c0 < L.npad; c0 += 16) {
                 float v[16];
@@ -519,7 +643,7 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
                 for (int h = 0; h < 2; ++h) {
                     const int kc = c0 / 8 + h;
                     if (kc >= nchunk) break;
-                    const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(row, kc & 7);
+                    const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(r, kc & 7);
                     const uint4 hv = *reinterpret_cast<const uint4 *>(ahi + off);
                     const uint4 lv = X3 ? *reinterpret_cast<const uint4 *>(alo + off) : make_uint4(0, 0, 0, 0);
                     const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
@@ -530,106 +654,112 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
                     }
                 }
             }
-            if (p < g.npix) xacc += pixel_w(g, f, t, p) * (0.5f / sscale[b]) * acc;
+            if (p < g.npix) wbar[(size_t)ft * g.npix + p] = pixel_w(g, f, t, p) * (0.5f / sscale[0]) * acc;
         }
         tc_fence_before();
         __syncthreads();
         return true;
     };
 
-    for (int task = blockIdx.x; task < ntask && !aborted; task += gridDim.x) {
-        const int f = task / ntile, p0 = (task % ntile) * 128;
-        float xacc = 0.f;
-        for (int t = 0; t < g.T; ++t, ++gi) {
+    for (int ft = blockIdx.x; ft < ntask && !aborted; ft += gridDim.x) {
+        const int f = ft / g.T, t = ft % g.T;
+        // omega of (f, t) into shared memory and its largest component
+        const float *om = omega + (size_t)ft * g.B * 2;
+        float mx = 0.f;
+        for (int e = tid; e < 2 * g.B; e += TC_THREADS) {
+            const float v = om[e];
+            som[e] = v;
+            mx = fmaxf(mx, fabsf(v));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) sred[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            float m = 0.f;
+            for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, sred[w]);
+            float sc = 1.f;
+            if (ET == 1 && m > 0.f && isfinite(m)) {
+                int e;
+                frexpf(m, &e);
+                sc = ldexpf(1.f, 14 - e);
+            }
+            sscale[0] = sc;
+        }
+        __syncthreads();
+        {   // B tile: row n = 2i (Re Y_i) or 2i+1 (Im Y_i); C_ij = omega_ij (i<j), conj(omega_ji) (i>j)
+            const float sc = sscale[0];
+            for (int item = tid; item < kused * nchunk; item += TC_THREADS) {
+                const int n = item / nchunk, kc = item % nchunk, i = n >> 1;
+                const bool im_row = n & 1;
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jx = 4 * kc + q;
+                    float cr = 0.f, ci = 0.f;
+                    if (jx < g.A && jx != i) {
+                        if (i < jx) { const int bb = pair_idx(i, jx, g.A); cr = som[2 * bb]; ci = som[2 * bb + 1]; }
+                        else { const int bb = pair_idx(jx, i, g.A); cr = som[2 * bb]; ci = -som[2 * bb + 1]; }
+                    }
+                    cr *= sc;
+                    ci *= sc;
+                    v[2 * q] = im_row ? ci : cr;          // Re Y = Cr Er - Ci Ei ; Im Y = Ci Er + Cr Ei
+                    v[2 * q + 1] = im_row ? cr : -ci;
+                }
+                uint4 hh, ll;
+                Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
+                Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
+                const uint32_t off = (uint32_t)(kc >> 3) * b_atom + sw128_off(n, kc & 7);
+                *reinterpret_cast<uint4 *>(bt_hi + off) = hh;
+                if (X3) *reinterpret_cast<uint4 *>(bt_lo + off) = ll;
+            }
+        }
+        // stream the pixel chunks
+        float s6n[6];
+        {
+            const int p = row;
+            if (p < g.npix) load_s6(g, t, p, s6n);
+        }
+        long long pending = -1;
+        int pending_p0 = 0;
+        for (int c = 0; c < nchk; ++c, ++gi) {
             const int b = (int)(gi & 1);
-            // omega of (f, t) into shared memory and its largest component
-            const float *om = omega + (size_t)(f * g.T + t) * g.B * 2;
-            float mx = 0.f;
-            for (int e = tid; e < 2 * g.B; e += TC_THREADS) {
-                const float v = om[e];
-                som[e] = v;
-                mx = fmaxf(mx, fabsf(v));
-            }
+            const int p0 = c * 128, p = p0 + row;
+            float s6[6];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) sred[warp] = mx;
-            __syncthreads();
-            if (tid == 0) {
-                float m = 0.f;
-                for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, sred[w]);
-                float sc = 1.f;
-                if (ET == 1 && m > 0.f && isfinite(m)) {
-                    int e;
-                    frexpf(m, &e);
-                    sc = ldexpf(1.f, 14 - e);
-                }
-                sscale[b] = sc;
-            }
-            uint8_t *ahi = gbase + (size_t)b * L.buf_bytes, *alo = ahi + L.a_bytes;
-            uint8_t *bhi = ahi + ntl * L.a_bytes, *blo = bhi + L.b_bytes;
-            {   // A tile: row = pixel, chunk kc = (Re E_j, Im E_j) for j = 4kc .. 4kc+3
-                const int row = tid & 127, hsel = tid >> 7, p = p0 + row;
-                float s6[6];
-                const bool vp = p < g.npix;
-                if (vp) load_s6(g, t, p, s6);
-                const int kc0 = hsel * half, kc1 = min(nchunk, kc0 + half);
-                for (int kc = kc0; kc < kc1; ++kc) {
-                    float v[8];
+            for (int z = 0; z < 6; ++z) s6[z] = s6n[z];
+            if (c + 1 < nchk && p + 128 < g.npix) load_s6(g, t, p + 128, s6n);   // prefetch next chunk
+            uint8_t *ahi = gbase + (size_t)b * L.abuf_bytes, *alo = ahi + L.a_bytes;
+            const bool vp = p < g.npix;
+            const int kc0 = hsel * half, kc1 = min(nchunk, kc0 + half);
+            for (int kc = kc0; kc < kc1; ++kc) {
+                float v[8];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jx = 4 * kc + q;
-                        float er = 0.f, ei = 0.f;
-                        if (vp && jx < g.A) {
-                            float k6[6];
+                for (int q = 0; q < 4; ++q) {
+                    const int jx = 4 * kc + q;
+                    float er = 0.f, ei = 0.f;
+                    if (vp && jx < g.A) {
+                        float k6[6];
 #pragma unroll
-                            for (int z = 0; z < 6; ++z) k6[z] = g.kap32[((size_t)f * g.A + jx) * 6 + z];
-                            phasor_of(phase_frac(k6, s6), er, ei);
-                        }
-                        v[2 * q] = er;
-                        v[2 * q + 1] = ei;
+                        for (int z = 0; z < 6; ++z) k6[z] = g.kap32[((size_t)f * g.A + jx) * 6 + z];
+                        phasor_of(phase_frac(k6, s6), er, ei);
                     }
-                    uint4 hh, ll;
-                    Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
-                    Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
-                    const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(row, kc & 7);
-                    *reinterpret_cast<uint4 *>(ahi + off) = hh;
-                    if (X3) *reinterpret_cast<uint4 *>(alo + off) = ll;
+                    v[2 * q] = er;
+                    v[2 * q + 1] = ei;
                 }
-            }
-            __syncthreads();   // som and sscale visible
-            {   // B tile: row n = 2i (Re Y_i) or 2i+1 (Im Y_i); C_ij = omega_ij (i<j), conj(omega_ji) (i>j)
-                const float sc = sscale[b];
-                for (int item = tid; item < kused * nchunk; item += TC_THREADS) {
-                    const int n = item / nchunk, kc = item % nchunk, i = n >> 1;
-                    const bool im_row = n & 1;
-                    float v[8];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jx = 4 * kc + q;
-                        float cr = 0.f, ci = 0.f;
-                        if (jx < g.A && jx != i) {
-                            if (i < jx) { const int bb = pair_idx(i, jx, g.A); cr = som[2 * bb]; ci = som[2 * bb + 1]; }
-                            else { const int bb = pair_idx(jx, i, g.A); cr = som[2 * bb]; ci = -som[2 * bb + 1]; }
-                        }
-                        cr *= sc;
-                        ci *= sc;
-                        v[2 * q] = im_row ? ci : cr;          // Re Y = Cr Er - Ci Ei ; Im Y = Ci Er + Cr Ei
-                        v[2 * q + 1] = im_row ? cr : -ci;
-                    }
-                    uint4 hh, ll;
-                    Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
-                    Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
-                    const uint32_t off = (uint32_t)(kc >> 3) * b_atom + sw128_off(n, kc & 7);
-                    *reinterpret_cast<uint4 *>(bhi + off) = hh;
-                    if (X3) *reinterpret_cast<uint4 *>(blo + off) = ll;
-                }
+                uint4 hh, ll;
+                Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
+                Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
+                const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(row, kc & 7);
+                *reinterpret_cast<uint4 *>(ahi + off) = hh;
+                if (X3) *reinterpret_cast<uint4 *>(alo + off) = ll;
             }
             fence_async_smem();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                const uint32_t sa_hi = base + (uint32_t)b * L.buf_bytes, sa_lo = sa_hi + L.a_bytes;
-                const uint32_t sb_hi = sa_hi + (uint32_t)ntl * L.a_bytes, sb_lo = sb_hi + L.b_bytes;
+                const uint32_t sa_hi = base + (uint32_t)b * L.abuf_bytes, sa_lo = sa_hi + L.a_bytes;
+                const uint32_t sb_hi = base + L.b_off, sb_lo = sb_hi + L.b_bytes;
                 const uint32_t dcol = tmem0 + (uint32_t)(b * L.npad);
                 for (int kk = 0; kk < L.ksteps; ++kk) {
                     const uint32_t oa = (uint32_t)(kk >> 2) * a_atom + 32u * (kk & 3);
@@ -645,17 +775,13 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
             }
             last_issued = gi;
             if (pending >= 0) {
-                if (!epilogue(pending, f, t - 1, p0, xacc)) { aborted = true; break; }
+                if (!epilogue(pending, ft, f, t, pending_p0)) { aborted = true; break; }
             }
             pending = gi;
+            pending_p0 = p0;
         }
         if (aborted) break;
-        if (!epilogue(pending, f, g.T - 1, p0, xacc)) { aborted = true; break; }
-        pending = -1;
-        if (warp < 4) {
-            const int p = p0 + 32 * warp + lane;
-            if (p < g.npix) xbar[(size_t)f * g.npix + p] = xacc;
-        }
+        if (!epilogue(pending, ft, f, t, pending_p0)) { aborted = true; break; }
     }
     if (aborted) {
         if (tid == 0) {
@@ -667,6 +793,19 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem0, (uint32_t)L.ncols);
+    }
+}
+
+// xbar[f][p] = sum_t wbar[f][t][p] in a fixed order
+__global__ void k_wbar_reduce(int F, int T, int npix, const float *__restrict__ wbar, float *__restrict__ xbar)
+{
+    const long long n = (long long)F * npix;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(e / npix), p = (int)(e % npix);
+        const float *w = wbar + (size_t)f * T * npix + p;
+        float s = 0.f;
+        for (int t = 0; t < T; ++t) s += w[(size_t)t * npix];
+        xbar[e] = s;
     }
 }
 
@@ -686,15 +825,15 @@ static int num_sms()
 }  // namespace
 
 template <int ET, bool X3>
-static fm_status vis_tc_launch(Ctx &c, const FwdLayout &L, int rch, size_t smem, int grid, const float *x, float *vis,
-                               cudaStream_t st)
+static fm_status vis_tc_launch(Ctx &c, const FwdLayout &L, int rch, int sub, size_t smem, int grid, const float *x,
+                               float *vis, cudaStream_t st)
 {
     if (c.A <= 40) {
         FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vis_tc<ET, X3, 5><<<grid, TC_THREADS, smem, st>>>(c.g, L, rch, x, c.tc_scale, vis);
+        k_vis_tc<ET, X3, 5><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
     } else {
         FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vis_tc<ET, X3, 8><<<grid, TC_THREADS, smem, st>>>(c.g, L, rch, x, c.tc_scale, vis);
+        k_vis_tc<ET, X3, 8><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
     }
     FM_CK_LAUNCH();
     return FM_OK;
@@ -710,42 +849,57 @@ fm_status launch_vis_tc(Ctx &c, const float *x, float *vis, cudaStream_t st)
     const bool f16 = c.prec == FM_PREC_FP16X1 || c.prec == FM_PREC_FP16X3;
     FwdLayout L;
     L.npad = ((2 * c.A + 15) / 16) * 16;
-    // channels per task (frequency recurrence): enough tasks to fill the GPU, TMEM for rch accumulators
+    // channels per task (frequency recurrence), two TMEM accumulator sets of rch x npad
+    // columns, enough tasks to fill the GPU
     int rch = 1;
     if (c.g.uniform_freq) {
         rch = 4;
-        while (rch > 1 && (rch * L.npad > 512 || (long long)c.T * ((c.F + rch - 1) / rch) < 4LL * num_sms())) --rch;
+        while (rch > 1 && (2 * rch * L.npad > 512 || (long long)c.T * ((c.F + rch - 1) / rch) < 4LL * num_sms())) --rch;
+        if (const char *e = getenv("FM_TC_CHANNELS_PER_TASK")) {
+            const int v = atoi(e);
+            if (v >= 1) rch = v;
+            while (rch > 1 && 2 * rch * L.npad > 512) --rch;
+        }
         if (rch > c.F) rch = c.F;
     }
     L.ncols = 32;
-    while (L.ncols < rch * L.npad) L.ncols *= 2;
+    while (L.ncols < 2 * rch * L.npad) L.ncols *= 2;
     L.a_bytes = 128 * 128;
     L.b_bytes = (uint32_t)L.npad * 128;
     L.stage_bytes = (x3 ? 2u : 1u) * (L.a_bytes + L.b_bytes);
-    const size_t budget = 225 * 1024;
-    L.nstage = (int)((budget - 1024 - 64) / L.stage_bytes);
+    const size_t vbytes = ((size_t)rch * c.B * 2 * 4 + 15) / 16 * 16;
+    const size_t fixed = 1024 + vbytes + 16 * 4 + 64 + 64;
+    const size_t budget = 226 * 1024;
+    if (fixed >= budget) return FM_ERR_UNSUPPORTED;
+    L.nstage = (int)((budget - fixed) / L.stage_bytes);
     if (L.nstage > 4) L.nstage = 4;
-    if (L.nstage < 2) return FM_ERR_UNSUPPORTED;
-    const size_t smem = 1024 + (size_t)L.nstage * L.stage_bytes + 8 * L.nstage + 16;
+    if (L.nstage < 2) { set_error("forward tiles exceed shared memory"); return FM_ERR_UNSUPPORTED; }
+    const size_t smem = 1024 + (size_t)L.nstage * L.stage_bytes + vbytes + 16 * L.nstage + 32 + 16;
     const int ntask = c.T * ((c.F + rch - 1) / rch);
     int grid = num_sms();
     if (grid > ntask) grid = ntask;
+    // stages per TMEM accumulation chain (1024 pixels): bounds the accumulation error
+    int sub = 16;
+    if (const char *e = getenv("FM_TC_STAGES_PER_PARTIAL")) {
+        const int v = atoi(e);
+        if (v >= 1) sub = v;
+    }
     if (f16) {
         k_chan_scale<<<c.F, 256, 0, st>>>(c.npix, x, c.domega_max, c.tc_scale);
         FM_CK_LAUNCH();
-        return x3 ? vis_tc_launch<1, true>(c, L, rch, smem, grid, x, vis, st)
-                  : vis_tc_launch<1, false>(c, L, rch, smem, grid, x, vis, st);
+        return x3 ? vis_tc_launch<1, true>(c, L, rch, sub, smem, grid, x, vis, st)
+                  : vis_tc_launch<1, false>(c, L, rch, sub, smem, grid, x, vis, st);
     }
-    return x3 ? vis_tc_launch<0, true>(c, L, rch, smem, grid, x, vis, st)
-              : vis_tc_launch<0, false>(c, L, rch, smem, grid, x, vis, st);
+    return x3 ? vis_tc_launch<0, true>(c, L, rch, sub, smem, grid, x, vis, st)
+              : vis_tc_launch<0, false>(c, L, rch, sub, smem, grid, x, vis, st);
 }
 
 template <int ET, bool X3>
-static fm_status adj_tc_launch(Ctx &c, const AdjLayout &L, size_t smem, int grid, const float *omega, float *xbar,
+static fm_status adj_tc_launch(Ctx &c, const AdjLayout &L, size_t smem, int grid, const float *omega, float *wbar,
                                cudaStream_t st)
 {
     FM_CK(cudaFuncSetAttribute(k_adj_tc<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_adj_tc<ET, X3><<<grid, TC_THREADS, smem, st>>>(c.g, L, omega, xbar);
+    k_adj_tc<ET, X3><<<grid, TC_THREADS, smem, st>>>(c.g, L, omega, wbar);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -755,6 +909,15 @@ fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_
     if (2 * c.A > 128) {
         set_error("tensor-core adjoint supports at most 64 antennas in this build");
         return FM_ERR_UNSUPPORTED;
+    }
+    if (!c.tc_wbar) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(float) * (size_t)c.F * c.T * c.npix) != cudaSuccess) {
+            set_error("cudaMalloc of the adjoint pixel-weight buffer failed");
+            return FM_ERR_ALLOC;
+        }
+        c.allocs.push_back(p);
+        c.tc_wbar = (float *)p;
     }
     const bool x3 = c.prec == FM_PREC_BF16X3 || c.prec == FM_PREC_FP16X3;
     const bool f16 = c.prec == FM_PREC_FP16X1 || c.prec == FM_PREC_FP16X3;
@@ -766,15 +929,25 @@ fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_
     while (L.ncols < 2 * L.npad) L.ncols *= 2;
     L.a_bytes = (uint32_t)L.katoms * 128u * 128u;
     L.b_bytes = (uint32_t)L.katoms * (uint32_t)L.npad * 128u;
-    L.buf_bytes = (x3 ? 2u : 1u) * (L.a_bytes + L.b_bytes);
-    const size_t smem = 1024 + 2 * (size_t)L.buf_bytes + 128 + 2 * sizeof(float) * (size_t)c.B;
+    L.abuf_bytes = (x3 ? 2u : 1u) * L.a_bytes;
+    L.b_off = 2 * L.abuf_bytes;
+    L.tail_off = L.b_off + (x3 ? 2u : 1u) * L.b_bytes;
+    const size_t smem = 1024 + (size_t)L.tail_off + 128 + 2 * sizeof(float) * (size_t)c.B;
     if (smem > 227 * 1024) { set_error("adjoint tiles exceed shared memory"); return FM_ERR_UNSUPPORTED; }
-    const int ntask = c.F * ((c.npix + 127) / 128);
+    const int ntask = c.F * c.T;
     int grid = num_sms();
     if (grid > ntask) grid = ntask;
+    fm_status s;
     if (f16)
-        return x3 ? adj_tc_launch<1, true>(c, L, smem, grid, omega, xbar, st) : adj_tc_launch<1, false>(c, L, smem, grid, omega, xbar, st);
-    return x3 ? adj_tc_launch<0, true>(c, L, smem, grid, omega, xbar, st) : adj_tc_launch<0, false>(c, L, smem, grid, omega, xbar, st);
+        s = x3 ? adj_tc_launch<1, true>(c, L, smem, grid, omega, c.tc_wbar, st)
+               : adj_tc_launch<1, false>(c, L, smem, grid, omega, c.tc_wbar, st);
+    else
+        s = x3 ? adj_tc_launch<0, true>(c, L, smem, grid, omega, c.tc_wbar, st)
+               : adj_tc_launch<0, false>(c, L, smem, grid, omega, c.tc_wbar, st);
+    if (s != FM_OK) return s;
+    k_wbar_reduce<<<1024, 256, 0, st>>>(c.F, c.T, c.npix, c.tc_wbar, xbar);
+    FM_CK_LAUNCH();
+    return FM_OK;
 }
 
 }  // namespace fm

@@ -165,6 +165,10 @@ def config(name: str) -> Problem:
     if name == "mid":
         # 19 antennas (tensor-core tile padding), ragged pixel tail
         return drift_scan_problem("mid", 3, 4, 145e6, 155e6, 3, 24, 70, 16, 16, 50, 13)
+    if name == "ant37":
+        # the cfg1 array (37 antennas: two 64-wide K atoms in the adjoint tiles) on a small
+        # grid, 8 equally spaced channels (frequency-recurrence groups), ragged pixel tail
+        return drift_scan_problem("ant37", 4, 8, 146e6, 153e6, 3, 20, 58, 16, 8, 50, 17)
     raise KeyError(name)
 
 

@@ -1,7 +1,13 @@
 """Parity at the full benchmark size (cfg1: 37 antennas, 64 channels, 60 LSTs, 24,576
 pixels, 16,384 modes per channel) in the launch configuration bench.py times: sampled
 visibilities computed one by one by the oracle, and the complete sky gradient of one
-channel (all LSTs) against the oracle's per-baseline adjoint."""
+channel (all LSTs) against the oracle's per-baseline adjoint.
+
+The gradient is compared away from the truth (sky modes perturbed by 1 % of the channel
+rms).  At the truth the residual is pure noise, the true gradient is its incoherent
+projection, and any model error eps adds a coherent bias of relative size about
+eps |m|/sigma sqrt(N_vis) -- at cfg1 that is percent level even for FP32 -- so the
+relative metric there measures the noise, not the kernels."""
 import numpy as np
 import pytest
 
@@ -11,7 +17,16 @@ from gpu_cases import as_complex, quant, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL_VIS = {"fp32": 1e-5, "fp16x3": 1e-5, "bf16x3": 2e-5}
-TOL_GRAD = {"fp32": 1e-4, "fp16x3": 3e-4, "bf16x3": 3e-4}
+# split modes: the gradient error is about 100 x the visibility error (|m| / |m - d| at a
+# 1 % perturbation); 3.5e-6 on V at this size gives ~4e-4
+TOL_GRAD = {"fp32": 1e-4, "fp16x3": 1e-3, "bf16x3": 1e-3}
+
+
+def _perturbed(o, theta, frac, seed):
+    a, _ = o.split(theta)
+    sc = np.zeros(o.n_par)
+    sc[: o.n_sky] = np.repeat(np.sqrt(np.mean(a ** 2, axis=1)), o.nk)
+    return theta + frac * sc * np.random.default_rng(seed).standard_normal(o.n_par)
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +61,7 @@ def test_cfg1_sampled_visibilities(cfg1, prec):
     assert rel_l2(np.array(got), np.array(want)) < TOL_VIS[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp16x3"])
+@pytest.mark.parametrize("prec", ["fp16x3", "fp32"])
 def test_cfg1_one_channel_gradient(cfg1, prec):
     import torch
     from paper_2504_07090_gb300 import fm
@@ -64,7 +79,8 @@ def test_cfg1_one_channel_gradient(cfg1, prec):
     d_full = quant(prec, d_full)
     h = fm.ForwardModel(p, prec, sigma=sigma)
     h.set_data(torch.tensor(np.stack([d_full.real, d_full.imag], -1), dtype=torch.float32, device="cuda").contiguous())
-    _, grad = h.chi2_grad(torch.tensor(th, dtype=torch.float32, device="cuda"))
-    chi2, U, g = o.chi2_grad(th, d_full, fts=[(f0, t) for t in range(p.n_lst)])
+    th_eval = quant(prec, _perturbed(o, th, 0.01, 6))
+    _, grad = h.chi2_grad(torch.tensor(th_eval, dtype=torch.float32, device="cuda"))
+    chi2, U, g = o.chi2_grad(th_eval, d_full, fts=[(f0, t) for t in range(p.n_lst)])
     sl = slice(f0 * o.nk, (f0 + 1) * o.nk)
     assert rel_l2(grad.cpu().numpy()[sl], g[sl]) < TOL_GRAD[prec]

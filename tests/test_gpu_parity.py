@@ -7,7 +7,7 @@ Tolerances (visibilities / gradients and HVPs):
   fp16x3  1e-5  / 3e-4
   bf16x3  2e-5  / 3e-4
   fp16x1  2e-3  / 5e-3
-  bf16x1  1e-2  / 2e-2
+  bf16x1  1e-2  / 1e-1
 The split-precision operand rounding (2^-9 BF16, 2^-12 FP16 per product; about 2^-17 and
 2^-22 after the hi/lo split) is amplified by the cancellation of the fringe sum, and the
 gradient amplifies visibility errors by |m| / |m - d| (about 100 at a noise level of 1 % of
@@ -21,7 +21,7 @@ from gpu_cases import as_complex, handle, make_case, perturbed, quant, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL_VIS = {"fp64": 1e-10, "fp32": 1e-5, "bf16x1": 1e-2, "bf16x3": 2e-5, "fp16x1": 2e-3, "fp16x3": 1e-5}
-TOL_GRAD = {"fp64": 1e-10, "fp32": 1e-4, "bf16x1": 2e-2, "bf16x3": 3e-4, "fp16x1": 5e-3, "fp16x3": 3e-4}
+TOL_GRAD = {"fp64": 1e-10, "fp32": 1e-4, "bf16x1": 1e-1, "bf16x3": 3e-4, "fp16x1": 5e-3, "fp16x3": 3e-4}
 CASES = ["tiny", "small", "mid"]
 PRECS = ["fp64", "fp32", "bf16x1", "bf16x3", "fp16x1", "fp16x3"]
 
@@ -121,3 +121,22 @@ def test_sky_pixels_match_oracle(prec):
     a, _ = o.split(th)
     got = h.sky_pixels(_t(th, h)).cpu().numpy().reshape(p.n_freq, -1)
     assert rel_l2(got, o.sky(a)) < (1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("rch,sub", [("1", "32"), ("3", "4"), ("4", "7")])
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3", "fp16x1"])
+def test_37_antennas_with_channel_recurrence_groups(prec, rch, sub, monkeypatch):
+    # the cfg1 array on a small grid: two K atoms in the adjoint tiles, the frequency
+    # recurrence forced to groups of 1, 3 (ragged last group) and 4 channels, and the
+    # accumulation restarted every 4 or 7 stages (several partials, ragged last one)
+    monkeypatch.setenv("FM_TC_CHANNELS_PER_TASK", rch)
+    monkeypatch.setenv("FM_TC_STAGES_PER_PARTIAL", sub)
+    p, o, th, d, mu, lam = make_case("ant37")
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 12))
+    got = as_complex(h.forward(_t(th, h)))
+    assert rel_l2(got, o.model(th)) < TOL_VIS[prec]
+    chi2, U, g = o.chi2_grad(th, d, mu, lam)
+    _, grad = h.chi2_grad(_t(th, h))
+    assert rel_l2(grad.cpu().numpy(), g) < TOL_GRAD[prec]
