@@ -190,6 +190,10 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
         FM_CK(cudaMemcpy(ddk, dk.data(), sizeof(float) * dk.size(), cudaMemcpyHostToDevice));
         g.dkap32 = ddk;
         g.uniform_freq = uni ? 1 : 0;
+        bool flat = true;
+        for (int i = 0; i < c->A; ++i)
+            if (c->ant[3 * i + 2] != 0.0) flat = false;
+        g.flat_array = flat ? 1 : 0;
     }
 
     size_t rs = c->rsz;

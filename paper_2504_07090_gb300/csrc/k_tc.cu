@@ -29,7 +29,6 @@
 namespace fm {
 namespace {
 
-constexpr int TC_THREADS = 256;
 constexpr int KST = 64;                               // pixels per stage (one swizzle row of bf16)
 constexpr long long WAIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
 
@@ -38,23 +37,6 @@ __device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uin
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
@@ -82,11 +64,6 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
             return false;
         }
     }
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -148,12 +125,6 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 // Byte offset of the 16-byte chunk `chunk` (0..7) of row `row` in a 128B-swizzled tile.
 __device__ __forceinline__ uint32_t sw128_off(int row, int chunk)
 {
@@ -201,11 +172,12 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, uint32_t fmt)
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+template <int NC = 3>
 __device__ __forceinline__ float phase_frac(const float *kap, const float *s)
 {
     float accf = 0.f, acce = 0.f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NC; ++c) {
         float kh = kap[2 * c], kl = kap[2 * c + 1], sh = s[2 * c], sl = s[2 * c + 1];
         float p = __fmul_rn(kh, sh);
         float e = __fmaf_rn(kh, sh, -p);
@@ -234,11 +206,14 @@ __device__ __forceinline__ void sincos_turns(float r, float &s, float &c)
     c = (qi == 0) ? cp : (qi == 1) ? -sp : (qi == 2) ? -cp : sp;
 }
 
-// E = exp(-2 pi i frac)
+// E = exp(-2 pi i frac); FAST uses the hardware approximation (abs. error ~4e-7), for
+// the single-product modes whose 2^-9 / 2^-12 operand rounding dominates anyway
+template <bool FAST = false>
 __device__ __forceinline__ void phasor_of(float fr, float &er, float &ei)
 {
     float sn, cs;
-    sincos_turns(fr, sn, cs);
+    if (FAST) __sincosf(6.28318530717958647692f * fr, &sn, &cs);
+    else sincos_turns(fr, sn, cs);
     er = cs;
     ei = -sn;
 }
@@ -297,9 +272,9 @@ __global__ void __launch_bounds__(256) k_chan_scale(int npix, const float *__res
 // Producers: lane l of every warp owns pixels 2l, 2l+1 of the 64-pixel stage; warp w
 // generates antennas w, w+8, ...  Each thread writes 32-bit words (2 pixels) of rows
 // 2i (Re) and 2i+1 (Im) of A_op = W Ahat and B_op = Ahat, hi and (x3) lo parts.
-// Warp-specialised forward: warps 0-7 produce operand stages, warp 12 (one lane) issues
-// the MMAs, warps 8-11 drain the TMEM accumulators.  Hand-offs use mbarriers only:
-//   full[s]     8 producer-warp arrivals -> stage s holds operands
+// Warp-specialised forward: warps 0-15 produce operand stages, warp 20 (one lane) issues
+// the MMAs, warps 16-19 drain the TMEM accumulators.  Hand-offs use mbarriers only:
+//   full[s]     16 producer-warp arrivals -> stage s holds operands
 //   empty[s]    tcgen05.commit after the MMAs that read stage s
 //   accfull[q]  tcgen05.commit after the last MMA of a pixel sub-range into set q
 //   accempty[q] 4 epilogue-warp arrivals after set q was read
@@ -307,10 +282,9 @@ __global__ void __launch_bounds__(256) k_chan_scale(int npix, const float *__res
 // of the task's frequency-recurrence group.  Accumulator set q = sub-range parity, so
 // the epilogue of one sub-range overlaps the MMAs of the next; partial visibilities
 // are summed in FP32 in shared memory and written once per task.
-constexpr int FWD_PROD_WARPS = 8;
-constexpr int FWD_EPI_WARP0 = 8;
-constexpr int FWD_MMA_WARP = 12;
-constexpr int FWD_THREADS = 13 * 32;
+constexpr int FWD_PROD_WARPS = 16;
+constexpr int FWD_MMA_WARP = 20;
+constexpr int FWD_THREADS = 21 * 32;
 
 template <int ET, bool X3, int KMAX>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
@@ -398,12 +372,21 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
 #pragma unroll
                             for (int q = 0; q < 6; ++q) k6[q] = g.kap32[((size_t)f * g.A + i) * 6 + q];
                             er[k][0] = ei[k][0] = er[k][1] = ei[k][1] = 0.f;
-                            if (va) phasor_of(phase_frac(k6, sa), er[k][0], ei[k][0]);
-                            if (vb) phasor_of(phase_frac(k6, sb), er[k][1], ei[k][1]);
-                            if (nr > 1) {
-                                const float d0 = g.dkap32[3 * i], d1 = g.dkap32[3 * i + 1], d2 = g.dkap32[3 * i + 2];
-                                phasor_of(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]) + d2 * (sa[4] + sa[5]), dr[k][0], di[k][0]);
-                                phasor_of(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]) + d2 * (sb[4] + sb[5]), dr[k][1], di[k][1]);
+                            const float d0 = g.dkap32[3 * i], d1 = g.dkap32[3 * i + 1], d2 = g.dkap32[3 * i + 2];
+                            if (g.flat_array) {
+                                if (va) phasor_of<!X3>(phase_frac<2>(k6, sa), er[k][0], ei[k][0]);
+                                if (vb) phasor_of<!X3>(phase_frac<2>(k6, sb), er[k][1], ei[k][1]);
+                                if (nr > 1) {
+                                    phasor_of<!X3>(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]), dr[k][0], di[k][0]);
+                                    phasor_of<!X3>(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]), dr[k][1], di[k][1]);
+                                }
+                            } else {
+                                if (va) phasor_of<!X3>(phase_frac<3>(k6, sa), er[k][0], ei[k][0]);
+                                if (vb) phasor_of<!X3>(phase_frac<3>(k6, sb), er[k][1], ei[k][1]);
+                                if (nr > 1) {
+                                    phasor_of<!X3>(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]) + d2 * (sa[4] + sa[5]), dr[k][0], di[k][0]);
+                                    phasor_of<!X3>(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]) + d2 * (sb[4] + sb[5]), dr[k][1], di[k][1]);
+                                }
                             }
                         } else {
 #pragma unroll
@@ -571,127 +554,124 @@ done:
 }
 
 // ------------------------------------------------------------------ adjoint kernel
-// One task per (channel, LST): the residual-weight tile B = Chat (built once) stays in
-// shared memory while 128-pixel chunks stream through a double-buffered A tile (rows =
-// pixels, K = interleaved Re/Im phasors of the antennas); D = A B^T lands in a TMEM
-// double buffer and the epilogue of chunk c-1 (wbar_p = A_p dOmega sum_i Re(conj(E_i) Y_i)/2)
-// overlaps the MMAs of chunk c.  wbar[f][t][p] is summed over t by k_wbar_reduce.
+// One task per (channel, LST).  Warp-specialised like the forward:
+//   producers (warps 0-15): per task, warp 0 stages omega and its FP16 scale (sready),
+//     all build the residual-weight tile B = Chat (bfull); then 128-pixel chunks of
+//     A = Ehat^T (rows = pixels, K = interleaved Re/Im phasors) go into a 2-slot ring;
+//   MMA warp (20): D(s) = A(s) B^T into TMEM slot s, commits dfull[s] and empty[s], and
+//     bempty once the task's last MMA has read B;
+//   epilogue (warps 16-19): wbar_p = A_p dOmega sum_i Re(conj(E_i) Y_i) / 2 from D(s) and
+//     the phasors still in A(s), then releases the slot (empty[s]: 1 commit + 4 warps).
+// The pixel adjoint of each (channel, LST) goes to wbar[f][t][p]; k_wbar_reduce sums t.
 struct AdjLayout {
     int npad, katoms, ksteps, ncols;
     uint32_t a_bytes, b_bytes;        // one hi (or lo) tile
-    uint32_t abuf_bytes;              // A buffer (hi + lo)
-    uint32_t b_off;                   // offset of the B tiles (after the two A buffers)
-    uint32_t tail_off;                // barriers, TMEM slot, scale, omega
+    uint32_t abuf_bytes;              // A slot (hi + lo)
+    uint32_t b_off;                   // offset of the B tiles (after the A slots)
+    uint32_t om_off;                  // omega staging [2B] floats
+    uint32_t meta_off;                // slot metadata, barriers, TMEM slot, abort flag
 };
+constexpr int ADJ_SLOTS = 2;
+constexpr int ADJ_PROD_WARPS = 16;
+constexpr int ADJ_MMA_WARP = 20;
+constexpr int ADJ_THREADS = 21 * 32;
 
 template <int ET, bool X3>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(ADJ_THREADS, 1)
 k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restrict__ wbar)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t bar0 = base + L.tail_off;                      // 2 mbarriers
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + L.tail_off + 16);
-    float *sscale = reinterpret_cast<float *>(gbase + L.tail_off + 32);
-    float *sred = sscale + 2;                                       // [8]
-    float *som = reinterpret_cast<float *>(gbase + L.tail_off + 128);   // [2B]
+    float *som = reinterpret_cast<float *>(gbase + L.om_off);
+    uint8_t *meta = gbase + L.meta_off;
+    float *slot_scale = reinterpret_cast<float *>(meta);             // [2]
+    int *slot_ft = reinterpret_cast<int *>(meta + 8);                // [2]
+    int *slot_p0 = reinterpret_cast<int *>(meta + 16);               // [2]
+    float *task_scale = reinterpret_cast<float *>(meta + 24);
+    float *wmax = reinterpret_cast<float *>(meta + 32);              // unused slot (alignment)
+    const uint32_t bar0 = base + L.meta_off + 64;
+    const uint32_t full0 = bar0, empty0 = bar0 + 16, dfull0 = bar0 + 32;
+    const uint32_t sready = bar0 + 48, bfull = bar0 + 56, bempty = bar0 + 64;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(meta + 64 + 72);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(meta + 64 + 76);
+    (void)wmax;
+
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int kused = 2 * g.A;
     const uint32_t a_atom = 128u * 128u, b_atom = (uint32_t)L.npad * 128u;
     uint8_t *bt_hi = gbase + L.b_off, *bt_lo = bt_hi + L.b_bytes;
 
-    for (uint32_t e = tid; e < L.tail_off / 16; e += TC_THREADS)
+    for (uint32_t e = tid; e < L.om_off / 16; e += ADJ_THREADS)
         reinterpret_cast<uint4 *>(gbase)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
+        for (int q = 0; q < ADJ_SLOTS; ++q) {
+            mbar_init(full0 + 8 * q, ADJ_PROD_WARPS);
+            mbar_init(empty0 + 8 * q, 1 + 4);
+            mbar_init(dfull0 + 8 * q, 1);
+        }
+        mbar_init(sready, 1);
+        mbar_init(bfull, ADJ_PROD_WARPS);
+        mbar_init(bempty, 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
+    if (warp == ADJ_MMA_WARP) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem0 = *tmem_slot;
-    const uint32_t idesc = idesc_f16(128, L.npad, Elem<ET>::kFmt);
     const int nchk = (g.npix + 127) / 128;
     const int ntask = g.F * g.T;
     const int nchunk = (kused + 7) / 8;            // 16-byte chunks of K actually used
-    const int half = (nchunk + 1) / 2;             // A-tile chunks per thread (two threads per pixel row)
-    const int row = tid & 127, hsel = tid >> 7;
-    long long gi = 0;
-    bool aborted = false;
-    long long last_issued = -1;
 
-    // epilogue of chunk iteration `it`: wbar for its 128 pixels
-    auto epilogue = [&](long long it, int ft, int f, int t, int p0) -> bool {
-        const int b = (int)(it & 1);
-        bool bad = false;
-        if (tid == 0) bad = !mbar_wait(bar0 + 8 * b, (uint32_t)((it >> 1) & 1));
-        if (__syncthreads_or(bad)) return false;
-        if (warp < 4) {
-            tc_fence_after();
-            const int r = 32 * warp + lane, p = p0 + r;
-            const uint8_t *ahi = gbase + (size_t)b * L.abuf_bytes, *alo = ahi + L.a_bytes;
-            float acc = 0.f;
-            for (int c0 = 0; c0 < L.npad; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem0 + (uint32_t)(b * L.npad) + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int kc = c0 / 8 + h;
-                    if (kc >= nchunk) break;
-                    const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(r, kc & 7);
-                    const uint4 hv = *reinterpret_cast<const uint4 *>(ahi + off);
-                    const uint4 lv = X3 ? *reinterpret_cast<const uint4 *>(alo + off) : make_uint4(0, 0, 0, 0);
-                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float2 eh = Elem<ET>::unpack(hw[q]), el = Elem<ET>::unpack(lw[q]);
-                        acc += (eh.x + el.x) * v[8 * h + 2 * q] + (eh.y + el.y) * v[8 * h + 2 * q + 1];
-                    }
+    if (warp < ADJ_PROD_WARPS) {
+        // ------------------------------------------------------------ producers
+        const int ptid = tid;                      // 0 .. 511
+        long long gs = 0;
+        int n = 0;
+        for (int ft = blockIdx.x; ft < ntask; ft += gridDim.x, ++n) {
+            const int f = ft / g.T, t = ft % g.T;
+            if (warp == 0) {
+                bool ok = true;
+                if (lane == 0 && n >= 1) ok = mbar_wait_ab(bfull, (uint32_t)((n - 1) & 1), abort_flag);
+                __syncwarp();
+                if (*abort_flag || !ok) goto done;
+                const float *om = omega + (size_t)ft * g.B * 2;
+                float mx = 0.f;
+                for (int e = lane; e < 2 * g.B; e += 32) {
+                    const float v = om[e];
+                    som[e] = v;
+                    mx = fmaxf(mx, fabsf(v));
                 }
-            }
-            if (p < g.npix) wbar[(size_t)ft * g.npix + p] = pixel_w(g, f, t, p) * (0.5f / sscale[0]) * acc;
-        }
-        tc_fence_before();
-        __syncthreads();
-        return true;
-    };
-
-    for (int ft = blockIdx.x; ft < ntask && !aborted; ft += gridDim.x) {
-        const int f = ft / g.T, t = ft % g.T;
-        // omega of (f, t) into shared memory and its largest component
-        const float *om = omega + (size_t)ft * g.B * 2;
-        float mx = 0.f;
-        for (int e = tid; e < 2 * g.B; e += TC_THREADS) {
-            const float v = om[e];
-            som[e] = v;
-            mx = fmaxf(mx, fabsf(v));
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) sred[warp] = mx;
-        __syncthreads();
-        if (tid == 0) {
-            float m = 0.f;
-            for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, sred[w]);
-            float sc = 1.f;
-            if (ET == 1 && m > 0.f && isfinite(m)) {
-                int e;
-                frexpf(m, &e);
-                sc = ldexpf(1.f, 14 - e);
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) {
+                    float sc = 1.f;
+                    if (ET == 1 && mx > 0.f && isfinite(mx)) {
+                        int e;
+                        frexpf(mx, &e);
+                        sc = ldexpf(1.f, 14 - e);
+                    }
+                    *task_scale = sc;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(sready);
             }
-            sscale[0] = sc;
-        }
-        __syncthreads();
-        {   // B tile: row n = 2i (Re Y_i) or 2i+1 (Im Y_i); C_ij = omega_ij (i<j), conj(omega_ji) (i>j)
-            const float sc = sscale[0];
-            for (int item = tid; item < kused * nchunk; item += TC_THREADS) {
-                const int n = item / nchunk, kc = item % nchunk, i = n >> 1;
-                const bool im_row = n & 1;
+            {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_ab(sready, (uint32_t)(n & 1), abort_flag);
+                if (lane == 0 && ok && n >= 1) ok = mbar_wait_ab(bempty, (uint32_t)((n - 1) & 1), abort_flag);
+                __syncwarp();
+                if (*abort_flag || !ok) goto done;
+            }
+            const float sc = *task_scale;
+            // B tile: row nrow = 2i (Re Y_i) or 2i+1 (Im Y_i); C_ij = omega_ij (i<j), conj(omega_ji) (i>j)
+            for (int item = ptid; item < kused * nchunk; item += ADJ_PROD_WARPS * 32) {
+                const int nrow = item / nchunk, kc = item % nchunk, i = nrow >> 1;
+                const bool im_row = nrow & 1;
                 float v[8];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -709,88 +689,155 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
                 uint4 hh, ll;
                 Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
                 Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
-                const uint32_t off = (uint32_t)(kc >> 3) * b_atom + sw128_off(n, kc & 7);
+                const uint32_t off = (uint32_t)(kc >> 3) * b_atom + sw128_off(nrow, kc & 7);
                 *reinterpret_cast<uint4 *>(bt_hi + off) = hh;
                 if (X3) *reinterpret_cast<uint4 *>(bt_lo + off) = ll;
             }
-        }
-        // stream the pixel chunks
-        float s6n[6];
-        {
-            const int p = row;
-            if (p < g.npix) load_s6(g, t, p, s6n);
-        }
-        long long pending = -1;
-        int pending_p0 = 0;
-        for (int c = 0; c < nchk; ++c, ++gi) {
-            const int b = (int)(gi & 1);
-            const int p0 = c * 128, p = p0 + row;
-            float s6[6];
-#pragma unroll
-            for (int z = 0; z < 6; ++z) s6[z] = s6n[z];
-            if (c + 1 < nchk && p + 128 < g.npix) load_s6(g, t, p + 128, s6n);   // prefetch next chunk
-            uint8_t *ahi = gbase + (size_t)b * L.abuf_bytes, *alo = ahi + L.a_bytes;
-            const bool vp = p < g.npix;
-            const int kc0 = hsel * half, kc1 = min(nchunk, kc0 + half);
-            for (int kc = kc0; kc < kc1; ++kc) {
-                float v[8];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int jx = 4 * kc + q;
-                    float er = 0.f, ei = 0.f;
-                    if (vp && jx < g.A) {
-                        float k6[6];
-#pragma unroll
-                        for (int z = 0; z < 6; ++z) k6[z] = g.kap32[((size_t)f * g.A + jx) * 6 + z];
-                        phasor_of(phase_frac(k6, s6), er, ei);
-                    }
-                    v[2 * q] = er;
-                    v[2 * q + 1] = ei;
-                }
-                uint4 hh, ll;
-                Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
-                Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
-                const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(row, kc & 7);
-                *reinterpret_cast<uint4 *>(ahi + off) = hh;
-                if (X3) *reinterpret_cast<uint4 *>(alo + off) = ll;
-            }
             fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bfull);
+            // pixel chunks through the A-slot ring
+            for (int c = 0; c < nchk; ++c, ++gs) {
+                const int s = (int)(gs % ADJ_SLOTS);
+                const long long use = gs / ADJ_SLOTS;
+                bool ok = true;
+                if (lane == 0 && use >= 1) ok = mbar_wait_ab(empty0 + 8 * s, (uint32_t)((use - 1) & 1), abort_flag);
+                __syncwarp();
+                if (*abort_flag || !ok) goto done;
+                uint8_t *ahi = gbase + (size_t)s * L.abuf_bytes, *alo = ahi + L.a_bytes;
+                const int p0 = c * 128;
+                for (int item = ptid; item < 128 * nchunk; item += ADJ_PROD_WARPS * 32) {
+                    const int row = item / nchunk, kc = item % nchunk, p = p0 + row;
+                    const bool vp = p < g.npix;
+                    float s6[6];
+                    if (vp) load_s6(g, t, p, s6);
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int jx = 4 * kc + q;
+                        float er = 0.f, ei = 0.f;
+                        if (vp && jx < g.A) {
+                            float k6[6];
+#pragma unroll
+                            for (int z = 0; z < 6; ++z) k6[z] = g.kap32[((size_t)f * g.A + jx) * 6 + z];
+                            if (g.flat_array) phasor_of<!X3>(phase_frac<2>(k6, s6), er, ei);
+                            else phasor_of<!X3>(phase_frac<3>(k6, s6), er, ei);
+                        }
+                        v[2 * q] = er;
+                        v[2 * q + 1] = ei;
+                    }
+                    uint4 hh, ll;
+                    Elem<ET>::split(v[0], v[1], hh.x, ll.x); Elem<ET>::split(v[2], v[3], hh.y, ll.y);
+                    Elem<ET>::split(v[4], v[5], hh.z, ll.z); Elem<ET>::split(v[6], v[7], hh.w, ll.w);
+                    const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(row, kc & 7);
+                    *reinterpret_cast<uint4 *>(ahi + off) = hh;
+                    if (X3) *reinterpret_cast<uint4 *>(alo + off) = ll;
+                }
+                if (ptid == 0) {
+                    slot_scale[s] = sc;
+                    slot_ft[s] = ft;
+                    slot_p0[s] = p0;
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full0 + 8 * s);
+            }
+        }
+    } else if (warp == ADJ_MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, L.npad, Elem<ET>::kFmt);
+            long long gs = 0, last = -1;
+            int n = 0;
+            for (int ft = blockIdx.x; ft < ntask; ft += gridDim.x, ++n) {
+                if (!mbar_wait_ab(bfull, (uint32_t)(n & 1), abort_flag)) goto mma_done;
+                for (int c = 0; c < nchk; ++c, ++gs) {
+                    const int s = (int)(gs % ADJ_SLOTS);
+                    if (!mbar_wait_ab(full0 + 8 * s, (uint32_t)((gs / ADJ_SLOTS) & 1), abort_flag)) goto mma_done;
+                    tc_fence_after();
+                    const uint32_t sa_hi = base + (uint32_t)s * L.abuf_bytes, sa_lo = sa_hi + L.a_bytes;
+                    const uint32_t sb_hi = base + L.b_off, sb_lo = sb_hi + L.b_bytes;
+                    const uint32_t dcol = tmem0 + (uint32_t)(s * L.npad);
+                    for (int kk = 0; kk < L.ksteps; ++kk) {
+                        const uint32_t oa = (uint32_t)(kk >> 2) * a_atom + 32u * (kk & 3);
+                        const uint32_t ob = (uint32_t)(kk >> 2) * b_atom + 32u * (kk & 3);
+                        const uint64_t dah = sdesc_sw128(sa_hi + oa), dbh = sdesc_sw128(sb_hi + ob);
+                        mma_bf16(dcol, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+                        if (X3) {
+                            mma_bf16(dcol, dah, sdesc_sw128(sb_lo + ob), idesc, 1u);
+                            mma_bf16(dcol, sdesc_sw128(sa_lo + oa), dbh, idesc, 1u);
+                        }
+                    }
+                    mma_commit(dfull0 + 8 * s);
+                    mma_commit(empty0 + 8 * s);
+                    last = gs;
+                }
+                mma_commit(bempty);
+            }
+        mma_done:
+            if (*abort_flag && last >= 0) {
+                const int s = (int)(last % ADJ_SLOTS);
+                long long t0 = clock64();
+                while (clock64() - t0 < WAIT_CYCLES) {
+                    uint32_t ok;
+                    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                                 : "=r"(ok) : "r"(dfull0 + 8 * s), "r"((uint32_t)((last / ADJ_SLOTS) & 1)) : "memory");
+                    if (ok) break;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 16-19)
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        long long gs = 0;
+        for (int ft = blockIdx.x; ft < ntask; ft += gridDim.x) {
+            for (int c = 0; c < nchk; ++c, ++gs) {
+                const int s = (int)(gs % ADJ_SLOTS);
+                const uint32_t par = (uint32_t)((gs / ADJ_SLOTS) & 1);
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_ab(full0 + 8 * s, par, abort_flag);
+                if (lane == 0 && ok) ok = mbar_wait_ab(dfull0 + 8 * s, par, abort_flag);
+                __syncwarp();
+                if (*abort_flag || !ok) goto done;
                 tc_fence_after();
-                const uint32_t sa_hi = base + (uint32_t)b * L.abuf_bytes, sa_lo = sa_hi + L.a_bytes;
-                const uint32_t sb_hi = base + L.b_off, sb_lo = sb_hi + L.b_bytes;
-                const uint32_t dcol = tmem0 + (uint32_t)(b * L.npad);
-                for (int kk = 0; kk < L.ksteps; ++kk) {
-                    const uint32_t oa = (uint32_t)(kk >> 2) * a_atom + 32u * (kk & 3);
-                    const uint32_t ob = (uint32_t)(kk >> 2) * b_atom + 32u * (kk & 3);
-                    const uint64_t dah = sdesc_sw128(sa_hi + oa), dbh = sdesc_sw128(sb_hi + ob);
-                    mma_bf16(dcol, dah, dbh, idesc, kk > 0 ? 1u : 0u);
-                    if (X3) {
-                        mma_bf16(dcol, dah, sdesc_sw128(sb_lo + ob), idesc, 1u);
-                        mma_bf16(dcol, sdesc_sw128(sa_lo + oa), dbh, idesc, 1u);
+                const int ftm = slot_ft[s], p = slot_p0[s] + row;
+                const float inv = 0.5f / slot_scale[s];
+                const uint8_t *ahi = gbase + (size_t)s * L.abuf_bytes, *alo = ahi + L.a_bytes;
+                float acc = 0.f;
+                for (int c0 = 0; c0 < L.npad; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem0 + (uint32_t)(s * L.npad) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int kc = c0 / 8 + h;
+                        if (kc >= nchunk) break;
+                        const uint32_t off = (uint32_t)(kc >> 3) * a_atom + sw128_off(row, kc & 7);
+                        const uint4 hv = *reinterpret_cast<const uint4 *>(ahi + off);
+                        const uint4 lv = X3 ? *reinterpret_cast<const uint4 *>(alo + off) : make_uint4(0, 0, 0, 0);
+                        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float2 eh = Elem<ET>::unpack(hw[q]), el = Elem<ET>::unpack(lw[q]);
+                            acc += (eh.x + el.x) * v[8 * h + 2 * q] + (eh.y + el.y) * v[8 * h + 2 * q + 1];
+                        }
                     }
                 }
-                mma_commit(bar0 + 8 * b);
+                if (p < g.npix) {
+                    const int fe = ftm / g.T, te = ftm % g.T;
+                    wbar[(size_t)ftm * g.npix + p] = pixel_w(g, fe, te, p) * inv * acc;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty0 + 8 * s);
             }
-            last_issued = gi;
-            if (pending >= 0) {
-                if (!epilogue(pending, ft, f, t, pending_p0)) { aborted = true; break; }
-            }
-            pending = gi;
-            pending_p0 = p0;
         }
-        if (aborted) break;
-        if (!epilogue(pending, ft, f, t, pending_p0)) { aborted = true; break; }
     }
-    if (aborted) {
-        if (tid == 0) {
-            atomicExch(g.status, (int)FM_ERR_TIMEOUT);
-            if (last_issued >= 0) mbar_wait(bar0 + 8 * (last_issued & 1), (uint32_t)((last_issued >> 1) & 1));
-        }
-        __syncthreads();
-    }
-    if (warp == 0) {
+done:
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicExch(g.status, (int)FM_ERR_TIMEOUT);
+    if (warp == ADJ_MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tmem0, (uint32_t)L.ncols);
     }
@@ -828,12 +875,12 @@ template <int ET, bool X3>
 static fm_status vis_tc_launch(Ctx &c, const FwdLayout &L, int rch, int sub, size_t smem, int grid, const float *x,
                                float *vis, cudaStream_t st)
 {
-    if (c.A <= 40) {
-        FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vis_tc<ET, X3, 5><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
+    if (c.A <= 48) {
+        FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_vis_tc<ET, X3, 3><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
     } else {
-        FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vis_tc<ET, X3, 8><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
+        FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_vis_tc<ET, X3, 4><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
     }
     FM_CK_LAUNCH();
     return FM_OK;
@@ -899,7 +946,7 @@ static fm_status adj_tc_launch(Ctx &c, const AdjLayout &L, size_t smem, int grid
                                cudaStream_t st)
 {
     FM_CK(cudaFuncSetAttribute(k_adj_tc<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_adj_tc<ET, X3><<<grid, TC_THREADS, smem, st>>>(c.g, L, omega, wbar);
+    k_adj_tc<ET, X3><<<grid, ADJ_THREADS, smem, st>>>(c.g, L, omega, wbar);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -926,13 +973,14 @@ fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_
     L.ksteps = (2 * c.A + 15) / 16;
     L.katoms = (L.ksteps + 3) / 4;
     L.ncols = 32;
-    while (L.ncols < 2 * L.npad) L.ncols *= 2;
+    while (L.ncols < ADJ_SLOTS * L.npad) L.ncols *= 2;
     L.a_bytes = (uint32_t)L.katoms * 128u * 128u;
     L.b_bytes = (uint32_t)L.katoms * (uint32_t)L.npad * 128u;
     L.abuf_bytes = (x3 ? 2u : 1u) * L.a_bytes;
-    L.b_off = 2 * L.abuf_bytes;
-    L.tail_off = L.b_off + (x3 ? 2u : 1u) * L.b_bytes;
-    const size_t smem = 1024 + (size_t)L.tail_off + 128 + 2 * sizeof(float) * (size_t)c.B;
+    L.b_off = ADJ_SLOTS * L.abuf_bytes;
+    L.om_off = L.b_off + (x3 ? 2u : 1u) * L.b_bytes;
+    L.meta_off = L.om_off + (uint32_t)((2 * sizeof(float) * (size_t)c.B + 15) / 16 * 16);
+    const size_t smem = 1024 + (size_t)L.meta_off + 64 + 72 + 16;
     if (smem > 227 * 1024) { set_error("adjoint tiles exceed shared memory"); return FM_ERR_UNSUPPORTED; }
     const int ntask = c.F * c.T;
     int grid = num_sms();
