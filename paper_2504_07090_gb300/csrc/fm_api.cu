@@ -183,8 +183,17 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
         for (int f = 1; f < c->F && uni; ++f)
             if (std::fabs((c->freq[f] - c->freq[f - 1]) - dnu) > 1e-9 * c->freq[f]) uni = false;
         std::vector<float> dk(3 * (size_t)c->A, 0.f);
-        for (int i = 0; i < c->A; ++i)
-            for (int k = 0; k < 3; ++k) dk[3 * i + k] = (float)(dnu * c->ant[3 * i + k] / kCLight);
+        for (int i = 0; i < c->A; ++i) {
+            double n2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double v = dnu * c->ant[3 * i + k] / kCLight;
+                dk[3 * i + k] = (float)v;
+                n2 += v * v;
+            }
+            // the step factor exp(-2 pi i dkap . s) is evaluated by a short series that
+            // holds for phases up to 1/8 turn (|s| = 1)
+            if (std::sqrt(n2) > 0.125) uni = false;
+        }
         float *ddk;
         FM_TRY(dalloc(*c, &ddk, dk.size()));
         FM_CK(cudaMemcpy(ddk, dk.data(), sizeof(float) * dk.size(), cudaMemcpyHostToDevice));

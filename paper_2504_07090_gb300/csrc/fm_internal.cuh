@@ -41,7 +41,7 @@ struct DevGeom {
     const float *bcoef32;     // [F]
     const float *dompix32;    // [npix] cell solid angle of each pixel
     const float *dkap32;      // [A][3] channel step dnu * r_i / c (turns per unit direction cosine)
-    int uniform_freq;         // channels equally spaced: E(nu + dnu) = E(nu) exp(-2 pi i dkap . s)
+    int uniform_freq;         // channels equally spaced and |dkap| <= 1/8: E(nu + dnu) = E(nu) exp(-2 pi i dkap . s)
     int flat_array;           // every antenna has up = 0: phases need only east and north
     const int *bl_i, *bl_j;   // [B]
     int *status;              // device status word (fm_status codes)

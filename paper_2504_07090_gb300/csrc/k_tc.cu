@@ -218,6 +218,21 @@ __device__ __forceinline__ void phasor_of(float fr, float &er, float &ei)
     ei = -sn;
 }
 
+// exp(-2 pi i d) for a small phase d (|d| <= 1/8 turn, the channel-step factor of the
+// frequency recurrence): Taylor series of sin and cos to degree 9 / 10 in y = 2 pi d,
+// no quadrant reduction needed (truncation below 2e-9 for |y| <= pi/4)
+__device__ __forceinline__ void phasor_small(float d, float &er, float &ei)
+{
+    const float y = d * 6.28318530717958647692f;
+    const float y2 = y * y;
+    const float sp = fmaf(y * y2, fmaf(y2, fmaf(y2, fmaf(y2, 2.7557319e-6f, -1.9841270e-4f), 8.3333333e-3f),
+                                       -1.6666667e-1f), y);
+    const float cp = fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, -2.7557319e-7f, 2.4801587e-5f), -1.3888889e-3f),
+                                            4.1666667e-2f), -0.5f), 1.f);
+    er = cp;
+    ei = -sp;
+}
+
 __device__ __forceinline__ float pixel_w(const DevGeom &g, int f, int t, int p)
 {
     float z2 = g.za2_32[(size_t)t * g.npix + p];
@@ -344,7 +359,9 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
         // ------------------------------------------------------------ producers
         const uint32_t wsub = (uint32_t)(lane & 3) * 4u;
         const int wchunk = lane >> 2;
-        long long gs = 0;
+        int s = 0;                 // ring slot of the next stage
+        uint32_t phase = 0;        // its fill count parity
+        bool wrapped = false;      // the slot was filled before (wait for its release)
         for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
             const int t = task % g.T, f0 = (task / g.T) * rch;
             const int nr = min(rch, g.F - f0);
@@ -355,10 +372,8 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                 if (va) { load_s6(g, t, pa, sa); za = g.za2_32[(size_t)t * g.npix + pa]; da = g.dompix32[pa]; }
                 if (vb) { load_s6(g, t, pb, sb); zb = g.za2_32[(size_t)t * g.npix + pb]; db = g.dompix32[pb]; }
                 float er[KMAX][2], ei[KMAX][2], dr[KMAX][2], di[KMAX][2];
-                for (int r = 0; r < nr; ++r, ++gs) {
+                for (int r = 0; r < nr; ++r) {
                     const int f = f0 + r;
-                    const int s = (int)(gs % L.nstage);
-                    const long long use = gs / L.nstage;
                     const float scale = ET == 1 ? chan_scale[f] : 1.f;
                     const float bc = g.bcoef32[f];
                     const float wa = (za >= 0.f) ? da * __expf(bc * za) * x[(size_t)f * g.npix + pa] * scale : 0.f;
@@ -377,15 +392,15 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                                 if (va) phasor_of<!X3>(phase_frac<2>(k6, sa), er[k][0], ei[k][0]);
                                 if (vb) phasor_of<!X3>(phase_frac<2>(k6, sb), er[k][1], ei[k][1]);
                                 if (nr > 1) {
-                                    phasor_of<!X3>(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]), dr[k][0], di[k][0]);
-                                    phasor_of<!X3>(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]), dr[k][1], di[k][1]);
+                                    phasor_small(d0 * sa[0] + d1 * sa[2], dr[k][0], di[k][0]);
+                                    phasor_small(d0 * sb[0] + d1 * sb[2], dr[k][1], di[k][1]);
                                 }
                             } else {
                                 if (va) phasor_of<!X3>(phase_frac<3>(k6, sa), er[k][0], ei[k][0]);
                                 if (vb) phasor_of<!X3>(phase_frac<3>(k6, sb), er[k][1], ei[k][1]);
                                 if (nr > 1) {
-                                    phasor_of<!X3>(d0 * (sa[0] + sa[1]) + d1 * (sa[2] + sa[3]) + d2 * (sa[4] + sa[5]), dr[k][0], di[k][0]);
-                                    phasor_of<!X3>(d0 * (sb[0] + sb[1]) + d1 * (sb[2] + sb[3]) + d2 * (sb[4] + sb[5]), dr[k][1], di[k][1]);
+                                    phasor_small(d0 * sa[0] + d1 * sa[2] + d2 * sa[4], dr[k][0], di[k][0]);
+                                    phasor_small(d0 * sb[0] + d1 * sb[2] + d2 * sb[4], dr[k][1], di[k][1]);
                                 }
                             }
                         } else {
@@ -398,7 +413,7 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                         }
                     }
                     bool ok = true;
-                    if (lane == 0 && use >= 1) ok = mbar_wait_ab(empty0 + 8 * s, (uint32_t)((use - 1) & 1), abort_flag);
+                    if (lane == 0 && wrapped) ok = mbar_wait_ab(empty0 + 8 * s, phase ^ 1u, abort_flag);
                     __syncwarp();
                     if (*abort_flag || !ok) goto done;
                     {
@@ -430,6 +445,7 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full0 + 8 * s);
+                    if (++s == L.nstage) { s = 0; phase ^= 1u; wrapped = true; }
                 }
             }
         }
@@ -437,18 +453,20 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(128, L.npad, Elem<ET>::kFmt);
-            long long gs = 0, sr = 0, last = -1;
+            long long sr = 0;
+            int s = 0, last_s = -1;
+            uint32_t phase = 0, last_phase = 0;
             for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
                 const int f0 = (task / g.T) * rch;
                 const int nr = min(rch, g.F - f0);
+                int jmod = 0;              // j % sub
                 for (int j = 0; j < nst; ++j) {
                     const int q = (int)(sr & 1);
-                    if (j % sub == 0 && (sr >> 1) >= 1) {
+                    if (jmod == 0 && (sr >> 1) >= 1) {
                         if (!mbar_wait_ab(acce0 + 8 * q, (uint32_t)(((sr >> 1) - 1) & 1), abort_flag)) goto mma_done;
                     }
-                    for (int r = 0; r < nr; ++r, ++gs) {
-                        const int s = (int)(gs % L.nstage);
-                        if (!mbar_wait_ab(full0 + 8 * s, (uint32_t)((gs / L.nstage) & 1), abort_flag)) goto mma_done;
+                    for (int r = 0; r < nr; ++r) {
+                        if (!mbar_wait_ab(full0 + 8 * s, phase, abort_flag)) goto mma_done;
                         tc_fence_after();
                         const uint32_t sa_hi = base + (uint32_t)s * L.stage_bytes;
                         const uint32_t sa_lo = sa_hi + L.a_bytes;
@@ -459,31 +477,33 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                         for (int kk = 0; kk < KST / 16; ++kk) {
                             const uint32_t off = 32u * kk;
                             const uint64_t dah = sdesc_sw128(sa_hi + off), dbh = sdesc_sw128(sb_hi + off);
-                            mma_bf16(dacc, dah, dbh, idesc, ((j % sub) > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(dacc, dah, dbh, idesc, (jmod > 0 || kk > 0) ? 1u : 0u);
                             if (X3) {
                                 mma_bf16(dacc, dah, sdesc_sw128(sb_lo + off), idesc, 1u);
                                 mma_bf16(dacc, sdesc_sw128(sa_lo + off), dbh, idesc, 1u);
                             }
                         }
                         mma_commit(empty0 + 8 * s);
-                        last = gs;
+                        last_s = s;
+                        last_phase = phase;
+                        if (++s == L.nstage) { s = 0; phase ^= 1u; }
                     }
-                    if ((j % sub) == sub - 1 || j == nst - 1) {
+                    if (jmod == sub - 1 || j == nst - 1) {
                         mma_commit(accf0 + 8 * q);
                         ++sr;
                     }
+                    if (++jmod == sub) jmod = 0;
                 }
             }
         mma_done:
-            if (*abort_flag && last >= 0) {
+            if (*abort_flag && last_s >= 0) {
                 // drain this CTA's MMAs before TMEM is freed (bounded)
-                const int s = (int)(last % L.nstage);
                 long long t0 = clock64();
                 while (clock64() - t0 < WAIT_CYCLES) {
                     uint32_t ok;
                     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                                  "selp.u32 %0, 1, 0, p;\n\t}\n"
-                                 : "=r"(ok) : "r"(empty0 + 8 * s), "r"((uint32_t)((last / L.nstage) & 1)) : "memory");
+                                 : "=r"(ok) : "r"(empty0 + 8 * last_s), "r"(last_phase) : "memory");
                     if (ok) break;
                 }
             }
@@ -497,8 +517,8 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
         for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
             const int t = task % g.T, f0 = (task / g.T) * rch;
             const int nr = min(rch, g.F - f0);
-            for (int j = 0; j < nst; ++j) {
-                if (!((j % sub) == sub - 1 || j == nst - 1)) continue;
+            for (int j = sub - 1;; j += sub) {
+                if (j >= nst) j = nst - 1;
                 const int q = (int)(sr & 1);
                 const bool first = j < sub, last_sub = j == nst - 1;
                 bool ok = true;
@@ -541,6 +561,7 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acce0 + 8 * q);
                 ++sr;
+                if (last_sub) break;
             }
         }
     }
@@ -630,6 +651,13 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
     if (warp < ADJ_PROD_WARPS) {
         // ------------------------------------------------------------ producers
         const int ptid = tid;                      // 0 .. 511
+        // this thread's (pixel row, K chunk) items, the same for every chunk
+        int it_row[3], it_kc[3], nits = 0;
+        for (int item = ptid; item < 128 * nchunk && nits < 3; item += ADJ_PROD_WARPS * 32) {
+            it_row[nits] = item / nchunk;
+            it_kc[nits] = item % nchunk;
+            ++nits;
+        }
         long long gs = 0;
         int n = 0;
         for (int ft = blockIdx.x; ft < ntask; ft += gridDim.x, ++n) {
@@ -698,16 +726,17 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
             if (lane == 0) mbar_arrive(bfull);
             // pixel chunks through the A-slot ring
             for (int c = 0; c < nchk; ++c, ++gs) {
-                const int s = (int)(gs % ADJ_SLOTS);
-                const long long use = gs / ADJ_SLOTS;
+                const int s = (int)(gs & 1);
+                const long long use = gs >> 1;
                 bool ok = true;
                 if (lane == 0 && use >= 1) ok = mbar_wait_ab(empty0 + 8 * s, (uint32_t)((use - 1) & 1), abort_flag);
                 __syncwarp();
                 if (*abort_flag || !ok) goto done;
                 uint8_t *ahi = gbase + (size_t)s * L.abuf_bytes, *alo = ahi + L.a_bytes;
                 const int p0 = c * 128;
-                for (int item = ptid; item < 128 * nchunk; item += ADJ_PROD_WARPS * 32) {
-                    const int row = item / nchunk, kc = item % nchunk, p = p0 + row;
+#pragma unroll 1
+                for (int it = 0; it < nits; ++it) {
+                    const int row = it_row[it], kc = it_kc[it], p = p0 + row;
                     const bool vp = p < g.npix;
                     float s6[6];
                     if (vp) load_s6(g, t, p, s6);
@@ -752,8 +781,8 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
             for (int ft = blockIdx.x; ft < ntask; ft += gridDim.x, ++n) {
                 if (!mbar_wait_ab(bfull, (uint32_t)(n & 1), abort_flag)) goto mma_done;
                 for (int c = 0; c < nchk; ++c, ++gs) {
-                    const int s = (int)(gs % ADJ_SLOTS);
-                    if (!mbar_wait_ab(full0 + 8 * s, (uint32_t)((gs / ADJ_SLOTS) & 1), abort_flag)) goto mma_done;
+                    const int s = (int)(gs & 1);
+                    if (!mbar_wait_ab(full0 + 8 * s, (uint32_t)((gs >> 1) & 1), abort_flag)) goto mma_done;
                     tc_fence_after();
                     const uint32_t sa_hi = base + (uint32_t)s * L.abuf_bytes, sa_lo = sa_hi + L.a_bytes;
                     const uint32_t sb_hi = base + L.b_off, sb_lo = sb_hi + L.b_bytes;
@@ -776,13 +805,13 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
             }
         mma_done:
             if (*abort_flag && last >= 0) {
-                const int s = (int)(last % ADJ_SLOTS);
+                const int s = (int)(last & 1);
                 long long t0 = clock64();
                 while (clock64() - t0 < WAIT_CYCLES) {
                     uint32_t ok;
                     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                                  "selp.u32 %0, 1, 0, p;\n\t}\n"
-                                 : "=r"(ok) : "r"(dfull0 + 8 * s), "r"((uint32_t)((last / ADJ_SLOTS) & 1)) : "memory");
+                                 : "=r"(ok) : "r"(dfull0 + 8 * s), "r"((uint32_t)((last >> 1) & 1)) : "memory");
                     if (ok) break;
                 }
             }
@@ -794,8 +823,8 @@ k_adj_tc(DevGeom g, AdjLayout L, const float *__restrict__ omega, float *__restr
         long long gs = 0;
         for (int ft = blockIdx.x; ft < ntask; ft += gridDim.x) {
             for (int c = 0; c < nchk; ++c, ++gs) {
-                const int s = (int)(gs % ADJ_SLOTS);
-                const uint32_t par = (uint32_t)((gs / ADJ_SLOTS) & 1);
+                const int s = (int)(gs & 1);
+                const uint32_t par = (uint32_t)((gs >> 1) & 1);
                 bool ok = true;
                 if (lane == 0) ok = mbar_wait_ab(full0 + 8 * s, par, abort_flag);
                 if (lane == 0 && ok) ok = mbar_wait_ab(dfull0 + 8 * s, par, abort_flag);
