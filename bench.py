@@ -271,20 +271,43 @@ def main():
     value = world * K * evals_per_step / (total_ms / 1000.0)
 
     # roofline of the dominant contraction kernel (live CUDA events around each launch)
-    flops_launch = 8.0 * prob.n_ant ** 2 * prob.n_pix * prob.n_freq * prob.n_lst
-    dom = "forward contraction (k_vis_tc)" if fwd_ms >= adj_ms else "adjoint contraction (k_adj_tc)"
-    dom_ms, dom_n = (fwd_ms, fwd_n) if fwd_ms >= adj_ms else (adj_ms, adj_n)
+    info = h.contraction_info()
     pk, pk_src = peaks()
     nprod = N_PRODUCTS.get(args.precision, 1)
     peak = pk["bf16_tflops_sustained"] / nprod
-    achieved = flops_launch / (dom_ms / max(dom_n, 1) / 1000.0) / 1e12 if dom_n else None
+    fwd_ms1, adj_ms1 = fwd_ms / max(fwd_n, 1), adj_ms / max(adj_n, 1)
+    if info["form"] == "hour_angle":
+        # grouped complex-by-real contraction over the band of non-zero Toeplitz entries:
+        # 4 flops per (fringe group, pixel, channel, LST), the same count for the adjoint
+        flops_launch = 4.0 * info["fringes"] * prob.n_pix * prob.n_freq * prob.n_lst
+        formula = "4 n_groups n_pix n_freq n_lst"
+        names = ("forward contraction (k_vis_ha)", "adjoint contraction (k_adj_ha)")
+        npad = (prob.n_lst + 15) // 16 * 16
+        nhp = info["hour_angle_cells"]
+        n_mt, n_kq = (info["fringes"] + 63) // 64, (info["fringes"] + 31) // 32
+        exe = (nprod * 2.0 * 128 * n_mt * npad * nhp * prob.n_dec * prob.n_freq,
+               nprod * 2.0 * nhp * npad * 64 * n_kq * prob.n_dec * prob.n_freq)
+    else:
+        flops_launch = 8.0 * prob.n_ant ** 2 * prob.n_pix * prob.n_freq * prob.n_lst
+        formula = "8 n_ant^2 n_pix n_freq n_lst"
+        names = ("forward contraction (k_vis_tc)", "adjoint contraction (k_adj_tc)")
+        exe = (None, None)
+    fwd_dom = fwd_ms >= adj_ms
+    dom = names[0] if fwd_dom else names[1]
+    dom_ms1, dom_n = (fwd_ms1, fwd_n) if fwd_dom else (adj_ms1, adj_n)
+    achieved = flops_launch / (dom_ms1 / 1000.0) / 1e12 if dom_n else None
     roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
                 "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
                                f"(FP32-equivalent rate of the {args.precision} split); algorithmic flops per launch "
-                               f"= 8 n_ant^2 n_pix n_freq n_lst = {flops_launch:.4g}",
-                "forward_ms_per_launch": fwd_ms / max(fwd_n, 1), "adjoint_ms_per_launch": adj_ms / max(adj_n, 1),
+                               f"= {formula} = {flops_launch:.4g}",
+                "form": info["form"], "fringes": info["fringes"],
+                "forward_ms_per_launch": fwd_ms1, "adjoint_ms_per_launch": adj_ms1,
                 "launches": {"forward": fwd_n, "adjoint": adj_n}}
+    if exe[0] is not None and dom_n:
+        e_dom = exe[0] if fwd_dom else exe[1]
+        roofline["tensor_executed_tflops"] = e_dom / (dom_ms1 / 1000.0) / 1e12
+        roofline["tensor_executed_frac_of_bf16_sustained"] = roofline["tensor_executed_tflops"] / pk["bf16_tflops_sustained"]
 
     # end to end through the C ABI with host buffers: H2D (q, z) -> step -> D2H (q, H, accepted)
     e2e = None

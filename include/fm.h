@@ -164,8 +164,8 @@ FM_API fm_status fm_leapfrog(fm_handle h, void *dev_q, void *dev_p, double eps, 
  * Needs fm_build_precond first (FM_ERR_STATE otherwise).  in and out may not alias. */
 FM_API fm_status fm_precond_apply(fm_handle h, int op, const void *dev_in, void *dev_out, fm_stream stream);
 
-/* Event timing of the two contraction kernels (forward fringe sum, pixel adjoint) on
- * the stream each call uses: fm_set_profiling(h, 1) starts recording, fm_get_profile
+/* Event timing of the two contraction kernels (forward fringe sum, pixel adjoint; the
+ * main kernel of each, without its operand preparation) on the stream each call uses: fm_set_profiling(h, 1) starts recording, fm_get_profile
  * synchronises, writes total milliseconds and launch counts per class
  * (out_ms[2], out_count[2]: 0 = forward contraction, 1 = adjoint contraction) and
  * clears the record.  Off by default; recording adds two events per contraction. */
@@ -191,6 +191,21 @@ FM_API fm_status fm_get_profile(fm_handle h, double *out_ms, int64_t *out_count)
 FM_API fm_status fm_sky_pixels_noalloc(int n_freq, int n_ra, int n_dec, int n_mode_ra, int n_mode_dec,
                                        const float *dev_phi, const float *dev_leg, const float *dev_a, float *dev_x,
                                        fm_stream stream);
+
+/* Which form of the fringe contraction (Eq. rime_discrete) the handle runs, written to
+ * out[4] (host int32):
+ *   out[0]  0 = direct per-baseline SIMT sum (FP64 / FP32 precisions),
+ *           1 = antenna form on the tensor cores (V = E W E^H per channel and LST),
+ *           2 = hour-angle form on the tensor cores (drift scan with the LST step a whole
+ *               number of RA pixels: one phasor table per channel, the sky as a Toeplitz
+ *               operand, baselines with equal vectors up to sign computed once);
+ *   out[1]  distinct fringes computed per channel and LST (form 2: baseline groups;
+ *           otherwise the number of baselines);
+ *   out[2]  LST step in RA pixels (form 2), else 0;
+ *   out[3]  hour-angle cells per declination row, padded (form 2), else 0.
+ * The form is fixed at fm_create; the environment variable FM_HA=0 read there
+ * disables form 2 and FM_HA_GROUPS=0 makes it compute every baseline separately. */
+FM_API fm_status fm_contraction_info(fm_handle h, int32_t *out);
 
 /* Kernels launched by this library in this process so far (all handles). */
 FM_API int64_t fm_kernel_launches(void);

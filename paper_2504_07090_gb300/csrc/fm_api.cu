@@ -13,30 +13,6 @@ namespace fm {
 static thread_local char g_err[512] = "";
 long long g_launches = 0;
 
-static cudaEvent_t prof_event(Ctx &c)
-{
-    if (c.prof_next >= c.prof_pool.size()) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-        c.prof_pool.push_back(e);
-    }
-    return c.prof_pool[c.prof_next++];
-}
-
-// records an event pair of class `cls` around the enqueued work of `fn`
-template <typename F>
-static fm_status profiled(Ctx &c, int cls, cudaStream_t st, F fn)
-{
-    if (!c.prof_on) return fn();
-    cudaEvent_t a = prof_event(c), b = prof_event(c);
-    if (!a || !b) return fn();
-    cudaEventRecord(a, st);
-    fm_status s = fn();
-    cudaEventRecord(b, st);
-    c.prof_rec.push_back({cls, {a, b}});
-    return s;
-}
-
 void set_error(const char *fmt, ...)
 {
     va_list ap;
@@ -256,6 +232,7 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
         if (s != FM_OK) return s;
         FM_CK(e2);
     }
+    FM_TRY(ha_setup(*c));
     return FM_OK;
 }
 
@@ -263,23 +240,22 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 template <typename R>
 static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st)
 {
-    return profiled(c, 0, st, [&]() -> fm_status {
-        if constexpr (std::is_same<R, float>::value) {
-            if (c.prec >= FM_PREC_BF16X1) return launch_vis_tc(c, x, vis, st);
-        }
-        return launch_vis<R>(c, x, vis, st);
-    });
+    // the tensor-core launchers time their main kernel themselves
+    if constexpr (std::is_same<R, float>::value) {
+        if (c.ha.on) return launch_vis_ha(c, x, vis, st);
+        if (c.prec >= FM_PREC_BF16X1) return launch_vis_tc(c, x, vis, st);
+    }
+    return profiled(c, 0, st, [&]() -> fm_status { return launch_vis<R>(c, x, vis, st); });
 }
 
 template <typename R>
 static fm_status run_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st)
 {
-    return profiled(c, 1, st, [&]() -> fm_status {
-        if constexpr (std::is_same<R, float>::value) {
-            if (c.prec >= FM_PREC_BF16X1) return launch_adjoint_tc(c, omega, xbar, st);
-        }
-        return launch_adjoint<R>(c, omega, xbar, st);
-    });
+    if constexpr (std::is_same<R, float>::value) {
+        if (c.ha.on) return launch_adjoint_ha(c, omega, xbar, st);
+        if (c.prec >= FM_PREC_BF16X1) return launch_adjoint_tc(c, omega, xbar, st);
+    }
+    return profiled(c, 1, st, [&]() -> fm_status { return launch_adjoint<R>(c, omega, xbar, st); });
 }
 
 template <typename R>
@@ -544,6 +520,18 @@ fm_status fm_get_profile(fm_handle h, double *out_ms, int64_t *out_count)
     c.prof_rec.clear();
     c.prof_next = 0;
     for (int k = 0; k < 2; ++k) { out_ms[k] = ms[k]; out_count[k] = cnt[k]; }
+    return FM_OK;
+}
+
+fm_status fm_contraction_info(fm_handle h, int32_t *out)
+{
+    FM_HANDLE_OK(h);
+    if (!out) return invalid("out is NULL");
+    const Ctx &c = *reinterpret_cast<const Ctx *>(h);
+    out[0] = c.ha.on ? 2 : (c.prec >= FM_PREC_BF16X1 ? 1 : 0);
+    out[1] = c.ha.on ? c.ha.U : c.B;
+    out[2] = c.ha.on ? c.ha.k : 0;
+    out[3] = c.ha.on ? c.ha.nhp : 0;
     return FM_OK;
 }
 

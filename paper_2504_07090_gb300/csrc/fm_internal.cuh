@@ -61,6 +61,36 @@ template <> struct Tab<float> {
     static __device__ __forceinline__ const float *bcoef(const DevGeom &g) { return g.bcoef32; }
 };
 
+// Hour-angle form of the contraction for drift scans (k_ha.cu): valid when the LSTs are
+// spaced by an integer number k of RA pixels, so that the direction of pixel (r, d) at
+// LST t depends on n = t k - r + R - 1 only.
+struct HaState {
+    bool on = false;
+    int k = 1;                 // LST step in RA pixels
+    int nh = 0, nhp = 0;       // hour-angle indices used, padded to a multiple of 128
+    int nbc = 0;               // 64-index chunks per declination row (nhp / 64)
+    int U = 0;                 // fringe groups: baselines with equal vectors up to sign
+    int nmt = 0;               // forward M-tiles, ceil(U / 64)
+    int nkq = 0;               // adjoint K-chunks, ceil(U / 32)
+    int npad = 0;              // n_lst rounded up to 16 (MMA N)
+    int P0 = 0, L = 0;         // sky-strip offset and length (16-bit elements)
+    int grid = 0, J = 0;       // forward CTAs; most CTAs sharing one (M-tile, channel) segment
+    float sp = 1.f;            // response scale 2^e (e even): the table holds sqrt(dOmega A) 2^(e/2)
+    float2 *E = nullptr;       // [F][D][nbc][A][64] per-antenna phasor table
+    int2 *uij = nullptr;       // [nmt * 64] representative pair (i, j) of each group, (-1, -1) pad
+    int *bmap = nullptr;       // [B] group * 2 + (1 if the baseline is the reversed vector)
+    int *moff = nullptr;       // [U + 1] CSR offsets of group members
+    int *mem = nullptr;        // [B] members, b * 2 + reversed
+    int *ncontrib = nullptr;   // [nmt * F] forward CTAs contributing to each segment
+    uint16_t *xs = nullptr;    // [2][F][D][L] scaled reversed sky strips, hi then lo
+    float *xscale = nullptr;   // [F]
+    float *vpart = nullptr;    // [nmt * F][J][128][npad] forward partial sums
+    float *q32 = nullptr;      // [F][T][U][2] residual weights summed per group
+    unsigned *qmax = nullptr;  // [F] max |Q| as float bits
+    float *qscale = nullptr;   // [F]
+    uint8_t *qimg = nullptr;   // [F][nkq][2][npad * 128] swizzled B tiles of the adjoint
+};
+
 // Device workspace and state of one handle.
 struct Ctx {
     fm_config cfg;
@@ -97,6 +127,7 @@ struct Ctx {
     std::vector<cudaEvent_t> prof_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_rec;
     size_t prof_next = 0;
+    HaState ha;
     // leapfrog scratch
     void *lf_q0 = nullptr, *lf_g = nullptr, *lf_z = nullptr;
     double *lf_scal = nullptr;
@@ -126,6 +157,32 @@ extern long long g_launches;     // kernels launched by the library (relaxed cou
     } while (0)
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ profiling
+inline cudaEvent_t prof_event(Ctx &c)
+{
+    if (c.prof_next >= c.prof_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c.prof_pool.push_back(e);
+    }
+    return c.prof_pool[c.prof_next++];
+}
+
+// records an event pair of class `cls` (0 forward contraction kernel, 1 adjoint
+// contraction kernel) around the work `fn` enqueues on `st`
+template <typename F>
+fm_status profiled(Ctx &c, int cls, cudaStream_t st, F fn)
+{
+    if (!c.prof_on) return fn();
+    cudaEvent_t a = prof_event(c), b = prof_event(c);
+    if (!a || !b) return fn();
+    cudaEventRecord(a, st);
+    fm_status s = fn();
+    cudaEventRecord(b, st);
+    c.prof_rec.push_back({cls, {a, b}});
+    return s;
+}
 
 // ------------------------------------------------------------ stage launchers
 // (each defined in the .cu file that owns the kernels; all enqueue on `st`)
@@ -170,6 +227,11 @@ fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st);
 // shape does not fit its tiles
 fm_status launch_vis_tc(Ctx &c, const float *x, float *vis, cudaStream_t st);
 fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_t st);
+// hour-angle form (drift scans with the LST step a whole number of RA pixels); ha_setup
+// leaves c.ha.on false when the geometry, precision or sizes do not allow it
+fm_status ha_setup(Ctx &c);
+fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st);
+fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st);
 
 // preconditioner and leapfrog
 template <typename R>

@@ -1,0 +1,1063 @@
+// Hour-angle form of the fringe contraction for drift scans (sm_103a tcgen05).
+//
+// Eq. (rime_discrete) with K_ij = E_i conj(E_j) sums, for every baseline, channel and
+// LST, the beam- and solid-angle-weighted sky times the fringe over all pixels.  In a
+// drift scan (Sec. 2.1: the array points at a fixed topocentric direction) with LSTs
+// spaced by a whole number k of RA pixels, LST_t - RA_r = LST_0 - RA_{R-1} + (t k - r + R - 1) dRA,
+// so the direction of pixel (r, d) at LST t depends on the hour-angle index
+// n = t k - r + R - 1 only.  With one primary beam for all antennas (Sec. 3.4), baselines
+// with equal vectors b = r_i - r_j (up to sign) also have equal (or conjugate) fringes.
+// For one channel and one fringe group u the visibility is then
+//   V_u(t) = sum_{d, n} P_u(n, d) x(t k + R - 1 - n, d),
+//   P_u(n, d) = E_i(n, d) conj(E_j(n, d)),  E_i = sqrt(dOmega_d A(n, d)) exp(-2 pi i nu r_i . s(n, d) / c),
+// a real GEMM  D[rho][t] = sum_K A[rho][K] B[t][K],  rho = (u, Re | Im), K = (d, n),
+// whose A operand is generated tile by tile from a per-channel table of E (computed once
+// per handle with FP64 phases) and whose B operand is the Toeplitz matrix of the sky,
+// built per tile from a reversed copy of each declination row.
+//
+// The adjoint (the pixel gradient through the same response) is
+//   xbar(r, d) = sum_t sum_rho P_rho(n(r, t), d) Q_rho(t),   Q_u = sum_{b in u} omega_b,
+// (conj(omega_b) for baselines reversed with respect to the group's representative): the
+// GEMM X[n][t] = sum_rho P^T[n][rho] Q[t][rho], then sums along the diagonals
+// n = t k + R - 1 - r, done with warp shuffles in the TMEM epilogue.
+//
+// Both kernels are warp-specialised like the antenna-form kernels: 16 producer warps
+// fill 128-byte-swizzled operand tiles, one thread issues tcgen05.mma into TMEM, four
+// warps drain the accumulators and one thread issues bulk copies.  Every wait is
+// bounded; a timeout records FM_ERR_TIMEOUT and the CTA winds down in order.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "fm_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fm {
+namespace {
+
+using namespace tc;
+
+constexpr int HA_PROD_WARPS = 16;
+constexpr int HA_EPI_WARP0 = 16;          // warps 16..19 drain TMEM (lane quarter = warp & 3)
+constexpr int HA_MMA_WARP = 20;
+constexpr int HA_LOAD_WARP = 21;
+constexpr int HA_THREADS = 22 * 32;
+constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulation chain
+constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
+
+// kernel parameters, by value
+struct HaDev {
+    int F, D, T, R, A, U, k, nhp, nbc, npad, P0, L, nchunk, nmt, nkq, J;
+    long long Q;                          // forward work units: nmt * F * nchunk
+    const float2 *E;
+    const int2 *uij;
+};
+
+struct HaLayout {
+    int nstage, neslot, ncols;
+    uint32_t a_bytes, b_bytes, stage_bytes, eslot_bytes;
+    uint32_t e_off, v_off, bar_off, vstride, jw;
+    size_t smem;
+};
+
+// first work unit of CTA g when Q units are cut into G contiguous ranges
+__host__ __device__ __forceinline__ long long range_lo(long long Q, int G, int g) { return Q * g / G; }
+
+__host__ __device__ inline int cta_of(long long q, long long Q, int G)
+{
+    int g = (int)(q * G / Q);
+    while (g + 1 < G && range_lo(Q, G, g + 1) <= q) ++g;
+    while (g > 0 && range_lo(Q, G, g) > q) --g;
+    return g;
+}
+
+__device__ __forceinline__ void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
+
+// ------------------------------------------------------------ per-handle phasor table
+// E[f][d][nb][i][nl], n = 64 nb + nl: sqrt(dOmega_d A(za; nu_f)) 2^(e/2) exp(-2 pi i nu r_i . s / c)
+// at hour angle H(n) = LST_0 - (ra_min + (R - 1 - n + 1/2) dRA); zero below the horizon
+// and for n >= nh.  FP64 throughout, stored as FP32.
+struct HaTabArgs {
+    int F, D, R, A, nh, nhp, nbc;
+    double lst0, ra_min, dra, dec_min, ddec, lat, amp_scale;
+    const double *kap64, *bcoef64, *domega64;
+};
+
+__global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
+{
+    const long long total = (long long)a.F * a.D * a.nhp * a.A;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int nl = (int)(e % 64);
+        long long r = e / 64;
+        const int i = (int)(r % a.A);
+        r /= a.A;
+        const int nb = (int)(r % a.nbc);
+        r /= a.nbc;
+        const int d = (int)(r % a.D);
+        const int f = (int)(r / a.D);
+        const int n = 64 * nb + nl;
+        float2 out = make_float2(0.f, 0.f);
+        if (n < a.nh) {
+            const double H = a.lst0 - (a.ra_min + ((double)(a.R - 1 - n) + 0.5) * a.dra);
+            const double dec = a.dec_min + (d + 0.5) * a.ddec;
+            double sd, cd, sh, ch, sl, cl;
+            sincos(dec, &sd, &cd);
+            sincos(H, &sh, &ch);
+            sincos(a.lat, &sl, &cl);
+            const double sE = -cd * sh, sN = cl * sd - sl * cd * ch, sU = sl * sd + cl * cd * ch;
+            if (sU > 0.0) {
+                const double za = acos(sU > 1.0 ? 1.0 : sU);
+                const double beta = a.domega64[d] * exp(a.bcoef64[f] * za * za);
+                const double amp = sqrt(beta) * a.amp_scale;
+                const double *kp = a.kap64 + ((size_t)f * a.A + i) * 3;
+                double ph = kp[0] * sE + kp[1] * sN + kp[2] * sU;
+                ph -= rint(ph);
+                double sn, cs;
+                sincospi(2.0 * ph, &sn, &cs);
+                out = make_float2((float)(amp * cs), (float)(-amp * sn));
+            }
+        }
+        E[e] = out;
+    }
+}
+
+// ------------------------------------------------------------ forward operand prep
+// xs[f][d][m'] = S_f x(r = R - 1 - (m' - P0), d) for 0 <= m' - P0 < R, else 0; split into
+// 16-bit hi and lo parts of the operand type.
+template <int ET>
+__global__ void k_ha_xprep(HaDev h, const float *__restrict__ x, const float *__restrict__ xscale,
+                           uint16_t *__restrict__ xs_hi, uint16_t *__restrict__ xs_lo)
+{
+    const long long total = (long long)h.F * h.D * (h.L / 2);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int mp = 2 * (int)(e % (h.L / 2));
+        const long long fd = e / (h.L / 2);
+        const int d = (int)(fd % h.D), f = (int)(fd / h.D);
+        const float sc = xscale[f];
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int m = mp + q - h.P0;
+            v[q] = (m >= 0 && m < h.R) ? sc * x[((size_t)f * h.D + d) * h.R + (h.R - 1 - m)] : 0.f;
+        }
+        uint32_t hi, lo;
+        Elem<ET>::split(v[0], v[1], hi, lo);
+        reinterpret_cast<uint32_t *>(xs_hi)[e] = hi;
+        reinterpret_cast<uint32_t *>(xs_lo)[e] = lo;
+    }
+}
+
+// ------------------------------------------------------------ forward kernel
+// Work units q in [0, Q), q = (mt F + f) nchunk + c with K chunk c = d nbc + nb; CTA g
+// takes the contiguous range [Q g / G, Q (g+1) / G).  A segment is the part of one
+// (M-tile, channel) pair inside a CTA's range; its partial sum goes to
+// vpart[segment][j] with j the CTA's rank among the segment's contributors.
+//   producers (warps 0-15): per unit, rows 2u, 2u+1 of the P tile for the 4 groups
+//     u = 4w .. 4w+3 (lane l: hour-angle cells 2l, 2l+1) and rows t = w, w+16, .. of the
+//     Toeplitz sky tile;  full[s] (16 arrivals), then eempty[se] (16 arrivals)
+//   load warp (21): per unit, the E chunk [A][64] by one bulk copy;  efull[se] (tx)
+//   MMA warp (20): 4 K-steps x (1 | 3) MMAs;  commits empty[s] and, at the end of a
+//     chain of HA_SUB units or a segment, accf[q]
+//   epilogue (16-19): adds the chain into the FP32 row sums in shared memory; writes
+//     them at the end of a segment;  acce[q] (4 arrivals)
+template <int ET, bool X3>
+__global__ void __launch_bounds__(HA_THREADS, 1)
+k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t *__restrict__ xs_lo,
+         float *__restrict__ vpart, int *__restrict__ status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    constexpr int NT = X3 ? 2 : 1;
+    float *vacc = reinterpret_cast<float *>(gbase + L.v_off);
+    const uint32_t full0 = base + L.bar_off, empty0 = full0 + 8 * L.nstage;
+    const uint32_t efull0 = empty0 + 8 * L.nstage, eempty0 = efull0 + 8 * L.neslot;
+    const uint32_t accf0 = eempty0 + 8 * L.neslot, acce0 = accf0 + 16;
+    const uint32_t misc = L.bar_off + 16 * (L.nstage + L.neslot) + 32;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + misc + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // B-tile rows t >= T stay zero (producers write rows t < T only)
+    const int zrows = h.npad - h.T;
+    for (int s = 0; s < L.nstage; ++s) {
+        uint8_t *bt = gbase + (size_t)s * L.stage_bytes + NT * L.a_bytes;
+        for (int e = tid; e < NT * zrows * 8; e += HA_THREADS) {
+            const int tl = e / (zrows * 8), r = e % (zrows * 8);
+            reinterpret_cast<uint4 *>(bt + tl * L.b_bytes + (size_t)h.T * 128)[r] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    for (int e = tid; e < 128 * (int)L.vstride; e += HA_THREADS) vacc[e] = 0.f;
+    if (tid == 0) {
+        for (int s = 0; s < L.nstage; ++s) {
+            mbar_init(full0 + 8 * s, HA_PROD_WARPS);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int s = 0; s < L.neslot; ++s) {
+            mbar_init(efull0 + 8 * s, 1);
+            mbar_init(eempty0 + 8 * s, HA_PROD_WARPS);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(accf0 + 8 * q, 1);
+            mbar_init(acce0 + 8 * q, 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == HA_MMA_WARP) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_d = *tmem_slot;
+    const int G = gridDim.x;
+    const long long q0 = range_lo(h.Q, G, blockIdx.x), q1 = range_lo(h.Q, G, blockIdx.x + 1);
+
+    if (warp < HA_PROD_WARPS) {
+        // ------------------------------------------------------------ producers
+        int s = 0, se = 0;
+        uint32_t ph = 0, eph = 0;
+        bool wrapped = false;
+        const uint32_t wsub = (uint32_t)(lane & 3) * 4u;       // lane's word in its 16-byte chunk
+        for (long long q = q0; q < q1; ++q) {
+            const int seg = (int)(q / h.nchunk), c = (int)(q % h.nchunk);
+            const int mt = seg / h.F, f = seg % h.F, d = c / h.nbc, nb = c % h.nbc;
+            // a failed wait has raised the abort flag before returning, so after the
+            // warp barrier every lane takes the same branch
+            mbar_wait_ab(efull0 + 8 * se, eph, abort_flag);
+            if (lane == 0 && wrapped) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
+            __syncwarp();
+            if (*abort_flag) goto done;
+            {
+                uint8_t *st = gbase + (size_t)s * L.stage_bytes;
+                uint8_t *a_hi = st, *a_lo = st + L.a_bytes;
+                uint8_t *b_hi = st + NT * L.a_bytes, *b_lo = b_hi + L.b_bytes;
+                const float4 *Es = reinterpret_cast<const float4 *>(gbase + L.e_off + (size_t)se * L.eslot_bytes);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int ul = 4 * warp + k;
+                    const int2 ij = h.uij[mt * 64 + ul];
+                    float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
+                    if (ij.x >= 0) {
+                        const float4 a = Es[ij.x * 32 + lane], b = Es[ij.y * 32 + lane];
+                        pr0 = fmaf(a.x, b.x, a.y * b.y);
+                        pi0 = fmaf(a.y, b.x, -a.x * b.y);
+                        pr1 = fmaf(a.z, b.z, a.w * b.w);
+                        pi1 = fmaf(a.w, b.z, -a.z * b.w);
+                    }
+                    uint32_t hr, lr, hm, lm;
+                    Elem<ET>::split(pr0, pr1, hr, lr);
+                    Elem<ET>::split(pi0, pi1, hm, lm);
+                    const uint32_t o_re = sw128_off(2 * ul, lane >> 2) + wsub;
+                    const uint32_t o_im = sw128_off(2 * ul + 1, lane >> 2) + wsub;
+                    st32(a_hi + o_re, hr);
+                    st32(a_hi + o_im, hm);
+                    if (X3) {
+                        st32(a_lo + o_re, lr);
+                        st32(a_lo + o_im, lm);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(eempty0 + 8 * se);
+                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(xs_hi + ((size_t)f * h.D + d) * h.L);
+                const uint32_t *l32 = reinterpret_cast<const uint32_t *>(xs_lo + ((size_t)f * h.D + d) * h.L);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int t = warp + HA_PROD_WARPS * k;
+                    if (t >= h.T) break;
+                    const int m0 = 64 * nb - t * h.k + h.P0;     // >= 0 by the choice of P0
+                    const int w = (m0 >> 1) + lane;
+                    const uint32_t h0 = __ldg(h32 + w), h1 = __ldg(h32 + w + 1);
+                    const uint32_t hv = (m0 & 1) ? __byte_perm(h0, h1, 0x5432) : h0;
+                    const uint32_t ob = sw128_off(t, lane >> 2) + wsub;
+                    st32(b_hi + ob, hv);
+                    if (X3) {
+                        const uint32_t l0 = __ldg(l32 + w), l1 = __ldg(l32 + w + 1);
+                        st32(b_lo + ob, (m0 & 1) ? __byte_perm(l0, l1, 0x5432) : l0);
+                    }
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full0 + 8 * s);
+            if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
+            if (++se == L.neslot) { se = 0; eph ^= 1u; }
+        }
+    } else if (warp == HA_LOAD_WARP) {
+        // ------------------------------------------------------------ bulk loads of E chunks
+        if (lane == 0) {
+            int se = 0, last_se = -1;
+            uint32_t eph = 0, last_eph = 0;
+            bool wrapped = false;
+            for (long long q = q0; q < q1; ++q) {
+                const int seg = (int)(q / h.nchunk), c = (int)(q % h.nchunk);
+                const int f = seg % h.F;
+                if (wrapped && !mbar_wait_ab(eempty0 + 8 * se, eph ^ 1u, abort_flag)) break;
+                const float2 *src = h.E + (((size_t)f * h.D * h.nbc + c) * h.A) * 64;
+                mbar_expect_tx(efull0 + 8 * se, L.eslot_bytes);
+                bulk_g2s(base + L.e_off + (uint32_t)se * L.eslot_bytes, src, L.eslot_bytes, efull0 + 8 * se);
+                last_se = se;
+                last_eph = eph;
+                if (++se == L.neslot) { se = 0; eph ^= 1u; wrapped = true; }
+            }
+            // copies still in flight must land before the CTA exits (bounded); without an
+            // abort the producers have already waited for every one of them
+            if (*abort_flag && last_se >= 0) {
+                for (int k = 0; k < L.neslot; ++k) {
+                    int s2 = last_se - k;
+                    uint32_t p2 = last_eph;
+                    if (s2 < 0) { s2 += L.neslot; p2 ^= 1u; }
+                    if ((long long)k < q1 - q0) mbar_drain(efull0 + 8 * s2, p2);
+                }
+            }
+        }
+    } else if (warp == HA_MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, h.npad, Elem<ET>::kFmt);
+            int s = 0, last_s = -1;
+            uint32_t ph = 0, last_ph = 0;
+            long long nacc = 0, local = 0;
+            for (long long q = q0; q < q1; ++q) {
+                const int c = (int)(q % h.nchunk);
+                if (q == q0 || c == 0) local = 0;
+                const bool chain_first = (local % HA_SUB) == 0;
+                const int qa = (int)(nacc & 1);
+                if (chain_first && nacc >= 2 &&
+                    !mbar_wait_ab(acce0 + 8 * qa, (uint32_t)(((nacc >> 1) - 1) & 1), abort_flag))
+                    goto mma_done;
+                if (!mbar_wait_ab(full0 + 8 * s, ph, abort_flag)) goto mma_done;
+                tc_fence_after();
+                {
+                    const uint32_t sa = base + (uint32_t)s * L.stage_bytes;
+                    const uint32_t a_hi = sa, a_lo = sa + L.a_bytes;
+                    const uint32_t b_hi = sa + NT * L.a_bytes, b_lo = b_hi + L.b_bytes;
+                    const uint32_t dacc = tmem_d + (uint32_t)(qa * h.npad);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t dah = sdesc_sw128(a_hi + 32u * kk), dbh = sdesc_sw128(b_hi + 32u * kk);
+                        mma_bf16(dacc, dah, dbh, idesc, (chain_first && kk == 0) ? 0u : 1u);
+                        if (X3) {
+                            mma_bf16(dacc, dah, sdesc_sw128(b_lo + 32u * kk), idesc, 1u);
+                            mma_bf16(dacc, sdesc_sw128(a_lo + 32u * kk), dbh, idesc, 1u);
+                        }
+                    }
+                }
+                mma_commit(empty0 + 8 * s);
+                last_s = s;
+                last_ph = ph;
+                if (++s == L.nstage) { s = 0; ph ^= 1u; }
+                ++local;
+                const bool seg_last = (q == q1 - 1) || (c == h.nchunk - 1);
+                if ((local % HA_SUB) == 0 || seg_last) {
+                    mma_commit(accf0 + 8 * qa);
+                    ++nacc;
+                }
+            }
+        mma_done:
+            if (*abort_flag && last_s >= 0) mbar_drain(empty0 + 8 * last_s, last_ph);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 16-19)
+        const int quarter = warp & 3, row = 32 * quarter + lane;
+        float *vr = vacc + (size_t)row * L.vstride;
+        long long nacc = 0, local = 0;
+        for (long long q = q0; q < q1; ++q) {
+            const int seg = (int)(q / h.nchunk), c = (int)(q % h.nchunk);
+            if (q == q0 || c == 0) local = 0;
+            ++local;
+            const bool seg_last = (q == q1 - 1) || (c == h.nchunk - 1);
+            if (!((local % HA_SUB) == 0 || seg_last)) continue;
+            const int qa = (int)(nacc & 1);
+            mbar_wait_ab(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
+            __syncwarp();
+            if (*abort_flag) goto done;
+            tc_fence_after();
+            const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
+            for (int c16 = 0; c16 < h.npad; c16 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c16, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) vr[c16 + j] += v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * qa);
+            ++nacc;
+            if (seg_last) {
+                const int jrank = blockIdx.x - cta_of((long long)seg * h.nchunk, h.Q, G);
+                float *dst = vpart + (((size_t)seg * h.J + jrank) * 128 + row) * h.npad;
+                for (int t = 0; t < h.T; ++t) {
+                    dst[t] = vr[t];
+                    vr[t] = 0.f;
+                }
+            }
+        }
+    }
+done:
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicExch(status, (int)FM_ERR_TIMEOUT);
+    if (warp == HA_MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tmem_d, (uint32_t)L.ncols);
+    }
+}
+
+// Sum of the forward partials in fixed order, unscaled, expanded to every baseline.
+__global__ void k_ha_vfinish(HaDev h, int B, const float *__restrict__ vpart, const int *__restrict__ ncontrib,
+                             const int *__restrict__ bmap, const float *__restrict__ xscale, float sp,
+                             float *__restrict__ vis)
+{
+    const long long total = (long long)h.F * h.T * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e % B);
+        const long long ft = e / B;
+        const int t = (int)(ft % h.T), f = (int)(ft / h.T);
+        const int code = bmap[b], u = code >> 1;
+        const int seg = (u >> 6) * h.F + f, row = 2 * (u & 63);
+        const int nc = ncontrib[seg];
+        float re = 0.f, im = 0.f;
+        for (int j = 0; j < nc; ++j) {
+            const float *p = vpart + (((size_t)seg * h.J + j) * 128 + row) * h.npad + t;
+            re += p[0];
+            im += p[h.npad];
+        }
+        const float sc = 1.f / (sp * xscale[f]);
+        vis[2 * e] = re * sc;
+        vis[2 * e + 1] = ((code & 1) ? -im : im) * sc;
+    }
+}
+
+// power of two putting the largest |x| of a channel below 2^14, one CTA per channel
+__global__ void __launch_bounds__(256) k_ha_xscale(int npix, const float *__restrict__ x, float *__restrict__ scale)
+{
+    __shared__ float red[256];
+    const int f = blockIdx.x;
+    float m = 0.f;
+    for (int p = threadIdx.x; p < npix; p += blockDim.x) m = fmaxf(m, fabsf(x[(size_t)f * npix + p]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float sc = 1.f;
+        if (red[0] > 0.f && isfinite(red[0])) {
+            int e;
+            frexpf(red[0], &e);
+            sc = ldexpf(1.f, 14 - e);
+        }
+        scale[f] = sc;
+    }
+}
+
+// ------------------------------------------------------------ adjoint operand prep
+// Q_u(f, t) = sum of omega over the group's members (conjugated for reversed ones) and
+// the per-channel max |Re|, |Im| (non-negative floats order like their bit patterns).
+__global__ void k_ha_qsum(HaDev h, int B, const float *__restrict__ omega, const int *__restrict__ moff,
+                          const int *__restrict__ mem, float *__restrict__ q32, unsigned *__restrict__ qmax)
+{
+    const long long total = (long long)h.F * h.T * h.U;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(e % h.U);
+        const long long ft = e / h.U;
+        const float *om = omega + (size_t)ft * B * 2;
+        float re = 0.f, im = 0.f;
+        for (int m = moff[u]; m < moff[u + 1]; ++m) {
+            const int code = mem[m], b = code >> 1;
+            re += om[2 * b];
+            im += (code & 1) ? -om[2 * b + 1] : om[2 * b + 1];
+        }
+        q32[2 * e] = re;
+        q32[2 * e + 1] = im;
+        const int f = (int)(ft / h.T);
+        atomicMax(qmax + f, __float_as_uint(fmaxf(fabsf(re), fabsf(im))));
+    }
+}
+
+// power of two putting max |Q| below 2^14
+__device__ __forceinline__ float pow2_scale(float mx)
+{
+    float sc = 1.f;
+    if (mx > 0.f && isfinite(mx)) {
+        int e;
+        frexpf(mx, &e);
+        sc = ldexpf(1.f, 14 - e);
+    }
+    return sc;
+}
+
+// One CTA per (channel, K chunk): the swizzled B tile [npad rows t][64 rho] of the
+// adjoint, hi then (x3) lo, ready for one bulk copy.
+template <int ET, bool X3>
+__global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const unsigned *__restrict__ qmax,
+                          float *__restrict__ qscale, uint8_t *__restrict__ qimg)
+{
+    constexpr int NT = X3 ? 2 : 1;
+    const int f = blockIdx.x / h.nkq, kq = blockIdx.x % h.nkq;
+    const float sc = pow2_scale(__uint_as_float(qmax[f]));
+    if (kq == 0 && threadIdx.x == 0) qscale[f] = sc;
+    const uint32_t b_bytes = (uint32_t)h.npad * 128u;
+    uint8_t *img = qimg + ((size_t)f * h.nkq + kq) * NT * b_bytes;
+    for (int e = threadIdx.x; e < h.npad * 8; e += blockDim.x) {
+        const int t = e >> 3, ch = e & 7;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int u = 32 * kq + 4 * ch + q;
+            float re = 0.f, im = 0.f;
+            if (t < h.T && u < h.U) {
+                const float *p = q32 + (((size_t)f * h.T + t) * h.U + u) * 2;
+                re = p[0] * sc;
+                im = p[1] * sc;
+            }
+            Elem<ET>::split(re, im, hw[q], lw[q]);
+        }
+        const uint32_t off = sw128_off(t, ch);
+        *reinterpret_cast<uint4 *>(img + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if (X3) *reinterpret_cast<uint4 *>(img + b_bytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
+// ------------------------------------------------------------ adjoint kernel
+// Items (f, d), CTA g takes items g, g + G, ...; per item the nhp / 128 M-tiles of 128
+// hour-angle cells, per M-tile the nkq K chunks of 64 rho = 32 groups.
+//   load warp (21): per M-tile, the two E chunks (bulk, efull[se]); per K chunk, the
+//     Q tile into the stage's B part (bulk, bfull[s])
+//   producers (0-15): thread (row n = tid & 127, quarter = tid >> 7) writes the 8 groups
+//     8 quarter .. +7 of row n (two 16-byte words hi, two lo);  then full[s]
+//   MMA warp (20): D[n][t] of the M-tile into TMEM set (M-tile count & 1);  accf[q]
+//   epilogue (16-19): warp w holds rows n = 32 (w & 3) + lane; the diagonal sums
+//     S(j) = sum_t D[t k + 31 - j][t] of its 32 rows are carried across lanes by shfl_up
+//     and written once each into xacc; after the item (named barrier over the 4 warps,
+//     OR-reduced abort) every r of the row sums the xacc entries that cover it.
+template <int ET, bool X3>
+__global__ void __launch_bounds__(HA_THREADS, 1)
+k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__restrict__ qscale, float sp,
+         float *__restrict__ xbar, int *__restrict__ status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    constexpr int NT = X3 ? 2 : 1;
+    float *xacc = reinterpret_cast<float *>(gbase + L.v_off);    // [2][4][nmta][jw]
+    const uint32_t full0 = base + L.bar_off, empty0 = full0 + 8 * L.nstage;
+    const uint32_t efull0 = empty0 + 8 * L.nstage, eempty0 = efull0 + 8 * L.neslot;
+    const uint32_t accf0 = eempty0 + 8 * L.neslot, acce0 = accf0 + 16;
+    const uint32_t bfull0 = acce0 + 16;
+    const uint32_t misc = L.bar_off + 16 * (L.nstage + L.neslot) + 32 + 8 * L.nstage;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + misc + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < L.nstage; ++s) {
+            mbar_init(full0 + 8 * s, HA_PROD_WARPS);
+            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(bfull0 + 8 * s, 1);
+        }
+        for (int s = 0; s < L.neslot; ++s) {
+            mbar_init(efull0 + 8 * s, 1);
+            mbar_init(eempty0 + 8 * s, HA_PROD_WARPS);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(accf0 + 8 * q, 1);
+            mbar_init(acce0 + 8 * q, 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == HA_MMA_WARP) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_d = *tmem_slot;
+    const int nitem = h.F * h.D, nmta = h.nhp / 128;
+    const uint32_t echunk = (uint32_t)h.A * 512u;
+
+    if (warp < HA_PROD_WARPS) {
+        // ------------------------------------------------------------ producers
+        const int n = tid & 127, qq = tid >> 7;
+        int s = 0, se = 0;
+        uint32_t ph = 0, eph = 0;
+        bool wrapped = false;
+        for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+            for (int mt = 0; mt < nmta; ++mt) {
+                mbar_wait_ab(efull0 + 8 * se, eph, abort_flag);
+                __syncwarp();
+                if (*abort_flag) goto done;
+                const uint8_t *es = gbase + L.e_off + (size_t)se * L.eslot_bytes + (size_t)(n >> 6) * echunk +
+                                    (size_t)(n & 63) * 8;
+                for (int kq = 0; kq < h.nkq; ++kq) {
+                    if (lane == 0 && wrapped) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
+                    __syncwarp();
+                    if (*abort_flag) goto done;
+                    uint8_t *st = gbase + (size_t)s * L.stage_bytes;
+                    uint32_t hw[8], lw[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int2 ij = h.uij[32 * kq + 8 * qq + q];
+                        float pr = 0.f, pim = 0.f;
+                        if (ij.x >= 0) {
+                            const float2 a = *reinterpret_cast<const float2 *>(es + (size_t)ij.x * 512);
+                            const float2 b = *reinterpret_cast<const float2 *>(es + (size_t)ij.y * 512);
+                            pr = fmaf(a.x, b.x, a.y * b.y);
+                            pim = fmaf(a.y, b.x, -a.x * b.y);
+                        }
+                        Elem<ET>::split(pr, pim, hw[q], lw[q]);
+                    }
+                    const uint32_t o0 = sw128_off(n, 2 * qq), o1 = sw128_off(n, 2 * qq + 1);
+                    *reinterpret_cast<uint4 *>(st + o0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(st + o1) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+                    if (X3) {
+                        *reinterpret_cast<uint4 *>(st + L.a_bytes + o0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        *reinterpret_cast<uint4 *>(st + L.a_bytes + o1) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(full0 + 8 * s);
+                    if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(eempty0 + 8 * se);
+                if (++se == L.neslot) { se = 0; eph ^= 1u; }
+            }
+        }
+    } else if (warp == HA_LOAD_WARP) {
+        // ------------------------------------------------------------ bulk loads
+        if (lane == 0) {
+            int s = 0, se = 0, last_s = -1, last_se = -1;
+            uint32_t ph = 0, eph = 0, last_ph = 0, last_eph = 0;
+            bool wrapped = false, ewrapped = false;
+            long long ns = 0, nse = 0;
+            const uint32_t bbytes = NT * L.b_bytes;
+            for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+                const int f = it / h.D, d = it % h.D;
+                for (int mt = 0; mt < nmta; ++mt) {
+                    if (ewrapped && !mbar_wait_ab(eempty0 + 8 * se, eph ^ 1u, abort_flag)) goto load_done;
+                    const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + 2 * mt) * h.A * 64;
+                    const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes;
+                    mbar_expect_tx(efull0 + 8 * se, 2 * echunk);
+                    bulk_g2s(dst, src, echunk, efull0 + 8 * se);
+                    bulk_g2s(dst + echunk, src + (size_t)h.A * 64, echunk, efull0 + 8 * se);
+                    last_se = se;
+                    last_eph = eph;
+                    ++nse;
+                    if (++se == L.neslot) { se = 0; eph ^= 1u; ewrapped = true; }
+                    for (int kq = 0; kq < h.nkq; ++kq) {
+                        if (wrapped && !mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag)) goto load_done;
+                        mbar_expect_tx(bfull0 + 8 * s, bbytes);
+                        bulk_g2s(base + (uint32_t)s * L.stage_bytes + NT * L.a_bytes,
+                                 qimg + ((size_t)f * h.nkq + kq) * bbytes, bbytes, bfull0 + 8 * s);
+                        last_s = s;
+                        last_ph = ph;
+                        ++ns;
+                        if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
+                    }
+                }
+            }
+        load_done:
+            // copies in flight land before the CTA exits (bounded)
+            if (*abort_flag) {
+                for (int k = 0; k < L.neslot && k < nse; ++k) {
+                    int s2 = last_se - k;
+                    uint32_t p2 = last_eph;
+                    if (s2 < 0) { s2 += L.neslot; p2 ^= 1u; }
+                    mbar_drain(efull0 + 8 * s2, p2);
+                }
+                for (int k = 0; k < L.nstage && k < ns; ++k) {
+                    int s2 = last_s - k;
+                    uint32_t p2 = last_ph;
+                    if (s2 < 0) { s2 += L.nstage; p2 ^= 1u; }
+                    mbar_drain(bfull0 + 8 * s2, p2);
+                }
+            }
+        }
+    } else if (warp == HA_MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, h.npad, Elem<ET>::kFmt);
+            int s = 0, last_s = -1;
+            uint32_t ph = 0, last_ph = 0;
+            long long nacc = 0;
+            for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+                for (int mt = 0; mt < nmta; ++mt) {
+                    const int qa = (int)(nacc & 1);
+                    if (nacc >= 2 && !mbar_wait_ab(acce0 + 8 * qa, (uint32_t)(((nacc >> 1) - 1) & 1), abort_flag))
+                        goto mma_done;
+                    const uint32_t dacc = tmem_d + (uint32_t)(qa * h.npad);
+                    for (int kq = 0; kq < h.nkq; ++kq) {
+                        if (!mbar_wait_ab(full0 + 8 * s, ph, abort_flag)) goto mma_done;
+                        if (!mbar_wait_ab(bfull0 + 8 * s, ph, abort_flag)) goto mma_done;
+                        tc_fence_after();
+                        const uint32_t sa = base + (uint32_t)s * L.stage_bytes;
+                        const uint32_t a_hi = sa, a_lo = sa + L.a_bytes;
+                        const uint32_t b_hi = sa + NT * L.a_bytes, b_lo = b_hi + L.b_bytes;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t dah = sdesc_sw128(a_hi + 32u * kk), dbh = sdesc_sw128(b_hi + 32u * kk);
+                            mma_bf16(dacc, dah, dbh, idesc, (kq == 0 && kk == 0) ? 0u : 1u);
+                            if (X3) {
+                                mma_bf16(dacc, dah, sdesc_sw128(b_lo + 32u * kk), idesc, 1u);
+                                mma_bf16(dacc, sdesc_sw128(a_lo + 32u * kk), dbh, idesc, 1u);
+                            }
+                        }
+                        mma_commit(empty0 + 8 * s);
+                        last_s = s;
+                        last_ph = ph;
+                        if (++s == L.nstage) { s = 0; ph ^= 1u; }
+                    }
+                    mma_commit(accf0 + 8 * qa);
+                    ++nacc;
+                }
+            }
+        mma_done:
+            if (*abort_flag && last_s >= 0) mbar_drain(empty0 + 8 * last_s, last_ph);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 16-19)
+        const int quarter = warp & 3, et = tid - 32 * HA_EPI_WARP0;     // 0..127
+        const int jw = (int)L.jw;
+        long long nacc = 0;
+        int ni = 0;
+        for (int it = blockIdx.x; it < nitem; it += gridDim.x, ++ni) {
+            const int f = it / h.D, d = it % h.D;
+            float *xb = xacc + (size_t)(ni & 1) * 4 * nmta * jw;
+            bool fail = false;
+            for (int mt = 0; mt < nmta; ++mt, ++nacc) {
+                const int qa = (int)(nacc & 1);
+                if (fail) continue;
+                mbar_wait_ab(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
+                __syncwarp();
+                if (*abort_flag) { fail = true; continue; }
+                tc_fence_after();
+                float *xw = xb + ((size_t)quarter * nmta + mt) * jw;
+                const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
+                float acc = 0.f;
+                for (int c16 = 0; c16 < h.npad; c16 += 16) {
+                    float v[16];
+                    tmem_ld16(taddr + (uint32_t)c16, v);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int t = c16 + q;
+                        if (t < h.T) {
+                            if (t > 0) {
+                                // lanes >= 32 - k hold finished sums j = t' k - lane + 31 (t' = t - 1)
+                                if (lane >= 32 - h.k) xw[(t - 1) * h.k - lane + 31] = acc;
+                                const float up = __shfl_up_sync(0xffffffffu, acc, h.k);
+                                acc = (lane >= h.k) ? up : 0.f;
+                            }
+                            acc += v[q];
+                        }
+                    }
+                }
+                xw[(h.T - 1) * h.k - lane + 31] = acc;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * qa);
+            }
+            if (bar_or(1, 128, fail || *abort_flag != 0)) break;
+            const float sc = 1.f / (sp * qscale[f]);
+            for (int r = et; r < h.R; r += 128) {
+                float sum = 0.f;
+                for (int mt = 0; mt < nmta; ++mt)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int j = r - (h.R - 32 - 128 * mt - 32 * w);
+                        if (j >= 0 && j < jw) sum += xb[((size_t)w * nmta + mt) * jw + j];
+                    }
+                xbar[((size_t)f * h.D + d) * h.R + r] = sum * sc;
+            }
+        }
+    }
+done:
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicExch(status, (int)FM_ERR_TIMEOUT);
+    if (warp == HA_MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tmem_d, (uint32_t)L.ncols);
+    }
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+}
+
+HaDev make_dev(const Ctx &c)
+{
+    const HaState &s = c.ha;
+    HaDev h;
+    h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = c.A; h.U = s.U; h.k = s.k;
+    h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.P0 = s.P0; h.L = s.L;
+    h.nchunk = c.D * s.nbc; h.nmt = s.nmt; h.nkq = s.nkq; h.J = s.J;
+    h.Q = (long long)s.nmt * c.F * h.nchunk;
+    h.E = s.E; h.uij = s.uij;
+    return h;
+}
+
+bool x3_of(int prec) { return prec == FM_PREC_BF16X3 || prec == FM_PREC_FP16X3; }
+bool f16_of(int prec) { return prec == FM_PREC_FP16X1 || prec == FM_PREC_FP16X3; }
+
+// shared-memory layout common to both kernels; `vbytes` is the epilogue's scratch
+bool make_layout(const Ctx &c, bool x3, uint32_t eslot_bytes, uint32_t vbytes, HaLayout &L)
+{
+    const int nt = x3 ? 2 : 1;
+    L.a_bytes = 128u * 128u;
+    L.b_bytes = (uint32_t)c.ha.npad * 128u;
+    L.stage_bytes = nt * (L.a_bytes + L.b_bytes);
+    L.eslot_bytes = eslot_bytes;
+    L.neslot = 2;
+    L.ncols = 32;
+    while (L.ncols < 2 * c.ha.npad) L.ncols *= 2;
+    const size_t fixed = 2 * (size_t)eslot_bytes + ((vbytes + 15) / 16) * 16 + 256;
+    if (fixed + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET) return false;
+    L.nstage = (int)((HA_SMEM_BUDGET - fixed) / L.stage_bytes);
+    if (L.nstage > 4) L.nstage = 4;
+    L.e_off = (uint32_t)L.nstage * L.stage_bytes;
+    L.v_off = L.e_off + 2 * eslot_bytes;
+    L.bar_off = L.v_off + ((vbytes + 15) / 16) * 16;
+    L.smem = 1024 + (size_t)L.bar_off + 24 * L.nstage + 16 * L.neslot + 32 + 16;
+    return L.smem <= 227 * 1024;
+}
+
+template <int ET, bool X3>
+fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cudaStream_t st)
+{
+    HaState &s = c.ha;
+    HaLayout L;
+    if (!make_layout(c, X3, (uint32_t)c.A * 512u, 128u * (uint32_t)(s.npad + 1) * 4u, L)) {
+        set_error("hour-angle forward tiles exceed shared memory");
+        return FM_ERR_UNSUPPORTED;
+    }
+    L.vstride = (uint32_t)s.npad + 1;
+    L.jw = 0;
+    uint16_t *xs_hi = s.xs, *xs_lo = s.xs + (size_t)c.F * c.D * s.L;
+    k_ha_xscale<<<c.F, 256, 0, st>>>(c.npix, x, s.xscale);
+    FM_CK_LAUNCH();
+    k_ha_xprep<ET><<<1024, 256, 0, st>>>(h, x, s.xscale, xs_hi, xs_lo);
+    FM_CK_LAUNCH();
+    FM_CK(cudaFuncSetAttribute(k_vis_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
+        k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(h, L, xs_hi, xs_lo, s.vpart, c.status);
+        FM_CK_LAUNCH();
+        return FM_OK;
+    }));
+    k_ha_vfinish<<<1024, 256, 0, st>>>(h, c.B, s.vpart, s.ncontrib, s.bmap, s.xscale, s.sp, vis);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+template <int ET, bool X3>
+fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar, cudaStream_t st)
+{
+    HaState &s = c.ha;
+    const int nmta = s.nhp / 128;
+    const uint32_t jw = (uint32_t)((c.T - 1) * s.k + 32);
+    HaLayout L;
+    if (!make_layout(c, X3, 2u * (uint32_t)c.A * 512u, 2u * 4u * (uint32_t)nmta * jw * 4u, L)) {
+        set_error("hour-angle adjoint tiles exceed shared memory");
+        return FM_ERR_UNSUPPORTED;
+    }
+    L.vstride = 0;
+    L.jw = jw;
+    FM_CK(cudaMemsetAsync(s.qmax, 0, sizeof(unsigned) * c.F, st));
+    k_ha_qsum<<<1024, 256, 0, st>>>(h, c.B, omega, s.moff, s.mem, s.q32, s.qmax);
+    FM_CK_LAUNCH();
+    k_ha_qimg<ET, X3><<<c.F * s.nkq, 256, 0, st>>>(h, s.q32, s.qmax, s.qscale, s.qimg);
+    FM_CK_LAUNCH();
+    int grid = sm_count();
+    if (grid > c.F * c.D) grid = c.F * c.D;
+    FM_CK(cudaFuncSetAttribute(k_adj_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    FM_TRY(profiled(c, 1, st, [&]() -> fm_status {
+        k_adj_ha<ET, X3><<<grid, HA_THREADS, L.smem, st>>>(h, L, s.qimg, s.qscale, s.sp, xbar, c.status);
+        FM_CK_LAUNCH();
+        return FM_OK;
+    }));
+    return FM_OK;
+}
+
+}  // namespace
+
+template <typename T>
+static fm_status ha_alloc(Ctx &c, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (hour-angle path)", __FILE__, __LINE__);
+    c.allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return FM_OK;
+}
+
+// Geometry test, fringe groups, work partition and the per-handle phasor table.  The
+// path is used for the tensor-core precisions when the LSTs are equally spaced by
+// k = 1 .. 32 RA pixels, n_ant <= 64, n_lst <= 64 and the buffers take at most half of
+// the free device memory; otherwise c.ha.on stays false and the antenna form runs.
+fm_status ha_setup(Ctx &c)
+{
+    HaState &s = c.ha;
+    s.on = false;
+    if (c.prec < FM_PREC_BF16X1) return FM_OK;
+    if (const char *e = getenv("FM_HA"))
+        if (atoi(e) == 0) return FM_OK;
+    if (c.A < 2 || c.A > 64 || c.T > 64) return FM_OK;
+    const double dra = (c.cfg.ra_max - c.cfg.ra_min) / c.R;
+    int k = 1;
+    if (c.T > 1) {
+        const double dl = c.lst[1] - c.lst[0];
+        for (int t = 1; t < c.T; ++t)
+            if (std::fabs(c.lst[t] - c.lst[0] - t * dl) > 1e-9 * dra) return FM_OK;
+        const double kr = dl / dra;
+        k = (int)std::llround(kr);
+        if (k < 1 || k > 32 || std::fabs(kr - k) > 1e-9 * k) return FM_OK;
+    }
+    s.k = k;
+    s.nh = c.R + (c.T - 1) * k;
+    s.nhp = (s.nh + 127) / 128 * 128;
+    s.nbc = s.nhp / 64;
+    s.npad = (c.T + 15) / 16 * 16;
+    if (s.npad < 16) s.npad = 16;
+    s.P0 = ((c.T - 1) * k + 1) / 2 * 2;
+    s.L = s.P0 + s.nhp + 8;
+
+    // fringe groups: equal baseline vectors (to 1 nm) up to sign
+    bool group = true;
+    if (const char *e = getenv("FM_HA_GROUPS"))
+        if (atoi(e) == 0) group = false;
+    std::vector<int> rep_i, rep_j, bmap(c.B);
+    std::vector<double> rep_b;
+    std::vector<std::vector<int>> members;
+    for (int i = 0, b = 0; i < c.A; ++i)
+        for (int j = i + 1; j < c.A; ++j, ++b) {
+            const double v0 = c.ant[3 * i] - c.ant[3 * j], v1 = c.ant[3 * i + 1] - c.ant[3 * j + 1],
+                         v2 = c.ant[3 * i + 2] - c.ant[3 * j + 2];
+            int found = -1, cj = 0;
+            if (group)
+                for (size_t u = 0; u < rep_i.size() && found < 0; ++u) {
+                    const double *r = &rep_b[3 * u];
+                    const double dp = std::fmax(std::fabs(v0 - r[0]), std::fmax(std::fabs(v1 - r[1]), std::fabs(v2 - r[2])));
+                    const double dm = std::fmax(std::fabs(v0 + r[0]), std::fmax(std::fabs(v1 + r[1]), std::fabs(v2 + r[2])));
+                    if (dp < 1e-9) { found = (int)u; cj = 0; }
+                    else if (dm < 1e-9) { found = (int)u; cj = 1; }
+                }
+            if (found < 0) {
+                found = (int)rep_i.size();
+                rep_i.push_back(i);
+                rep_j.push_back(j);
+                rep_b.push_back(v0);
+                rep_b.push_back(v1);
+                rep_b.push_back(v2);
+                members.emplace_back();
+            }
+            bmap[b] = 2 * found + cj;
+            members[found].push_back(2 * b + cj);
+        }
+    s.U = (int)rep_i.size();
+    s.nmt = (s.U + 63) / 64;
+    s.nkq = (s.U + 31) / 32;
+
+    // partition of the forward work units over the CTAs
+    const int nchunk = c.D * s.nbc;
+    const long long Q = (long long)s.nmt * c.F * nchunk;
+    int G = sm_count();
+    if (G > Q) G = (int)Q;
+    s.grid = G;
+    std::vector<int> ncontrib((size_t)s.nmt * c.F);
+    s.J = 1;
+    for (size_t seg = 0; seg < ncontrib.size(); ++seg) {
+        const int g0 = cta_of((long long)seg * nchunk, Q, G), g1 = cta_of((long long)(seg + 1) * nchunk - 1, Q, G);
+        ncontrib[seg] = g1 - g0 + 1;
+        if (ncontrib[seg] > s.J) s.J = ncontrib[seg];
+    }
+
+    // device memory, all of it within half of what is free
+    const size_t e_n = (size_t)c.F * c.D * s.nhp * c.A;
+    const size_t xs_n = 2 * (size_t)c.F * c.D * s.L;
+    const size_t vp_n = (size_t)s.nmt * c.F * s.J * 128 * s.npad;
+    const size_t q_n = (size_t)c.F * c.T * s.U * 2;
+    const size_t qi_n = (size_t)c.F * s.nkq * 2 * s.npad * 128;
+    const size_t need = e_n * 8 + xs_n * 2 + vp_n * 4 + q_n * 4 + qi_n + (size_t)c.B * 16 + (size_t)s.nmt * 64 * 8;
+    size_t fr = 0, tot = 0;
+    FM_CK(cudaMemGetInfo(&fr, &tot));
+    if (need > fr / 2) return FM_OK;
+
+    FM_TRY(ha_alloc(c, &s.E, e_n));
+    FM_TRY(ha_alloc(c, &s.uij, (size_t)s.nmt * 64));
+    FM_TRY(ha_alloc(c, &s.bmap, (size_t)c.B));
+    FM_TRY(ha_alloc(c, &s.moff, (size_t)s.U + 1));
+    FM_TRY(ha_alloc(c, &s.mem, (size_t)c.B));
+    FM_TRY(ha_alloc(c, &s.ncontrib, ncontrib.size()));
+    FM_TRY(ha_alloc(c, &s.xs, xs_n));
+    FM_TRY(ha_alloc(c, &s.xscale, (size_t)c.F));
+    FM_TRY(ha_alloc(c, &s.vpart, vp_n));
+    FM_TRY(ha_alloc(c, &s.q32, q_n));
+    FM_TRY(ha_alloc(c, &s.qmax, (size_t)c.F));
+    FM_TRY(ha_alloc(c, &s.qscale, (size_t)c.F));
+    FM_TRY(ha_alloc(c, &s.qimg, qi_n));
+
+    std::vector<int2> huij((size_t)s.nmt * 64, make_int2(-1, -1));
+    for (int u = 0; u < s.U; ++u) huij[u] = make_int2(rep_i[u], rep_j[u]);
+    std::vector<int> hoff(s.U + 1, 0), hmem;
+    hmem.reserve(c.B);
+    for (int u = 0; u < s.U; ++u) {
+        hoff[u] = (int)hmem.size();
+        for (int m : members[u]) hmem.push_back(m);
+    }
+    hoff[s.U] = (int)hmem.size();
+    FM_CK(cudaMemcpy(s.uij, huij.data(), sizeof(int2) * huij.size(), cudaMemcpyHostToDevice));
+    FM_CK(cudaMemcpy(s.bmap, bmap.data(), sizeof(int) * bmap.size(), cudaMemcpyHostToDevice));
+    FM_CK(cudaMemcpy(s.moff, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice));
+    FM_CK(cudaMemcpy(s.mem, hmem.data(), sizeof(int) * hmem.size(), cudaMemcpyHostToDevice));
+    FM_CK(cudaMemcpy(s.ncontrib, ncontrib.data(), sizeof(int) * ncontrib.size(), cudaMemcpyHostToDevice));
+
+    // response scale 2^e, e even, with 2^e dOmega_max <= 2^14 (the beam is at most 1)
+    int e2 = 0;
+    if (c.domega_max > 0.f) {
+        e2 = (int)std::floor(std::log2(16384.0 / (double)c.domega_max));
+        if (e2 & 1) --e2;
+    }
+    s.sp = (float)std::ldexp(1.0, e2);
+    HaTabArgs a;
+    a.F = c.F; a.D = c.D; a.R = c.R; a.A = c.A; a.nh = s.nh; a.nhp = s.nhp; a.nbc = s.nbc;
+    a.lst0 = c.lst[0]; a.ra_min = c.cfg.ra_min; a.dra = dra;
+    a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D;
+    a.lat = c.cfg.latitude_rad; a.amp_scale = std::ldexp(1.0, e2 / 2);
+    a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
+    k_ha_table<<<2048, 256>>>(a, s.E);
+    FM_CK_LAUNCH();
+    FM_CK(cudaDeviceSynchronize());
+    s.on = true;
+    return FM_OK;
+}
+
+fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st)
+{
+    const HaDev h = make_dev(c);
+    const bool x3 = x3_of(c.prec);
+    if (f16_of(c.prec)) return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st) : vis_ha_launch<1, false>(c, h, x, vis, st);
+    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st) : vis_ha_launch<0, false>(c, h, x, vis, st);
+}
+
+fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st)
+{
+    const HaDev h = make_dev(c);
+    const bool x3 = x3_of(c.prec);
+    if (f16_of(c.prec))
+        return x3 ? adj_ha_launch<1, true>(c, h, omega, xbar, st) : adj_ha_launch<1, false>(c, h, omega, xbar, st);
+    return x3 ? adj_ha_launch<0, true>(c, h, omega, xbar, st) : adj_ha_launch<0, false>(c, h, omega, xbar, st);
+}
+
+}  // namespace fm

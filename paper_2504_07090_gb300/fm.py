@@ -30,7 +30,9 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x1": 2, "bf16x3": 3, "fp16x1": 4, "fp16
 EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_data", "fm_set_prior", "fm_forward",
            "fm_forward_pixels", "fm_sky_pixels", "fm_chi2_grad", "fm_hvp", "fm_build_precond", "fm_get_precond_blocks",
            "fm_precond_size", "fm_leapfrog", "fm_precond_apply", "fm_set_profiling", "fm_get_profile",
-           "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status", "fm_last_error"]
+           "fm_contraction_info", "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status",
+           "fm_last_error"]
+CONTRACTION_FORMS = {0: "direct", 1: "antenna", 2: "hour_angle"}
 
 
 class FmError(RuntimeError):
@@ -87,6 +89,7 @@ def load(path: str = LIB_PATH):
     L.fm_set_profiling.argtypes = [vp, c_int]
     L.fm_get_profile.argtypes = [vp, POINTER(c_double), POINTER(c_int64)]
     L.fm_sky_pixels_noalloc.argtypes = [c_int, c_int, c_int, c_int, c_int, vp, vp, vp, vp, vp]
+    L.fm_contraction_info.argtypes = [vp, POINTER(ctypes.c_int32)]
     L.fm_kernel_launches.argtypes = []
     L.fm_kernel_launches.restype = c_int64
     L.fm_last_error.restype = ctypes.c_char_p
@@ -245,6 +248,13 @@ class ForwardModel:
         cnt = (c_int64 * 2)()
         _check(self.lib.fm_get_profile(self.h, ms, cnt), "fm_get_profile")
         return (ms[0], ms[1]), (int(cnt[0]), int(cnt[1]))
+
+    def contraction_info(self) -> dict:
+        """Form of the fringe contraction this handle runs (fm_contraction_info)."""
+        out = (ctypes.c_int32 * 4)()
+        _check(self.lib.fm_contraction_info(self.h, out), "fm_contraction_info")
+        return {"form": CONTRACTION_FORMS[int(out[0])], "fringes": int(out[1]), "lst_step_pixels": int(out[2]),
+                "hour_angle_cells": int(out[3])}
 
     def sync_status(self):
         _check(self.lib.fm_sync_status(self.h, _stream()), "fm_sync_status")

@@ -169,6 +169,22 @@ def config(name: str) -> Problem:
         # the cfg1 array (37 antennas: two 64-wide K atoms in the adjoint tiles) on a small
         # grid, 8 equally spaced channels (frequency-recurrence groups), ragged pixel tail
         return drift_scan_problem("ant37", 4, 8, 146e6, 153e6, 3, 20, 58, 16, 8, 50, 17)
+    if name == "ha7":
+        # drift-scan grid with the LST step equal to 2 RA pixels (5 LSTs 3 deg apart,
+        # 32 RA cells of 1.5 deg): the hour-angle form with stride 2; 7-antenna hexagon
+        # (21 baselines in 9 distinct vectors), odd declination count
+        return drift_scan_problem("ha7", 2, 4, 150e6, 156e6, 5, 9, 32, 8, 4, 20, 21)
+    if name == "ha37":
+        # the cfg1 array (666 baselines, 63 distinct vectors) with the LST step equal to
+        # one RA pixel (10 LSTs, 32 RA cells of 1.5 deg)
+        return drift_scan_problem("ha37", 4, 3, 148e6, 152e6, 10, 7, 32, 8, 4, 20, 23)
+    if name == "harand":
+        # 12 antennas at seeded random east/north/up offsets (66 distinct baselines: two
+        # forward M-tiles, the second ragged), LST step equal to one RA pixel
+        rng = np.random.default_rng(29)
+        ant = np.column_stack([rng.uniform(-40.0, 40.0, 12), rng.uniform(-40.0, 40.0, 12),
+                               rng.uniform(-0.5, 0.5, 12)])
+        return drift_scan_problem("harand", 2, 3, 150e6, 155e6, 5, 6, 16, 8, 4, 20, 29, ant_enu=ant)
     raise KeyError(name)
 
 

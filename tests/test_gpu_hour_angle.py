@@ -1,0 +1,116 @@
+"""Hour-angle form of the tensor-core contraction (drift scans whose LST step is a whole
+number of RA pixels) against the FP64 oracle, element by element.
+
+ha7: 7-antenna hexagon, LST step 2 pixels (9 baseline groups); ha37: the 37-antenna
+hexagon, step 1 (63 groups, 666 baselines); harand: 12 antennas at random 3-D offsets
+(66 groups: two forward M-tiles, three adjoint K chunks).  Each runs with baseline
+grouping on and off (FM_HA_GROUPS=0: every baseline its own group, 11 M-tiles and 21 K
+chunks for ha37), at the tolerances of the antenna form."""
+import numpy as np
+import pytest
+
+from gpu_cases import TOL_GRAD, TOL_VIS, as_complex, handle, make_case, perturbed, quant, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = {"ha7": (9, 21, 2), "ha37": (63, 666, 1), "harand": (66, 66, 1)}
+PRECS = ["bf16x1", "bf16x3", "fp16x1", "fp16x3"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2504_07090_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _t(a, h):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=h.dtype, device="cuda").contiguous()
+
+
+def _groups(monkeypatch, on):
+    monkeypatch.setenv("FM_HA_GROUPS", "1" if on else "0")
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("grouped", [True, False])
+def test_handle_runs_the_hour_angle_form(name, grouped, monkeypatch):
+    _groups(monkeypatch, grouped)
+    p, o, th, d, mu, lam = make_case(name)
+    info = handle(p, "fp16x3").contraction_info()
+    ng, nb, k = CASES[name]
+    assert info["form"] == "hour_angle"
+    assert info["fringes"] == (ng if grouped else nb)
+    assert info["lst_step_pixels"] == k
+    assert info["hour_angle_cells"] % 128 == 0 and info["hour_angle_cells"] >= p.n_ra + (p.n_lst - 1) * k
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("grouped", [True, False])
+def test_forward_pixels_matches_oracle(name, prec, grouped, monkeypatch):
+    _groups(monkeypatch, grouped)
+    p, o, th, d, mu, lam = make_case(name)
+    h = handle(p, prec)
+    a, _ = o.split(th)
+    x = quant(prec, o.sky(a))
+    got = as_complex(h.forward_pixels(_t(x, h)))
+    assert rel_l2(got, o.vis(x)) < TOL_VIS[prec]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("grouped", [True, False])
+def test_chi2_and_gradient_match_oracle(name, prec, grouped, monkeypatch):
+    _groups(monkeypatch, grouped)
+    p, o, th, d, mu, lam = make_case(name)
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 2))
+    chi2, U, g = o.chi2_grad(th, d, mu, lam)
+    scal, grad = h.chi2_grad(_t(th, h))
+    scal = scal.cpu().numpy()
+    dm = TOL_VIS[prec] * np.linalg.norm(o.model(th)) / o.sigma
+    bound = 2.0 * (2.0 * np.sqrt(chi2) * dm + dm * dm) + 1e-12 * chi2
+    assert abs(scal[0] - chi2) < bound
+    assert rel_l2(grad.cpu().numpy(), g) < TOL_GRAD[prec]
+    h.sync_status()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("full", [True, False])
+def test_hvp_matches_oracle(prec, full):
+    p, o, th, d, mu, lam = make_case("ha37")
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    th = quant(prec, perturbed(o, th, 0.01, 3))
+    v = quant(prec, perturbed(o, np.zeros_like(th), 1.0, 4))
+    got = h.hvp(_t(th, h), _t(v, h), full=full).cpu().numpy()
+    assert rel_l2(got, o.hvp(th, d, v, lam, full=full)) < TOL_GRAD[prec]
+
+
+def test_repeat_runs_are_bitwise_identical():
+    p, o, th, d, mu, lam = make_case("ha37")
+    h = handle(p, "fp16x3", d, mu, lam)
+    t = _t(th, h)
+    s1, g1 = h.chi2_grad(t)
+    s1, g1 = s1.clone(), g1.clone()
+    s2, g2 = h.chi2_grad(t)
+    assert bool((s1 == s2).all()) and bool((g1 == g2).all())
+
+
+def test_antenna_form_is_used_when_disabled(monkeypatch):
+    monkeypatch.setenv("FM_HA", "0")
+    p, o, th, d, mu, lam = make_case("ha37")
+    h = handle(p, "fp16x3")
+    assert h.contraction_info()["form"] == "antenna"
+    a, _ = o.split(th)
+    x = quant("fp16x3", o.sky(a))
+    assert rel_l2(as_complex(h.forward_pixels(_t(x, h))), o.vis(x)) < TOL_VIS["fp16x3"]
+
+
+def test_non_commensurate_grid_keeps_the_antenna_form():
+    p, o, th, d, mu, lam = make_case("ant37")
+    assert handle(p, "fp16x3").contraction_info()["form"] == "antenna"

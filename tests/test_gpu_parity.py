@@ -16,12 +16,9 @@ uses the bound implied by the visibility tolerance."""
 import numpy as np
 import pytest
 
-from gpu_cases import as_complex, handle, make_case, perturbed, quant, rel_l2
+from gpu_cases import TOL_GRAD, TOL_VIS, as_complex, handle, make_case, perturbed, quant, rel_l2
 
 pytestmark = pytest.mark.gpu
-
-TOL_VIS = {"fp64": 1e-10, "fp32": 1e-5, "bf16x1": 1e-2, "bf16x3": 2e-5, "fp16x1": 2e-3, "fp16x3": 1e-5}
-TOL_GRAD = {"fp64": 1e-10, "fp32": 1e-4, "bf16x1": 1e-1, "bf16x3": 3e-4, "fp16x1": 5e-3, "fp16x3": 3e-4}
 CASES = ["tiny", "small", "mid"]
 PRECS = ["fp64", "fp32", "bf16x1", "bf16x3", "fp16x1", "fp16x3"]
 
