@@ -41,8 +41,10 @@ using namespace tc;
 constexpr int HA_PROD_WARPS = 16;
 constexpr int HA_EPI_WARP0 = 16;          // warps 16..19 drain TMEM (lane quarter = warp & 3)
 constexpr int HA_MMA_WARP = 20;
-constexpr int HA_LOAD_WARP = 21;
-constexpr int HA_THREADS = 22 * 32;
+constexpr int HA_LOAD_WARP = 21;          // bulk copies of the phasor table (and sky strips)
+constexpr int HA_QLOAD_WARP = 22;         // adjoint only: bulk copies of the residual tiles
+constexpr int HA_THREADS = 22 * 32;       // forward
+constexpr int HA_ADJ_THREADS = 23 * 32;   // adjoint
 constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulation chain
 constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
 
@@ -57,7 +59,7 @@ struct HaDev {
 struct HaLayout {
     int nstage, neslot, ncols;
     uint32_t a_bytes, b_bytes, stage_bytes, eslot_bytes;
-    uint32_t e_off, v_off, bar_off, vstride, jw;
+    uint32_t e_off, v_off, bar_off, vstride;
     size_t smem;
 };
 
@@ -72,14 +74,28 @@ __host__ __device__ inline int cta_of(long long q, long long Q, int G)
     return g;
 }
 
+// power of two putting max below 2^14 (FP16 operand range), 1 for 0 or non-finite
+__device__ __forceinline__ float pow2_scale(float mx)
+{
+    float sc = 1.f;
+    if (mx > 0.f && isfinite(mx)) {
+        int e;
+        frexpf(mx, &e);
+        sc = ldexpf(1.f, 14 - e);
+    }
+    return sc;
+}
+
 __device__ __forceinline__ void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
 // ------------------------------------------------------------ per-handle phasor table
-// E[f][d][nb][i][nl], n = 64 nb + nl: sqrt(dOmega_d A(za; nu_f)) 2^(e/2) exp(-2 pi i nu r_i . s / c)
+// E[f][d][nb][i][nl], n = 64 nb + nl, i over the table's antenna subset plus one all-zero
+// entry (padding pairs point at it): sqrt(dOmega_d A(za; nu_f)) 2^(e/2) exp(-2 pi i nu r_i . s / c)
 // at hour angle H(n) = LST_0 - (ra_min + (R - 1 - n + 1/2) dRA); zero below the horizon
 // and for n >= nh.  FP64 throughout, stored as FP32.
 struct HaTabArgs {
-    int F, D, R, A, nh, nhp, nbc;
+    int F, D, R, A, A_all, nh, nhp, nbc;
+    int ant[64];                          // table entry -> antenna index
     double lst0, ra_min, dra, dec_min, ddec, lat, amp_scale;
     const double *kap64, *bcoef64, *domega64;
 };
@@ -99,7 +115,7 @@ __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
         const int f = (int)(r / a.D);
         const int n = 64 * nb + nl;
         float2 out = make_float2(0.f, 0.f);
-        if (n < a.nh) {
+        if (n < a.nh && i < a.A - 1) {           // entry A - 1 is the zero antenna of padded pairs
             const double H = a.lst0 - (a.ra_min + ((double)(a.R - 1 - n) + 0.5) * a.dra);
             const double dec = a.dec_min + (d + 0.5) * a.ddec;
             double sd, cd, sh, ch, sl, cl;
@@ -111,7 +127,7 @@ __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
                 const double za = acos(sU > 1.0 ? 1.0 : sU);
                 const double beta = a.domega64[d] * exp(a.bcoef64[f] * za * za);
                 const double amp = sqrt(beta) * a.amp_scale;
-                const double *kp = a.kap64 + ((size_t)f * a.A + i) * 3;
+                const double *kp = a.kap64 + ((size_t)f * a.A_all + a.ant[i]) * 3;
                 double ph = kp[0] * sE + kp[1] * sN + kp[2] * sU;
                 ph -= rint(ph);
                 double sn, cs;
@@ -127,7 +143,7 @@ __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
 // xs[f][d][m'] = S_f x(r = R - 1 - (m' - P0), d) for 0 <= m' - P0 < R, else 0; split into
 // 16-bit hi and lo parts of the operand type.
 template <int ET>
-__global__ void k_ha_xprep(HaDev h, const float *__restrict__ x, const float *__restrict__ xscale,
+__global__ void k_ha_xprep(HaDev h, const float *__restrict__ x, const unsigned *__restrict__ xmax,
                            uint16_t *__restrict__ xs_hi, uint16_t *__restrict__ xs_lo)
 {
     const long long total = (long long)h.F * h.D * (h.L / 2);
@@ -136,7 +152,7 @@ __global__ void k_ha_xprep(HaDev h, const float *__restrict__ x, const float *__
         const int mp = 2 * (int)(e % (h.L / 2));
         const long long fd = e / (h.L / 2);
         const int d = (int)(fd % h.D), f = (int)(fd / h.D);
-        const float sc = xscale[f];
+        const float sc = pow2_scale(__uint_as_float(xmax[f]));
         float v[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -151,6 +167,8 @@ __global__ void k_ha_xprep(HaDev h, const float *__restrict__ x, const float *__
 }
 
 // ------------------------------------------------------------ forward kernel
+// (the table slot of a unit holds its E chunk [A][64] followed by the sky strip of its
+// (channel, declination) row, hi then lo: the producers read no global memory)
 // Work units q in [0, Q), q = (mt F + f) nchunk + c with K chunk c = d nbc + nb; CTA g
 // takes the contiguous range [Q g / G, Q (g+1) / G).  A segment is the part of one
 // (M-tile, channel) pair inside a CTA's range; its partial sum goes to
@@ -223,9 +241,25 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
         uint32_t ph = 0, eph = 0;
         bool wrapped = false;
         const uint32_t wsub = (uint32_t)(lane & 3) * 4u;       // lane's word in its 16-byte chunk
+        const uint32_t lch = (uint32_t)(lane >> 2);               // lane's 16-byte chunk (before the swizzle)
+        // P-tile rows 2 ul, 2 ul + 1 (ul = 4 warp + k) sit at row & 7 = 2k, 2k + 1; Toeplitz
+        // rows t = warp + 16 k all sit at t & 7 = warp & 7, and their strip offsets
+        // P0 - t kst share one parity
+        const uint32_t a_row0 = (uint32_t)(8 * warp) * 128u + wsub;
+        const uint32_t b_off0 = (uint32_t)warp * 128u + ((lch ^ (uint32_t)(warp & 7)) << 4) + wsub;
+        const int b_base = h.P0 - warp * h.k;                    // >= 0
+        const bool b_odd = b_base & 1;
+        const int b_word0 = (b_base >> 1) + lane;
+        // unit coordinates, advanced incrementally (nb fastest, then d, f, mt)
+        int mt, f, d, nb;
+        {
+            const int seg = (int)(q0 / h.nchunk), c = (int)(q0 % h.nchunk);
+            mt = seg / h.F; f = seg % h.F; d = c / h.nbc; nb = c % h.nbc;
+        }
+        int2 ij4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ij4[k] = h.uij[mt * 64 + 4 * warp + k];
         for (long long q = q0; q < q1; ++q) {
-            const int seg = (int)(q / h.nchunk), c = (int)(q % h.nchunk);
-            const int mt = seg / h.F, f = seg % h.F, d = c / h.nbc, nb = c % h.nbc;
             // a failed wait has raised the abort flag before returning, so after the
             // warp barrier every lane takes the same branch
             mbar_wait_ab(efull0 + 8 * se, eph, abort_flag);
@@ -236,24 +270,24 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
                 uint8_t *st = gbase + (size_t)s * L.stage_bytes;
                 uint8_t *a_hi = st, *a_lo = st + L.a_bytes;
                 uint8_t *b_hi = st + NT * L.a_bytes, *b_lo = b_hi + L.b_bytes;
-                const float4 *Es = reinterpret_cast<const float4 *>(gbase + L.e_off + (size_t)se * L.eslot_bytes);
+                const uint8_t *eslot = gbase + L.e_off + (size_t)se * L.eslot_bytes;
+                const float4 *Es = reinterpret_cast<const float4 *>(eslot);
+                // the slot also holds this (channel, declination) row's sky strip, hi then lo
+                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(eslot + (size_t)h.A * 512);
+                const uint32_t *l32 = h32 + h.L / 2;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int ul = 4 * warp + k;
-                    const int2 ij = h.uij[mt * 64 + ul];
-                    float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
-                    if (ij.x >= 0) {
-                        const float4 a = Es[ij.x * 32 + lane], b = Es[ij.y * 32 + lane];
-                        pr0 = fmaf(a.x, b.x, a.y * b.y);
-                        pi0 = fmaf(a.y, b.x, -a.x * b.y);
-                        pr1 = fmaf(a.z, b.z, a.w * b.w);
-                        pi1 = fmaf(a.w, b.z, -a.z * b.w);
-                    }
+                    const int2 ij = ij4[k];
+                    const float4 a = Es[ij.x * 32 + lane], b = Es[ij.y * 32 + lane];
+                    const float pr0 = fmaf(a.x, b.x, a.y * b.y), pi0 = fmaf(a.y, b.x, -a.x * b.y);
+                    const float pr1 = fmaf(a.z, b.z, a.w * b.w), pi1 = fmaf(a.w, b.z, -a.z * b.w);
                     uint32_t hr, lr, hm, lm;
                     Elem<ET>::split(pr0, pr1, hr, lr);
                     Elem<ET>::split(pi0, pi1, hm, lm);
-                    const uint32_t o_re = sw128_off(2 * ul, lane >> 2) + wsub;
-                    const uint32_t o_im = sw128_off(2 * ul + 1, lane >> 2) + wsub;
+                    (void)ul;
+                    const uint32_t o_re = a_row0 + (uint32_t)(2 * k) * 128u + ((lch ^ (uint32_t)(2 * k)) << 4);
+                    const uint32_t o_im = a_row0 + (uint32_t)(2 * k + 1) * 128u + ((lch ^ (uint32_t)(2 * k + 1)) << 4);
                     st32(a_hi + o_re, hr);
                     st32(a_hi + o_im, hm);
                     if (X3) {
@@ -261,31 +295,45 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
                         st32(a_lo + o_im, lm);
                     }
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(eempty0 + 8 * se);
-                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(xs_hi + ((size_t)f * h.D + d) * h.L);
-                const uint32_t *l32 = reinterpret_cast<const uint32_t *>(xs_lo + ((size_t)f * h.D + d) * h.L);
+                // row t = warp + 16 k: strip words from 32 nb + ((P0 - t kst) >> 1) + lane
+                const int wrow = 32 * nb + b_word0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int t = warp + HA_PROD_WARPS * k;
-                    if (t >= h.T) break;
-                    const int m0 = 64 * nb - t * h.k + h.P0;     // >= 0 by the choice of P0
-                    const int w = (m0 >> 1) + lane;
-                    const uint32_t h0 = __ldg(h32 + w), h1 = __ldg(h32 + w + 1);
-                    const uint32_t hv = (m0 & 1) ? __byte_perm(h0, h1, 0x5432) : h0;
-                    const uint32_t ob = sw128_off(t, lane >> 2) + wsub;
-                    st32(b_hi + ob, hv);
-                    if (X3) {
-                        const uint32_t l0 = __ldg(l32 + w), l1 = __ldg(l32 + w + 1);
-                        st32(b_lo + ob, (m0 & 1) ? __byte_perm(l0, l1, 0x5432) : l0);
+                    if (t < h.T) {
+                        const int w = wrow - 8 * k * h.k;
+                        const uint32_t ob = b_off0 + (uint32_t)(2048 * k);
+                        if (b_odd) {
+                            st32(b_hi + ob, __byte_perm(h32[w], h32[w + 1], 0x5432));
+                            if (X3) st32(b_lo + ob, __byte_perm(l32[w], l32[w + 1], 0x5432));
+                        } else {
+                            st32(b_hi + ob, h32[w]);
+                            if (X3) st32(b_lo + ob, l32[w]);
+                        }
                     }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(eempty0 + 8 * se);
             }
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(full0 + 8 * s);
             if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
             if (++se == L.neslot) { se = 0; eph ^= 1u; }
+            if (++nb == h.nbc) {
+                nb = 0;
+                if (++d == h.D) {
+                    d = 0;
+                    if (++f == h.F) {
+                        f = 0;
+                        ++mt;
+                        if (q + 1 < q1) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) ij4[k] = h.uij[mt * 64 + 4 * warp + k];
+                        }
+                    }
+                }
+            }
         }
     } else if (warp == HA_LOAD_WARP) {
         // ------------------------------------------------------------ bulk loads of E chunks
@@ -293,16 +341,24 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
             int se = 0, last_se = -1;
             uint32_t eph = 0, last_eph = 0;
             bool wrapped = false;
+            int f = (int)((q0 / h.nchunk) % h.F), c = (int)(q0 % h.nchunk);
             for (long long q = q0; q < q1; ++q) {
-                const int seg = (int)(q / h.nchunk), c = (int)(q % h.nchunk);
-                const int f = seg % h.F;
-                if (wrapped && !mbar_wait_ab(eempty0 + 8 * se, eph ^ 1u, abort_flag)) break;
+                if (wrapped && !mbar_wait_ab<64>(eempty0 + 8 * se, eph ^ 1u, abort_flag)) break;
                 const float2 *src = h.E + (((size_t)f * h.D * h.nbc + c) * h.A) * 64;
-                mbar_expect_tx(efull0 + 8 * se, L.eslot_bytes);
-                bulk_g2s(base + L.e_off + (uint32_t)se * L.eslot_bytes, src, L.eslot_bytes, efull0 + 8 * se);
+                const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes, eb = (uint32_t)h.A * 512u;
+                const uint32_t sb = (uint32_t)h.L * 2u;
+                const size_t row = ((size_t)f * h.D + c / h.nbc) * h.L;
+                mbar_expect_tx(efull0 + 8 * se, eb + (X3 ? 2u : 1u) * sb);
+                bulk_g2s(dst, src, eb, efull0 + 8 * se);
+                bulk_g2s(dst + eb, xs_hi + row, sb, efull0 + 8 * se);
+                if (X3) bulk_g2s(dst + eb + sb, xs_lo + row, sb, efull0 + 8 * se);
                 last_se = se;
                 last_eph = eph;
                 if (++se == L.neslot) { se = 0; eph ^= 1u; wrapped = true; }
+                if (++c == h.nchunk) {
+                    c = 0;
+                    if (++f == h.F) f = 0;
+                }
             }
             // copies still in flight must land before the CTA exits (bounded); without an
             // abort the producers have already waited for every one of them
@@ -321,16 +377,16 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
             const uint32_t idesc = idesc_f16(128, h.npad, Elem<ET>::kFmt);
             int s = 0, last_s = -1;
             uint32_t ph = 0, last_ph = 0;
-            long long nacc = 0, local = 0;
-            for (long long q = q0; q < q1; ++q) {
-                const int c = (int)(q % h.nchunk);
+            long long nacc = 0;
+            int local = 0, c = (int)(q0 % h.nchunk);
+            for (long long q = q0; q < q1; ++q, c = (c + 1 == h.nchunk) ? 0 : c + 1) {
                 if (q == q0 || c == 0) local = 0;
                 const bool chain_first = (local % HA_SUB) == 0;
                 const int qa = (int)(nacc & 1);
                 if (chain_first && nacc >= 2 &&
-                    !mbar_wait_ab(acce0 + 8 * qa, (uint32_t)(((nacc >> 1) - 1) & 1), abort_flag))
+                    !mbar_wait_ab<64>(acce0 + 8 * qa, (uint32_t)(((nacc >> 1) - 1) & 1), abort_flag))
                     goto mma_done;
-                if (!mbar_wait_ab(full0 + 8 * s, ph, abort_flag)) goto mma_done;
+                if (!mbar_wait_ab<32>(full0 + 8 * s, ph, abort_flag)) goto mma_done;
                 tc_fence_after();
                 {
                     const uint32_t sa = base + (uint32_t)s * L.stage_bytes;
@@ -365,15 +421,16 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
         // ------------------------------------------------------------ epilogue (warps 16-19)
         const int quarter = warp & 3, row = 32 * quarter + lane;
         float *vr = vacc + (size_t)row * L.vstride;
-        long long nacc = 0, local = 0;
+        long long nacc = 0;
+        int local = 0, seg = (int)(q0 / h.nchunk), c = (int)(q0 % h.nchunk);
         for (long long q = q0; q < q1; ++q) {
-            const int seg = (int)(q / h.nchunk), c = (int)(q % h.nchunk);
+            if (q != q0 && ++c == h.nchunk) { c = 0; ++seg; }
             if (q == q0 || c == 0) local = 0;
             ++local;
             const bool seg_last = (q == q1 - 1) || (c == h.nchunk - 1);
             if (!((local % HA_SUB) == 0 || seg_last)) continue;
             const int qa = (int)(nacc & 1);
-            mbar_wait_ab(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
+            mbar_wait_ab<128>(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
             __syncwarp();
             if (*abort_flag) goto done;
             tc_fence_after();
@@ -408,90 +465,92 @@ done:
 }
 
 // Sum of the forward partials in fixed order, unscaled, expanded to every baseline.
-__global__ void k_ha_vfinish(HaDev h, int B, const float *__restrict__ vpart, const int *__restrict__ ncontrib,
-                             const int *__restrict__ bmap, const float *__restrict__ xscale, float sp,
-                             float *__restrict__ vis)
+// CTA (segment, LST block of HA_VF_T): the contributors' partials of the segment's 128
+// rows are added into shared memory, then every baseline of the segment's groups gets
+// its (possibly conjugated) value, written coalesced over baselines.
+constexpr int HA_VF_T = 8;
+
+__global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float *__restrict__ vpart,
+                                                    const int *__restrict__ ncontrib, const int *__restrict__ bmap,
+                                                    const unsigned *__restrict__ xmax, float sp, float *__restrict__ vis)
 {
-    const long long total = (long long)h.F * h.T * B;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(e % B);
-        const long long ft = e / B;
-        const int t = (int)(ft % h.T), f = (int)(ft / h.T);
+    __shared__ float sv[128][HA_VF_T];
+    const int seg = blockIdx.x, mt = seg / h.F, f = seg % h.F;
+    const int t0 = blockIdx.y * HA_VF_T, tn = min(HA_VF_T, h.T - t0);
+    const int nc = ncontrib[seg];
+    for (int e = threadIdx.x; e < 128 * HA_VF_T; e += blockDim.x) {
+        const int row = e / HA_VF_T, tl = e % HA_VF_T;
+        float a = 0.f;
+        if (tl < tn)
+            for (int j = 0; j < nc; ++j) a += vpart[(((size_t)seg * h.J + j) * 128 + row) * h.npad + t0 + tl];
+        sv[row][tl] = a;
+    }
+    __syncthreads();
+    const float sc = 1.f / (sp * pow2_scale(__uint_as_float(xmax[f])));
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
         const int code = bmap[b], u = code >> 1;
-        const int seg = (u >> 6) * h.F + f, row = 2 * (u & 63);
-        const int nc = ncontrib[seg];
-        float re = 0.f, im = 0.f;
-        for (int j = 0; j < nc; ++j) {
-            const float *p = vpart + (((size_t)seg * h.J + j) * 128 + row) * h.npad + t;
-            re += p[0];
-            im += p[h.npad];
+        if ((u >> 6) != mt) continue;
+        const int row = 2 * (u & 63);
+        const float sgn = (code & 1) ? -1.f : 1.f;
+        for (int tl = 0; tl < tn; ++tl) {
+            float2 *o = reinterpret_cast<float2 *>(vis) + ((size_t)f * h.T + t0 + tl) * B + b;
+            *o = make_float2(sv[row][tl] * sc, sgn * sv[row + 1][tl] * sc);
         }
-        const float sc = 1.f / (sp * xscale[f]);
-        vis[2 * e] = re * sc;
-        vis[2 * e + 1] = ((code & 1) ? -im : im) * sc;
     }
 }
 
-// power of two putting the largest |x| of a channel below 2^14, one CTA per channel
-__global__ void __launch_bounds__(256) k_ha_xscale(int npix, const float *__restrict__ x, float *__restrict__ scale)
+// largest |x| of each channel as float bits (non-negative floats order like their bit
+// patterns): blockIdx.y = channel, the CTAs of a channel split its pixels
+__global__ void __launch_bounds__(256) k_ha_xmax(int npix, const float *__restrict__ x, unsigned *__restrict__ xmax)
 {
     __shared__ float red[256];
-    const int f = blockIdx.x;
+    const int f = blockIdx.y;
     float m = 0.f;
-    for (int p = threadIdx.x; p < npix; p += blockDim.x) m = fmaxf(m, fabsf(x[(size_t)f * npix + p]));
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[(size_t)f * npix + p]));
     red[threadIdx.x] = m;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        float sc = 1.f;
-        if (red[0] > 0.f && isfinite(red[0])) {
-            int e;
-            frexpf(red[0], &e);
-            sc = ldexpf(1.f, 14 - e);
-        }
-        scale[f] = sc;
-    }
+    if (threadIdx.x == 0) atomicMax(xmax + f, __float_as_uint(red[0]));
 }
 
 // ------------------------------------------------------------ adjoint operand prep
 // Q_u(f, t) = sum of omega over the group's members (conjugated for reversed ones) and
 // the per-channel max |Re|, |Im| (non-negative floats order like their bit patterns).
-__global__ void k_ha_qsum(HaDev h, int B, const float *__restrict__ omega, const int *__restrict__ moff,
-                          const int *__restrict__ mem, float *__restrict__ q32, unsigned *__restrict__ qmax)
+__global__ void __launch_bounds__(256) k_ha_qsum(HaDev h, int B, const float *__restrict__ omega,
+                                                 const int *__restrict__ moff, const int *__restrict__ mem,
+                                                 float *__restrict__ q32, unsigned *__restrict__ qmax)
 {
-    const long long total = (long long)h.F * h.T * h.U;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int u = (int)(e % h.U);
-        const long long ft = e / h.U;
-        const float *om = omega + (size_t)ft * B * 2;
+    // one CTA per (channel, LST): the omega row is staged in shared memory, each thread
+    // sums the members of its groups, and one atomic per CTA records the channel maximum
+    extern __shared__ float som[];                  // [2 B]
+    __shared__ float red[256];
+    const int ft = blockIdx.x, f = ft / h.T;
+    const float *om = omega + (size_t)ft * B * 2;
+    for (int e = threadIdx.x; e < 2 * B; e += blockDim.x) som[e] = om[e];
+    __syncthreads();
+    float mx = 0.f;
+    for (int u = threadIdx.x; u < h.U; u += blockDim.x) {
         float re = 0.f, im = 0.f;
         for (int m = moff[u]; m < moff[u + 1]; ++m) {
             const int code = mem[m], b = code >> 1;
-            re += om[2 * b];
-            im += (code & 1) ? -om[2 * b + 1] : om[2 * b + 1];
+            re += som[2 * b];
+            im += (code & 1) ? -som[2 * b + 1] : som[2 * b + 1];
         }
-        q32[2 * e] = re;
-        q32[2 * e + 1] = im;
-        const int f = (int)(ft / h.T);
-        atomicMax(qmax + f, __float_as_uint(fmaxf(fabsf(re), fabsf(im))));
+        q32[((size_t)ft * h.U + u) * 2] = re;
+        q32[((size_t)ft * h.U + u) * 2 + 1] = im;
+        mx = fmaxf(mx, fmaxf(fabsf(re), fabsf(im)));
     }
-}
-
-// power of two putting max |Q| below 2^14
-__device__ __forceinline__ float pow2_scale(float mx)
-{
-    float sc = 1.f;
-    if (mx > 0.f && isfinite(mx)) {
-        int e;
-        frexpf(mx, &e);
-        sc = ldexpf(1.f, 14 - e);
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
     }
-    return sc;
+    if (threadIdx.x == 0) atomicMax(qmax + f, __float_as_uint(red[0]));
 }
 
 // One CTA per (channel, K chunk): the swizzled B tile [npad rows t][64 rho] of the
@@ -529,17 +588,15 @@ __global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const unsigned
 // ------------------------------------------------------------ adjoint kernel
 // Items (f, d), CTA g takes items g, g + G, ...; per item the nhp / 128 M-tiles of 128
 // hour-angle cells, per M-tile the nkq K chunks of 64 rho = 32 groups.
-//   load warp (21): per M-tile, the two E chunks (bulk, efull[se]); per K chunk, the
-//     Q tile into the stage's B part (bulk, bfull[s])
+//   table warp (21): per M-tile, the two E chunks (bulk, efull[se])
+//   Q warp (22): per K chunk, the Q tile into the stage's B part (bulk, bfull[s])
 //   producers (0-15): thread (row n = tid & 127, quarter = tid >> 7) writes the 8 groups
 //     8 quarter .. +7 of row n (two 16-byte words hi, two lo);  then full[s]
 //   MMA warp (20): D[n][t] of the M-tile into TMEM set (M-tile count & 1);  accf[q]
-//   epilogue (16-19): warp w holds rows n = 32 (w & 3) + lane; the diagonal sums
-//     S(j) = sum_t D[t k + 31 - j][t] of its 32 rows are carried across lanes by shfl_up
-//     and written once each into xacc; after the item (named barrier over the 4 warps,
-//     OR-reduced abort) every r of the row sums the xacc entries that cover it.
+//   epilogue (16-19): the diagonal sums over the M-tiles of the item (see below), one
+//     output row xbar(., d) per item.
 template <int ET, bool X3>
-__global__ void __launch_bounds__(HA_THREADS, 1)
+__global__ void __launch_bounds__(HA_ADJ_THREADS, 1)
 k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__restrict__ qscale, float sp,
          float *__restrict__ xbar, int *__restrict__ status)
 {
@@ -548,7 +605,6 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     constexpr int NT = X3 ? 2 : 1;
-    float *xacc = reinterpret_cast<float *>(gbase + L.v_off);    // [2][4][nmta][jw]
     const uint32_t full0 = base + L.bar_off, empty0 = full0 + 8 * L.nstage;
     const uint32_t efull0 = empty0 + 8 * L.nstage, eempty0 = efull0 + 8 * L.neslot;
     const uint32_t accf0 = eempty0 + 8 * L.neslot, acce0 = accf0 + 16;
@@ -558,6 +614,8 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + misc + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int2 *suij = reinterpret_cast<int2 *>(gbase + L.v_off + (size_t)32 * 129 * 4);
+    for (int e = tid; e < 32 * h.nkq; e += blockDim.x) suij[e] = h.uij[e];
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
             mbar_init(full0 + 8 * s, HA_PROD_WARPS);
@@ -605,15 +663,10 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                     uint32_t hw[8], lw[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const int2 ij = h.uij[32 * kq + 8 * qq + q];
-                        float pr = 0.f, pim = 0.f;
-                        if (ij.x >= 0) {
-                            const float2 a = *reinterpret_cast<const float2 *>(es + (size_t)ij.x * 512);
-                            const float2 b = *reinterpret_cast<const float2 *>(es + (size_t)ij.y * 512);
-                            pr = fmaf(a.x, b.x, a.y * b.y);
-                            pim = fmaf(a.y, b.x, -a.x * b.y);
-                        }
-                        Elem<ET>::split(pr, pim, hw[q], lw[q]);
+                        const int2 ij = suij[32 * kq + 8 * qq + q];
+                        const float2 a = *reinterpret_cast<const float2 *>(es + (size_t)ij.x * 512);
+                        const float2 b = *reinterpret_cast<const float2 *>(es + (size_t)ij.y * 512);
+                        Elem<ET>::split(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y), hw[q], lw[q]);
                     }
                     const uint32_t o0 = sw128_off(n, 2 * qq), o1 = sw128_off(n, 2 * qq + 1);
                     *reinterpret_cast<uint4 *>(st + o0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -633,17 +686,16 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
             }
         }
     } else if (warp == HA_LOAD_WARP) {
-        // ------------------------------------------------------------ bulk loads
+        // ------------------------------------------------------------ bulk loads of E
         if (lane == 0) {
-            int s = 0, se = 0, last_s = -1, last_se = -1;
-            uint32_t ph = 0, eph = 0, last_ph = 0, last_eph = 0;
-            bool wrapped = false, ewrapped = false;
-            long long ns = 0, nse = 0;
-            const uint32_t bbytes = NT * L.b_bytes;
+            int se = 0, last_se = -1;
+            uint32_t eph = 0, last_eph = 0;
+            bool ewrapped = false;
+            long long nse = 0;
             for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
                 const int f = it / h.D, d = it % h.D;
                 for (int mt = 0; mt < nmta; ++mt) {
-                    if (ewrapped && !mbar_wait_ab(eempty0 + 8 * se, eph ^ 1u, abort_flag)) goto load_done;
+                    if (ewrapped && !mbar_wait_ab<64>(eempty0 + 8 * se, eph ^ 1u, abort_flag)) goto eload_done;
                     const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + 2 * mt) * h.A * 64;
                     const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes;
                     mbar_expect_tx(efull0 + 8 * se, 2 * echunk);
@@ -653,19 +705,9 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                     last_eph = eph;
                     ++nse;
                     if (++se == L.neslot) { se = 0; eph ^= 1u; ewrapped = true; }
-                    for (int kq = 0; kq < h.nkq; ++kq) {
-                        if (wrapped && !mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag)) goto load_done;
-                        mbar_expect_tx(bfull0 + 8 * s, bbytes);
-                        bulk_g2s(base + (uint32_t)s * L.stage_bytes + NT * L.a_bytes,
-                                 qimg + ((size_t)f * h.nkq + kq) * bbytes, bbytes, bfull0 + 8 * s);
-                        last_s = s;
-                        last_ph = ph;
-                        ++ns;
-                        if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
-                    }
                 }
             }
-        load_done:
+        eload_done:
             // copies in flight land before the CTA exits (bounded)
             if (*abort_flag) {
                 for (int k = 0; k < L.neslot && k < nse; ++k) {
@@ -674,6 +716,32 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                     if (s2 < 0) { s2 += L.neslot; p2 ^= 1u; }
                     mbar_drain(efull0 + 8 * s2, p2);
                 }
+            }
+        }
+    } else if (warp == HA_QLOAD_WARP) {
+        // ------------------------------------------------------------ bulk loads of Q tiles
+        if (lane == 0) {
+            int s = 0, last_s = -1;
+            uint32_t ph = 0, last_ph = 0;
+            bool wrapped = false;
+            long long ns = 0;
+            const uint32_t bbytes = NT * L.b_bytes;
+            for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+                const int f = it / h.D;
+                for (int mt = 0; mt < nmta; ++mt)
+                    for (int kq = 0; kq < h.nkq; ++kq) {
+                        if (wrapped && !mbar_wait_ab<64>(empty0 + 8 * s, ph ^ 1u, abort_flag)) goto qload_done;
+                        mbar_expect_tx(bfull0 + 8 * s, bbytes);
+                        bulk_g2s(base + (uint32_t)s * L.stage_bytes + NT * L.a_bytes,
+                                 qimg + ((size_t)f * h.nkq + kq) * bbytes, bbytes, bfull0 + 8 * s);
+                        last_s = s;
+                        last_ph = ph;
+                        ++ns;
+                        if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
+                    }
+            }
+        qload_done:
+            if (*abort_flag) {
                 for (int k = 0; k < L.nstage && k < ns; ++k) {
                     int s2 = last_s - k;
                     uint32_t p2 = last_ph;
@@ -692,12 +760,12 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
             for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
                 for (int mt = 0; mt < nmta; ++mt) {
                     const int qa = (int)(nacc & 1);
-                    if (nacc >= 2 && !mbar_wait_ab(acce0 + 8 * qa, (uint32_t)(((nacc >> 1) - 1) & 1), abort_flag))
+                    if (nacc >= 2 && !mbar_wait_ab<64>(acce0 + 8 * qa, (uint32_t)(((nacc >> 1) - 1) & 1), abort_flag))
                         goto mma_done;
                     const uint32_t dacc = tmem_d + (uint32_t)(qa * h.npad);
                     for (int kq = 0; kq < h.nkq; ++kq) {
-                        if (!mbar_wait_ab(full0 + 8 * s, ph, abort_flag)) goto mma_done;
-                        if (!mbar_wait_ab(bfull0 + 8 * s, ph, abort_flag)) goto mma_done;
+                        if (!mbar_wait_ab<32>(full0 + 8 * s, ph, abort_flag)) goto mma_done;
+                        if (!mbar_wait_ab<32>(bfull0 + 8 * s, ph, abort_flag)) goto mma_done;
                         tc_fence_after();
                         const uint32_t sa = base + (uint32_t)s * L.stage_bytes;
                         const uint32_t a_hi = sa, a_lo = sa + L.a_bytes;
@@ -723,60 +791,60 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
         mma_done:
             if (*abort_flag && last_s >= 0) mbar_drain(empty0 + 8 * last_s, last_ph);
         }
-    } else {
+    } else if (warp >= HA_EPI_WARP0 && warp < HA_EPI_WARP0 + 4) {
         // ------------------------------------------------------------ epilogue (warps 16-19)
+        // Per M-tile, the accumulator D[n][t] goes through shared memory in two halves of
+        // 32 LSTs (sk[t][n], row stride 129); thread et then adds, for its outputs
+        // r = et + 128 j, the entries on the diagonal n = t k + R - 1 - r - 128 mt
+        // in LST order.  Named barrier 1 spans the four epilogue warps; its OR-reduced
+        // form decides a wind-down for all four at once.
         const int quarter = warp & 3, et = tid - 32 * HA_EPI_WARP0;     // 0..127
-        const int jw = (int)L.jw;
+        float *sk = reinterpret_cast<float *>(gbase + L.v_off);          // [32][129]
         long long nacc = 0;
-        int ni = 0;
-        for (int it = blockIdx.x; it < nitem; it += gridDim.x, ++ni) {
+        for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
             const int f = it / h.D, d = it % h.D;
-            float *xb = xacc + (size_t)(ni & 1) * 4 * nmta * jw;
-            bool fail = false;
-            for (int mt = 0; mt < nmta; ++mt, ++nacc) {
+            float xr[4] = {0.f, 0.f, 0.f, 0.f};      // outputs r = et + 128 j (R <= 512)
+            bool stop = false;
+            for (int mt = 0; mt < nmta && !stop; ++mt, ++nacc) {
                 const int qa = (int)(nacc & 1);
-                if (fail) continue;
-                mbar_wait_ab(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
+                mbar_wait_ab<128>(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
                 __syncwarp();
-                if (*abort_flag) { fail = true; continue; }
+                if (bar_or(1, 128, *abort_flag != 0)) { stop = true; break; }
                 tc_fence_after();
-                float *xw = xb + ((size_t)quarter * nmta + mt) * jw;
                 const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
-                float acc = 0.f;
-                for (int c16 = 0; c16 < h.npad; c16 += 16) {
-                    float v[16];
-                    tmem_ld16(taddr + (uint32_t)c16, v);
+                const int c0 = h.R - 1 - 128 * mt;                           // n = t k + c0 - r
+                for (int t0 = 0; t0 < h.T; t0 += 32) {
+                    float v[32];
+                    tmem_ld16(taddr + (uint32_t)t0, v);
+                    if (t0 + 16 < h.npad) tmem_ld16(taddr + (uint32_t)(t0 + 16), v + 16);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int t = c16 + q;
-                        if (t < h.T) {
-                            if (t > 0) {
-                                // lanes >= 32 - k hold finished sums j = t' k - lane + 31 (t' = t - 1)
-                                if (lane >= 32 - h.k) xw[(t - 1) * h.k - lane + 31] = acc;
-                                const float up = __shfl_up_sync(0xffffffffu, acc, h.k);
-                                acc = (lane >= h.k) ? up : 0.f;
-                            }
-                            acc += v[q];
-                        }
+                    for (int q = 0; q < 32; ++q) sk[q * 129 + et] = v[q];
+                    bar_or(1, 128, false);
+                    const int tn = min(32, h.T - t0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (et + 128 * j >= h.R) break;
+                        // n = nb0 + q kst must lie in [0, 128): q in [q_lo, q_hi)
+                        const int nb0 = t0 * h.k + c0 - et - 128 * j;
+                        const int q_lo = nb0 >= 0 ? 0 : (-nb0 + h.k - 1) / h.k;
+                        const int q_hi = nb0 >= 128 ? 0 : min(tn, (128 - nb0 + h.k - 1) / h.k);
+                        float a = 0.f;
+                        const float *col = sk + nb0;              // entry (q, nb0 + q kst)
+                        for (int q = q_lo; q < q_hi; ++q) a += col[q * (129 + h.k)];
+                        xr[j] += a;
                     }
+                    bar_or(1, 128, false);
                 }
-                xw[(h.T - 1) * h.k - lane + 31] = acc;
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acce0 + 8 * qa);
             }
-            if (bar_or(1, 128, fail || *abort_flag != 0)) break;
+            if (stop) break;
             const float sc = 1.f / (sp * qscale[f]);
-            for (int r = et; r < h.R; r += 128) {
-                float sum = 0.f;
-                for (int mt = 0; mt < nmta; ++mt)
+            float *xo = xbar + ((size_t)f * h.D + d) * h.R;
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const int j = r - (h.R - 32 - 128 * mt - 32 * w);
-                        if (j >= 0 && j < jw) sum += xb[((size_t)w * nmta + mt) * jw + j];
-                    }
-                xbar[((size_t)f * h.D + d) * h.R + r] = sum * sc;
-            }
+            for (int j = 0; j < 4; ++j)
+                if (et + 128 * j < h.R) xo[et + 128 * j] = xr[j] * sc;
         }
     }
 done:
@@ -800,7 +868,7 @@ HaDev make_dev(const Ctx &c)
 {
     const HaState &s = c.ha;
     HaDev h;
-    h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = c.A; h.U = s.U; h.k = s.k;
+    h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = s.nant + 1; h.U = s.U; h.k = s.k;
     h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.P0 = s.P0; h.L = s.L;
     h.nchunk = c.D * s.nbc; h.nmt = s.nmt; h.nkq = s.nkq; h.J = s.J;
     h.Q = (long long)s.nmt * c.F * h.nchunk;
@@ -811,6 +879,18 @@ HaDev make_dev(const Ctx &c)
 bool x3_of(int prec) { return prec == FM_PREC_BF16X3 || prec == FM_PREC_FP16X3; }
 bool f16_of(int prec) { return prec == FM_PREC_FP16X1 || prec == FM_PREC_FP16X3; }
 
+// forward table slot: E chunk [A + 1][64] and the two sky-strip rows
+uint32_t fwd_slot_bytes(const Ctx &c, bool x3)
+{
+    return (uint32_t)(c.ha.nant + 1) * 512u + (x3 ? 2u : 1u) * (uint32_t)c.ha.L * 2u;
+}
+
+// adjoint scratch: the epilogue's half tile sk [32][129] and the group pairs [32 nkq]
+uint32_t adj_scratch_bytes(const Ctx &c)
+{
+    return 32u * 129u * 4u + 32u * (uint32_t)c.ha.nkq * 8u;
+}
+
 // shared-memory layout common to both kernels; `vbytes` is the epilogue's scratch
 bool make_layout(const Ctx &c, bool x3, uint32_t eslot_bytes, uint32_t vbytes, HaLayout &L)
 {
@@ -819,15 +899,20 @@ bool make_layout(const Ctx &c, bool x3, uint32_t eslot_bytes, uint32_t vbytes, H
     L.b_bytes = (uint32_t)c.ha.npad * 128u;
     L.stage_bytes = nt * (L.a_bytes + L.b_bytes);
     L.eslot_bytes = eslot_bytes;
-    L.neslot = 2;
     L.ncols = 32;
     while (L.ncols < 2 * c.ha.npad) L.ncols *= 2;
-    const size_t fixed = 2 * (size_t)eslot_bytes + ((vbytes + 15) / 16) * 16 + 256;
+    // as many table slots in flight as fit next to two operand stages (up to 4), then
+    // as many stages as fit (up to 4)
+    const size_t vb = ((vbytes + 15) / 16) * 16 + 256;
+    L.neslot = 4;
+    while (L.neslot > 1 && (size_t)L.neslot * eslot_bytes + vb + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET)
+        --L.neslot;
+    const size_t fixed = (size_t)L.neslot * eslot_bytes + vb;
     if (fixed + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET) return false;
     L.nstage = (int)((HA_SMEM_BUDGET - fixed) / L.stage_bytes);
     if (L.nstage > 4) L.nstage = 4;
     L.e_off = (uint32_t)L.nstage * L.stage_bytes;
-    L.v_off = L.e_off + 2 * eslot_bytes;
+    L.v_off = L.e_off + (uint32_t)L.neslot * eslot_bytes;
     L.bar_off = L.v_off + ((vbytes + 15) / 16) * 16;
     L.smem = 1024 + (size_t)L.bar_off + 24 * L.nstage + 16 * L.neslot + 32 + 16;
     return L.smem <= 227 * 1024;
@@ -838,16 +923,16 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
 {
     HaState &s = c.ha;
     HaLayout L;
-    if (!make_layout(c, X3, (uint32_t)c.A * 512u, 128u * (uint32_t)(s.npad + 1) * 4u, L)) {
+    if (!make_layout(c, X3, fwd_slot_bytes(c, X3), 128u * (uint32_t)(s.npad + 1) * 4u, L)) {
         set_error("hour-angle forward tiles exceed shared memory");
         return FM_ERR_UNSUPPORTED;
     }
     L.vstride = (uint32_t)s.npad + 1;
-    L.jw = 0;
     uint16_t *xs_hi = s.xs, *xs_lo = s.xs + (size_t)c.F * c.D * s.L;
-    k_ha_xscale<<<c.F, 256, 0, st>>>(c.npix, x, s.xscale);
+    FM_CK(cudaMemsetAsync(s.xmax, 0, sizeof(unsigned) * c.F, st));
+    k_ha_xmax<<<dim3(cdiv(c.npix, 256 * 8), c.F), 256, 0, st>>>(c.npix, x, s.xmax);
     FM_CK_LAUNCH();
-    k_ha_xprep<ET><<<1024, 256, 0, st>>>(h, x, s.xscale, xs_hi, xs_lo);
+    k_ha_xprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, xs_hi, xs_lo);
     FM_CK_LAUNCH();
     FM_CK(cudaFuncSetAttribute(k_vis_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
@@ -855,7 +940,8 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
         FM_CK_LAUNCH();
         return FM_OK;
     }));
-    k_ha_vfinish<<<1024, 256, 0, st>>>(h, c.B, s.vpart, s.ncontrib, s.bmap, s.xscale, s.sp, vis);
+    k_ha_vfinish<<<dim3(s.nmt * c.F, cdiv(c.T, HA_VF_T)), 256, 0, st>>>(h, c.B, s.vpart, s.ncontrib, s.bmap,
+                                                                        s.xmax, s.sp, vis);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -864,17 +950,14 @@ template <int ET, bool X3>
 fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar, cudaStream_t st)
 {
     HaState &s = c.ha;
-    const int nmta = s.nhp / 128;
-    const uint32_t jw = (uint32_t)((c.T - 1) * s.k + 32);
     HaLayout L;
-    if (!make_layout(c, X3, 2u * (uint32_t)c.A * 512u, 2u * 4u * (uint32_t)nmta * jw * 4u, L)) {
+    if (!make_layout(c, X3, 2u * (uint32_t)(s.nant + 1) * 512u, adj_scratch_bytes(c), L)) {
         set_error("hour-angle adjoint tiles exceed shared memory");
         return FM_ERR_UNSUPPORTED;
     }
     L.vstride = 0;
-    L.jw = jw;
     FM_CK(cudaMemsetAsync(s.qmax, 0, sizeof(unsigned) * c.F, st));
-    k_ha_qsum<<<1024, 256, 0, st>>>(h, c.B, omega, s.moff, s.mem, s.q32, s.qmax);
+    k_ha_qsum<<<c.F * c.T, 256, sizeof(float) * 2 * (size_t)c.B, st>>>(h, c.B, omega, s.moff, s.mem, s.q32, s.qmax);
     FM_CK_LAUNCH();
     k_ha_qimg<ET, X3><<<c.F * s.nkq, 256, 0, st>>>(h, s.q32, s.qmax, s.qscale, s.qimg);
     FM_CK_LAUNCH();
@@ -882,7 +965,7 @@ fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar,
     if (grid > c.F * c.D) grid = c.F * c.D;
     FM_CK(cudaFuncSetAttribute(k_adj_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     FM_TRY(profiled(c, 1, st, [&]() -> fm_status {
-        k_adj_ha<ET, X3><<<grid, HA_THREADS, L.smem, st>>>(h, L, s.qimg, s.qscale, s.sp, xbar, c.status);
+        k_adj_ha<ET, X3><<<grid, HA_ADJ_THREADS, L.smem, st>>>(h, L, s.qimg, s.qscale, s.sp, xbar, c.status);
         FM_CK_LAUNCH();
         return FM_OK;
     }));
@@ -904,7 +987,7 @@ static fm_status ha_alloc(Ctx &c, T **p, size_t count)
 
 // Geometry test, fringe groups, work partition and the per-handle phasor table.  The
 // path is used for the tensor-core precisions when the LSTs are equally spaced by
-// k = 1 .. 32 RA pixels, n_ant <= 64, n_lst <= 64 and the buffers take at most half of
+// k = 1 .. 32 RA pixels, n_ant <= 64, n_lst <= 64, n_ra <= 512 and the buffers take at most half of
 // the free device memory; otherwise c.ha.on stays false and the antenna form runs.
 fm_status ha_setup(Ctx &c)
 {
@@ -913,7 +996,7 @@ fm_status ha_setup(Ctx &c)
     if (c.prec < FM_PREC_BF16X1) return FM_OK;
     if (const char *e = getenv("FM_HA"))
         if (atoi(e) == 0) return FM_OK;
-    if (c.A < 2 || c.A > 64 || c.T > 64) return FM_OK;
+    if (c.A < 2 || c.A > 64 || c.T > 64 || c.R > 512) return FM_OK;
     const double dra = (c.cfg.ra_max - c.cfg.ra_min) / c.R;
     int k = 1;
     if (c.T > 1) {
@@ -930,18 +1013,20 @@ fm_status ha_setup(Ctx &c)
     s.nbc = s.nhp / 64;
     s.npad = (c.T + 15) / 16 * 16;
     if (s.npad < 16) s.npad = 16;
-    s.P0 = ((c.T - 1) * k + 1) / 2 * 2;
+    s.P0 = ((c.T - 1) * k + 7) / 8 * 8;      // strip rows stay multiples of 16 bytes
     s.L = s.P0 + s.nhp + 8;
 
     // fringe groups: equal baseline vectors (to 1 nm) up to sign
     bool group = true;
     if (const char *e = getenv("FM_HA_GROUPS"))
         if (atoi(e) == 0) group = false;
-    std::vector<int> rep_i, rep_j, bmap(c.B);
+    std::vector<int> rep_i, rep_j, bmap(c.B), bi(c.B), bj(c.B);
     std::vector<double> rep_b;
     std::vector<std::vector<int>> members;
     for (int i = 0, b = 0; i < c.A; ++i)
         for (int j = i + 1; j < c.A; ++j, ++b) {
+            bi[b] = i;
+            bj[b] = j;
             const double v0 = c.ant[3 * i] - c.ant[3 * j], v1 = c.ant[3 * i + 1] - c.ant[3 * j + 1],
                          v2 = c.ant[3 * i + 2] - c.ant[3 * j + 2];
             int found = -1, cj = 0;
@@ -969,6 +1054,64 @@ fm_status ha_setup(Ctx &c)
     s.nmt = (s.U + 63) / 64;
     s.nkq = (s.U + 31) / 32;
 
+    // Antennas whose phasors the table holds: a small set S such that every group has a
+    // member pair inside S (greedy: add the antenna that completes the most groups, ties
+    // broken by partial coverage); each group's representative is then such a pair.
+    std::vector<int> in_s(c.A, 0), uncovered(s.U, 1);
+    int n_unc = s.U;
+    if (!group) {
+        for (int a = 0; a < c.A; ++a) in_s[a] = 1;
+        n_unc = 0;
+    }
+    while (n_unc > 0) {
+        int best = -1;
+        long long bfull = -1, bpart = -1;
+        for (int a = 0; a < c.A; ++a) {
+            if (in_s[a]) continue;
+            long long full = 0, part = 0;
+            for (int u = 0; u < s.U; ++u) {
+                if (!uncovered[u]) continue;
+                bool f1 = false, p1 = false;
+                for (int m : members[u]) {
+                    const int b = m >> 1, i = bi[b], j = bj[b];
+                    const bool hi = in_s[i] || i == a, hj = in_s[j] || j == a;
+                    if (hi && hj) { f1 = true; break; }
+                    if (hi || hj) p1 = true;
+                }
+                full += f1;
+                part += p1;
+            }
+            if (full > bfull || (full == bfull && part > bpart)) { best = a; bfull = full; bpart = part; }
+        }
+        in_s[best] = 1;
+        for (int u = 0; u < s.U; ++u) {
+            if (!uncovered[u]) continue;
+            for (int m : members[u]) {
+                const int b = m >> 1;
+                if (in_s[bi[b]] && in_s[bj[b]]) { uncovered[u] = 0; --n_unc; break; }
+            }
+        }
+    }
+    std::vector<int> pos(c.A, -1);
+    s.nant = 0;
+    for (int a = 0; a < c.A; ++a)
+        if (in_s[a]) { pos[a] = s.nant; s.ant_of[s.nant] = a; ++s.nant; }
+    // representatives inside S, member orientation relative to them
+    for (int u = 0; u < s.U; ++u) {
+        int rb = -1;
+        for (int m : members[u]) {
+            const int b = m >> 1;
+            if (in_s[bi[b]] && in_s[bj[b]]) { rb = m; break; }
+        }
+        const int rflip = rb & 1;   // representative reversed w.r.t. the group's first member
+        rep_i[u] = pos[bi[rb >> 1]];
+        rep_j[u] = pos[bj[rb >> 1]];
+        for (int &m : members[u]) {
+            m ^= rflip;
+            bmap[m >> 1] = 2 * u + (m & 1);
+        }
+    }
+
     // partition of the forward work units over the CTAs
     const int nchunk = c.D * s.nbc;
     const long long Q = (long long)s.nmt * c.F * nchunk;
@@ -983,8 +1126,17 @@ fm_status ha_setup(Ctx &c)
         if (ncontrib[seg] > s.J) s.J = ncontrib[seg];
     }
 
+    // both kernels' tiles must fit in shared memory
+    {
+        HaLayout L1, L2;
+        const bool x3 = x3_of(c.prec);
+        if (!make_layout(c, x3, fwd_slot_bytes(c, x3), 128u * (uint32_t)(s.npad + 1) * 4u, L1) ||
+            !make_layout(c, x3, 2u * (uint32_t)(s.nant + 1) * 512u, adj_scratch_bytes(c), L2))
+            return FM_OK;
+    }
+
     // device memory, all of it within half of what is free
-    const size_t e_n = (size_t)c.F * c.D * s.nhp * c.A;
+    const size_t e_n = (size_t)c.F * c.D * s.nhp * (s.nant + 1);
     const size_t xs_n = 2 * (size_t)c.F * c.D * s.L;
     const size_t vp_n = (size_t)s.nmt * c.F * s.J * 128 * s.npad;
     const size_t q_n = (size_t)c.F * c.T * s.U * 2;
@@ -1001,14 +1153,14 @@ fm_status ha_setup(Ctx &c)
     FM_TRY(ha_alloc(c, &s.mem, (size_t)c.B));
     FM_TRY(ha_alloc(c, &s.ncontrib, ncontrib.size()));
     FM_TRY(ha_alloc(c, &s.xs, xs_n));
-    FM_TRY(ha_alloc(c, &s.xscale, (size_t)c.F));
+    FM_TRY(ha_alloc(c, &s.xmax, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.vpart, vp_n));
     FM_TRY(ha_alloc(c, &s.q32, q_n));
     FM_TRY(ha_alloc(c, &s.qmax, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.qscale, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.qimg, qi_n));
 
-    std::vector<int2> huij((size_t)s.nmt * 64, make_int2(-1, -1));
+    std::vector<int2> huij((size_t)s.nmt * 64, make_int2(s.nant, s.nant));   // padding: the zero entry
     for (int u = 0; u < s.U; ++u) huij[u] = make_int2(rep_i[u], rep_j[u]);
     std::vector<int> hoff(s.U + 1, 0), hmem;
     hmem.reserve(c.B);
@@ -1031,7 +1183,8 @@ fm_status ha_setup(Ctx &c)
     }
     s.sp = (float)std::ldexp(1.0, e2);
     HaTabArgs a;
-    a.F = c.F; a.D = c.D; a.R = c.R; a.A = c.A; a.nh = s.nh; a.nhp = s.nhp; a.nbc = s.nbc;
+    a.F = c.F; a.D = c.D; a.R = c.R; a.A = s.nant + 1; a.A_all = c.A; a.nh = s.nh; a.nhp = s.nhp; a.nbc = s.nbc;
+    for (int q = 0; q < s.nant; ++q) a.ant[q] = s.ant_of[q];
     a.lst0 = c.lst[0]; a.ra_min = c.cfg.ra_min; a.dra = dra;
     a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D;
     a.lat = c.cfg.latitude_rad; a.amp_scale = std::ldexp(1.0, e2 / 2);

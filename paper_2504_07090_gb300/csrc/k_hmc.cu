@@ -7,6 +7,7 @@
 //   - Cholesky of every block with prior inflation until positive definite;
 //   - leapfrog kicks, the drift q += eps L^-T L^-1 p, kinetic energy z.z/2 (L z = p)
 //     in FP64, and the Metropolis test u < exp(H0 - H1) on the device.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -481,65 +482,201 @@ __global__ void k_copy(long long n, const R *__restrict__ x, R *__restrict__ y)
         y[k] = x[k];
 }
 
-// Block-diagonal triangular algebra with one CTA per block (the dense gain block too):
-// v = in; if (fwd) v = L^-1 v (forward substitution, kin[blk] = sum v^2 in FP64);
+// Block-diagonal triangular algebra of the mass-matrix factor M = L L^T (App. B):
+// v = in; if (fwd) v = L^-1 v (forward substitution; kin[blk] = sum v^2 in FP64);
 // if (bwd) v = L^-T v (backward substitution); then q += eps v (q != NULL) and/or
-// out = v (out != NULL).  mul: out = L in instead.
+// out = v (out != NULL).  mul: out = L in instead.  Arithmetic in the working type R.
+//
+// One warp per 64 x 64 sky block: the block is copied to shared memory with cp.async
+// (16-byte pieces, XOR-permuted within each row), lane l owns entries l and l + 32, and
+// each substitution step broadcasts the solved entry (scaled by the reciprocal of its
+// diagonal) by a shuffle: column k of L updates the entries below k in the forward
+// sweep, row k of L the entries above k in the backward one.  CTA 0 (when n_dense > 0) solves the dense gain block of order
+// n_dense, panel by panel (32 columns): the diagonal panel is staged in shared memory
+// and solved by warp 0 with shuffles, then the CTA updates the remaining entries from
+// global memory (rows of L for the forward sweep, coalesced columns for the backward).
+constexpr int LF_WARPS = 4;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_lf_solve(int n, long long base, const R *__restrict__ L, const R *__restrict__ in,
-                                                  int fwd, int bwd, int mul, R *__restrict__ q, double eps,
-                                                  R *__restrict__ out, double *__restrict__ kin)
+__device__ __forceinline__ R warp_sum(R a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// Shared-memory image of a 64 x 64 block: row-major, the 16-byte pieces of row r
+// permuted by XOR with (r mod pieces per row), so that a column read (32 lanes, 32 rows)
+// touches few banks and a row read none twice.
+template <typename R>
+__device__ __forceinline__ int swz(int r, int c)
+{
+    constexpr int PER = 16 / sizeof(R), NP = 64 / PER;
+    return r * 64 + (((c / PER) ^ (r & (NP - 1))) * PER) + (c % PER);
+}
+
+// lane l holds entries l and l + 32 of a 64-vector; inv0, inv1 = 1 / L[l][l], 1 / L[l+32][l+32]
+template <typename R>
+__device__ __forceinline__ void sky_fwd(const R *S, R inv0, R inv1, R &v0, R &v1)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < 64; ++k) {
+        const bool hi = k >= 32;
+        const R vk = __shfl_sync(0xffffffffu, hi ? v1 * inv1 : v0 * inv0, k & 31);
+        if (lane == (k & 31)) { if (hi) v1 = vk; else v0 = vk; }
+        if (!hi && lane > k) v0 -= S[swz<R>(lane, k)] * vk;
+        if (lane + 32 > k) v1 -= S[swz<R>(lane + 32, k)] * vk;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void sky_bwd(const R *S, R inv0, R inv1, R &v0, R &v1)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = 63; k >= 0; --k) {
+        const bool hi = k >= 32;
+        const R vk = __shfl_sync(0xffffffffu, hi ? v1 * inv1 : v0 * inv0, k & 31);
+        if (lane == (k & 31)) { if (hi) v1 = vk; else v0 = vk; }
+        if (lane < k) v0 -= S[swz<R>(k, lane)] * vk;
+        if (lane + 32 < k) v1 -= S[swz<R>(k, lane + 32)] * vk;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, int n_dense,
+                                                          const R *__restrict__ L, const R *__restrict__ in, int fwd,
+                                                          int bwd, int mul, R *__restrict__ q, double eps,
+                                                          R *__restrict__ out, double *__restrict__ kin)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *v = reinterpret_cast<double *>(smem_raw);     // [n]
-    double *red = v + n;                                   // [blockDim]
-    const long long blk = blockIdx.x;
-    const R *Lb = L + (size_t)blk * n * n;
-    const long long off = base + blk * n;
-    const int tid = threadIdx.x;
-    for (int r = tid; r < n; r += blockDim.x) v[r] = (double)in[off + r];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const bool dense = n_dense > 0 && blockIdx.x == 0;
+    if (!dense) {
+        // ------------------------------------------------ one 64 x 64 block per warp
+        const long long blk = (long long)(blockIdx.x - (n_dense > 0 ? 1 : 0)) * LF_WARPS + w;
+        if (blk >= nblk) return;
+        R *S = sm + (size_t)w * 4096;
+        const R *Lb = L + blk * 4096;
+        constexpr int PER = 16 / sizeof(R), NP = 64 / PER;     // elements per 16-byte piece, pieces per row
+        for (int e = lane; e < 64 * NP; e += 32) {
+            const int r = e / NP, pc = e % NP;
+            cp_async16(S + r * 64 + ((pc ^ (r & (NP - 1))) * PER), Lb + r * 64 + pc * PER);
+        }
+        const long long off = blk * 64;
+        R v0 = in[off + lane], v1 = in[off + lane + 32];
+        cp_async_wait_all();
+        __syncwarp();
+        if (mul) {
+            R a0 = 0, a1 = 0;
+            for (int cc = 0; cc < 64; ++cc) {
+                const R zc = __shfl_sync(0xffffffffu, cc < 32 ? v0 : v1, cc & 31);
+                if (cc <= lane) a0 += S[swz<R>(lane, cc)] * zc;
+                if (cc <= lane + 32) a1 += S[swz<R>(lane + 32, cc)] * zc;
+            }
+            out[off + lane] = a0;
+            out[off + lane + 32] = a1;
+            return;
+        }
+        const R inv0 = (R)1 / S[swz<R>(lane, lane)], inv1 = (R)1 / S[swz<R>(lane + 32, lane + 32)];
+        if (fwd) {
+            sky_fwd<R>(S, inv0, inv1, v0, v1);
+            if (kin) {
+                double sq = warp_sum((double)v0 * (double)v0 + (double)v1 * (double)v1);
+                if (lane == 0) kin[blk] = sq;
+            }
+        }
+        if (bwd) sky_bwd<R>(S, inv0, inv1, v0, v1);
+        if (q) { q[off + lane] += (R)(eps * v0); q[off + lane + 32] += (R)(eps * v1); }
+        if (out) { out[off + lane] = v0; out[off + lane + 32] = v1; }
+        return;
+    }
+    // ---------------------------------------------------- dense gain block (CTA 0)
+    const int n = n_dense;
+    const long long base = nblk * 64;
+    const R *Lg = L + nblk * 4096;
+    R *v = sm;                                  // [n]
+    R *Pd = sm + ((n + 3) / 4) * 4;             // diagonal panel [32][33]
+    for (int r = tid; r < n; r += blockDim.x) v[r] = in[base + r];
     __syncthreads();
     if (mul) {
         for (int r = tid; r < n; r += blockDim.x) {
-            double acc = 0.0;
-            for (int c = 0; c <= r; ++c) acc += (double)Lb[(size_t)r * n + c] * v[c];
-            out[off + r] = (R)acc;
+            R a = 0;
+            for (int cc = 0; cc <= r; ++cc) a += Lg[(size_t)r * n + cc] * v[cc];
+            out[base + r] = a;
         }
         return;
     }
+    const int npan = (n + 31) / 32;
+    auto load_panel = [&](int p0, int m) {
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int r = e >> 5, cc = e & 31;
+            Pd[r * 33 + cc] = (r < m && cc < m) ? Lg[(size_t)(p0 + r) * n + p0 + cc] : (R)(r == cc ? 1 : 0);
+        }
+    };
     if (fwd) {
-        for (int k = 0; k < n; ++k) {
-            if (tid == 0) v[k] /= (double)Lb[(size_t)k * n + k];
+        double ks = 0.0;
+        for (int pn = 0; pn < npan; ++pn) {
+            const int p0 = 32 * pn, m = min(32, n - p0);
+            load_panel(p0, m);
             __syncthreads();
-            const double vk = v[k];
-            for (int r = k + 1 + tid; r < n; r += blockDim.x) v[r] -= (double)Lb[(size_t)r * n + k] * vk;
+            if (w == 0) {
+                R x = lane < m ? v[p0 + lane] : (R)0;
+                for (int k = 0; k < m; ++k) {
+                    const R xk = __shfl_sync(0xffffffffu, x, k) / Pd[k * 33 + k];
+                    if (lane == k) x = xk;
+                    if (lane > k) x -= Pd[lane * 33 + k] * xk;
+                }
+                if (lane < m) { v[p0 + lane] = x; ks += (double)x * (double)x; }
+            }
+            __syncthreads();
+            for (int r = p0 + m + tid; r < n; r += blockDim.x) {
+                const R *row = Lg + (size_t)r * n + p0;
+                R a = 0;
+                for (int k = 0; k < m; ++k) a += row[k] * v[p0 + k];
+                v[r] -= a;
+            }
             __syncthreads();
         }
-        if (kin) {
-            double s = 0.0;
-            for (int r = tid; r < n; r += blockDim.x) s += v[r] * v[r];
-            red[tid] = s;
-            __syncthreads();
-            for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-                if (tid < w) red[tid] += red[tid + w];
-                __syncthreads();
-            }
-            if (tid == 0) kin[blk] = red[0];
-            __syncthreads();
+        if (w == 0) {
+            ks = warp_sum(ks);
+            if (kin && lane == 0) kin[nblk] = ks;
         }
     }
     if (bwd) {
-        for (int k = n - 1; k >= 0; --k) {
-            if (tid == 0) v[k] /= (double)Lb[(size_t)k * n + k];
+        for (int pn = npan - 1; pn >= 0; --pn) {
+            const int p0 = 32 * pn, m = min(32, n - p0);
+            load_panel(p0, m);
             __syncthreads();
-            const double vk = v[k];
-            for (int r = tid; r < k; r += blockDim.x) v[r] -= (double)Lb[(size_t)k * n + r] * vk;
+            if (w == 0) {
+                R x = lane < m ? v[p0 + lane] : (R)0;
+                for (int k = m - 1; k >= 0; --k) {
+                    const R xk = __shfl_sync(0xffffffffu, x, k) / Pd[k * 33 + k];
+                    if (lane == k) x = xk;
+                    if (lane < k) x -= Pd[k * 33 + lane] * xk;
+                }
+                if (lane < m) v[p0 + lane] = x;
+            }
+            __syncthreads();
+            // entries c < p0 lose sum over the panel rows of L[p0 + k][c] v[p0 + k]
+            for (int cc = tid; cc < p0; cc += blockDim.x) {
+                R a = 0;
+                for (int k = 0; k < m; ++k) a += Lg[(size_t)(p0 + k) * n + cc] * v[p0 + k];
+                v[cc] -= a;
+            }
             __syncthreads();
         }
     }
     for (int r = tid; r < n; r += blockDim.x) {
-        if (q) q[off + r] += (R)(eps * v[r]);
-        if (out) out[off + r] = (R)v[r];
+        if (q) q[base + r] += (R)(eps * v[r]);
+        if (out) out[base + r] = v[r];
     }
 }
 
@@ -618,14 +755,14 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
     if (bs > 1) {
         const long long nb = c.n_sky / bs;
         const int ng = 2 * c.A * c.NG;
-        k_lf_solve<R><<<(unsigned)nb, 64, (bs + 64) * sizeof(double), st>>>(bs, 0, L, in, fwd, bwd, mul, q, eps, out,
-                                                                          kin_out ? part : nullptr);
-        FM_CK_LAUNCH();
-        k_lf_solve<R><<<1, 256, (ng + 256) * sizeof(double), st>>>(ng, c.n_sky, L + (size_t)nb * bs * bs, in, fwd, bwd,
-                                                                    mul, q, eps, out, kin_out ? part + nb : nullptr);
+        const size_t smem = sizeof(R) * std::max((size_t)LF_WARPS * 4096, (size_t)(ng + 3) / 4 * 4 + 32 * 33);
+        FM_CK(cudaFuncSetAttribute(k_lf_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const long long grid = (nb + LF_WARPS - 1) / LF_WARPS + (ng > 0 ? 1 : 0);
+        k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, ng, L, in, fwd, bwd, mul, q, eps, out,
+                                                                kin_out ? part : nullptr);
         FM_CK_LAUNCH();
         if (kin_out) {
-            k_sum_to<<<1, 256, 0, st>>>((int)(nb + 1), part, kin_out);
+            k_sum_to<<<1, 256, 0, st>>>((int)(nb + (ng > 0 ? 1 : 0)), part, kin_out);
             FM_CK_LAUNCH();
         }
     } else {

@@ -28,7 +28,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
 }
 
-// bounded wait that also gives up when another warp raised the CTA's abort flag
+// bounded wait that also gives up when another warp raised the CTA's abort flag;
+// SLEEP_NS > 0 backs off between polls (for roles that mostly wait: the MMA issuer,
+// the bulk-copy issuer and the epilogue), keeping the issue slots for the producers
+template <int SLEEP_NS = 0>
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int *abort_flag)
 {
     long long t0 = clock64();
@@ -47,6 +50,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
             *abort_flag = 1;
             return false;
         }
+        if (SLEEP_NS > 0) __nanosleep(SLEEP_NS);
     }
 }
 
