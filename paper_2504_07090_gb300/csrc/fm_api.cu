@@ -233,6 +233,7 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
         FM_CK(e2);
     }
     FM_TRY(ha_setup(*c));
+    FM_TRY(modes_tc_setup(*c));
     return FM_OK;
 }
 

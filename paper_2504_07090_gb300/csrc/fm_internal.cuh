@@ -93,6 +93,16 @@ struct HaState {
     uint8_t *qimg = nullptr;   // [F][nkq][2][npad * 128] swizzled B tiles of the adjoint
 };
 
+// Mode <-> pixel transforms on the tensor cores (k_modes.cu): FP16 hi/lo images of the
+// basis tables, 128-byte-swizzled per 64-wide K atom.
+struct ModesTc {
+    bool on = false;
+    uint8_t *leg_img = nullptr;    // Leg [D tiles of 128][N]   (forward, first product)
+    uint8_t *phi_img = nullptr;    // Phi [R][M]                 (forward, second product)
+    uint8_t *phit_img = nullptr;   // Phi^T [M tiles of 128][R]  (adjoint, first product)
+    uint8_t *legt_img = nullptr;   // Leg^T [N][D]               (adjoint, second product)
+};
+
 // Device workspace and state of one handle.
 struct Ctx {
     fm_config cfg;
@@ -114,6 +124,9 @@ struct Ctx {
     int pc_block = 0;
     double *pc_blocks = nullptr;      // FP64 GN blocks (sky then gain)
     void *pc_chol = nullptr;          // factors in the working real type
+    void *pc_ginv = nullptr;          // inverse of the dense gain-block factor (block 64 only)
+    void *pc_linv = nullptr;          // inverses of the 64 x 64 sky-block factors (block 64 only)
+    double *pc_tmp = nullptr;         // FP64 scratch of the gain-block inverse
     int64_t pc_size = 0;
     // tensor-core path: per-channel power-of-two operand scale (FP16 modes), max cell solid angle
     float *tc_scale = nullptr;
@@ -130,6 +143,7 @@ struct Ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_rec;
     size_t prof_next = 0;
     HaState ha;
+    ModesTc mtc;
     // leapfrog scratch
     void *lf_q0 = nullptr, *lf_g = nullptr, *lf_z = nullptr;
     double *lf_scal = nullptr;
@@ -232,6 +246,10 @@ fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_
 // hour-angle form (drift scans with the LST step a whole number of RA pixels); ha_setup
 // leaves c.ha.on false when the geometry, precision or sizes do not allow it
 fm_status ha_setup(Ctx &c);
+// tensor-core mode transforms (float handles of the split precisions)
+fm_status modes_tc_setup(Ctx &c);
+fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc);
+fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st);
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st);
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st);
 

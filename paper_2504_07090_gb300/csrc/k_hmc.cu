@@ -341,6 +341,57 @@ __global__ void __launch_bounds__(256) k_pc_chol_big(int n, const double *__rest
     }
 }
 
+// Inverse of the dense lower-triangular gain-block factor W (FP64, row-major): thread j
+// solves W x = e_j by forward substitution in FP64 (x kept in Xd[j][.]), then stores
+// Ginv[r][j] = x_r in the working type.  Used by the leapfrog's dense solves, which then
+// become triangular matrix-vector products.
+template <typename R>
+__global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restrict__ W, double *__restrict__ Xd,
+                                                    R *__restrict__ Ginv)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double *x = Xd + (size_t)j * n;
+        for (int r = 0; r < j; ++r) x[r] = 0.0;
+        x[j] = 1.0 / W[(size_t)j * n + j];
+        for (int r = j + 1; r < n; ++r) {
+            const double *row = W + (size_t)r * n;
+            double a = 0.0;
+            for (int cc = j; cc < r; ++cc) a += row[cc] * x[cc];
+            x[r] = -a / row[r];
+        }
+        for (int r = 0; r < n; ++r) Ginv[(size_t)r * n + j] = (R)x[r];
+    }
+}
+
+// Inverses of the stored 64 x 64 sky-block factors (one CTA of 64 threads per block):
+// the factor, as stored in the working type, is read into FP64 shared memory and thread
+// j solves L x = e_j by forward substitution; Linv[r][j] = x_r.  Inverting the stored
+// factor keeps L^-1 (L z) = z to FP64 rounding before the final store.
+template <typename R>
+__global__ void __launch_bounds__(64) k_pc_blk_inv(const R *__restrict__ L, R *__restrict__ Linv)
+{
+    extern __shared__ double sd[];
+    double *sL = sd;                  // [64][65]
+    double *sX = sd + 64 * 65;        // [64 columns][65]
+    const R *Lb = L + (size_t)blockIdx.x * 4096;
+    for (int e = threadIdx.x; e < 4096; e += 64) sL[(e >> 6) * 65 + (e & 63)] = (double)Lb[e];
+    __syncthreads();
+    const int j = threadIdx.x;
+    double *x = sX + j * 65;
+    for (int r = 0; r < 64; ++r) {
+        double v = 0.0;
+        if (r == j) v = 1.0 / sL[r * 65 + r];
+        else if (r > j) {
+            double a = 0.0;
+            for (int cc = j; cc < r; ++cc) a += sL[r * 65 + cc] * x[cc];
+            v = -a / sL[r * 65 + r];
+        }
+        x[r] = v;
+    }
+    R *Ib = Linv + (size_t)blockIdx.x * 4096;
+    for (int r = 0; r < 64; ++r) Ib[r * 64 + j] = (R)x[r];
+}
+
 // Sky prior on the block diagonals: blocks[k/bs][k%bs][k%bs] += lam[k]
 template <typename R>
 __global__ void k_pc_add_prior(long long nsky, int bs, const R *__restrict__ lam, double *__restrict__ blocks)
@@ -446,6 +497,30 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
                                                                   c.have_prior ? 1 : 0, Lf, c.status);
             k_pc_chol_big<R><<<1, 256, 0, st>>>(ng, c.pc_blocks + sky_sz, (const R *)c.lam, c.n_sky,
                                                 c.have_prior ? 1 : 0, W, Lf + sky_sz, c.status);
+            if (!c.pc_linv) {
+                if (cudaMalloc(&c.pc_linv, c.rsz * (size_t)sky_sz) != cudaSuccess) {
+                    rc = FM_ERR_ALLOC;
+                    set_error("cudaMalloc sky-block inverses");
+                    break;
+                }
+                c.allocs.push_back(c.pc_linv);
+            }
+            cudaFuncSetAttribute(k_pc_blk_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * 64 * 65 * sizeof(double)));
+            k_pc_blk_inv<R><<<(unsigned)nsky_blk, 64, 2 * 64 * 65 * sizeof(double), st>>>(Lf, (R *)c.pc_linv);
+            if (ng > 0) {
+                if (!c.pc_ginv) {
+                    if (cudaMalloc(&c.pc_ginv, c.rsz * (size_t)ng * ng) != cudaSuccess ||
+                        cudaMalloc(&c.pc_tmp, sizeof(double) * (size_t)ng * ng) != cudaSuccess) {
+                        rc = FM_ERR_ALLOC;
+                        set_error("cudaMalloc gain-block inverse");
+                        break;
+                    }
+                    c.allocs.push_back(c.pc_ginv);
+                    c.allocs.push_back(c.pc_tmp);
+                }
+                k_pc_tri_inv<R><<<cdiv(ng, 128), 128, 0, st>>>(ng, W, c.pc_tmp, (R *)c.pc_ginv);
+            }
         } else {
             k_pc_chol_diag<R><<<cdiv(need, 256), 256, 0, st>>>(need, c.pc_blocks, (const R *)c.lam,
                                                                c.have_prior ? 1 : 0, Lf, c.status);
@@ -487,14 +562,13 @@ __global__ void k_copy(long long n, const R *__restrict__ x, R *__restrict__ y)
 // if (bwd) v = L^-T v (backward substitution); then q += eps v (q != NULL) and/or
 // out = v (out != NULL).  mul: out = L in instead.  Arithmetic in the working type R.
 //
-// One warp per 64 x 64 sky block: the block is copied to shared memory with cp.async
-// (16-byte pieces, XOR-permuted within each row), lane l owns entries l and l + 32, and
-// each substitution step broadcasts the solved entry (scaled by the reciprocal of its
-// diagonal) by a shuffle: column k of L updates the entries below k in the forward
-// sweep, row k of L the entries above k in the backward one.  CTA 0 (when n_dense > 0) solves the dense gain block of order
-// n_dense, panel by panel (32 columns): the diagonal panel is staged in shared memory
-// and solved by warp 0 with shuffles, then the CTA updates the remaining entries from
-// global memory (rows of L for the forward sweep, coalesced columns for the backward).
+// The solves use the explicit inverses of the factors (computed in FP64 from the stored
+// factors when the preconditioner is built), so every operation is a triangular
+// matrix-vector product without a serial dependency.  One warp per 64 x 64 sky block:
+// the block (L^-1, or L for mul) is copied to shared memory with cp.async (16-byte
+// pieces, XOR-permuted within each row), lane l owns entries l and l + 32, and the
+// vector entries are broadcast by shuffles.  CTA 0 (when n_dense > 0) handles the dense
+// gain block of order n_dense the same way from global memory, overlapping the sky blocks.
 constexpr int LF_WARPS = 4;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
@@ -522,40 +596,39 @@ __device__ __forceinline__ int swz(int r, int c)
     return r * 64 + (((c / PER) ^ (r & (NP - 1))) * PER) + (c % PER);
 }
 
-// lane l holds entries l and l + 32 of a 64-vector; inv0, inv1 = 1 / L[l][l], 1 / L[l+32][l+32]
+// y = T v for a 64 x 64 lower-triangular T stored with zeros above the diagonal in the
+// XOR-permuted image S: lane l forms rows l and l + 32 from whole 16-byte pieces of its
+// rows and broadcast pieces of v (vs, shared)
 template <typename R>
-__device__ __forceinline__ void sky_fwd(const R *S, R inv0, R inv1, R &v0, R &v1)
+__device__ __forceinline__ void lower_mv(const R *S, const R *vs, R &y0, R &y1)
 {
+    constexpr int PER = 16 / sizeof(R), NP = 64 / PER;
     const int lane = threadIdx.x & 31;
-    for (int k = 0; k < 64; ++k) {
-        const bool hi = k >= 32;
-        const R vk = __shfl_sync(0xffffffffu, hi ? v1 * inv1 : v0 * inv0, k & 31);
-        if (lane == (k & 31)) { if (hi) v1 = vk; else v0 = vk; }
-        if (!hi && lane > k) v0 -= S[swz<R>(lane, k)] * vk;
-        if (lane + 32 > k) v1 -= S[swz<R>(lane + 32, k)] * vk;
+    const R *r0 = S + lane * 64, *r1 = S + (lane + 32) * 64;
+    const int x0 = lane & (NP - 1);
+    R a0 = 0, a1 = 0;
+#pragma unroll
+    for (int pc = 0; pc < NP; ++pc) {
+        const int ph = (pc ^ x0) * PER;              // rows l and l + 32 share the permutation
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const R vq = vs[pc * PER + q];
+            a0 += r0[ph + q] * vq;
+            a1 += r1[ph + q] * vq;
+        }
     }
+    y0 = a0;
+    y1 = a1;
 }
 
 template <typename R>
-__device__ __forceinline__ void sky_bwd(const R *S, R inv0, R inv1, R &v0, R &v1)
-{
-    const int lane = threadIdx.x & 31;
-    for (int k = 63; k >= 0; --k) {
-        const bool hi = k >= 32;
-        const R vk = __shfl_sync(0xffffffffu, hi ? v1 * inv1 : v0 * inv0, k & 31);
-        if (lane == (k & 31)) { if (hi) v1 = vk; else v0 = vk; }
-        if (lane < k) v0 -= S[swz<R>(k, lane)] * vk;
-        if (lane + 32 < k) v1 -= S[swz<R>(k, lane + 32)] * vk;
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, int n_dense,
-                                                          const R *__restrict__ L, const R *__restrict__ in, int fwd,
+__global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, int n_dense, const R *__restrict__ Gi,
+                                                          const R *__restrict__ Li, const R *__restrict__ L, const R *__restrict__ in, int fwd,
                                                           int bwd, int mul, R *__restrict__ q, double eps,
                                                           R *__restrict__ out, double *__restrict__ kin)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[LF_WARPS];
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const bool dense = n_dense > 0 && blockIdx.x == 0;
@@ -563,116 +636,105 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, int n_
         // ------------------------------------------------ one 64 x 64 block per warp
         const long long blk = (long long)(blockIdx.x - (n_dense > 0 ? 1 : 0)) * LF_WARPS + w;
         if (blk >= nblk) return;
-        R *S = sm + (size_t)w * 4096;
-        const R *Lb = L + blk * 4096;
+        R *S = sm + (size_t)w * (4096 + 64);            // block image, then the 64-vector
+        R *vs = S + 4096;
+        const R *Lb = (mul ? L : Li) + blk * 4096;      // the factor for mul, its inverse for the solves
         constexpr int PER = 16 / sizeof(R), NP = 64 / PER;     // elements per 16-byte piece, pieces per row
         for (int e = lane; e < 64 * NP; e += 32) {
             const int r = e / NP, pc = e % NP;
             cp_async16(S + r * 64 + ((pc ^ (r & (NP - 1))) * PER), Lb + r * 64 + pc * PER);
         }
         const long long off = blk * 64;
-        R v0 = in[off + lane], v1 = in[off + lane + 32];
+        vs[lane] = in[off + lane];
+        vs[lane + 32] = in[off + lane + 32];
         cp_async_wait_all();
         __syncwarp();
         if (mul) {
-            R a0 = 0, a1 = 0;
-            for (int cc = 0; cc < 64; ++cc) {
-                const R zc = __shfl_sync(0xffffffffu, cc < 32 ? v0 : v1, cc & 31);
-                if (cc <= lane) a0 += S[swz<R>(lane, cc)] * zc;
-                if (cc <= lane + 32) a1 += S[swz<R>(lane + 32, cc)] * zc;
-            }
-            out[off + lane] = a0;
-            out[off + lane + 32] = a1;
+            R y0, y1;
+            lower_mv<R>(S, vs, y0, y1);
+            out[off + lane] = y0;
+            out[off + lane + 32] = y1;
             return;
         }
-        const R inv0 = (R)1 / S[swz<R>(lane, lane)], inv1 = (R)1 / S[swz<R>(lane + 32, lane + 32)];
+        R v0 = vs[lane], v1 = vs[lane + 32];
         if (fwd) {
-            sky_fwd<R>(S, inv0, inv1, v0, v1);
+            lower_mv<R>(S, vs, v0, v1);
             if (kin) {
                 double sq = warp_sum((double)v0 * (double)v0 + (double)v1 * (double)v1);
                 if (lane == 0) kin[blk] = sq;
             }
         }
-        if (bwd) sky_bwd<R>(S, inv0, inv1, v0, v1);
+        if (bwd) {
+            // v = T^T v: lane l forms entries l and l + 32 from rows r (column reads)
+            __syncwarp();
+            vs[lane] = v0;
+            vs[lane + 32] = v1;
+            __syncwarp();
+            R b0 = 0, b1 = 0;
+            const int c0 = lane / PER, c1 = (lane + 32) / PER, q0 = lane % PER;
+#pragma unroll 8
+            for (int r = 0; r < 64; ++r) {
+                const R zr = vs[r];
+                const int x = r & (NP - 1);
+                b0 += S[r * 64 + ((c0 ^ x) * PER) + q0] * zr;
+                b1 += S[r * 64 + ((c1 ^ x) * PER) + q0] * zr;
+            }
+            v0 = b0;
+            v1 = b1;
+        }
         if (q) { q[off + lane] += (R)(eps * v0); q[off + lane + 32] += (R)(eps * v1); }
         if (out) { out[off + lane] = v0; out[off + lane + 32] = v1; }
         return;
     }
     // ---------------------------------------------------- dense gain block (CTA 0)
+    // with Gi = L_g^-1 (stored at build time): L_g^-1 v is a row-wise product (warp per
+    // row, lanes along the row) and L_g^-T v a column-wise one (thread per column, rows
+    // read coalesced across threads)
     const int n = n_dense;
     const long long base = nblk * 64;
     const R *Lg = L + nblk * 4096;
     R *v = sm;                                  // [n]
-    R *Pd = sm + ((n + 3) / 4) * 4;             // diagonal panel [32][33]
+    R *y = sm + ((n + 3) / 4) * 4;              // [n]
     for (int r = tid; r < n; r += blockDim.x) v[r] = in[base + r];
     __syncthreads();
     if (mul) {
-        for (int r = tid; r < n; r += blockDim.x) {
+        for (int r = w; r < n; r += LF_WARPS) {
+            const R *row = Lg + (size_t)r * n;
             R a = 0;
-            for (int cc = 0; cc <= r; ++cc) a += Lg[(size_t)r * n + cc] * v[cc];
-            out[base + r] = a;
+            for (int cc = lane; cc <= r; cc += 32) a += row[cc] * v[cc];
+            a = warp_sum(a);
+            if (lane == 0) out[base + r] = a;
         }
         return;
     }
-    const int npan = (n + 31) / 32;
-    auto load_panel = [&](int p0, int m) {
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
-            const int r = e >> 5, cc = e & 31;
-            Pd[r * 33 + cc] = (r < m && cc < m) ? Lg[(size_t)(p0 + r) * n + p0 + cc] : (R)(r == cc ? 1 : 0);
-        }
-    };
     if (fwd) {
         double ks = 0.0;
-        for (int pn = 0; pn < npan; ++pn) {
-            const int p0 = 32 * pn, m = min(32, n - p0);
-            load_panel(p0, m);
-            __syncthreads();
-            if (w == 0) {
-                R x = lane < m ? v[p0 + lane] : (R)0;
-                for (int k = 0; k < m; ++k) {
-                    const R xk = __shfl_sync(0xffffffffu, x, k) / Pd[k * 33 + k];
-                    if (lane == k) x = xk;
-                    if (lane > k) x -= Pd[lane * 33 + k] * xk;
-                }
-                if (lane < m) { v[p0 + lane] = x; ks += (double)x * (double)x; }
-            }
-            __syncthreads();
-            for (int r = p0 + m + tid; r < n; r += blockDim.x) {
-                const R *row = Lg + (size_t)r * n + p0;
-                R a = 0;
-                for (int k = 0; k < m; ++k) a += row[k] * v[p0 + k];
-                v[r] -= a;
-            }
-            __syncthreads();
+        for (int r = w; r < n; r += LF_WARPS) {
+            const R *row = Gi + (size_t)r * n;
+            R a = 0;
+            for (int cc = lane; cc <= r; cc += 32) a += row[cc] * v[cc];
+            a = warp_sum(a);
+            if (lane == 0) { y[r] = a; ks += (double)a * (double)a; }
         }
-        if (w == 0) {
-            ks = warp_sum(ks);
-            if (kin && lane == 0) kin[nblk] = ks;
+        __syncthreads();
+        for (int r = tid; r < n; r += blockDim.x) v[r] = y[r];
+        if (lane == 0) red[w] = ks;
+        __syncthreads();
+        if (kin && tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < LF_WARPS; ++k) t += red[k];
+            kin[nblk] = t;
         }
     }
     if (bwd) {
-        for (int pn = npan - 1; pn >= 0; --pn) {
-            const int p0 = 32 * pn, m = min(32, n - p0);
-            load_panel(p0, m);
-            __syncthreads();
-            if (w == 0) {
-                R x = lane < m ? v[p0 + lane] : (R)0;
-                for (int k = m - 1; k >= 0; --k) {
-                    const R xk = __shfl_sync(0xffffffffu, x, k) / Pd[k * 33 + k];
-                    if (lane == k) x = xk;
-                    if (lane < k) x -= Pd[k * 33 + lane] * xk;
-                }
-                if (lane < m) v[p0 + lane] = x;
-            }
-            __syncthreads();
-            // entries c < p0 lose sum over the panel rows of L[p0 + k][c] v[p0 + k]
-            for (int cc = tid; cc < p0; cc += blockDim.x) {
-                R a = 0;
-                for (int k = 0; k < m; ++k) a += Lg[(size_t)(p0 + k) * n + cc] * v[p0 + k];
-                v[cc] -= a;
-            }
-            __syncthreads();
+        for (int cc = tid; cc < n; cc += blockDim.x) {
+            R a = 0;
+            for (int r = cc; r < n; ++r) a += Gi[(size_t)r * n + cc] * v[r];
+            y[cc] = a;
         }
+        __syncthreads();
+        for (int r = tid; r < n; r += blockDim.x) v[r] = y[r];
+        __syncthreads();
     }
     for (int r = tid; r < n; r += blockDim.x) {
         if (q) q[base + r] += (R)(eps * v[r]);
@@ -755,11 +817,12 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
     if (bs > 1) {
         const long long nb = c.n_sky / bs;
         const int ng = 2 * c.A * c.NG;
-        const size_t smem = sizeof(R) * std::max((size_t)LF_WARPS * 4096, (size_t)(ng + 3) / 4 * 4 + 32 * 33);
+        const size_t smem = sizeof(R) * std::max((size_t)LF_WARPS * (4096 + 64), 2 * ((size_t)(ng + 3) / 4 * 4));
         FM_CK(cudaFuncSetAttribute(k_lf_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS + (ng > 0 ? 1 : 0);
-        k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, ng, L, in, fwd, bwd, mul, q, eps, out,
-                                                                kin_out ? part : nullptr);
+        k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, ng, (const R *)c.pc_ginv,
+                                                                (const R *)c.pc_linv, L, in, fwd, bwd, mul, q, eps,
+                                                                out, kin_out ? part : nullptr);
         FM_CK_LAUNCH();
         if (kin_out) {
             k_sum_to<<<1, 256, 0, st>>>((int)(nb + (ng > 0 ? 1 : 0)), part, kin_out);

@@ -1,0 +1,551 @@
+// Mode <-> pixel transforms on the tensor cores (sm_103a tcgen05), Eq. (fg_separable):
+//   forward  x[f][d][r] = sum_m Phi[r][m] W[d][m],   W[d][m] = sum_n Leg[d][n] a[f][m][n]
+//   adjoint  abar[f][m][n] = sum_d U[m][d] Leg[d][n],  U[m][d] = sum_r Phi[r][m] xbar[f][d][r]
+// Each direction is two chained GEMMs in one CTA per (channel, 128-row tile): the first
+// product accumulates in TMEM, is scaled by a power of two, split into FP16 hi/lo parts
+// and written to shared memory as the A operand of the second product.  Every operand is
+// used in its natural K-major layout (no transposes at run time): the basis tables and
+// their transposes are prepared once per handle as 128-byte-swizzled FP16 hi/lo images,
+// the modes a and the pixel gradient xbar are converted tile by tile.  Products use the
+// three-term split hi*hi + hi*lo + lo*hi with FP32 accumulation.
+//
+// K is processed one 64-wide atom at a time with single-buffered tiles: fill (bulk copy
+// of an image atom, conversion of the other operand), fence, one thread issues 4 x 3 MMAs
+// and commits to an mbarrier that all threads wait on (bounded) before the next atom.
+#include <cmath>
+#include <cstdlib>
+
+#include "fm_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fm {
+namespace {
+
+using namespace tc;
+
+constexpr int MD_THREADS = 256;
+constexpr float MD_CSCALE = 16384.f;     // basis tables (|value| <= 1) are stored times 2^14
+
+struct MdDims {
+    int F, M, N, R, D;         // modes (RA, Dec), pixels (RA, Dec)
+    int Mp, Np, Rp, Dp;        // padded to multiples of 64
+};
+
+// 128-byte-swizzled K-major atom: element (row, k) of a [rows][64] atom at byte offset
+__device__ __forceinline__ uint32_t atom_off(int row, int k)
+{
+    return (uint32_t)row * 128u + ((uint32_t)(((k >> 3) ^ (row & 7))) << 4) + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ void split_h(float v, __half &h, __half &l)
+{
+    h = __float2half_rn(v);
+    l = __float2half_rn(v - __half2float(h));
+}
+
+// image of an operand [rows_pad][k_pad]: per 64-wide K atom, the hi rows then the lo rows
+// (element (row, k) = scale * (transpose ? src[k][row0 + row] : src[row0 + row][k]), zero
+// outside the source)
+__global__ void k_md_image(const double *__restrict__ src, int src_rows, int src_cols, int transpose, int row0,
+                           int rows_pad, int k_pad, float scale, uint8_t *__restrict__ img)
+{
+    const long long total = (long long)rows_pad * k_pad;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / k_pad), k = (int)(e % k_pad);
+        const int sr = transpose ? k : row0 + row, sc = transpose ? row0 + row : k;
+        const double v = (sr < src_rows && sc < src_cols) ? src[(size_t)sr * src_cols + sc] : 0.0;
+        __half h, l;
+        split_h((float)(v * scale), h, l);
+        uint8_t *atom = img + (size_t)(k >> 6) * 2 * rows_pad * 128;
+        *reinterpret_cast<__half *>(atom + atom_off(row, k & 63)) = h;
+        *reinterpret_cast<__half *>(atom + (size_t)rows_pad * 128 + atom_off(row, k & 63)) = l;
+    }
+}
+
+__device__ __forceinline__ float block_max(float v, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    float m = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+    return m;
+}
+
+__device__ __forceinline__ float pow2_below(float mx)
+{
+    float sc = 1.f;
+    if (mx > 0.f && isfinite(mx)) {
+        int e;
+        frexpf(mx, &e);
+        sc = ldexpf(1.f, 14 - e);
+    }
+    return sc;
+}
+
+// One K atom: A (128 rows) and B (nrows rows) tiles are in shared memory at a_s / b_s,
+// hi rows then lo rows; D[tmem] (+)= A B^T over the atom's 64 K values.
+__device__ __forceinline__ void issue_atom(uint32_t tmem, uint32_t a_s, uint32_t b_s, int nrows, bool first,
+                                           uint32_t idesc)
+{
+    const uint32_t a_lo = a_s + 128u * 128u, b_lo = b_s + (uint32_t)nrows * 128u;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t dah = sdesc_sw128(a_s + 32u * kk), dbh = sdesc_sw128(b_s + 32u * kk);
+        mma_bf16(tmem, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+        mma_bf16(tmem, dah, sdesc_sw128(b_lo + 32u * kk), idesc, 1u);
+        mma_bf16(tmem, sdesc_sw128(a_lo + 32u * kk), dbh, idesc, 1u);
+    }
+}
+
+// Shared state of both kernels.
+struct MdSmem {
+    uint8_t *a, *b;            // operand atoms
+    uint32_t a_s, b_s;         // their shared addresses
+    uint32_t bar;              // MMA completion barrier
+    uint32_t *tmem_slot;
+    volatile int *abort_flag;
+    float *red;
+};
+
+__device__ __forceinline__ MdSmem md_smem(int b_rows_max)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *g = smem_raw + (base - raw);
+    MdSmem m;
+    m.a = g;
+    m.a_s = base;
+    m.b = g + 2 * 128 * 128;
+    m.b_s = base + 2u * 128u * 128u;
+    const uint32_t tail = 2u * 128u * 128u + 2u * (uint32_t)b_rows_max * 128u;
+    m.bar = base + tail;
+    m.tmem_slot = reinterpret_cast<uint32_t *>(g + tail + 8);
+    m.abort_flag = reinterpret_cast<volatile int *>(g + tail + 12);
+    m.red = reinterpret_cast<float *>(g + tail + 16);
+    return m;
+}
+
+// wait for the atom's MMAs (phase `ph`), all threads; returns false after a timeout
+__device__ __forceinline__ bool md_wait(const MdSmem &m, uint32_t ph)
+{
+    mbar_wait_ab<32>(m.bar, ph, m.abort_flag);
+    __syncthreads();
+    return *m.abort_flag == 0;
+}
+
+// after an atom is filled: make the generic-proxy writes visible to the tensor core
+__device__ __forceinline__ void md_filled()
+{
+    fence_async_smem();
+    __syncthreads();
+}
+
+// copy a 2 x rows x 128-byte image atom into shared memory (all threads, 16-byte pieces,
+// eight loads in flight per thread)
+__device__ __forceinline__ void md_copy_atom(uint8_t *dst, const uint8_t *src, int rows)
+{
+    const int n = rows * 2 * 128 / 16;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int e0 = threadIdx.x; e0 < n; e0 += 8 * blockDim.x) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < n) v[u] = __ldg(s4 + e);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < n) d4[e] = v[u];
+        }
+    }
+}
+
+// largest |v| over a row-major [rows][cols] array (16-byte loads when rows are 16-byte
+// aligned, eight in flight per thread); every thread receives the result
+__device__ __forceinline__ float md_absmax(const float *a, int rows, int cols, bool skip_first, float *red)
+{
+    float m = 0.f;
+    const long long n = (long long)rows * cols;
+    if ((cols & 3) == 0) {
+        const float4 *a4 = reinterpret_cast<const float4 *>(a);
+        const long long n4 = n / 4;
+        for (long long e0 = threadIdx.x; e0 < n4; e0 += 8LL * blockDim.x) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const long long e = e0 + (long long)u * blockDim.x;
+                v[u] = e < n4 ? __ldg(a4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const long long e = e0 + (long long)u * blockDim.x;
+                const float x0 = (skip_first && e == 0) ? 0.f : v[u].x;
+                m = fmaxf(m, fmaxf(fmaxf(fabsf(x0), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+            }
+        }
+    } else {
+        for (long long e = threadIdx.x; e < n; e += blockDim.x)
+            if (!(skip_first && e == 0)) m = fmaxf(m, fabsf(__ldg(a + e)));
+    }
+    return block_max(m, red);
+}
+
+// B operand atom from a row-major FP32 matrix src [rows][cols] (rows_pad rows, K values
+// 64 ka .. 64 ka + 63), scaled and split into FP16 hi / lo rows; entry (0, 0) is read as
+// zero when zero00.  16-byte loads (eight in flight) when cols is a multiple of 4.
+__device__ __forceinline__ void md_convert_atom(const float *src, int rows, int cols, int rows_pad, int ka,
+                                                float sc, bool zero00, uint8_t *b)
+{
+    const int n4 = rows_pad * 16;                  // 4-value pieces in the atom
+    const bool vec = (cols & 3) == 0;
+    for (int e0 = threadIdx.x; e0 < n4; e0 += 8 * blockDim.x) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int row = e >> 4, k = 64 * ka + 4 * (e & 15);
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < n4 && row < rows) {
+                const float *p = src + (size_t)row * cols + k;
+                if (vec && k + 3 < cols) x = __ldg(reinterpret_cast<const float4 *>(p));
+                else {
+                    if (k < cols) x.x = __ldg(p);
+                    if (k + 1 < cols) x.y = __ldg(p + 1);
+                    if (k + 2 < cols) x.z = __ldg(p + 2);
+                    if (k + 3 < cols) x.w = __ldg(p + 3);
+                }
+                if (zero00 && row == 0 && k == 0) x.x = 0.f;
+            }
+            v[u] = x;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= n4) break;
+            const int row = e >> 4, k = 4 * (e & 15);
+            __half h0, l0, h1, l1, h2, l2, h3, l3;
+            split_h(v[u].x * sc, h0, l0);
+            split_h(v[u].y * sc, h1, l1);
+            split_h(v[u].z * sc, h2, l2);
+            split_h(v[u].w * sc, h3, l3);
+            const uint32_t off = atom_off(row, k);     // 4 consecutive K values stay in one 16-byte chunk
+            auto pk = [](__half lo16, __half hi16) {
+                return (uint32_t)__half_as_ushort(lo16) | ((uint32_t)__half_as_ushort(hi16) << 16);
+            };
+            *reinterpret_cast<uint2 *>(b + off) = make_uint2(pk(h0, h1), pk(h2, h3));
+            *reinterpret_cast<uint2 *>(b + (size_t)rows_pad * 128 + off) = make_uint2(pk(l0, l1), pk(l2, l3));
+        }
+    }
+}
+
+// TMEM accumulator (128 lanes x ncols columns at column c0) -> scaled FP16 hi/lo A atom
+// for K atom ka of the next product; warps w and w + 4 share lane quarter w & 3 and take
+// alternate 16-column groups
+__device__ __forceinline__ void md_tmem_to_atom(uint32_t tmem, int c0, int ka, float sc, uint8_t *a)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = w & 3, half = w >> 2;
+    const int row = 32 * quarter + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(c0 + 64 * ka);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const int cg = 16 * (2 * g + half);          // columns cg .. cg + 15 of the atom
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)cg, v);
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+            __half h0, l0, h1, l1;
+            split_h(v[q] * sc, h0, l0);
+            split_h(v[q + 1] * sc, h1, l1);
+            const uint32_t off = atom_off(row, cg + q);
+            *reinterpret_cast<__half2 *>(a + off) = __halves2half2(h0, h1);
+            *reinterpret_cast<__half2 *>(a + 128 * 128 + off) = __halves2half2(l0, l1);
+        }
+    }
+}
+
+// largest |value| of a TMEM accumulator (all threads receive it)
+__device__ __forceinline__ float md_tmem_max(uint32_t tmem, int c0, int ncols, float *red)
+{
+    const int w = threadIdx.x >> 5, quarter = w & 3, half = w >> 2;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+    float m = 0.f;
+    for (int cg = 16 * half; cg < ncols; cg += 32) {
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)cg, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) m = fmaxf(m, fabsf(v[q]));
+    }
+    return block_max(m, red);
+}
+
+// ---------------------------------------------------------------- forward
+// CTA (f, d tile): stage 1 D1[d][m] (TMEM columns 0 .. Mp) = Leg_tile a_f^T over n;
+// stage 2 D2[d][r] (columns Mp .. Mp + Rp) = W Phi^T over m; x[f][d][r] = D2 / scales.
+__global__ void __launch_bounds__(MD_THREADS, 1)
+k_modes_fwd(MdDims z, const float *__restrict__ a_all, int skip_dc, const uint8_t *__restrict__ leg_img,
+            const uint8_t *__restrict__ phi_img, float *__restrict__ x_all, int *__restrict__ status, int ncols)
+{
+    const int f = blockIdx.x, dt = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    MdSmem m = md_smem(z.Mp > z.Rp ? z.Mp : z.Rp);
+    if (tid == 0) {
+        mbar_init(m.bar, 1);
+        *m.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(su32(m.tmem_slot), (uint32_t)ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *m.tmem_slot;
+    const float *a = a_all + (size_t)f * z.M * z.N;
+    uint32_t ph = 0;
+    bool ok = true;
+
+    // scale of the modes
+    const float sa = pow2_below(md_absmax(a, z.M, z.N, skip_dc != 0, m.red));
+
+    // stage 1: K = n, A = Leg tile image, B = a_f rows m
+    const uint32_t idesc1 = idesc_f16(128, z.Mp, 0);
+    for (int ka = 0; ka < z.Np / 64 && ok; ++ka) {
+        md_copy_atom(m.a, leg_img + ((size_t)dt * (z.Np / 64) + ka) * 2 * 128 * 128, 128);
+        md_convert_atom(a, z.M, z.N, z.Mp, ka, sa, skip_dc != 0, m.b);
+        md_filled();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_atom(tmem, m.a_s, m.b_s, z.Mp, ka == 0, idesc1);
+            mma_commit(m.bar);
+        }
+        ok = md_wait(m, ph);
+        ph ^= 1u;
+    }
+    tc_fence_after();
+
+    // stage 2: K = m, A = scaled W from TMEM, B = Phi image
+    const float g = ok ? pow2_below(md_tmem_max(tmem, 0, z.Mp, m.red)) : 1.f;
+    const uint32_t idesc2 = idesc_f16(128, z.Rp, 0);
+    for (int ka = 0; ka < z.Mp / 64 && ok; ++ka) {
+        md_tmem_to_atom(tmem, 0, ka, g, m.a);
+        md_copy_atom(m.b, phi_img + (size_t)ka * 2 * z.Rp * 128, z.Rp);
+        tc_fence_before();
+        md_filled();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_atom(tmem + (uint32_t)z.Mp, m.a_s, m.b_s, z.Rp, ka == 0, idesc2);
+            mma_commit(m.bar);
+        }
+        ok = md_wait(m, ph);
+        ph ^= 1u;
+    }
+    tc_fence_after();
+
+    // x = D2 / (g 2^28 sa)
+    if (ok) {
+        const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sa);
+        const int quarter = warp & 3, half = warp >> 2, lane = tid & 31;
+        const int d = 128 * dt + 32 * quarter + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)z.Mp;
+        float *xr = x_all + ((size_t)f * z.D + d) * z.R;
+        for (int cg = 16 * half; cg < z.Rp; cg += 32) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)cg, v);
+            if (d < z.D)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (cg + q < z.R) xr[cg + q] = v[q] * inv;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*m.abort_flag && tid == 0) {
+        mbar_drain(m.bar, ph ^ 1u);            // the atom whose wait gave up
+        atomicExch(status, (int)FM_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)ncols);
+    }
+}
+
+// ---------------------------------------------------------------- adjoint
+// CTA (f, m tile): stage 1 D1[m][d] (columns 0 .. Dp) = PhiT_tile xbar_f^T over r;
+// stage 2 D2[m][n] (columns Dp .. Dp + Np) = U LegT^T over d; abar = D2 / scales.
+__global__ void __launch_bounds__(MD_THREADS, 1)
+k_modes_adj(MdDims z, const float *__restrict__ xb_all, const uint8_t *__restrict__ phit_img,
+            const uint8_t *__restrict__ legt_img, float *__restrict__ abar_all, int *__restrict__ status, int ncols)
+{
+    const int f = blockIdx.x, mtile = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    MdSmem m = md_smem(z.Dp > z.Np ? z.Dp : z.Np);
+    if (tid == 0) {
+        mbar_init(m.bar, 1);
+        *m.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(su32(m.tmem_slot), (uint32_t)ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *m.tmem_slot;
+    const float *xb = xb_all + (size_t)f * z.D * z.R;
+    uint32_t ph = 0;
+    bool ok = true;
+
+    const float sx = pow2_below(md_absmax(xb, z.D, z.R, false, m.red));
+
+    // stage 1: K = r, A = PhiT tile image, B = xbar_f rows d
+    const uint32_t idesc1 = idesc_f16(128, z.Dp, 0);
+    for (int ka = 0; ka < z.Rp / 64 && ok; ++ka) {
+        md_copy_atom(m.a, phit_img + ((size_t)mtile * (z.Rp / 64) + ka) * 2 * 128 * 128, 128);
+        md_convert_atom(xb, z.D, z.R, z.Dp, ka, sx, false, m.b);
+        md_filled();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_atom(tmem, m.a_s, m.b_s, z.Dp, ka == 0, idesc1);
+            mma_commit(m.bar);
+        }
+        ok = md_wait(m, ph);
+        ph ^= 1u;
+    }
+    tc_fence_after();
+
+    // stage 2: K = d, A = scaled U from TMEM, B = LegT image
+    const float g = ok ? pow2_below(md_tmem_max(tmem, 0, z.Dp, m.red)) : 1.f;
+    const uint32_t idesc2 = idesc_f16(128, z.Np, 0);
+    for (int ka = 0; ka < z.Dp / 64 && ok; ++ka) {
+        md_tmem_to_atom(tmem, 0, ka, g, m.a);
+        md_copy_atom(m.b, legt_img + (size_t)ka * 2 * z.Np * 128, z.Np);
+        tc_fence_before();
+        md_filled();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_atom(tmem + (uint32_t)z.Dp, m.a_s, m.b_s, z.Np, ka == 0, idesc2);
+            mma_commit(m.bar);
+        }
+        ok = md_wait(m, ph);
+        ph ^= 1u;
+    }
+    tc_fence_after();
+
+    if (ok) {
+        const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sx);
+        const int quarter = warp & 3, half = warp >> 2, lane = tid & 31;
+        const int mm = 128 * mtile + 32 * quarter + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)z.Dp;
+        float *ar = abar_all + ((size_t)f * z.M + mm) * z.N;
+        for (int cg = 16 * half; cg < z.Np; cg += 32) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)cg, v);
+            if (mm < z.M)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (cg + q < z.N) ar[cg + q] = v[q] * inv;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*m.abort_flag && tid == 0) {
+        mbar_drain(m.bar, ph ^ 1u);            // the atom whose wait gave up
+        atomicExch(status, (int)FM_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)ncols);
+    }
+}
+
+MdDims md_dims(const Ctx &c)
+{
+    MdDims z;
+    z.F = c.F; z.M = c.M; z.N = c.N; z.R = c.R; z.D = c.D;
+    z.Mp = (c.M + 63) / 64 * 64; z.Np = (c.N + 63) / 64 * 64;
+    z.Rp = (c.R + 63) / 64 * 64; z.Dp = (c.D + 63) / 64 * 64;
+    return z;
+}
+
+size_t md_smem_bytes(int b_rows_max) { return 1024 + 2 * 128 * 128 + 2 * (size_t)b_rows_max * 128 + 64 + 64; }
+
+int md_cols(int n)
+{
+    int c = 32;
+    while (c < n) c *= 2;
+    return c;
+}
+
+}  // namespace
+
+// Images of the basis tables (once per handle) and the on/off decision: the tensor-core
+// transforms run for the split-precision handles when every padded dimension is at most
+// 256 (one MMA N, two TMEM accumulators within 512 columns).
+fm_status modes_tc_setup(Ctx &c)
+{
+    ModesTc &s = c.mtc;
+    s.on = false;
+    if (c.prec < FM_PREC_BF16X1) return FM_OK;
+    if (const char *e = getenv("FM_MODES_TC"))
+        if (atoi(e) == 0) return FM_OK;
+    const MdDims z = md_dims(c);
+    if (z.Mp > 256 || z.Np > 256 || z.Rp > 256 || z.Dp > 256) return FM_OK;
+    const int ndt = (c.D + 127) / 128, nmt = (c.M + 127) / 128;
+    const size_t leg_n = (size_t)ndt * 2 * 128 * z.Np, phi_n = 2 * (size_t)z.Rp * z.Mp;
+    const size_t phit_n = (size_t)nmt * 2 * 128 * z.Rp, legt_n = 2 * (size_t)z.Np * z.Dp;
+    uint8_t *buf = nullptr;
+    FM_CK(cudaMalloc(&buf, 2 * (leg_n + phi_n + phit_n + legt_n)));
+    c.allocs.push_back(buf);
+    s.leg_img = buf;
+    s.phi_img = s.leg_img + 2 * leg_n;
+    s.phit_img = s.phi_img + 2 * phi_n;
+    s.legt_img = s.phit_img + 2 * phit_n;
+    for (int dt = 0; dt < ndt; ++dt) {
+        k_md_image<<<256, 256>>>(c.g.leg64, c.D, c.N, 0, 128 * dt, 128, z.Np, MD_CSCALE,
+                                 s.leg_img + (size_t)dt * 2 * 2 * 128 * z.Np);
+        FM_CK_LAUNCH();
+    }
+    k_md_image<<<256, 256>>>(c.g.phi64, c.R, c.M, 0, 0, z.Rp, z.Mp, MD_CSCALE, s.phi_img);
+    FM_CK_LAUNCH();
+    for (int mt = 0; mt < nmt; ++mt) {
+        k_md_image<<<256, 256>>>(c.g.phi64, c.R, c.M, 1, 128 * mt, 128, z.Rp, MD_CSCALE,
+                                 s.phit_img + (size_t)mt * 2 * 2 * 128 * z.Rp);
+        FM_CK_LAUNCH();
+    }
+    k_md_image<<<256, 256>>>(c.g.leg64, c.D, c.N, 1, 0, z.Np, z.Dp, MD_CSCALE, s.legt_img);
+    FM_CK_LAUNCH();
+    const size_t sf = md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp), sa = md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np);
+    FM_CK(cudaFuncSetAttribute(k_modes_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+    FM_CK(cudaFuncSetAttribute(k_modes_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+    FM_CK(cudaDeviceSynchronize());
+    s.on = true;
+    return FM_OK;
+}
+
+fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc)
+{
+    const MdDims z = md_dims(c);
+    const int ndt = (c.D + 127) / 128;
+    k_modes_fwd<<<dim3(c.F, ndt), MD_THREADS, md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp), st>>>(
+        z, a, skip_dc, c.mtc.leg_img, c.mtc.phi_img, x, c.status, md_cols(z.Mp + z.Rp));
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st)
+{
+    const MdDims z = md_dims(c);
+    const int nmt = (c.M + 127) / 128;
+    k_modes_adj<<<dim3(c.F, nmt), MD_THREADS, md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np), st>>>(
+        z, xbar, c.mtc.phit_img, c.mtc.legt_img, abar, c.status, md_cols(z.Dp + z.Np));
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+}  // namespace fm

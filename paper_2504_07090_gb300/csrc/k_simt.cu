@@ -7,6 +7,8 @@
 //   - gains, residual, chi^2 partials in FP64 and the adjoint weights (Eq. likelihood);
 //   - the pixel adjoint xbar_p = dOmega A sum_{p<q} Re[conj(omega_pq) K_pq];
 //   - deterministic reductions (fixed order, no floating-point atomics).
+#include <type_traits>
+
 #include "fm_internal.cuh"
 
 namespace fm {
@@ -156,6 +158,8 @@ template <> const float *tab_leg<float>(const Ctx &c) { return c.g.leg32; }
 template <typename R>
 fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc)
 {
+    if constexpr (std::is_same<R, float>::value)
+        if (c.mtc.on) return launch_modes_tc_forward(c, a, x, st, skip_dc);
     R *t1 = (R *)c.tmp;
     GemmArgs s1{c.R, c.N, c.M, 0, c.M, 1, c.nk, c.N, 1, (long long)c.R * c.N, c.N, 1, skip_dc};
     FM_TRY(gemm<R>(s1, c.F, tab_phi<R>(c), a, t1, st));
@@ -167,6 +171,8 @@ fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int sk
 template <typename R>
 fm_status launch_modes_adjoint(Ctx &c, const R *xbar, R *abar, cudaStream_t st)
 {
+    if constexpr (std::is_same<R, float>::value)
+        if (c.mtc.on) return launch_modes_tc_adjoint(c, xbar, abar, st);
     R *t2 = (R *)c.tmp;
     GemmArgs s1{c.R, c.N, c.D, c.npix, 1, c.R, 0, c.N, 1, (long long)c.R * c.N, c.N, 1, 0};
     FM_TRY(gemm<R>(s1, c.F, xbar, tab_leg<R>(c), t2, st));

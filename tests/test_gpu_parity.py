@@ -110,9 +110,12 @@ def test_repeat_runs_are_bitwise_identical():
     assert bool((s1 == s2).all()) and bool((g1 == g2).all())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_sky_pixels_match_oracle(prec):
-    p, o, th, d, mu, lam = make_case("small")
+@pytest.mark.parametrize("name", ["small", "ha37"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "fp16x3", "fp16x1"])
+def test_sky_pixels_match_oracle(prec, name):
+    # the split precisions run the mode -> pixel transform on the tensor cores (FP16
+    # three-term split, about 2^-22 per product)
+    p, o, th, d, mu, lam = make_case(name)
     h = handle(p, prec)
     th = quant(prec, th)
     a, _ = o.split(th)
