@@ -296,8 +296,13 @@ def main():
     dom = names[0] if fwd_dom else names[1]
     dom_ms1, dom_n = (fwd_ms1, fwd_n) if fwd_dom else (adj_ms1, adj_n)
     achieved = flops_launch / (dom_ms1 / 1000.0) / 1e12 if dom_n else None
+    # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
+    # of one ncu capture of these kernels at cfg1, fp16x3); None for other workloads
+    traffic = None
+    if args.config == "cfg1" and args.precision == "fp16x3" and info["form"] == "hour_angle":
+        traffic = (296.443904e6 + 4.962048e6) if fwd_dom else (287.371264e6 + 7.693824e6)
     roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
                                f"(FP32-equivalent rate of the {args.precision} split); algorithmic flops per launch "
                                f"= {formula} = {flops_launch:.4g}",
