@@ -193,7 +193,7 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
     FM_TRY(dalloc_bytes(*c, &c->vis, (size_t)c->n_vis * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->dvis, (size_t)c->n_vis * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->omega, (size_t)c->n_vis * 2 * rs));
-    FM_TRY(dalloc_bytes(*c, &c->zpart, (size_t)c->F * c->T * c->A * 2 * rs));
+    FM_TRY(dalloc_bytes(*c, &c->zpart, ((size_t)c->F * c->T + c->F) * c->A * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->gains, (size_t)c->F * c->A * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->dgains, (size_t)c->F * c->A * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->work_par, (size_t)c->n_par * rs));
@@ -250,10 +250,10 @@ static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st)
 }
 
 template <typename R>
-static fm_status run_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st)
+static fm_status run_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st, bool q_ready = false)
 {
     if constexpr (std::is_same<R, float>::value) {
-        if (c.ha.on) return launch_adjoint_ha(c, omega, xbar, st);
+        if (c.ha.on) return launch_adjoint_ha(c, omega, xbar, st, q_ready);
         if (c.prec >= FM_PREC_BF16X1) return launch_adjoint_tc(c, omega, xbar, st);
     }
     return profiled(c, 1, st, [&]() -> fm_status { return launch_adjoint<R>(c, omega, xbar, st); });
@@ -280,11 +280,13 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
     R *x = (R *)c.x, *vis = (R *)c.vis, *om = (R *)c.omega, *zp = (R *)c.zpart, *gn = (R *)c.gains;
     FM_TRY(launch_gains<R>(c, theta + c.n_sky, gn, st));
     FM_TRY(vis_of_modes<R>(c, theta, x, vis, st));
-    FM_TRY(launch_chi2_mid<R>(c, vis, gn, om, zp, c.chi2p, st));
-    FM_TRY(run_adjoint<R>(c, om, (R *)c.xbar, st));
+    // hour-angle form: the epilogue forms the group sums of omega itself
+    const bool groups = std::is_same<R, float>::value && c.ha.on;
+    FM_TRY(launch_chi2_chan<R>(c, vis, gn, om, zp, c.chi2p, groups, st));
+    FM_TRY(run_adjoint<R>(c, om, (R *)c.xbar, st, groups));
     FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, grad, st));
-    FM_TRY(launch_gain_reduce<R>(c, zp, grad + c.n_sky, st));
-    return launch_prior_and_total<R>(c, theta, grad, c.chi2p, chi2_out, u_out, st);
+    FM_TRY(launch_gain_reduce_chan<R>(c, zp, grad + c.n_sky, st));
+    return launch_prior_and_total<R>(c, theta, grad, c.chi2p, c.F * c.T, chi2_out, u_out, st);
 }
 
 template <typename R>

@@ -88,7 +88,7 @@ struct HaState {
     unsigned *xmax = nullptr;  // [F] max |x| of the centred sky per channel, as float bits
     float *vpart = nullptr;    // [nmt * F][J][128][npad] forward partial sums
     float *q32 = nullptr;      // [F][T][U][2] residual weights summed per group
-    unsigned *qmax = nullptr;  // [F] max |Q| as float bits
+    float *qmax_ft = nullptr;  // [F][T] max |Re Q|, |Im Q| per (channel, LST)
     float *qscale = nullptr;   // [F]
     uint8_t *qimg = nullptr;   // [F][nkq][2][npad * 128] swizzled B tiles of the adjoint
 };
@@ -124,7 +124,7 @@ struct Ctx {
     int pc_block = 0;
     double *pc_blocks = nullptr;      // FP64 GN blocks (sky then gain)
     void *pc_chol = nullptr;          // factors in the working real type
-    void *pc_ginv = nullptr;          // inverse of the dense gain-block factor (block 64 only)
+    void *pc_ginv = nullptr;          // inverse of the dense gain-block factor and its transpose (block 64 only)
     void *pc_linv = nullptr;          // inverses of the 64 x 64 sky-block factors (block 64 only)
     double *pc_tmp = nullptr;         // FP64 scratch of the gain-block inverse
     int64_t pc_size = 0;
@@ -146,6 +146,7 @@ struct Ctx {
     ModesTc mtc;
     // leapfrog scratch
     void *lf_q0 = nullptr, *lf_g = nullptr, *lf_z = nullptr;
+    void *lf_y = nullptr;             // [gain-block order] intermediate of the dense solves
     double *lf_scal = nullptr;
 };
 
@@ -224,8 +225,15 @@ fm_status launch_hvp_mid(Ctx &c, const R *vis, const R *dvis, const R *g, const 
                          R *zpart, cudaStream_t st);
 template <typename R>
 fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
+// per-channel form of the chi^2 epilogue (gradient path): chi2p[f], zchan[f][a][2] (the
+// LST sums of the gain partials), omega, or (groups) the hour-angle group sums of omega
 template <typename R>
-fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, double *chi2_out,
+fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zchan, double *chi2p, bool groups,
+                           cudaStream_t st);
+template <typename R>
+fm_status launch_gain_reduce_chan(Ctx &c, const R *zchan, R *grad_gain, cudaStream_t st);
+template <typename R>
+fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, int nchi2, double *chi2_out,
                                  double *u_out, cudaStream_t st);
 template <typename R>
 fm_status launch_prior_hvp(Ctx &c, const R *v, R *hv, cudaStream_t st);
@@ -251,7 +259,8 @@ fm_status modes_tc_setup(Ctx &c);
 fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc);
 fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st);
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st);
-fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st);
+// q_ready: the group sums q32 / qmax_ft were already formed from omega (by the chi^2 epilogue)
+fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready = false);
 
 // preconditioner and leapfrog
 template <typename R>

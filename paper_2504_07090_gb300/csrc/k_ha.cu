@@ -191,7 +191,6 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     constexpr int NT = X3 ? 2 : 1;
-    float *vacc = reinterpret_cast<float *>(gbase + L.v_off);
     const uint32_t full0 = base + L.bar_off, empty0 = full0 + 8 * L.nstage;
     const uint32_t efull0 = empty0 + 8 * L.nstage, eempty0 = efull0 + 8 * L.neslot;
     const uint32_t accf0 = eempty0 + 8 * L.neslot, acce0 = accf0 + 16;
@@ -209,7 +208,6 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
             reinterpret_cast<uint4 *>(bt + tl * L.b_bytes + (size_t)h.T * 128)[r] = make_uint4(0, 0, 0, 0);
         }
     }
-    for (int e = tid; e < 128 * (int)L.vstride; e += HA_THREADS) vacc[e] = 0.f;
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
             mbar_init(full0 + 8 * s, HA_PROD_WARPS);
@@ -420,7 +418,14 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
     } else {
         // ------------------------------------------------------------ epilogue (warps 16-19)
         const int quarter = warp & 3, row = 32 * quarter + lane;
-        float *vr = vacc + (size_t)row * L.vstride;
+        // the running sum of the segment lives in TMEM columns [2 npad, 3 npad)
+        const uint32_t tsum = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(2 * h.npad);
+        {
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) z[j] = 0.f;
+            for (int c16 = 0; c16 < h.npad; c16 += 16) tmem_st16(tsum + (uint32_t)c16, z);
+        }
         long long nacc = 0;
         int local = 0, seg = (int)(q0 / h.nchunk), c = (int)(q0 % h.nchunk);
         for (long long q = q0; q < q1; ++q) {
@@ -435,24 +440,30 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
             if (*abort_flag) goto done;
             tc_fence_after();
             const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
+            float *dst = nullptr;
+            if (seg_last) {
+                const int jrank = blockIdx.x - cta_of((long long)seg * h.nchunk, h.Q, G);
+                dst = vpart + (((size_t)seg * h.J + jrank) * 128 + row) * h.npad;
+            }
             for (int c16 = 0; c16 < h.npad; c16 += 16) {
-                float v[16];
+                float v[16], a[16];
                 tmem_ld16(taddr + (uint32_t)c16, v);
+                tmem_ld16(tsum + (uint32_t)c16, a);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) vr[c16 + j] += v[j];
+                for (int j = 0; j < 16; ++j) a[j] += v[j];
+                if (seg_last) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (c16 + j < h.T) dst[c16 + j] = a[j];
+                        a[j] = 0.f;
+                    }
+                }
+                tmem_st16(tsum + (uint32_t)c16, a);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * qa);
             ++nacc;
-            if (seg_last) {
-                const int jrank = blockIdx.x - cta_of((long long)seg * h.nchunk, h.Q, G);
-                float *dst = vpart + (((size_t)seg * h.J + jrank) * 128 + row) * h.npad;
-                for (int t = 0; t < h.T; ++t) {
-                    dst[t] = vr[t];
-                    vr[t] = 0.f;
-                }
-            }
         }
     }
 done:
@@ -519,13 +530,13 @@ __global__ void __launch_bounds__(256) k_ha_xmax(int npix, const float *__restri
 
 // ------------------------------------------------------------ adjoint operand prep
 // Q_u(f, t) = sum of omega over the group's members (conjugated for reversed ones) and
-// the per-channel max |Re|, |Im| (non-negative floats order like their bit patterns).
+// the largest |Re|, |Im| per (channel, LST).
 __global__ void __launch_bounds__(256) k_ha_qsum(HaDev h, int B, const float *__restrict__ omega,
                                                  const int *__restrict__ moff, const int *__restrict__ mem,
-                                                 float *__restrict__ q32, unsigned *__restrict__ qmax)
+                                                 float *__restrict__ q32, float *__restrict__ qmax_ft)
 {
     // one CTA per (channel, LST): the omega row is staged in shared memory, each thread
-    // sums the members of its groups, and one atomic per CTA records the channel maximum
+    // sums the members of its groups, and the CTA records its maximum
     extern __shared__ float som[];                  // [2 B]
     __shared__ float red[256];
     const int ft = blockIdx.x, f = ft / h.T;
@@ -550,18 +561,28 @@ __global__ void __launch_bounds__(256) k_ha_qsum(HaDev h, int B, const float *__
         if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicMax(qmax + f, __float_as_uint(red[0]));
+    if (threadIdx.x == 0) qmax_ft[ft] = red[0];
+    (void)f;
 }
 
 // One CTA per (channel, K chunk): the swizzled B tile [npad rows t][64 rho] of the
 // adjoint, hi then (x3) lo, ready for one bulk copy.
 template <int ET, bool X3>
-__global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const unsigned *__restrict__ qmax,
+__global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const float *__restrict__ qmax_ft,
                           float *__restrict__ qscale, uint8_t *__restrict__ qimg)
 {
     constexpr int NT = X3 ? 2 : 1;
     const int f = blockIdx.x / h.nkq, kq = blockIdx.x % h.nkq;
-    const float sc = pow2_scale(__uint_as_float(qmax[f]));
+    __shared__ float smx;
+    if (threadIdx.x < 32) {
+        float m = 0.f;
+        for (int t = threadIdx.x; t < h.T; t += 32) m = fmaxf(m, qmax_ft[(size_t)f * h.T + t]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) smx = m;
+    }
+    __syncthreads();
+    const float sc = pow2_scale(smx);
     if (kq == 0 && threadIdx.x == 0) qscale[f] = sc;
     const uint32_t b_bytes = (uint32_t)h.npad * 128u;
     uint8_t *img = qimg + ((size_t)f * h.nkq + kq) * NT * b_bytes;
@@ -900,17 +921,19 @@ bool make_layout(const Ctx &c, bool x3, uint32_t eslot_bytes, uint32_t vbytes, H
     L.stage_bytes = nt * (L.a_bytes + L.b_bytes);
     L.eslot_bytes = eslot_bytes;
     L.ncols = 32;
-    while (L.ncols < 2 * c.ha.npad) L.ncols *= 2;
-    // as many table slots in flight as fit next to two operand stages (up to 4), then
-    // as many stages as fit (up to 4)
+    while (L.ncols < 3 * c.ha.npad) L.ncols *= 2;     // two accumulator sets + the forward's running sum
+    // as many operand stages as fit next to two table slots (up to 4): the stage ring's
+    // round trip through the MMA commit bounds the unit rate; then as many table slots as
+    // fit (up to 4; one when even two do not fit)
     const size_t vb = ((vbytes + 15) / 16) * 16 + 256;
-    L.neslot = 4;
-    while (L.neslot > 1 && (size_t)L.neslot * eslot_bytes + vb + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET)
-        --L.neslot;
-    const size_t fixed = (size_t)L.neslot * eslot_bytes + vb;
-    if (fixed + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET) return false;
-    L.nstage = (int)((HA_SMEM_BUDGET - fixed) / L.stage_bytes);
+    L.neslot = 2;
+    if (2 * (size_t)eslot_bytes + vb + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET) L.neslot = 1;
+    L.nstage = (int)((HA_SMEM_BUDGET - (size_t)L.neslot * eslot_bytes - vb) / L.stage_bytes);
     if (L.nstage > 4) L.nstage = 4;
+    if (L.nstage < 2) return false;
+    while (L.neslot < 4 &&
+           (size_t)(L.neslot + 1) * eslot_bytes + vb + (size_t)L.nstage * L.stage_bytes <= (size_t)HA_SMEM_BUDGET)
+        ++L.neslot;
     L.e_off = (uint32_t)L.nstage * L.stage_bytes;
     L.v_off = L.e_off + (uint32_t)L.neslot * eslot_bytes;
     L.bar_off = L.v_off + ((vbytes + 15) / 16) * 16;
@@ -923,7 +946,7 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
 {
     HaState &s = c.ha;
     HaLayout L;
-    if (!make_layout(c, X3, fwd_slot_bytes(c, X3), 128u * (uint32_t)(s.npad + 1) * 4u, L)) {
+    if (!make_layout(c, X3, fwd_slot_bytes(c, X3), 0u, L)) {
         set_error("hour-angle forward tiles exceed shared memory");
         return FM_ERR_UNSUPPORTED;
     }
@@ -947,7 +970,7 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
 }
 
 template <int ET, bool X3>
-fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar, cudaStream_t st)
+fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar, cudaStream_t st, bool q_ready)
 {
     HaState &s = c.ha;
     HaLayout L;
@@ -956,10 +979,12 @@ fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar,
         return FM_ERR_UNSUPPORTED;
     }
     L.vstride = 0;
-    FM_CK(cudaMemsetAsync(s.qmax, 0, sizeof(unsigned) * c.F, st));
-    k_ha_qsum<<<c.F * c.T, 256, sizeof(float) * 2 * (size_t)c.B, st>>>(h, c.B, omega, s.moff, s.mem, s.q32, s.qmax);
-    FM_CK_LAUNCH();
-    k_ha_qimg<ET, X3><<<c.F * s.nkq, 256, 0, st>>>(h, s.q32, s.qmax, s.qscale, s.qimg);
+    if (!q_ready) {
+        k_ha_qsum<<<c.F * c.T, 256, sizeof(float) * 2 * (size_t)c.B, st>>>(h, c.B, omega, s.moff, s.mem, s.q32,
+                                                                            s.qmax_ft);
+        FM_CK_LAUNCH();
+    }
+    k_ha_qimg<ET, X3><<<c.F * s.nkq, 256, 0, st>>>(h, s.q32, s.qmax_ft, s.qscale, s.qimg);
     FM_CK_LAUNCH();
     int grid = sm_count();
     if (grid > c.F * c.D) grid = c.F * c.D;
@@ -1130,7 +1155,7 @@ fm_status ha_setup(Ctx &c)
     {
         HaLayout L1, L2;
         const bool x3 = x3_of(c.prec);
-        if (!make_layout(c, x3, fwd_slot_bytes(c, x3), 128u * (uint32_t)(s.npad + 1) * 4u, L1) ||
+        if (!make_layout(c, x3, fwd_slot_bytes(c, x3), 0u, L1) ||
             !make_layout(c, x3, 2u * (uint32_t)(s.nant + 1) * 512u, adj_scratch_bytes(c), L2))
             return FM_OK;
     }
@@ -1156,7 +1181,7 @@ fm_status ha_setup(Ctx &c)
     FM_TRY(ha_alloc(c, &s.xmax, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.vpart, vp_n));
     FM_TRY(ha_alloc(c, &s.q32, q_n));
-    FM_TRY(ha_alloc(c, &s.qmax, (size_t)c.F));
+    FM_TRY(ha_alloc(c, &s.qmax_ft, (size_t)c.F * c.T));
     FM_TRY(ha_alloc(c, &s.qscale, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.qimg, qi_n));
 
@@ -1204,13 +1229,15 @@ fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st)
     return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st) : vis_ha_launch<0, false>(c, h, x, vis, st);
 }
 
-fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st)
+fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready)
 {
     const HaDev h = make_dev(c);
     const bool x3 = x3_of(c.prec);
     if (f16_of(c.prec))
-        return x3 ? adj_ha_launch<1, true>(c, h, omega, xbar, st) : adj_ha_launch<1, false>(c, h, omega, xbar, st);
-    return x3 ? adj_ha_launch<0, true>(c, h, omega, xbar, st) : adj_ha_launch<0, false>(c, h, omega, xbar, st);
+        return x3 ? adj_ha_launch<1, true>(c, h, omega, xbar, st, q_ready)
+                  : adj_ha_launch<1, false>(c, h, omega, xbar, st, q_ready);
+    return x3 ? adj_ha_launch<0, true>(c, h, omega, xbar, st, q_ready)
+              : adj_ha_launch<0, false>(c, h, omega, xbar, st, q_ready);
 }
 
 }  // namespace fm

@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(256) k_pc_chol_big(int n, const double *__rest
 // become triangular matrix-vector products.
 template <typename R>
 __global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restrict__ W, double *__restrict__ Xd,
-                                                    R *__restrict__ Ginv)
+                                                    R *__restrict__ Ginv, R *__restrict__ GinvT)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         double *x = Xd + (size_t)j * n;
@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restr
             for (int cc = j; cc < r; ++cc) a += row[cc] * x[cc];
             x[r] = -a / row[r];
         }
-        for (int r = 0; r < n; ++r) Ginv[(size_t)r * n + j] = (R)x[r];
+        for (int r = 0; r < n; ++r) {
+            Ginv[(size_t)r * n + j] = (R)x[r];
+            GinvT[(size_t)j * n + r] = (R)x[r];
+        }
     }
 }
 
@@ -510,7 +513,7 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
             k_pc_blk_inv<R><<<(unsigned)nsky_blk, 64, 2 * 64 * 65 * sizeof(double), st>>>(Lf, (R *)c.pc_linv);
             if (ng > 0) {
                 if (!c.pc_ginv) {
-                    if (cudaMalloc(&c.pc_ginv, c.rsz * (size_t)ng * ng) != cudaSuccess ||
+                    if (cudaMalloc(&c.pc_ginv, 2 * c.rsz * (size_t)ng * ng) != cudaSuccess ||
                         cudaMalloc(&c.pc_tmp, sizeof(double) * (size_t)ng * ng) != cudaSuccess) {
                         rc = FM_ERR_ALLOC;
                         set_error("cudaMalloc gain-block inverse");
@@ -519,7 +522,8 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
                     c.allocs.push_back(c.pc_ginv);
                     c.allocs.push_back(c.pc_tmp);
                 }
-                k_pc_tri_inv<R><<<cdiv(ng, 128), 128, 0, st>>>(ng, W, c.pc_tmp, (R *)c.pc_ginv);
+                k_pc_tri_inv<R><<<cdiv(ng, 128), 128, 0, st>>>(ng, W, c.pc_tmp, (R *)c.pc_ginv,
+                                                               (R *)c.pc_ginv + (size_t)ng * ng);
             }
         } else {
             k_pc_chol_diag<R><<<cdiv(need, 256), 256, 0, st>>>(need, c.pc_blocks, (const R *)c.lam,
@@ -621,20 +625,42 @@ __device__ __forceinline__ void lower_mv(const R *S, const R *vs, R &y0, R &y1)
     y1 = a1;
 }
 
+// Dense gain block of the mass-matrix algebra: y_r = sum over c <= r (lower) or c >= r
+// (upper) of M[r][c] x_c with M = L_g, L_g^-1 or L_g^-T (row-major), one warp per row so
+// that all rows' loads are in flight together.  Outputs: y (scratch), kin[r] = y_r^2,
+// q[r] += eps y_r, out[r] = y_r (each when non-NULL).
 template <typename R>
-__global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, int n_dense, const R *__restrict__ Gi,
-                                                          const R *__restrict__ Li, const R *__restrict__ L, const R *__restrict__ in, int fwd,
+__global__ void __launch_bounds__(256) k_lf_dense(int n, const R *__restrict__ M, int lower,
+                                                  const R *__restrict__ x, R *__restrict__ y, double *__restrict__ kin,
+                                                  R *__restrict__ q, double eps, R *__restrict__ out)
+{
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const R *row = M + (size_t)r * n;
+    R a = 0;
+    for (int cc = lane; cc < n; cc += 32)
+        if (lower ? cc <= r : cc >= r) a += row[cc] * x[cc];
+    a = warp_sum(a);
+    if (lane == 0) {
+        if (y) y[r] = a;
+        if (kin) kin[r] = (double)a * (double)a;
+        if (q) q[r] += (R)(eps * a);
+        if (out) out[r] = a;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const R *__restrict__ Li,
+                                                          const R *__restrict__ L, const R *__restrict__ in, int fwd,
                                                           int bwd, int mul, R *__restrict__ q, double eps,
                                                           R *__restrict__ out, double *__restrict__ kin)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[LF_WARPS];
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const bool dense = n_dense > 0 && blockIdx.x == 0;
-    if (!dense) {
+    {
         // ------------------------------------------------ one 64 x 64 block per warp
-        const long long blk = (long long)(blockIdx.x - (n_dense > 0 ? 1 : 0)) * LF_WARPS + w;
+        const long long blk = (long long)blockIdx.x * LF_WARPS + w;
         if (blk >= nblk) return;
         R *S = sm + (size_t)w * (4096 + 64);            // block image, then the 64-vector
         R *vs = S + 4096;
@@ -685,60 +711,6 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, int n_
         if (q) { q[off + lane] += (R)(eps * v0); q[off + lane + 32] += (R)(eps * v1); }
         if (out) { out[off + lane] = v0; out[off + lane + 32] = v1; }
         return;
-    }
-    // ---------------------------------------------------- dense gain block (CTA 0)
-    // with Gi = L_g^-1 (stored at build time): L_g^-1 v is a row-wise product (warp per
-    // row, lanes along the row) and L_g^-T v a column-wise one (thread per column, rows
-    // read coalesced across threads)
-    const int n = n_dense;
-    const long long base = nblk * 64;
-    const R *Lg = L + nblk * 4096;
-    R *v = sm;                                  // [n]
-    R *y = sm + ((n + 3) / 4) * 4;              // [n]
-    for (int r = tid; r < n; r += blockDim.x) v[r] = in[base + r];
-    __syncthreads();
-    if (mul) {
-        for (int r = w; r < n; r += LF_WARPS) {
-            const R *row = Lg + (size_t)r * n;
-            R a = 0;
-            for (int cc = lane; cc <= r; cc += 32) a += row[cc] * v[cc];
-            a = warp_sum(a);
-            if (lane == 0) out[base + r] = a;
-        }
-        return;
-    }
-    if (fwd) {
-        double ks = 0.0;
-        for (int r = w; r < n; r += LF_WARPS) {
-            const R *row = Gi + (size_t)r * n;
-            R a = 0;
-            for (int cc = lane; cc <= r; cc += 32) a += row[cc] * v[cc];
-            a = warp_sum(a);
-            if (lane == 0) { y[r] = a; ks += (double)a * (double)a; }
-        }
-        __syncthreads();
-        for (int r = tid; r < n; r += blockDim.x) v[r] = y[r];
-        if (lane == 0) red[w] = ks;
-        __syncthreads();
-        if (kin && tid == 0) {
-            double t = 0.0;
-            for (int k = 0; k < LF_WARPS; ++k) t += red[k];
-            kin[nblk] = t;
-        }
-    }
-    if (bwd) {
-        for (int cc = tid; cc < n; cc += blockDim.x) {
-            R a = 0;
-            for (int r = cc; r < n; ++r) a += Gi[(size_t)r * n + cc] * v[r];
-            y[cc] = a;
-        }
-        __syncthreads();
-        for (int r = tid; r < n; r += blockDim.x) v[r] = y[r];
-        __syncthreads();
-    }
-    for (int r = tid; r < n; r += blockDim.x) {
-        if (q) q[base + r] += (R)(eps * v[r]);
-        if (out) out[base + r] = v[r];
     }
 }
 
@@ -817,15 +789,40 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
     if (bs > 1) {
         const long long nb = c.n_sky / bs;
         const int ng = 2 * c.A * c.NG;
-        const size_t smem = sizeof(R) * std::max((size_t)LF_WARPS * (4096 + 64), 2 * ((size_t)(ng + 3) / 4 * 4));
+        const size_t smem = sizeof(R) * (size_t)LF_WARPS * (4096 + 64);
         FM_CK(cudaFuncSetAttribute(k_lf_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const long long grid = (nb + LF_WARPS - 1) / LF_WARPS + (ng > 0 ? 1 : 0);
-        k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, ng, (const R *)c.pc_ginv,
-                                                                (const R *)c.pc_linv, L, in, fwd, bwd, mul, q, eps,
-                                                                out, kin_out ? part : nullptr);
+        const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
+        k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
+                                                                eps, out, kin_out ? part : nullptr);
         FM_CK_LAUNCH();
+        if (ng > 0) {
+            // the gain block: matrix-vector products with L_g (mul), L_g^-1 (fwd), L_g^-T (bwd)
+            const long long base = c.n_sky;
+            const R *Lg = L + (size_t)nb * bs * bs, *Gi = (const R *)c.pc_ginv, *GiT = Gi + (size_t)ng * ng;
+            const unsigned dg = cdiv(ng, 8);
+            R *y = (R *)c.lf_y;
+            if (mul) {
+                k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Lg, 1, in + base, nullptr, nullptr, nullptr, 0.0, out + base);
+                FM_CK_LAUNCH();
+            } else {
+                const R *src = in + base;
+                if (fwd) {
+                    const bool last = !bwd;
+                    k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi, 1, src, y, kin_out ? part + nb : nullptr,
+                                                      last && q ? q + base : nullptr, eps,
+                                                      last && out ? out + base : nullptr);
+                    FM_CK_LAUNCH();
+                    src = y;
+                }
+                if (bwd) {
+                    k_lf_dense<R><<<dg, 256, 0, st>>>(ng, GiT, 0, src, nullptr, nullptr, q ? q + base : nullptr, eps,
+                                                      out ? out + base : nullptr);
+                    FM_CK_LAUNCH();
+                }
+            }
+        }
         if (kin_out) {
-            k_sum_to<<<1, 256, 0, st>>>((int)(nb + (ng > 0 ? 1 : 0)), part, kin_out);
+            k_sum_to<<<1, 256, 0, st>>>((int)(nb + ng), part, kin_out);
             FM_CK_LAUNCH();
         }
     } else {
@@ -856,6 +853,11 @@ static fm_status lf_ensure(Ctx &c)
         return FM_ERR_ALLOC;
     }
     c.allocs.push_back(c.lf_scal);
+    if (cudaMalloc(&c.lf_y, c.rsz * (size_t)(2 * c.A * c.NG + 1)) != cudaSuccess) {
+        set_error("cudaMalloc leapfrog scratch");
+        return FM_ERR_ALLOC;
+    }
+    c.allocs.push_back(c.lf_y);
     return FM_OK;
 }
 

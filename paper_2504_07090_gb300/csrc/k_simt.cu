@@ -465,6 +465,168 @@ __global__ void __launch_bounds__(256) k_chi2_mid(DevGeom g, const R *__restrict
     }
 }
 
+// One CTA per (channel, LST): model, residual, chi^2 partial (FP64), the adjoint weights
+// omega_pq = conj(g_p) g_q r_pq / sigma^2 and the per-antenna gain partials
+// Z_a = [sum_{q>a} r_aq g_q conj(V_aq) + sum_{p<a} conj(r_pa) g_p V_pa] / sigma^2 (a warp per
+// antenna, lanes over its partners, shuffle sums in a fixed order).  With q32 != NULL
+// (hour-angle form) omega is not written: its sums over the baseline groups go to
+// q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].
+template <typename R>
+__global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict__ vis, const R *__restrict__ data,
+                                                 const R *__restrict__ gains, R *__restrict__ omega,
+                                                 R *__restrict__ zpart, double *__restrict__ chi2p, int U,
+                                                 const int *__restrict__ moff, const int *__restrict__ mem,
+                                                 float *__restrict__ q32, float *__restrict__ qmax_ft)
+{
+    using C2 = typename V2<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *sG = reinterpret_cast<C2 *>(smem_raw);            // [A]
+    C2 *sV = sG + g.A;                                     // [B]
+    C2 *sR = sV + g.B;                                     // [B] residuals
+    C2 *sW = sR + g.B;                                     // [B] omega (hour-angle form)
+    __shared__ double dred[8];
+    __shared__ float fred[8];
+    const int ft = blockIdx.x, f = ft / g.T, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < g.A; i += blockDim.x) {
+        sG[i].x = gains[2 * (f * g.A + i)];
+        sG[i].y = gains[2 * (f * g.A + i) + 1];
+    }
+    __syncthreads();
+    const R is2 = (R)g.inv_sigma2;
+    const C2 *vrow = reinterpret_cast<const C2 *>(vis) + (size_t)ft * g.B;
+    const C2 *drow = reinterpret_cast<const C2 *>(data) + (size_t)ft * g.B;
+    C2 *orow = reinterpret_cast<C2 *>(omega) + (size_t)ft * g.B;
+    double c2 = 0.0;
+    for (int b = tid; b < g.B; b += blockDim.x) {
+        const int i = g.bl_i[b], j = g.bl_j[b];
+        const C2 V = vrow[b], d = drow[b], gi = sG[i], gj = sG[j];
+        const R ggr = gi.x * gj.x + gi.y * gj.y, ggi = gi.y * gj.x - gi.x * gj.y;     // g_i conj(g_j)
+        C2 r, om;
+        r.x = ggr * V.x - ggi * V.y - d.x;
+        r.y = ggr * V.y + ggi * V.x - d.y;
+        c2 += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
+        om.x = (ggr * r.x + ggi * r.y) * is2;
+        om.y = (ggr * r.y - ggi * r.x) * is2;
+        if (q32) sW[b] = om;
+        else orow[b] = om;
+        sV[b] = V;
+        sR[b] = r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    if (lane == 0) dred[w] = c2;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += dred[k];
+        chi2p[ft] = a * g.inv_sigma2;
+    }
+    if (q32) {
+        float qm = 0.f;
+        for (int u = tid; u < U; u += blockDim.x) {
+            float qr = 0.f, qi = 0.f;
+            for (int m = moff[u]; m < moff[u + 1]; ++m) {
+                const int code = mem[m], b = code >> 1;
+                qr += (float)sW[b].x;
+                qi += (code & 1) ? -(float)sW[b].y : (float)sW[b].y;
+            }
+            float *qo = q32 + ((size_t)ft * U + u) * 2;
+            qo[0] = qr;
+            qo[1] = qi;
+            qm = fmaxf(qm, fmaxf(fabsf(qr), fabsf(qi)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qm = fmaxf(qm, __shfl_xor_sync(0xffffffffu, qm, o));
+        if (lane == 0) fred[w] = qm;
+        __syncthreads();
+        if (tid == 0) {
+            float m = 0.f;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, fred[k]);
+            qmax_ft[ft] = m;
+        }
+    }
+    for (int a = w; a < g.A; a += (int)(blockDim.x >> 5)) {
+        R zr = 0, zi = 0;
+        for (int j = lane; j < g.A; j += 32) {
+            if (j == a) continue;
+            const C2 gq = sG[j];
+            if (j > a) {          // r_aq g_q conj(V_aq)
+                const int b = pair_index(a, j, g.A);
+                const C2 r = sR[b], V = sV[b];
+                const R tr = r.x * gq.x - r.y * gq.y, ti = r.x * gq.y + r.y * gq.x;
+                zr += tr * V.x + ti * V.y;
+                zi += ti * V.x - tr * V.y;
+            } else {              // conj(r_pa) g_p V_pa
+                const int b = pair_index(j, a, g.A);
+                const C2 r = sR[b], V = sV[b];
+                const R tr = r.x * gq.x + r.y * gq.y, ti = r.x * gq.y - r.y * gq.x;
+                zr += tr * V.x - ti * V.y;
+                zi += tr * V.y + ti * V.x;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            zr += __shfl_xor_sync(0xffffffffu, zr, o);
+            zi += __shfl_xor_sync(0xffffffffu, zi, o);
+        }
+        if (lane == 0) {
+            zpart[((size_t)ft * g.A + a) * 2] = zr * is2;
+            zpart[((size_t)ft * g.A + a) * 2 + 1] = zi * is2;
+        }
+    }
+}
+
+// zchan[f][a][c] = sum_t zpart[f][t][a][c]  (fixed order in t)
+template <typename R>
+__global__ void k_zsum(DevGeom g, const R *__restrict__ zpart, R *__restrict__ zchan)
+{
+    const int f = blockIdx.x;
+    for (int e = threadIdx.x; e < 2 * g.A; e += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < g.T; ++t) s += (double)zpart[((size_t)f * g.T + t) * 2 * g.A + e];
+        zchan[(size_t)f * 2 * g.A + e] = (R)s;
+    }
+}
+
+// grad_gamma[a][k][re, im] = sum_f X_k(nu_f) Z[f][a]  (FP64, fixed order in f)
+template <typename R>
+__global__ void k_gain_reduce_chan(DevGeom g, const R *__restrict__ zchan, R *__restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.A * g.NG * 2) return;
+    const int c = e & 1, k = (e >> 1) % g.NG, a = (e >> 1) / g.NG;
+    double s = 0.0;
+    for (int f = 0; f < g.F; ++f)
+        s += (double)Tab<R>::gleg(g)[(size_t)f * g.NG + k] * (double)zchan[((size_t)f * g.A + a) * 2 + c];
+    out[(a * g.NG + k) * 2 + c] = (R)s;
+}
+
+template <typename R>
+fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zchan, double *chi2p, bool groups,
+                           cudaStream_t st)
+{
+    const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
+    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    R *zpart = zchan;                                    // [F][T][A][2]; the channel sums follow it
+    R *zc = zchan + (size_t)c.F * c.T * c.A * 2;
+    FM_CK(cudaFuncSetAttribute(k_chi2_ft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_chi2_ft<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p, c.ha.U,
+                                                c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft);
+    FM_CK_LAUNCH();
+    k_zsum<R><<<c.F, 128, 0, st>>>(c.g, zpart, zc);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
+template <typename R>
+fm_status launch_gain_reduce_chan(Ctx &c, const R *zchan, R *grad_gain, cudaStream_t st)
+{
+    const R *zc = zchan + (size_t)c.F * c.T * c.A * 2;   // channel sums written by launch_chi2_chan
+    k_gain_reduce_chan<R><<<cdiv(c.A * c.NG * 2, 128), 128, 0, st>>>(c.g, zc, grad_gain);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+
 template <typename R>
 fm_status launch_chi2_mid(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p, cudaStream_t st)
 {
@@ -654,21 +816,23 @@ fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t 
     return FM_OK;
 }
 
-// grad += lam (theta - mu); per-block partial sums of lam (theta - mu)^2 / 2
+// grad += lam (theta - mu); per-block partial sums of lam (theta - mu)^2 / 2 (each term
+// in the working type, the sums in FP64)
 template <typename R>
 __global__ void __launch_bounds__(256) k_prior(long long n, const R *__restrict__ theta, const R *__restrict__ mu,
                                                const R *__restrict__ lam, R *__restrict__ grad, double *__restrict__ part)
 {
     __shared__ double sred[256];
     double acc = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        if (lam) {
-            R dv = theta[k] - mu[k];
-            grad[k] += lam[k] * dv;
-            acc += 0.5 * (double)lam[k] * (double)dv * (double)dv;
+    if (lam) {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+             k += (long long)gridDim.x * blockDim.x) {
+            const R l = lam[k], dv = theta[k] - mu[k], ld = l * dv;
+            grad[k] += ld;
+            acc += (double)(ld * dv);
         }
     }
-    block_sum_double<R>(acc, part + blockIdx.x, sred);
+    block_sum_double<R>(0.5 * acc, part + blockIdx.x, sred);
 }
 
 // chi2 = sum of per-(f,t) partials; U = chi2/2 + prior (both in fixed order)
@@ -692,14 +856,14 @@ __global__ void __launch_bounds__(256) k_total(int nft, const double *__restrict
 }
 
 template <typename R>
-fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, double *chi2_out,
+fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, int nchi2, double *chi2_out,
                                  double *u_out, cudaStream_t st)
 {
-    const int nblk = 296;
+    const int nblk = 1024;
     k_prior<R><<<nblk, 256, 0, st>>>(c.n_par, theta, (const R *)c.mu, c.have_prior ? (const R *)c.lam : nullptr,
                                      grad, c.red);
     FM_CK_LAUNCH();
-    k_total<<<1, 256, 0, st>>>(c.F * c.T, chi2p, nblk, c.red, chi2_out, u_out, c.status);
+    k_total<<<1, 256, 0, st>>>(nchi2, chi2p, nblk, c.red, chi2_out, u_out, c.status);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -786,6 +950,8 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
 }
 
 #define FM_INST(R)                                                                                       \
+    template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t); \
+    template fm_status launch_gain_reduce_chan<R>(Ctx &, const R *, R *, cudaStream_t);                 \
     template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int);                \
     template fm_status launch_modes_adjoint<R>(Ctx &, const R *, R *, cudaStream_t);                     \
     template fm_status launch_gains<R>(Ctx &, const R *, R *, cudaStream_t);                             \
@@ -796,7 +962,7 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
     template fm_status launch_hvp_mid<R>(Ctx &, const R *, const R *, const R *, const R *, int, R *, R *, \
                                          cudaStream_t);                                                  \
     template fm_status launch_gain_reduce<R>(Ctx &, const R *, R *, cudaStream_t);                       \
-    template fm_status launch_prior_and_total<R>(Ctx &, const R *, R *, const double *, double *, double *, \
+    template fm_status launch_prior_and_total<R>(Ctx &, const R *, R *, const double *, int, double *, double *, \
                                                  cudaStream_t);                                          \
     template fm_status launch_prior_hvp<R>(Ctx &, const R *, R *, cudaStream_t);                         \
     template fm_status launch_add_dc<R>(Ctx &, const R *, long long, R *, cudaStream_t);                \
