@@ -152,6 +152,8 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
     g.bl_i = bl; g.bl_j = bl + c->B;
     FM_TRY(dalloc(*c, &c->status, 1));
     FM_CK(cudaMemset(c->status, 0, sizeof(int)));
+    FM_TRY(dalloc(*c, &c->ticket, 1));
+    FM_CK(cudaMemset(c->ticket, 0, sizeof(unsigned)));
     g.status = c->status;
     {   // equal channel spacing enables the frequency recurrence of the phasors
         double dnu = c->F > 1 ? c->freq[1] - c->freq[0] : 0.0;
@@ -193,7 +195,7 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
     FM_TRY(dalloc_bytes(*c, &c->vis, (size_t)c->n_vis * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->dvis, (size_t)c->n_vis * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->omega, (size_t)c->n_vis * 2 * rs));
-    FM_TRY(dalloc_bytes(*c, &c->zpart, ((size_t)c->F * c->T + c->F) * c->A * 2 * rs));
+    FM_TRY(dalloc_bytes(*c, &c->zpart, (size_t)c->F * c->T * c->A * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->gains, (size_t)c->F * c->A * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->dgains, (size_t)c->F * c->A * 2 * rs));
     FM_TRY(dalloc_bytes(*c, &c->work_par, (size_t)c->n_par * rs));
@@ -238,15 +240,21 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 }
 
 // ------------------------------------------------------------------ drivers
+// x -> V; with dc != nullptr the monopole visibilities dc[f * dcs] U[f][t][b] are added
+// (inside the last kernel of the hour-angle form, as a separate pass otherwise)
 template <typename R>
-static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st)
+static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st, const R *dc = nullptr, long long dcs = 0)
 {
     // the tensor-core launchers time their main kernel themselves
     if constexpr (std::is_same<R, float>::value) {
-        if (c.ha.on) return launch_vis_ha(c, x, vis, st);
-        if (c.prec >= FM_PREC_BF16X1) return launch_vis_tc(c, x, vis, st);
+        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs);
+        if (c.prec >= FM_PREC_BF16X1) {
+            FM_TRY(launch_vis_tc(c, x, vis, st));
+            return dc ? launch_add_dc<R>(c, dc, dcs, vis, st) : FM_OK;
+        }
     }
-    return profiled(c, 0, st, [&]() -> fm_status { return launch_vis<R>(c, x, vis, st); });
+    FM_TRY(profiled(c, 0, st, [&]() -> fm_status { return launch_vis<R>(c, x, vis, st); }));
+    return dc ? launch_add_dc<R>(c, dc, dcs, vis, st) : FM_OK;
 }
 
 template <typename R>
@@ -264,8 +272,7 @@ fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st)
 {
     if (c.dc_split) {
         FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 1));
-        FM_TRY(run_vis<R>(c, xbuf, vis, st));
-        return launch_add_dc<R>(c, a, c.nk, vis, st);
+        return run_vis<R>(c, xbuf, vis, st, a, c.nk);
     }
     FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 0));
     return run_vis<R>(c, xbuf, vis, st);
@@ -400,8 +407,7 @@ fm_status fm_forward_pixels(fm_handle h, const void *dev_x, void *dev_vis_out, f
     if (c.prec == FM_PREC_FP64_SIMT) return run_vis<double>(c, (const double *)dev_x, (double *)dev_vis_out, stream);
     if (c.dc_split) {
         FM_TRY(launch_center<float>(c, (const float *)dev_x, (float *)c.x, (float *)c.dc_mean, stream));
-        FM_TRY(run_vis<float>(c, (const float *)c.x, (float *)dev_vis_out, stream));
-        return launch_add_dc<float>(c, (const float *)c.dc_mean, 1, (float *)dev_vis_out, stream);
+        return run_vis<float>(c, (const float *)c.x, (float *)dev_vis_out, stream, (const float *)c.dc_mean, 1);
     }
     return run_vis<float>(c, (const float *)dev_x, (float *)dev_vis_out, stream);
 }

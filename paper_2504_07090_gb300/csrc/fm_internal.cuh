@@ -120,6 +120,7 @@ struct Ctx {
     void *gains = nullptr, *dgains = nullptr, *work_par = nullptr;
     double *chi2p = nullptr, *scal = nullptr, *red = nullptr;
     int *status = nullptr;
+    unsigned *ticket = nullptr;   // last-CTA ticket of k_prior_total (0 between launches)
     // preconditioner
     int pc_block = 0;
     double *pc_blocks = nullptr;      // FP64 GN blocks (sky then gain)
@@ -225,13 +226,14 @@ fm_status launch_hvp_mid(Ctx &c, const R *vis, const R *dvis, const R *g, const 
                          R *zpart, cudaStream_t st);
 template <typename R>
 fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
-// per-channel form of the chi^2 epilogue (gradient path): chi2p[f], zchan[f][a][2] (the
-// LST sums of the gain partials), omega, or (groups) the hour-angle group sums of omega
+// per-(channel, LST) form of the chi^2 epilogue (gradient path): chi2p[f][t], the gain
+// partials zpart[f][t][a][2], omega, or (groups) the hour-angle group sums of omega
 template <typename R>
-fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zchan, double *chi2p, bool groups,
+fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p, bool groups,
                            cudaStream_t st);
+// grad_gain from zpart in one pass over (channel, LST)
 template <typename R>
-fm_status launch_gain_reduce_chan(Ctx &c, const R *zchan, R *grad_gain, cudaStream_t st);
+fm_status launch_gain_reduce_chan(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
 template <typename R>
 fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, int nchi2, double *chi2_out,
                                  double *u_out, cudaStream_t st);
@@ -258,7 +260,9 @@ fm_status ha_setup(Ctx &c);
 fm_status modes_tc_setup(Ctx &c);
 fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc);
 fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st);
-fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st);
+// dc != nullptr: also adds the monopole visibilities dc[f * dcs] U[f][t][b]
+fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc = nullptr,
+                        long long dcs = 0);
 // q_ready: the group sums q32 / qmax_ft were already formed from omega (by the chi^2 epilogue)
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready = false);
 

@@ -478,12 +478,15 @@ done:
 // Sum of the forward partials in fixed order, unscaled, expanded to every baseline.
 // CTA (segment, LST block of HA_VF_T): the contributors' partials of the segment's 128
 // rows are added into shared memory, then every baseline of the segment's groups gets
-// its (possibly conjugated) value, written coalesced over baselines.
+// its (possibly conjugated) value, written coalesced over baselines.  With dc != nullptr
+// the monopole term c_f U[f][t][b] (c_f = dc[f * dcs]) is added in the same write.
 constexpr int HA_VF_T = 8;
 
 __global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float *__restrict__ vpart,
                                                     const int *__restrict__ ncontrib, const int *__restrict__ bmap,
-                                                    const unsigned *__restrict__ xmax, float sp, float *__restrict__ vis)
+                                                    const unsigned *__restrict__ xmax, float sp,
+                                                    const float *__restrict__ dc, long long dcs,
+                                                    const float *__restrict__ U, float *__restrict__ vis)
 {
     __shared__ float sv[128][HA_VF_T];
     const int seg = blockIdx.x, mt = seg / h.F, f = seg % h.F;
@@ -498,14 +501,21 @@ __global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float 
     }
     __syncthreads();
     const float sc = 1.f / (sp * pow2_scale(__uint_as_float(xmax[f])));
+    const float cf = dc ? dc[(size_t)f * dcs] : 0.f;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         const int code = bmap[b], u = code >> 1;
         if ((u >> 6) != mt) continue;
         const int row = 2 * (u & 63);
         const float sgn = (code & 1) ? -1.f : 1.f;
         for (int tl = 0; tl < tn; ++tl) {
-            float2 *o = reinterpret_cast<float2 *>(vis) + ((size_t)f * h.T + t0 + tl) * B + b;
-            *o = make_float2(sv[row][tl] * sc, sgn * sv[row + 1][tl] * sc);
+            const size_t e = ((size_t)f * h.T + t0 + tl) * B + b;
+            float2 v = make_float2(sv[row][tl] * sc, sgn * sv[row + 1][tl] * sc);
+            if (dc) {
+                const float2 u2 = reinterpret_cast<const float2 *>(U)[e];
+                v.x += cf * u2.x;
+                v.y += cf * u2.y;
+            }
+            reinterpret_cast<float2 *>(vis)[e] = v;
         }
     }
 }
@@ -942,7 +952,8 @@ bool make_layout(const Ctx &c, bool x3, uint32_t eslot_bytes, uint32_t vbytes, H
 }
 
 template <int ET, bool X3>
-fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cudaStream_t st)
+fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cudaStream_t st, const float *dc,
+                        long long dcs)
 {
     HaState &s = c.ha;
     HaLayout L;
@@ -964,7 +975,7 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
         return FM_OK;
     }));
     k_ha_vfinish<<<dim3(s.nmt * c.F, cdiv(c.T, HA_VF_T)), 256, 0, st>>>(h, c.B, s.vpart, s.ncontrib, s.bmap,
-                                                                        s.xmax, s.sp, vis);
+                                                                        s.xmax, s.sp, dc, dcs, c.dc_u, vis);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -1221,12 +1232,13 @@ fm_status ha_setup(Ctx &c)
     return FM_OK;
 }
 
-fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st)
+fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc, long long dcs)
 {
     const HaDev h = make_dev(c);
     const bool x3 = x3_of(c.prec);
-    if (f16_of(c.prec)) return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st) : vis_ha_launch<1, false>(c, h, x, vis, st);
-    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st) : vis_ha_launch<0, false>(c, h, x, vis, st);
+    if (f16_of(c.prec))
+        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs) : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs);
+    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs) : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs);
 }
 
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready)

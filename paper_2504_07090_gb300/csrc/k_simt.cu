@@ -465,7 +465,8 @@ __global__ void __launch_bounds__(256) k_chi2_mid(DevGeom g, const R *__restrict
     }
 }
 
-// One CTA per (channel, LST): model, residual, chi^2 partial (FP64), the adjoint weights
+// One CTA per (channel, LST): model, residual, chi^2 partial (a warp's terms summed in the
+// working type, the warps' sums in FP64), the adjoint weights
 // omega_pq = conj(g_p) g_q r_pq / sigma^2 and the per-antenna gain partials
 // Z_a = [sum_{q>a} r_aq g_q conj(V_aq) + sum_{p<a} conj(r_pa) g_p V_pa] / sigma^2 (a warp per
 // antenna, lanes over its partners, shuffle sums in a fixed order).  With q32 != NULL
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
     const C2 *vrow = reinterpret_cast<const C2 *>(vis) + (size_t)ft * g.B;
     const C2 *drow = reinterpret_cast<const C2 *>(data) + (size_t)ft * g.B;
     C2 *orow = reinterpret_cast<C2 *>(omega) + (size_t)ft * g.B;
-    double c2 = 0.0;
+    R c2 = 0;   // a warp's terms in the working type; FP64 across warps
     for (int b = tid; b < g.B; b += blockDim.x) {
         const int i = g.bl_i[b], j = g.bl_j[b];
         const C2 V = vrow[b], d = drow[b], gi = sG[i], gj = sG[j];
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
         C2 r, om;
         r.x = ggr * V.x - ggi * V.y - d.x;
         r.y = ggr * V.y + ggi * V.x - d.y;
-        c2 += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
+        c2 += r.x * r.x + r.y * r.y;
         om.x = (ggr * r.x + ggi * r.y) * is2;
         om.y = (ggr * r.y - ggi * r.x) * is2;
         if (q32) sW[b] = om;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-    if (lane == 0) dred[w] = c2;
+    if (lane == 0) dred[w] = (double)c2;
     __syncthreads();
     if (tid == 0) {
         double a = 0.0;
@@ -576,53 +577,71 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
     }
 }
 
-// zchan[f][a][c] = sum_t zpart[f][t][a][c]  (fixed order in t)
+// grad_gamma[a][k][c] = sum_{f,t} X_k(nu_f) zpart[f][t][a][c]: one CTA per (a, c); thread
+// j takes the (channel, LST) pairs j, j + GR_THREADS, ... in batches of GR_U independent
+// loads.  Per thread and across a warp (fixed shuffle order) the sums are in the working
+// type; the warps' sums are added in order in FP64 (the FP64 pipe is narrow on this part,
+// so it is kept off the per-element path).
+constexpr int GR_NGMAX = 8, GR_THREADS = 1024, GR_U = 4;
 template <typename R>
-__global__ void k_zsum(DevGeom g, const R *__restrict__ zpart, R *__restrict__ zchan)
+__global__ void __launch_bounds__(GR_THREADS) k_gain_reduce_ft(DevGeom g, const R *__restrict__ zpart,
+                                                               R *__restrict__ out)
 {
-    const int f = blockIdx.x;
-    for (int e = threadIdx.x; e < 2 * g.A; e += blockDim.x) {
-        double s = 0.0;
-        for (int t = 0; t < g.T; ++t) s += (double)zpart[((size_t)f * g.T + t) * 2 * g.A + e];
-        zchan[(size_t)f * 2 * g.A + e] = (R)s;
+    __shared__ double red[GR_THREADS / 32][GR_NGMAX];
+    const int a = blockIdx.x >> 1, c = blockIdx.x & 1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const R *gl = Tab<R>::gleg(g);
+    R acc[GR_NGMAX];
+#pragma unroll
+    for (int k = 0; k < GR_NGMAX; ++k) acc[k] = 0;
+    const int nft = g.F * g.T;
+    for (int base = 0; base < nft; base += GR_THREADS * GR_U) {
+        R z[GR_U];
+        int f[GR_U];
+#pragma unroll
+        for (int u = 0; u < GR_U; ++u) {
+            const int ft = base + u * GR_THREADS + (int)threadIdx.x;
+            z[u] = ft < nft ? zpart[((size_t)ft * g.A + a) * 2 + c] : (R)0;
+            f[u] = ft < nft ? ft / g.T : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < GR_U; ++u)
+#pragma unroll
+            for (int k = 0; k < GR_NGMAX; ++k)
+                if (k < g.NG) acc[k] += gl[(size_t)f[u] * g.NG + k] * z[u];
+    }
+#pragma unroll
+    for (int k = 0; k < GR_NGMAX; ++k) {
+        R v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[w][k] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < g.NG) {
+        double t = 0.0;
+        for (int k = 0; k < GR_THREADS / 32; ++k) t += red[k][threadIdx.x];
+        out[(a * g.NG + threadIdx.x) * 2 + c] = (R)t;
     }
 }
 
-// grad_gamma[a][k][re, im] = sum_f X_k(nu_f) Z[f][a]  (FP64, fixed order in f)
 template <typename R>
-__global__ void k_gain_reduce_chan(DevGeom g, const R *__restrict__ zchan, R *__restrict__ out)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= g.A * g.NG * 2) return;
-    const int c = e & 1, k = (e >> 1) % g.NG, a = (e >> 1) / g.NG;
-    double s = 0.0;
-    for (int f = 0; f < g.F; ++f)
-        s += (double)Tab<R>::gleg(g)[(size_t)f * g.NG + k] * (double)zchan[((size_t)f * g.A + a) * 2 + c];
-    out[(a * g.NG + k) * 2 + c] = (R)s;
-}
-
-template <typename R>
-fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zchan, double *chi2p, bool groups,
+fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p, bool groups,
                            cudaStream_t st)
 {
     const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
     if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
-    R *zpart = zchan;                                    // [F][T][A][2]; the channel sums follow it
-    R *zc = zchan + (size_t)c.F * c.T * c.A * 2;
     FM_CK(cudaFuncSetAttribute(k_chi2_ft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_chi2_ft<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p, c.ha.U,
                                                 c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft);
-    FM_CK_LAUNCH();
-    k_zsum<R><<<c.F, 128, 0, st>>>(c.g, zpart, zc);
     FM_CK_LAUNCH();
     return FM_OK;
 }
 
 template <typename R>
-fm_status launch_gain_reduce_chan(Ctx &c, const R *zchan, R *grad_gain, cudaStream_t st)
+fm_status launch_gain_reduce_chan(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st)
 {
-    const R *zc = zchan + (size_t)c.F * c.T * c.A * 2;   // channel sums written by launch_chi2_chan
-    k_gain_reduce_chan<R><<<cdiv(c.A * c.NG * 2, 128), 128, 0, st>>>(c.g, zc, grad_gain);
+    if (c.NG > GR_NGMAX) return launch_gain_reduce<R>(c, zpart, grad_gain, st);
+    k_gain_reduce_ft<R><<<2 * c.A, GR_THREADS, 0, st>>>(c.g, zpart, grad_gain);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -816,42 +835,98 @@ fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t 
     return FM_OK;
 }
 
-// grad += lam (theta - mu); per-block partial sums of lam (theta - mu)^2 / 2 (each term
-// in the working type, the sums in FP64)
-template <typename R>
-__global__ void __launch_bounds__(256) k_prior(long long n, const R *__restrict__ theta, const R *__restrict__ mu,
-                                               const R *__restrict__ lam, R *__restrict__ grad, double *__restrict__ part)
+// fixed-order sum over a CTA of 256 threads: lane shuffles in T, then the 8 warps' sums in
+// order in FP64; the result is valid in thread 0
+template <typename T>
+__device__ __forceinline__ double cta256_sum(T v, double *wred)
 {
-    __shared__ double sred[256];
-    double acc = 0.0;
-    if (lam) {
-        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-             k += (long long)gridDim.x * blockDim.x) {
-            const R l = lam[k], dv = theta[k] - mu[k], ld = l * dv;
-            grad[k] += ld;
-            acc += (double)(ld * dv);
-        }
-    }
-    block_sum_double<R>(0.5 * acc, part + blockIdx.x, sred);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) t += wred[k];
+    __syncthreads();
+    return t;
 }
 
-// chi2 = sum of per-(f,t) partials; U = chi2/2 + prior (both in fixed order)
-__global__ void __launch_bounds__(256) k_total(int nft, const double *__restrict__ chi2p, int npart,
-                                               const double *__restrict__ part, double *chi2_out, double *u_out,
-                                               int *status)
+template <typename R>
+struct __align__(16) Pack16 { R v[16 / sizeof(R)]; };
+
+// grad += lam (theta - mu) and the prior energy sum lam (theta - mu)^2 / 2 (a warp's terms
+// summed in the working type, the warps' sums in FP64), then chi^2 = sum of the per-(f,t)
+// partials (FP64, loads batched so that their latencies overlap) and U = chi^2 / 2 + prior.
+// Each CTA writes its partial; the CTA that takes the last ticket adds the partials in
+// index order (so the result does not depend on which CTA that is) and resets the ticket
+// for the next launch.  vec: the four arrays are 16-byte aligned.
+constexpr int PT_THREADS = 256;
+template <typename R>
+__global__ void __launch_bounds__(PT_THREADS) k_prior_total(long long n, int vec, const R *__restrict__ theta,
+                                                            const R *__restrict__ mu, const R *__restrict__ lam,
+                                                            R *__restrict__ grad, double *part, int nft,
+                                                            const double *__restrict__ chi2p, double *chi2_out,
+                                                            double *u_out, int *status, unsigned *ticket)
 {
-    __shared__ double sred[256];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nft; i += blockDim.x) a += chi2p[i];
-    for (int i = threadIdx.x; i < npart; i += blockDim.x) b += part[i];
-    double ta, tb;
-    block_sum_double<float>(a, &ta, sred);
+    constexpr int W = 16 / sizeof(R);
+    __shared__ double wred[8];
+    __shared__ int last;
+    const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x, gstride = (long long)gridDim.x * blockDim.x;
+    R acc = 0;
+    if (lam) {
+        long long head = 0;
+        if (vec) {
+            const long long np = n / W;
+            head = np * W;
+            const Pack16<R> *th = reinterpret_cast<const Pack16<R> *>(theta);
+            const Pack16<R> *mp = reinterpret_cast<const Pack16<R> *>(mu);
+            const Pack16<R> *lp = reinterpret_cast<const Pack16<R> *>(lam);
+            Pack16<R> *gp = reinterpret_cast<Pack16<R> *>(grad);
+            for (long long k = gtid; k < np; k += gstride) {
+                const Pack16<R> t = th[k], m = mp[k], l = lp[k];
+                Pack16<R> gr = gp[k];
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    const R dv = t.v[e] - m.v[e], ld = l.v[e] * dv;
+                    gr.v[e] += ld;
+                    acc += ld * dv;
+                }
+                gp[k] = gr;
+            }
+        }
+        for (long long k = head + gtid; k < n; k += gstride) {
+            const R l = lam[k], dv = theta[k] - mu[k], ld = l * dv;
+            grad[k] += ld;
+            acc += ld * dv;
+        }
+    }
+    const double blk = cta256_sum<R>((R)0.5 * acc, wred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = blk;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    block_sum_double<float>(b, &tb, sred);
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i0 = 0; i0 < nft; i0 += 8 * PT_THREADS) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * PT_THREADS + (int)threadIdx.x;
+            v[u] = i < nft ? __ldcg(chi2p + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a += v[u];
+    }
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) b += __ldcg(part + i);
+    const double ta = cta256_sum<double>(a, wred), tb = cta256_sum<double>(b, wred);
     if (threadIdx.x == 0) {
         if (chi2_out) *chi2_out = ta;
         if (u_out) *u_out = 0.5 * ta + tb;
         if (!isfinite(ta) || !isfinite(tb)) atomicExch(status, (int)FM_ERR_NONFINITE);
+        *ticket = 0u;
     }
 }
 
@@ -859,11 +934,13 @@ template <typename R>
 fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, int nchi2, double *chi2_out,
                                  double *u_out, cudaStream_t st)
 {
-    const int nblk = 1024;
-    k_prior<R><<<nblk, 256, 0, st>>>(c.n_par, theta, (const R *)c.mu, c.have_prior ? (const R *)c.lam : nullptr,
-                                     grad, c.red);
-    FM_CK_LAUNCH();
-    k_total<<<1, 256, 0, st>>>(nchi2, chi2p, nblk, c.red, chi2_out, u_out, c.status);
+    const R *mu = (const R *)c.mu, *lam = c.have_prior ? (const R *)c.lam : nullptr;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const int vec = al(theta) && al(mu) && al(c.lam) && al(grad);
+    const long long units = vec ? c.n_par / (16 / (long long)sizeof(R)) : c.n_par;
+    const int nblk = (int)std::max(1LL, std::min<long long>(4 * 152, (long long)cdiv(units, PT_THREADS)));
+    k_prior_total<R><<<nblk, PT_THREADS, 0, st>>>(c.n_par, vec, theta, mu, lam, grad, c.red, nchi2, chi2p, chi2_out,
+                                                 u_out, c.status, c.ticket);
     FM_CK_LAUNCH();
     return FM_OK;
 }
