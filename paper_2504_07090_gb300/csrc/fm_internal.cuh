@@ -75,16 +75,16 @@ struct HaState {
     int nmt = 0;               // forward M-tiles, ceil(U / 64)
     int nkq = 0;               // adjoint K-chunks, ceil(U / 32)
     int npad = 0;              // n_lst rounded up to 16 (MMA N)
-    int P0 = 0, L = 0;         // sky-strip offset and length (16-bit elements)
+    int Jc = 0, Ly = 0;        // forward sky image chunks; sky-strip length (16-bit elements)
     int grid = 0, J = 0;       // forward CTAs; most CTAs sharing one (M-tile, channel) segment
     float sp = 1.f;            // response scale 2^e (e even): the table holds sqrt(dOmega A) 2^(e/2)
-    float2 *E = nullptr;       // [F][D][nbc][nant + 1][64] phasor table (entry nant is zero)
+    float2 *E = nullptr;       // [F][D][nbc][nant + 1][66] phasor table (entry nant is zero; 2 pad cells)
     int2 *uij = nullptr;       // [nmt * 64] representative pair (table entries) of each group; padding (nant, nant)
     int *bmap = nullptr;       // [B] group * 2 + (1 if the baseline is the reversed vector)
     int *moff = nullptr;       // [U + 1] CSR offsets of group members
     int *mem = nullptr;        // [B] members, b * 2 + reversed
     int *ncontrib = nullptr;   // [nmt * F] forward CTAs contributing to each segment
-    uint16_t *xs = nullptr;    // [2][F][D][L] scaled reversed sky strips, hi then lo
+    uint16_t *ys = nullptr;    // [2][F][D][Ly] scaled sky strips in the forward's cell order, hi then lo
     unsigned *xmax = nullptr;  // [F] max |x| of the centred sky per channel, as float bits
     float *vpart = nullptr;    // [nmt * F][J][128][npad] forward partial sums
     float *q32 = nullptr;      // [F][T][U][2] residual weights summed per group

@@ -47,19 +47,21 @@ constexpr int HA_THREADS = 22 * 32;       // forward
 constexpr int HA_ADJ_THREADS = 23 * 32;   // adjoint
 constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulation chain
 constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
+constexpr int HA_EW = 66;                 // float2 entries per table row: 64 cells + 16 bytes of padding
+constexpr int HA_NSTAGE = 4;              // operand stages (A in TMEM, and the adjoint's B in shared memory)
 
 // kernel parameters, by value
 struct HaDev {
-    int F, D, T, R, A, U, k, nhp, nbc, npad, P0, L, nchunk, nmt, nkq, J;
+    int F, D, T, R, A, U, k, nhp, nbc, npad, Ly, Jc, nchunk, nmt, nkq, J;
     long long Q;                          // forward work units: nmt * F * nchunk
     const float2 *E;
     const int2 *uij;
 };
 
 struct HaLayout {
-    int nstage, neslot, ncols;
-    uint32_t a_bytes, b_bytes, stage_bytes, eslot_bytes;
-    uint32_t e_off, v_off, bar_off, vstride;
+    int nstage, neslot, ncols, abase, acols;   // TMEM: allocated columns, first A column, columns per A stage
+    uint32_t b_bytes, stage_bytes, eslot_bytes, img_bytes;
+    uint32_t e_off, v_off, bar_off;
     size_t smem;
 };
 
@@ -89,8 +91,10 @@ __device__ __forceinline__ float pow2_scale(float mx)
 __device__ __forceinline__ void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
 // ------------------------------------------------------------ per-handle phasor table
-// E[f][d][nb][i][nl], n = 64 nb + nl, i over the table's antenna subset plus one all-zero
-// entry (padding pairs point at it): sqrt(dOmega_d A(za; nu_f)) 2^(e/2) exp(-2 pi i nu r_i . s / c)
+// E[f][d][nb][i][nl], n = 64 nb + nl (nl < 64; entries 64, 65 pad the row to 528 bytes so
+// that rows of different antennas start in different shared-memory banks), i over the
+// table's antenna subset plus one all-zero entry (padding pairs point at it):
+// sqrt(dOmega_d A(za; nu_f)) 2^(e/2) exp(-2 pi i nu r_i . s / c)
 // at hour angle H(n) = LST_0 - (ra_min + (R - 1 - n + 1/2) dRA); zero below the horizon
 // and for n >= nh.  FP64 throughout, stored as FP32.
 struct HaTabArgs {
@@ -102,11 +106,11 @@ struct HaTabArgs {
 
 __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
 {
-    const long long total = (long long)a.F * a.D * a.nhp * a.A;
+    const long long total = (long long)a.F * a.D * a.nbc * a.A * HA_EW;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int nl = (int)(e % 64);
-        long long r = e / 64;
+        const int nl = (int)(e % HA_EW);
+        long long r = e / HA_EW;
         const int i = (int)(r % a.A);
         r /= a.A;
         const int nb = (int)(r % a.nbc);
@@ -115,7 +119,7 @@ __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
         const int f = (int)(r / a.D);
         const int n = 64 * nb + nl;
         float2 out = make_float2(0.f, 0.f);
-        if (n < a.nh && i < a.A - 1) {           // entry A - 1 is the zero antenna of padded pairs
+        if (nl < 64 && n < a.nh && i < a.A - 1) {     // entry A - 1 is the zero antenna of padded pairs
             const double H = a.lst0 - (a.ra_min + ((double)(a.R - 1 - n) + 0.5) * a.dra);
             const double dec = a.dec_min + (d + 0.5) * a.ddec;
             double sd, cd, sh, ch, sl, cl;
@@ -140,50 +144,60 @@ __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
 }
 
 // ------------------------------------------------------------ forward operand prep
-// xs[f][d][m'] = S_f x(r = R - 1 - (m' - P0), d) for 0 <= m' - P0 < R, else 0; split into
-// 16-bit hi and lo parts of the operand type.
+// ys[f][d][j] = S_f x(r = j + R - nhp, d) for 0 <= r < R, else 0 (j < Ly), split into 16-bit
+// hi and lo parts of the operand type.  With m = nhp - 1 - n the sky operand of the forward
+// GEMM is B[t][m] = ys[m + t k], increasing in both indices (a Hankel matrix).
 template <int ET>
-__global__ void k_ha_xprep(HaDev h, const float *__restrict__ x, const unsigned *__restrict__ xmax,
-                           uint16_t *__restrict__ xs_hi, uint16_t *__restrict__ xs_lo)
+__global__ void k_ha_yprep(HaDev h, const float *__restrict__ x, const unsigned *__restrict__ xmax,
+                           uint16_t *__restrict__ ys_hi, uint16_t *__restrict__ ys_lo)
 {
-    const long long total = (long long)h.F * h.D * (h.L / 2);
+    const long long total = (long long)h.F * h.D * (h.Ly / 2);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int mp = 2 * (int)(e % (h.L / 2));
-        const long long fd = e / (h.L / 2);
-        const int d = (int)(fd % h.D), f = (int)(fd / h.D);
+        const int jp = 2 * (int)(e % (h.Ly / 2));
+        const long long fd = e / (h.Ly / 2);
+        const int f = (int)(fd / h.D);
         const float sc = pow2_scale(__uint_as_float(xmax[f]));
         float v[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int m = mp + q - h.P0;
-            v[q] = (m >= 0 && m < h.R) ? sc * x[((size_t)f * h.D + d) * h.R + (h.R - 1 - m)] : 0.f;
+            const int r = jp + q + h.R - h.nhp;
+            v[q] = (r >= 0 && r < h.R) ? sc * x[fd * h.R + r] : 0.f;
         }
         uint32_t hi, lo;
         Elem<ET>::split(v[0], v[1], hi, lo);
-        reinterpret_cast<uint32_t *>(xs_hi)[e] = hi;
-        reinterpret_cast<uint32_t *>(xs_lo)[e] = lo;
+        reinterpret_cast<uint32_t *>(ys_hi)[e] = hi;
+        reinterpret_cast<uint32_t *>(ys_lo)[e] = lo;
     }
 }
 
 // ------------------------------------------------------------ forward kernel
-// (the table slot of a unit holds its E chunk [A][64] followed by the sky strip of its
-// (channel, declination) row, hi then lo: the producers read no global memory)
-// Work units q in [0, Q), q = (mt F + f) nchunk + c with K chunk c = d nbc + nb; CTA g
-// takes the contiguous range [Q g / G, Q (g+1) / G).  A segment is the part of one
+// GEMM D[rho][t] = sum_{d, m} A[rho][m] B[t][m] per (M-tile, channel), K = (d, m) with the
+// hour-angle cells taken in the order m = nhp - 1 - n.
+//   A = P tile, written by the producers into TMEM (the MMA reads it from there): TMEM lane
+//       rho = 2 u + (0: Re, 1: Im), two cells per 32-bit column.
+//   B = Hankel sky tile B[t][m] = ys[m + t k], never materialised: per (channel, declination)
+//       the producers build the image img[j][rho'][e] = ys[8 j + rho' k + e] (rho' < 8,
+//       e < 8, 16 bytes per (j, rho')), in which the 8 x 16-byte core matrix of rows
+//       t = 8 g .. 8 g + 7 and cells m = 8 jj .. 8 jj + 7 is the 128 contiguous bytes at chunk
+//       jj + g k; a K-major descriptor without swizzle (K step 128 B, 8-row step 128 k B)
+//       then reads the tile of every chunk straight from the image.
+// Work units q in [0, Q), q = (mt F + f) nchunk + d nbc + c (c: 64-cell chunk in m order);
+// CTA g takes the contiguous range [Q g / G, Q (g+1) / G).  A segment is the part of one
 // (M-tile, channel) pair inside a CTA's range; its partial sum goes to
 // vpart[segment][j] with j the CTA's rank among the segment's contributors.
-//   producers (warps 0-15): per unit, rows 2u, 2u+1 of the P tile for the 4 groups
-//     u = 4w .. 4w+3 (lane l: hour-angle cells 2l, 2l+1) and rows t = w, w+16, .. of the
-//     Toeplitz sky tile;  full[s] (16 arrivals), then eempty[se] (16 arrivals)
-//   load warp (21): per unit, the E chunk [A][64] by one bulk copy;  efull[se] (tx)
-//   MMA warp (20): 4 K-steps x (1 | 3) MMAs;  commits empty[s] and, at the end of a
-//     chain of HA_SUB units or a segment, accf[q]
-//   epilogue (16-19): adds the chain into the FP32 row sums in shared memory; writes
-//     them at the end of a segment;  acce[q] (4 arrivals)
+//   load warp (21): per unit, the E chunk [A][HA_EW] (and, at the first unit of a
+//     (channel, declination) group, the two sky strips) by bulk copies;  efull[se] (tx)
+//   producers (warps 0-15): warp w fills TMEM lanes 32 (w & 3) .. +31, cells 16 (w >> 2) ..
+//     +15 of stage s (hi, lo), and at a group start its share of the image;  eempty[se]
+//     and full[s] (16 arrivals each)
+//   MMA warp (20): 4 K-steps x (1 | 3) MMAs;  commits empty[s], iempty[b] at the end of
+//     a group, and accf[q] at the end of a chain of HA_SUB units or a segment
+//   epilogue (16-19): adds the chain into the segment's running sum in TMEM columns
+//     [2 npad, 3 npad), writes it at the end of a segment;  acce[q] (4 arrivals)
 template <int ET, bool X3>
 __global__ void __launch_bounds__(HA_THREADS, 1)
-k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t *__restrict__ xs_lo,
+k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t *__restrict__ ys_lo,
          float *__restrict__ vpart, int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -193,21 +207,12 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
     constexpr int NT = X3 ? 2 : 1;
     const uint32_t full0 = base + L.bar_off, empty0 = full0 + 8 * L.nstage;
     const uint32_t efull0 = empty0 + 8 * L.nstage, eempty0 = efull0 + 8 * L.neslot;
-    const uint32_t accf0 = eempty0 + 8 * L.neslot, acce0 = accf0 + 16;
-    const uint32_t misc = L.bar_off + 16 * (L.nstage + L.neslot) + 32;
+    const uint32_t accf0 = eempty0 + 8 * L.neslot, acce0 = accf0 + 16, iempty0 = acce0 + 16;
+    const uint32_t misc = L.bar_off + 16 * (L.nstage + L.neslot) + 48;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + misc + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // B-tile rows t >= T stay zero (producers write rows t < T only)
-    const int zrows = h.npad - h.T;
-    for (int s = 0; s < L.nstage; ++s) {
-        uint8_t *bt = gbase + (size_t)s * L.stage_bytes + NT * L.a_bytes;
-        for (int e = tid; e < NT * zrows * 8; e += HA_THREADS) {
-            const int tl = e / (zrows * 8), r = e % (zrows * 8);
-            reinterpret_cast<uint4 *>(bt + tl * L.b_bytes + (size_t)h.T * 128)[r] = make_uint4(0, 0, 0, 0);
-        }
-    }
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
             mbar_init(full0 + 8 * s, HA_PROD_WARPS);
@@ -220,6 +225,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
         for (int q = 0; q < 2; ++q) {
             mbar_init(accf0 + 8 * q, 1);
             mbar_init(acce0 + 8 * q, 4);
+            mbar_init(iempty0 + 8 * q, 1);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -232,31 +238,28 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
     const uint32_t tmem_d = *tmem_slot;
     const int G = gridDim.x;
     const long long q0 = range_lo(h.Q, G, blockIdx.x), q1 = range_lo(h.Q, G, blockIdx.x + 1);
+    const uint32_t eb = (uint32_t)h.A * (uint32_t)(HA_EW * 8);    // E chunk bytes
+    const uint32_t sb = (uint32_t)h.Ly * 2u;                      // bytes of one strip part
 
     if (warp < HA_PROD_WARPS) {
         // ------------------------------------------------------------ producers
-        int s = 0, se = 0;
+        const int quarter = warp & 3, kq = warp >> 2;
+        const int ul = 16 * quarter + (lane >> 1);               // group within the M-tile
+        const bool im_row = lane & 1;
+        const uint32_t ta_row = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(L.abase + 8 * kq);
+        // column cc holds cells m = 16 kq + 2 cc (low half) and + 1, i.e. table cells
+        // n = 63 - 16 kq - 2 cc and n - 1: one 16-byte load at cell 62 - 16 kq - 2 cc
+        const int ne0 = 62 - 16 * kq;
+        int s = 0, se = 0, gb = 0;
         uint32_t ph = 0, eph = 0;
         bool wrapped = false;
-        const uint32_t wsub = (uint32_t)(lane & 3) * 4u;       // lane's word in its 16-byte chunk
-        const uint32_t lch = (uint32_t)(lane >> 2);               // lane's 16-byte chunk (before the swizzle)
-        // P-tile rows 2 ul, 2 ul + 1 (ul = 4 warp + k) sit at row & 7 = 2k, 2k + 1; Toeplitz
-        // rows t = warp + 16 k all sit at t & 7 = warp & 7, and their strip offsets
-        // P0 - t kst share one parity
-        const uint32_t a_row0 = (uint32_t)(8 * warp) * 128u + wsub;
-        const uint32_t b_off0 = (uint32_t)warp * 128u + ((lch ^ (uint32_t)(warp & 7)) << 4) + wsub;
-        const int b_base = h.P0 - warp * h.k;                    // >= 0
-        const bool b_odd = b_base & 1;
-        const int b_word0 = (b_base >> 1) + lane;
-        // unit coordinates, advanced incrementally (nb fastest, then d, f, mt)
-        int mt, f, d, nb;
+        long long ngrp = 0;                                      // (channel, declination) groups started
+        int mt, f, d, c;
         {
-            const int seg = (int)(q0 / h.nchunk), c = (int)(q0 % h.nchunk);
-            mt = seg / h.F; f = seg % h.F; d = c / h.nbc; nb = c % h.nbc;
+            const int seg = (int)(q0 / h.nchunk), cd = (int)(q0 % h.nchunk);
+            mt = seg / h.F; f = seg % h.F; d = cd / h.nbc; c = cd % h.nbc;
         }
-        int2 ij4[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) ij4[k] = h.uij[mt * 64 + 4 * warp + k];
+        int2 ij = h.uij[mt * 64 + ul];
         for (long long q = q0; q < q1; ++q) {
             // a failed wait has raised the abort flag before returning, so after the
             // warp barrier every lane takes the same branch
@@ -264,71 +267,68 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
             if (lane == 0 && wrapped) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
             __syncwarp();
             if (*abort_flag) goto done;
-            {
-                uint8_t *st = gbase + (size_t)s * L.stage_bytes;
-                uint8_t *a_hi = st, *a_lo = st + L.a_bytes;
-                uint8_t *b_hi = st + NT * L.a_bytes, *b_lo = b_hi + L.b_bytes;
-                const uint8_t *eslot = gbase + L.e_off + (size_t)se * L.eslot_bytes;
-                const float4 *Es = reinterpret_cast<const float4 *>(eslot);
-                // the slot also holds this (channel, declination) row's sky strip, hi then lo
-                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(eslot + (size_t)h.A * 512);
-                const uint32_t *l32 = h32 + h.L / 2;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int ul = 4 * warp + k;
-                    const int2 ij = ij4[k];
-                    const float4 a = Es[ij.x * 32 + lane], b = Es[ij.y * 32 + lane];
-                    const float pr0 = fmaf(a.x, b.x, a.y * b.y), pi0 = fmaf(a.y, b.x, -a.x * b.y);
-                    const float pr1 = fmaf(a.z, b.z, a.w * b.w), pi1 = fmaf(a.w, b.z, -a.z * b.w);
-                    uint32_t hr, lr, hm, lm;
-                    Elem<ET>::split(pr0, pr1, hr, lr);
-                    Elem<ET>::split(pi0, pi1, hm, lm);
-                    (void)ul;
-                    const uint32_t o_re = a_row0 + (uint32_t)(2 * k) * 128u + ((lch ^ (uint32_t)(2 * k)) << 4);
-                    const uint32_t o_im = a_row0 + (uint32_t)(2 * k + 1) * 128u + ((lch ^ (uint32_t)(2 * k + 1)) << 4);
-                    st32(a_hi + o_re, hr);
-                    st32(a_hi + o_im, hm);
-                    if (X3) {
-                        st32(a_lo + o_re, lr);
-                        st32(a_lo + o_im, lm);
-                    }
-                }
-                // row t = warp + 16 k: strip words from 32 nb + ((P0 - t kst) >> 1) + lane
-                const int wrow = 32 * nb + b_word0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int t = warp + HA_PROD_WARPS * k;
-                    if (t < h.T) {
-                        const int w = wrow - 8 * k * h.k;
-                        const uint32_t ob = b_off0 + (uint32_t)(2048 * k);
-                        if (b_odd) {
-                            st32(b_hi + ob, __byte_perm(h32[w], h32[w + 1], 0x5432));
-                            if (X3) st32(b_lo + ob, __byte_perm(l32[w], l32[w + 1], 0x5432));
-                        } else {
-                            st32(b_hi + ob, h32[w]);
-                            if (X3) st32(b_lo + ob, l32[w]);
-                        }
-                    }
-                }
+            const uint8_t *eslot = gbase + L.e_off + (size_t)se * L.eslot_bytes;
+            const bool gstart = (q == q0) || (c == 0);
+            if (gstart) {
+                gb = (int)(ngrp & 1);
+                if (lane == 0 && ngrp >= 2)
+                    mbar_wait_ab(iempty0 + 8 * gb, (uint32_t)(((ngrp >> 1) - 1) & 1), abort_flag);
                 __syncwarp();
-                if (lane == 0) mbar_arrive(eempty0 + 8 * se);
+                if (*abort_flag) goto done;
+                ++ngrp;
+                const uint32_t *strip = reinterpret_cast<const uint32_t *>(eslot + eb);
+                const int nch = h.Jc * 8;
+                for (int e = tid; e < NT * nch; e += HA_PROD_WARPS * 32) {
+                    const int part = e >= nch, r = e - part * nch, j = r >> 3, rho = r & 7;
+                    const int s0 = 8 * j + rho * h.k;
+                    const uint32_t *w = strip + part * (h.Ly / 2) + (s0 >> 1);
+                    uint4 o;
+                    if (s0 & 1) {
+                        o.x = __byte_perm(w[0], w[1], 0x5432);
+                        o.y = __byte_perm(w[1], w[2], 0x5432);
+                        o.z = __byte_perm(w[2], w[3], 0x5432);
+                        o.w = __byte_perm(w[3], w[4], 0x5432);
+                    } else {
+                        o = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                    *reinterpret_cast<uint4 *>(gbase + (size_t)(gb * NT + part) * L.img_bytes + (size_t)j * 128 +
+                                               rho * 16) = o;
+                }
             }
-            fence_async_smem();
+            {
+                const uint8_t *ei = eslot + (size_t)ij.x * (HA_EW * 8), *ej = eslot + (size_t)ij.y * (HA_EW * 8);
+                uint32_t hw[8], lw[8];
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    const int ne = ne0 - 2 * cc;
+                    const float4 a = *reinterpret_cast<const float4 *>(ei + ne * 8);
+                    const float4 b = *reinterpret_cast<const float4 *>(ej + ne * 8);
+                    // P = E_i conj(E_j); (x, y): cell ne (odd m), (z, w): cell ne + 1 (even m)
+                    const float re_e = fmaf(a.z, b.z, a.w * b.w), im_e = fmaf(a.w, b.z, -a.z * b.w);
+                    const float re_o = fmaf(a.x, b.x, a.y * b.y), im_o = fmaf(a.y, b.x, -a.x * b.y);
+                    Elem<ET>::split(im_row ? im_e : re_e, im_row ? im_o : re_o, hw[cc], lw[cc]);
+                }
+                const uint32_t ta = ta_row + (uint32_t)(s * L.acols);
+                tmem_st8(ta, hw);
+                if (X3) tmem_st8(ta + 32u, lw);
+                tmem_wait_st();
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(eempty0 + 8 * se);
+            if (gstart) fence_async_smem();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(full0 + 8 * s);
             if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
             if (++se == L.neslot) { se = 0; eph ^= 1u; }
-            if (++nb == h.nbc) {
-                nb = 0;
+            if (++c == h.nbc) {
+                c = 0;
                 if (++d == h.D) {
                     d = 0;
                     if (++f == h.F) {
                         f = 0;
                         ++mt;
-                        if (q + 1 < q1) {
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) ij4[k] = h.uij[mt * 64 + 4 * warp + k];
-                        }
+                        if (q + 1 < q1) ij = h.uij[mt * 64 + ul];
                     }
                 }
             }
@@ -339,22 +339,25 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
             int se = 0, last_se = -1;
             uint32_t eph = 0, last_eph = 0;
             bool wrapped = false;
-            int f = (int)((q0 / h.nchunk) % h.F), c = (int)(q0 % h.nchunk);
+            int f = (int)((q0 / h.nchunk) % h.F), cd = (int)(q0 % h.nchunk);
             for (long long q = q0; q < q1; ++q) {
                 if (wrapped && !mbar_wait_ab<64>(eempty0 + 8 * se, eph ^ 1u, abort_flag)) break;
-                const float2 *src = h.E + (((size_t)f * h.D * h.nbc + c) * h.A) * 64;
-                const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes, eb = (uint32_t)h.A * 512u;
-                const uint32_t sb = (uint32_t)h.L * 2u;
-                const size_t row = ((size_t)f * h.D + c / h.nbc) * h.L;
-                mbar_expect_tx(efull0 + 8 * se, eb + (X3 ? 2u : 1u) * sb);
+                const int d = cd / h.nbc, c = cd % h.nbc;
+                const bool gstart = (q == q0) || (c == 0);
+                const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + (h.nbc - 1 - c)) * h.A * HA_EW;
+                const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes;
+                const size_t row = ((size_t)f * h.D + d) * h.Ly;
+                mbar_expect_tx(efull0 + 8 * se, eb + (gstart ? (uint32_t)NT * sb : 0u));
                 bulk_g2s(dst, src, eb, efull0 + 8 * se);
-                bulk_g2s(dst + eb, xs_hi + row, sb, efull0 + 8 * se);
-                if (X3) bulk_g2s(dst + eb + sb, xs_lo + row, sb, efull0 + 8 * se);
+                if (gstart) {
+                    bulk_g2s(dst + eb, ys_hi + row, sb, efull0 + 8 * se);
+                    if (X3) bulk_g2s(dst + eb + sb, ys_lo + row, sb, efull0 + 8 * se);
+                }
                 last_se = se;
                 last_eph = eph;
                 if (++se == L.neslot) { se = 0; eph ^= 1u; wrapped = true; }
-                if (++c == h.nchunk) {
-                    c = 0;
+                if (++cd == h.nchunk) {
+                    cd = 0;
                     if (++f == h.F) f = 0;
                 }
             }
@@ -373,12 +376,15 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(128, h.npad, Elem<ET>::kFmt);
-            int s = 0, last_s = -1;
+            const uint32_t sbo = 128u * (uint32_t)h.k;
+            int s = 0, last_s = -1, gb = 0;
             uint32_t ph = 0, last_ph = 0;
-            long long nacc = 0;
-            int local = 0, c = (int)(q0 % h.nchunk);
-            for (long long q = q0; q < q1; ++q, c = (c + 1 == h.nchunk) ? 0 : c + 1) {
-                if (q == q0 || c == 0) local = 0;
+            long long nacc = 0, ngrp = 0;
+            int local = 0, cd = (int)(q0 % h.nchunk);
+            for (long long q = q0; q < q1; ++q, cd = (cd + 1 == h.nchunk) ? 0 : cd + 1) {
+                const int c = cd % h.nbc;
+                if (q == q0 || cd == 0) local = 0;
+                if (q == q0 || c == 0) gb = (int)(ngrp++ & 1);
                 const bool chain_first = (local % HA_SUB) == 0;
                 const int qa = (int)(nacc & 1);
                 if (chain_first && nacc >= 2 &&
@@ -387,26 +393,26 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ xs_hi, const uint16_t
                 if (!mbar_wait_ab<32>(full0 + 8 * s, ph, abort_flag)) goto mma_done;
                 tc_fence_after();
                 {
-                    const uint32_t sa = base + (uint32_t)s * L.stage_bytes;
-                    const uint32_t a_hi = sa, a_lo = sa + L.a_bytes;
-                    const uint32_t b_hi = sa + NT * L.a_bytes, b_lo = b_hi + L.b_bytes;
                     const uint32_t dacc = tmem_d + (uint32_t)(qa * h.npad);
+                    const uint32_t ta = tmem_d + (uint32_t)(L.abase + s * L.acols);
+                    const uint32_t ib = base + (uint32_t)(gb * NT) * L.img_bytes + (uint32_t)(8 * c) * 128u;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t dah = sdesc_sw128(a_hi + 32u * kk), dbh = sdesc_sw128(b_hi + 32u * kk);
-                        mma_bf16(dacc, dah, dbh, idesc, (chain_first && kk == 0) ? 0u : 1u);
+                        const uint64_t dbh = sdesc_none(ib + 256u * kk, 128u, sbo);
+                        mma_ts(dacc, ta + 8u * kk, dbh, idesc, (chain_first && kk == 0) ? 0u : 1u);
                         if (X3) {
-                            mma_bf16(dacc, dah, sdesc_sw128(b_lo + 32u * kk), idesc, 1u);
-                            mma_bf16(dacc, sdesc_sw128(a_lo + 32u * kk), dbh, idesc, 1u);
+                            mma_ts(dacc, ta + 8u * kk, sdesc_none(ib + L.img_bytes + 256u * kk, 128u, sbo), idesc, 1u);
+                            mma_ts(dacc, ta + 32u + 8u * kk, dbh, idesc, 1u);
                         }
                     }
                 }
                 mma_commit(empty0 + 8 * s);
+                if (q == q1 - 1 || c == h.nbc - 1) mma_commit(iempty0 + 8 * gb);
                 last_s = s;
                 last_ph = ph;
                 if (++s == L.nstage) { s = 0; ph ^= 1u; }
                 ++local;
-                const bool seg_last = (q == q1 - 1) || (c == h.nchunk - 1);
+                const bool seg_last = (q == q1 - 1) || (cd == h.nchunk - 1);
                 if ((local % HA_SUB) == 0 || seg_last) {
                     mma_commit(accf0 + 8 * qa);
                     ++nacc;
@@ -622,7 +628,8 @@ __global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const float *_
 //   table warp (21): per M-tile, the two E chunks (bulk, efull[se])
 //   Q warp (22): per K chunk, the Q tile into the stage's B part (bulk, bfull[s])
 //   producers (0-15): thread (row n = tid & 127, quarter = tid >> 7) writes the 8 groups
-//     8 quarter .. +7 of row n (two 16-byte words hi, two lo);  then full[s]
+//     8 quarter .. +7 of row n into TMEM lane n (A operand of stage s: 8 columns hi, 8 lo);
+//     then full[s]
 //   MMA warp (20): D[n][t] of the M-tile into TMEM set (M-tile count & 1);  accf[q]
 //   epilogue (16-19): the diagonal sums over the M-tiles of the item (see below), one
 //     output row xbar(., d) per item.
@@ -671,7 +678,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
     tc_fence_after();
     const uint32_t tmem_d = *tmem_slot;
     const int nitem = h.F * h.D, nmta = h.nhp / 128;
-    const uint32_t echunk = (uint32_t)h.A * 512u;
+    const uint32_t echunk = (uint32_t)h.A * (uint32_t)(HA_EW * 8);
 
     if (warp < HA_PROD_WARPS) {
         // ------------------------------------------------------------ producers
@@ -690,23 +697,21 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                     if (lane == 0 && wrapped) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
                     __syncwarp();
                     if (*abort_flag) goto done;
-                    uint8_t *st = gbase + (size_t)s * L.stage_bytes;
                     uint32_t hw[8], lw[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int2 ij = suij[32 * kq + 8 * qq + q];
-                        const float2 a = *reinterpret_cast<const float2 *>(es + (size_t)ij.x * 512);
-                        const float2 b = *reinterpret_cast<const float2 *>(es + (size_t)ij.y * 512);
+                        const float2 a = *reinterpret_cast<const float2 *>(es + (size_t)ij.x * (HA_EW * 8));
+                        const float2 b = *reinterpret_cast<const float2 *>(es + (size_t)ij.y * (HA_EW * 8));
                         Elem<ET>::split(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y), hw[q], lw[q]);
                     }
-                    const uint32_t o0 = sw128_off(n, 2 * qq), o1 = sw128_off(n, 2 * qq + 1);
-                    *reinterpret_cast<uint4 *>(st + o0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4 *>(st + o1) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-                    if (X3) {
-                        *reinterpret_cast<uint4 *>(st + L.a_bytes + o0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                        *reinterpret_cast<uint4 *>(st + L.a_bytes + o1) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
-                    }
-                    fence_async_smem();
+                    // TMEM lane n (= 32 (warp & 3) + lane), columns 8 qq .. 8 qq + 7 of stage s
+                    const uint32_t ta = tmem_d + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                        (uint32_t)(L.abase + s * L.acols + 8 * qq);
+                    tmem_st8(ta, hw);
+                    if (X3) tmem_st8(ta + 32u, lw);
+                    tmem_wait_st();
+                    tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full0 + 8 * s);
                     if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
@@ -727,11 +732,11 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                 const int f = it / h.D, d = it % h.D;
                 for (int mt = 0; mt < nmta; ++mt) {
                     if (ewrapped && !mbar_wait_ab<64>(eempty0 + 8 * se, eph ^ 1u, abort_flag)) goto eload_done;
-                    const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + 2 * mt) * h.A * 64;
+                    const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + 2 * mt) * h.A * HA_EW;
                     const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes;
                     mbar_expect_tx(efull0 + 8 * se, 2 * echunk);
                     bulk_g2s(dst, src, echunk, efull0 + 8 * se);
-                    bulk_g2s(dst + echunk, src + (size_t)h.A * 64, echunk, efull0 + 8 * se);
+                    bulk_g2s(dst + echunk, src + (size_t)h.A * HA_EW, echunk, efull0 + 8 * se);
                     last_se = se;
                     last_eph = eph;
                     ++nse;
@@ -763,7 +768,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                     for (int kq = 0; kq < h.nkq; ++kq) {
                         if (wrapped && !mbar_wait_ab<64>(empty0 + 8 * s, ph ^ 1u, abort_flag)) goto qload_done;
                         mbar_expect_tx(bfull0 + 8 * s, bbytes);
-                        bulk_g2s(base + (uint32_t)s * L.stage_bytes + NT * L.a_bytes,
+                        bulk_g2s(base + (uint32_t)s * L.stage_bytes,
                                  qimg + ((size_t)f * h.nkq + kq) * bbytes, bbytes, bfull0 + 8 * s);
                         last_s = s;
                         last_ph = ph;
@@ -798,16 +803,15 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                         if (!mbar_wait_ab<32>(full0 + 8 * s, ph, abort_flag)) goto mma_done;
                         if (!mbar_wait_ab<32>(bfull0 + 8 * s, ph, abort_flag)) goto mma_done;
                         tc_fence_after();
-                        const uint32_t sa = base + (uint32_t)s * L.stage_bytes;
-                        const uint32_t a_hi = sa, a_lo = sa + L.a_bytes;
-                        const uint32_t b_hi = sa + NT * L.a_bytes, b_lo = b_hi + L.b_bytes;
+                        const uint32_t b_hi = base + (uint32_t)s * L.stage_bytes, b_lo = b_hi + L.b_bytes;
+                        const uint32_t ta = tmem_d + (uint32_t)(L.abase + s * L.acols);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t dah = sdesc_sw128(a_hi + 32u * kk), dbh = sdesc_sw128(b_hi + 32u * kk);
-                            mma_bf16(dacc, dah, dbh, idesc, (kq == 0 && kk == 0) ? 0u : 1u);
+                            const uint64_t dbh = sdesc_sw128(b_hi + 32u * kk);
+                            mma_ts(dacc, ta + 8u * kk, dbh, idesc, (kq == 0 && kk == 0) ? 0u : 1u);
                             if (X3) {
-                                mma_bf16(dacc, dah, sdesc_sw128(b_lo + 32u * kk), idesc, 1u);
-                                mma_bf16(dacc, sdesc_sw128(a_lo + 32u * kk), dbh, idesc, 1u);
+                                mma_ts(dacc, ta + 8u * kk, sdesc_sw128(b_lo + 32u * kk), idesc, 1u);
+                                mma_ts(dacc, ta + 32u + 8u * kk, dbh, idesc, 1u);
                             }
                         }
                         mma_commit(empty0 + 8 * s);
@@ -900,7 +904,7 @@ HaDev make_dev(const Ctx &c)
     const HaState &s = c.ha;
     HaDev h;
     h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = s.nant + 1; h.U = s.U; h.k = s.k;
-    h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.P0 = s.P0; h.L = s.L;
+    h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.Ly = s.Ly; h.Jc = s.Jc;
     h.nchunk = c.D * s.nbc; h.nmt = s.nmt; h.nkq = s.nkq; h.J = s.J;
     h.Q = (long long)s.nmt * c.F * h.nchunk;
     h.E = s.E; h.uij = s.uij;
@@ -910,43 +914,67 @@ HaDev make_dev(const Ctx &c)
 bool x3_of(int prec) { return prec == FM_PREC_BF16X3 || prec == FM_PREC_FP16X3; }
 bool f16_of(int prec) { return prec == FM_PREC_FP16X1 || prec == FM_PREC_FP16X3; }
 
-// forward table slot: E chunk [A + 1][64] and the two sky-strip rows
-uint32_t fwd_slot_bytes(const Ctx &c, bool x3)
-{
-    return (uint32_t)(c.ha.nant + 1) * 512u + (x3 ? 2u : 1u) * (uint32_t)c.ha.L * 2u;
-}
-
 // adjoint scratch: the epilogue's half tile sk [32][129] and the group pairs [32 nkq]
 uint32_t adj_scratch_bytes(const Ctx &c)
 {
     return 32u * 129u * 4u + 32u * (uint32_t)c.ha.nkq * 8u;
 }
 
-// shared-memory layout common to both kernels; `vbytes` is the epilogue's scratch
-bool make_layout(const Ctx &c, bool x3, uint32_t eslot_bytes, uint32_t vbytes, HaLayout &L)
+// TMEM columns of both kernels: the accumulators (two sets, and the forward's running sum),
+// then HA_NSTAGE A stages of 32 columns per part
+void tmem_layout(const Ctx &c, bool x3, int nacc_sets, HaLayout &L)
+{
+    L.nstage = HA_NSTAGE;
+    L.acols = (x3 ? 2 : 1) * 32;
+    L.abase = (nacc_sets * c.ha.npad + 31) / 32 * 32;
+    L.ncols = 512;
+}
+
+// forward: two image buffers (hi, lo), then as many table slots (E chunk [A][HA_EW] and
+// the two sky strips) as fit, up to 8, at least 2
+bool make_layout_fwd(const Ctx &c, bool x3, HaLayout &L)
 {
     const int nt = x3 ? 2 : 1;
-    L.a_bytes = 128u * 128u;
+    tmem_layout(c, x3, 3, L);
+    if (L.abase + L.nstage * L.acols > L.ncols) return false;
+    L.b_bytes = 0;
+    L.stage_bytes = 0;
+    L.img_bytes = (uint32_t)c.ha.Jc * 128u;
+    L.eslot_bytes = (uint32_t)(c.ha.nant + 1) * (uint32_t)(HA_EW * 8) + (uint32_t)nt * (uint32_t)c.ha.Ly * 2u;
+    L.e_off = 2u * (uint32_t)nt * L.img_bytes;
+    const size_t bars = 16 * (size_t)L.nstage + 48 + 16;
+    L.neslot = 8;
+    while (L.neslot >= 2 && (size_t)L.e_off + (size_t)L.neslot * L.eslot_bytes + bars + 16 * L.neslot >
+                                (size_t)HA_SMEM_BUDGET)
+        --L.neslot;
+    if (L.neslot < 2) return false;
+    L.v_off = L.e_off + (uint32_t)L.neslot * L.eslot_bytes;
+    L.bar_off = L.v_off;
+    L.smem = 1024 + (size_t)L.bar_off + 16 * (L.nstage + L.neslot) + 48 + 16;
+    return L.smem <= 227 * 1024;
+}
+
+// adjoint: HA_NSTAGE residual tiles (B operand), table slots of two E chunks (up to 4, at
+// least 2) and the epilogue's scratch
+bool make_layout_adj(const Ctx &c, bool x3, HaLayout &L)
+{
+    const int nt = x3 ? 2 : 1;
+    tmem_layout(c, x3, 2, L);
+    if (L.abase + L.nstage * L.acols > L.ncols) return false;
     L.b_bytes = (uint32_t)c.ha.npad * 128u;
-    L.stage_bytes = nt * (L.a_bytes + L.b_bytes);
-    L.eslot_bytes = eslot_bytes;
-    L.ncols = 32;
-    while (L.ncols < 3 * c.ha.npad) L.ncols *= 2;     // two accumulator sets + the forward's running sum
-    // as many operand stages as fit next to two table slots (up to 4): the stage ring's
-    // round trip through the MMA commit bounds the unit rate; then as many table slots as
-    // fit (up to 4; one when even two do not fit)
-    const size_t vb = ((vbytes + 15) / 16) * 16 + 256;
-    L.neslot = 2;
-    if (2 * (size_t)eslot_bytes + vb + 2 * (size_t)L.stage_bytes > (size_t)HA_SMEM_BUDGET) L.neslot = 1;
-    L.nstage = (int)((HA_SMEM_BUDGET - (size_t)L.neslot * eslot_bytes - vb) / L.stage_bytes);
-    if (L.nstage > 4) L.nstage = 4;
-    if (L.nstage < 2) return false;
-    while (L.neslot < 4 &&
-           (size_t)(L.neslot + 1) * eslot_bytes + vb + (size_t)L.nstage * L.stage_bytes <= (size_t)HA_SMEM_BUDGET)
-        ++L.neslot;
+    L.stage_bytes = (uint32_t)nt * L.b_bytes;
+    L.img_bytes = 0;
+    L.eslot_bytes = 2u * (uint32_t)(c.ha.nant + 1) * (uint32_t)(HA_EW * 8);
+    const uint32_t vbytes = (adj_scratch_bytes(c) + 15) / 16 * 16;
+    const size_t bars = 24 * (size_t)L.nstage + 32 + 16;
     L.e_off = (uint32_t)L.nstage * L.stage_bytes;
-    L.v_off = L.e_off + (uint32_t)L.neslot * eslot_bytes;
-    L.bar_off = L.v_off + ((vbytes + 15) / 16) * 16;
+    L.neslot = 4;
+    while (L.neslot >= 2 &&
+           (size_t)L.e_off + (size_t)L.neslot * L.eslot_bytes + vbytes + bars + 16 * L.neslot > (size_t)HA_SMEM_BUDGET)
+        --L.neslot;
+    if (L.neslot < 2) return false;
+    L.v_off = L.e_off + (uint32_t)L.neslot * L.eslot_bytes;
+    L.bar_off = L.v_off + vbytes;
     L.smem = 1024 + (size_t)L.bar_off + 24 * L.nstage + 16 * L.neslot + 32 + 16;
     return L.smem <= 227 * 1024;
 }
@@ -957,20 +985,19 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
 {
     HaState &s = c.ha;
     HaLayout L;
-    if (!make_layout(c, X3, fwd_slot_bytes(c, X3), 0u, L)) {
+    if (!make_layout_fwd(c, X3, L)) {
         set_error("hour-angle forward tiles exceed shared memory");
         return FM_ERR_UNSUPPORTED;
     }
-    L.vstride = (uint32_t)s.npad + 1;
-    uint16_t *xs_hi = s.xs, *xs_lo = s.xs + (size_t)c.F * c.D * s.L;
+    uint16_t *ys_hi = s.ys, *ys_lo = s.ys + (size_t)c.F * c.D * s.Ly;
     FM_CK(cudaMemsetAsync(s.xmax, 0, sizeof(unsigned) * c.F, st));
     k_ha_xmax<<<dim3(cdiv(c.npix, 256 * 8), c.F), 256, 0, st>>>(c.npix, x, s.xmax);
     FM_CK_LAUNCH();
-    k_ha_xprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, xs_hi, xs_lo);
+    k_ha_yprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, ys_hi, ys_lo);
     FM_CK_LAUNCH();
     FM_CK(cudaFuncSetAttribute(k_vis_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
-        k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(h, L, xs_hi, xs_lo, s.vpart, c.status);
+        k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(h, L, ys_hi, ys_lo, s.vpart, c.status);
         FM_CK_LAUNCH();
         return FM_OK;
     }));
@@ -985,11 +1012,10 @@ fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar,
 {
     HaState &s = c.ha;
     HaLayout L;
-    if (!make_layout(c, X3, 2u * (uint32_t)(s.nant + 1) * 512u, adj_scratch_bytes(c), L)) {
+    if (!make_layout_adj(c, X3, L)) {
         set_error("hour-angle adjoint tiles exceed shared memory");
         return FM_ERR_UNSUPPORTED;
     }
-    L.vstride = 0;
     if (!q_ready) {
         k_ha_qsum<<<c.F * c.T, 256, sizeof(float) * 2 * (size_t)c.B, st>>>(h, c.B, omega, s.moff, s.mem, s.q32,
                                                                             s.qmax_ft);
@@ -1049,8 +1075,10 @@ fm_status ha_setup(Ctx &c)
     s.nbc = s.nhp / 64;
     s.npad = (c.T + 15) / 16 * 16;
     if (s.npad < 16) s.npad = 16;
-    s.P0 = ((c.T - 1) * k + 7) / 8 * 8;      // strip rows stay multiples of 16 bytes
-    s.L = s.P0 + s.nhp + 8;
+    // forward image: chunks j < Jc of 8 cells; the sky strip holds the Ly >= 8 Jc + 7 k + 8
+    // elements the image reads (a multiple of 8, so strips stay 16-byte aligned)
+    s.Jc = 8 * s.nbc + (s.npad / 8 - 1) * k;
+    s.Ly = 8 * s.Jc + 8 * k + 8;
 
     // fringe groups: equal baseline vectors (to 1 nm) up to sign
     bool group = true;
@@ -1166,18 +1194,16 @@ fm_status ha_setup(Ctx &c)
     {
         HaLayout L1, L2;
         const bool x3 = x3_of(c.prec);
-        if (!make_layout(c, x3, fwd_slot_bytes(c, x3), 0u, L1) ||
-            !make_layout(c, x3, 2u * (uint32_t)(s.nant + 1) * 512u, adj_scratch_bytes(c), L2))
-            return FM_OK;
+        if (!make_layout_fwd(c, x3, L1) || !make_layout_adj(c, x3, L2)) return FM_OK;
     }
 
     // device memory, all of it within half of what is free
-    const size_t e_n = (size_t)c.F * c.D * s.nhp * (s.nant + 1);
-    const size_t xs_n = 2 * (size_t)c.F * c.D * s.L;
+    const size_t e_n = (size_t)c.F * c.D * s.nbc * (s.nant + 1) * HA_EW;
+    const size_t ys_n = 2 * (size_t)c.F * c.D * s.Ly;
     const size_t vp_n = (size_t)s.nmt * c.F * s.J * 128 * s.npad;
     const size_t q_n = (size_t)c.F * c.T * s.U * 2;
     const size_t qi_n = (size_t)c.F * s.nkq * 2 * s.npad * 128;
-    const size_t need = e_n * 8 + xs_n * 2 + vp_n * 4 + q_n * 4 + qi_n + (size_t)c.B * 16 + (size_t)s.nmt * 64 * 8;
+    const size_t need = e_n * 8 + ys_n * 2 + vp_n * 4 + q_n * 4 + qi_n + (size_t)c.B * 16 + (size_t)s.nmt * 64 * 8;
     size_t fr = 0, tot = 0;
     FM_CK(cudaMemGetInfo(&fr, &tot));
     if (need > fr / 2) return FM_OK;
@@ -1188,7 +1214,7 @@ fm_status ha_setup(Ctx &c)
     FM_TRY(ha_alloc(c, &s.moff, (size_t)s.U + 1));
     FM_TRY(ha_alloc(c, &s.mem, (size_t)c.B));
     FM_TRY(ha_alloc(c, &s.ncontrib, ncontrib.size()));
-    FM_TRY(ha_alloc(c, &s.xs, xs_n));
+    FM_TRY(ha_alloc(c, &s.ys, ys_n));
     FM_TRY(ha_alloc(c, &s.xmax, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.vpart, vp_n));
     FM_TRY(ha_alloc(c, &s.q32, q_n));
