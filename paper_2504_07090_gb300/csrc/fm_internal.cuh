@@ -78,7 +78,8 @@ struct HaState {
     int Jc = 0, Ly = 0;        // forward sky image chunks; sky-strip length (16-bit elements)
     int grid = 0, J = 0;       // forward CTAs; most CTAs sharing one (M-tile, channel) segment
     float sp = 1.f;            // response scale 2^e (e even): the table holds sqrt(dOmega A) 2^(e/2)
-    float2 *E = nullptr;       // [F][D][nbc][nant + 1][66] phasor table (entry nant is zero; 2 pad cells)
+    float2 *E = nullptr;       // [F][D][nbc][nant + 1][66] phasor table, cells paired (entry nant is zero; 2 pad cells)
+    float2 *Ea = nullptr;      // the same table with one (Re, Im) per cell, for the adjoint
     int2 *uij = nullptr;       // [nmt * 64] representative pair (table entries) of each group; padding (nant, nant)
     int *bmap = nullptr;       // [B] group * 2 + (1 if the baseline is the reversed vector)
     int *moff = nullptr;       // [U + 1] CSR offsets of group members

@@ -48,13 +48,16 @@ constexpr int HA_ADJ_THREADS = 23 * 32;   // adjoint
 constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulation chain
 constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
 constexpr int HA_EW = 66;                 // float2 entries per table row: 64 cells + 16 bytes of padding
-constexpr int HA_NSTAGE = 4;              // operand stages (A in TMEM, and the adjoint's B in shared memory)
+constexpr int HA_NSTAGE = 4;              // adjoint operand stages (A in TMEM, B in shared memory)
+constexpr int HA_NSTAGE_FWD = 5;          // forward A stages in TMEM
+constexpr int HA_PGROUPS = 4;             // forward producer groups of HA_PROD_WARPS / 4 warps, one unit each
 
 // kernel parameters, by value
 struct HaDev {
     int F, D, T, R, A, U, k, nhp, nbc, npad, Ly, Jc, nchunk, nmt, nkq, J;
     long long Q;                          // forward work units: nmt * F * nchunk
-    const float2 *E;
+    const float2 *E;                      // phasor table, cells paired (forward)
+    const float2 *Ea;                     // the same, one (Re, Im) per cell (adjoint)
     const int2 *uij;
 };
 
@@ -91,9 +94,12 @@ __device__ __forceinline__ float pow2_scale(float mx)
 __device__ __forceinline__ void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
 // ------------------------------------------------------------ per-handle phasor table
-// E[f][d][nb][i][nl], n = 64 nb + nl (nl < 64; entries 64, 65 pad the row to 528 bytes so
-// that rows of different antennas start in different shared-memory banks), i over the
-// table's antenna subset plus one all-zero entry (padding pairs point at it):
+// E[f][d][nb][i][row], n = 64 nb + nl, i over the table's antenna subset plus one all-zero
+// entry (padding pairs point at it).  A row of 132 floats holds the 64 cells, then 16 bytes
+// of padding so that rows of different antennas start in different shared-memory banks;
+// `paired` = 1 (forward): the cells in pairs, (Re E_n, Re E_n+1, Im E_n, Im E_n+1) for even
+// n (one 16-byte load feeds packed FP32x2 arithmetic on two cells); 0 (adjoint): (Re, Im)
+// per cell.  Each cell holds
 // sqrt(dOmega_d A(za; nu_f)) 2^(e/2) exp(-2 pi i nu r_i . s / c)
 // at hour angle H(n) = LST_0 - (ra_min + (R - 1 - n + 1/2) dRA); zero below the horizon
 // and for n >= nh.  FP64 throughout, stored as FP32.
@@ -104,7 +110,7 @@ struct HaTabArgs {
     const double *kap64, *bcoef64, *domega64;
 };
 
-__global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
+__global__ void k_ha_table(HaTabArgs a, int paired, float *__restrict__ E)
 {
     const long long total = (long long)a.F * a.D * a.nbc * a.A * HA_EW;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -139,7 +145,17 @@ __global__ void k_ha_table(HaTabArgs a, float2 *__restrict__ E)
                 out = make_float2((float)(amp * cs), (float)(-amp * sn));
             }
         }
-        E[e] = out;
+        float *row = E + (size_t)(e / HA_EW) * (2 * HA_EW);
+        if (nl < 64 && paired) {
+            row[4 * (nl >> 1) + (nl & 1)] = out.x;
+            row[4 * (nl >> 1) + 2 + (nl & 1)] = out.y;
+        } else if (nl < 64) {
+            row[2 * nl] = out.x;
+            row[2 * nl + 1] = out.y;
+        } else {
+            row[128 + 2 * (nl - 64)] = 0.f;
+            row[129 + 2 * (nl - 64)] = 0.f;
+        }
     }
 }
 
@@ -188,9 +204,10 @@ __global__ void k_ha_yprep(HaDev h, const float *__restrict__ x, const unsigned 
 // vpart[segment][j] with j the CTA's rank among the segment's contributors.
 //   load warp (21): per unit, the E chunk [A][HA_EW] (and, at the first unit of a
 //     (channel, declination) group, the two sky strips) by bulk copies;  efull[se] (tx)
-//   producers (warps 0-15): warp w fills TMEM lanes 32 (w & 3) .. +31, cells 16 (w >> 2) ..
-//     +15 of stage s (hi, lo), and at a group start its share of the image;  eempty[se]
-//     and full[s] (16 arrivals each)
+//   producers (warps 0-15): four groups of four warps take turns by unit; warp w fills TMEM
+//     lanes 32 (w & 3) .. +31 of stage s over all 64 cells (hi, lo), and at the start of a
+//     (channel, declination) group its group builds the image;  eempty[se] and full[s]
+//     (4 arrivals each: one group)
 //   MMA warp (20): 4 K-steps x (1 | 3) MMAs;  commits empty[s], iempty[b] at the end of
 //     a group, and accf[q] at the end of a chain of HA_SUB units or a segment
 //   epilogue (16-19): adds the chain into the segment's running sum in TMEM columns
@@ -215,12 +232,12 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
-            mbar_init(full0 + 8 * s, HA_PROD_WARPS);
+            mbar_init(full0 + 8 * s, HA_PROD_WARPS / HA_PGROUPS);
             mbar_init(empty0 + 8 * s, 1);
         }
         for (int s = 0; s < L.neslot; ++s) {
             mbar_init(efull0 + 8 * s, 1);
-            mbar_init(eempty0 + 8 * s, HA_PROD_WARPS);
+            mbar_init(eempty0 + 8 * s, HA_PROD_WARPS / HA_PGROUPS);
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(accf0 + 8 * q, 1);
@@ -243,42 +260,46 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
 
     if (warp < HA_PROD_WARPS) {
         // ------------------------------------------------------------ producers
-        const int quarter = warp & 3, kq = warp >> 2;
+        // four groups of four warps; group pg builds the units l = q - q0 = pg, pg + 4, ...,
+        // its warp (pg, quarter) the 32 TMEM lanes of that quarter over all 64 cells
+        const int quarter = warp & 3, pg = warp / 4, gt = 32 * quarter + lane;
         const int ul = 16 * quarter + (lane >> 1);               // group within the M-tile
         const bool im_row = lane & 1;
-        const uint32_t ta_row = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(L.abase + 8 * kq);
-        // column cc holds cells m = 16 kq + 2 cc (low half) and + 1, i.e. table cells
-        // n = 63 - 16 kq - 2 cc and n - 1: one 16-byte load at cell 62 - 16 kq - 2 cc
-        const int ne0 = 62 - 16 * kq;
-        int s = 0, se = 0, gb = 0;
-        uint32_t ph = 0, eph = 0;
-        bool wrapped = false;
-        long long ngrp = 0;                                      // (channel, declination) groups started
-        int mt, f, d, c;
-        {
-            const int seg = (int)(q0 / h.nchunk), cd = (int)(q0 % h.nchunk);
-            mt = seg / h.F; f = seg % h.F; d = cd / h.nbc; c = cd % h.nbc;
-        }
+        const uint32_t ta_row = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)L.abase;
+        const int c0 = (int)(q0 % h.nbc);
+        const long long per_mt = (long long)h.F * h.nchunk;
+        int mt = (int)((q0 + pg) / per_mt);
+        long long next_mt = (long long)(mt + 1) * per_mt;
+        int c = (int)((q0 + pg) % h.nbc);
         int2 ij = h.uij[mt * 64 + ul];
-        for (long long q = q0; q < q1; ++q) {
+        for (long long l = pg; q0 + l < q1; l += HA_PGROUPS) {
+            const long long q = q0 + l;
+            if (q >= next_mt) {
+                mt = (int)(q / per_mt);
+                next_mt = (long long)(mt + 1) * per_mt;
+                ij = h.uij[mt * 64 + ul];
+            }
+            const int se = (int)(l % L.neslot), s = (int)(l % L.nstage);
+            const uint32_t eph = (uint32_t)((l / L.neslot) & 1), ph = (uint32_t)((l / L.nstage) & 1);
             // a failed wait has raised the abort flag before returning, so after the
             // warp barrier every lane takes the same branch
             mbar_wait_ab(efull0 + 8 * se, eph, abort_flag);
-            if (lane == 0 && wrapped) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
+            if (lane == 0 && l >= L.nstage) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
             __syncwarp();
             if (*abort_flag) goto done;
             const uint8_t *eslot = gbase + L.e_off + (size_t)se * L.eslot_bytes;
-            const bool gstart = (q == q0) || (c == 0);
+            const bool gstart = (l == 0) || (c == 0);
             if (gstart) {
-                gb = (int)(ngrp & 1);
-                if (lane == 0 && ngrp >= 2)
-                    mbar_wait_ab(iempty0 + 8 * gb, (uint32_t)(((ngrp >> 1) - 1) & 1), abort_flag);
+                // (channel, declination) group index among this CTA's groups; its image buffer
+                const long long gi = (c0 + l) / h.nbc;
+                const int gb = (int)(gi & 1);
+                if (lane == 0 && gi >= 2)
+                    mbar_wait_ab(iempty0 + 8 * gb, (uint32_t)(((gi >> 1) - 1) & 1), abort_flag);
                 __syncwarp();
                 if (*abort_flag) goto done;
-                ++ngrp;
                 const uint32_t *strip = reinterpret_cast<const uint32_t *>(eslot + eb);
                 const int nch = h.Jc * 8;
-                for (int e = tid; e < NT * nch; e += HA_PROD_WARPS * 32) {
+                for (int e = gt; e < NT * nch; e += 128) {
                     const int part = e >= nch, r = e - part * nch, j = r >> 3, rho = r & 7;
                     const int s0 = 8 * j + rho * h.k;
                     const uint32_t *w = strip + part * (h.Ly / 2) + (s0 >> 1);
@@ -297,20 +318,30 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
             }
             {
                 const uint8_t *ei = eslot + (size_t)ij.x * (HA_EW * 8), *ej = eslot + (size_t)ij.y * (HA_EW * 8);
-                uint32_t hw[8], lw[8];
-#pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    const int ne = ne0 - 2 * cc;
-                    const float4 a = *reinterpret_cast<const float4 *>(ei + ne * 8);
-                    const float4 b = *reinterpret_cast<const float4 *>(ej + ne * 8);
-                    // P = E_i conj(E_j); (x, y): cell ne (odd m), (z, w): cell ne + 1 (even m)
-                    const float re_e = fmaf(a.z, b.z, a.w * b.w), im_e = fmaf(a.w, b.z, -a.z * b.w);
-                    const float re_o = fmaf(a.x, b.x, a.y * b.y), im_o = fmaf(a.y, b.x, -a.x * b.y);
-                    Elem<ET>::split(im_row ? im_e : re_e, im_row ? im_o : re_o, hw[cc], lw[cc]);
-                }
                 const uint32_t ta = ta_row + (uint32_t)(s * L.acols);
-                tmem_st8(ta, hw);
-                if (X3) tmem_st8(ta + 32u, lw);
+#pragma unroll 1
+                for (int kq = 0; kq < 4; ++kq) {
+                    // column 8 kq + cc holds cells m = 16 kq + 2 cc (low half) and + 1, i.e.
+                    // table cells n + 1 and n with n = 62 - 16 kq - 2 cc: the row's cell pair n / 2
+                    uint32_t hw[8], lw[8];
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const int pc = 31 - 8 * kq - cc;
+                        const float4 a = *reinterpret_cast<const float4 *>(ei + pc * 16);
+                        const float4 b = *reinterpret_cast<const float4 *>(ej + pc * 16);
+                        // P = E_i conj(E_j) on the cell pair (n, n + 1), packed: .x cell n (odd m),
+                        // .y cell n + 1 (even m)
+                        const float2 xa = make_float2(a.x, a.y), ya = make_float2(a.z, a.w);
+                        const float2 xb = make_float2(b.x, b.y), yb = make_float2(b.z, b.w);
+                        const float2 re = __ffma2_rn(xa, xb, __fmul2_rn(ya, yb));
+                        const float2 mxy = __fmul2_rn(xa, yb);
+                        const float2 im = __ffma2_rn(ya, xb, make_float2(-mxy.x, -mxy.y));
+                        const float2 v = im_row ? im : re;
+                        Elem<ET>::split2(make_float2(v.y, v.x), hw[cc], lw[cc]);
+                    }
+                    tmem_st8(ta + 8u * kq, hw);
+                    if (X3) tmem_st8(ta + 32u + 8u * kq, lw);
+                }
                 tmem_wait_st();
             }
             __syncwarp();
@@ -319,19 +350,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(full0 + 8 * s);
-            if (++s == L.nstage) { s = 0; ph ^= 1u; wrapped = true; }
-            if (++se == L.neslot) { se = 0; eph ^= 1u; }
-            if (++c == h.nbc) {
-                c = 0;
-                if (++d == h.D) {
-                    d = 0;
-                    if (++f == h.F) {
-                        f = 0;
-                        ++mt;
-                        if (q + 1 < q1) ij = h.uij[mt * 64 + ul];
-                    }
-                }
-            }
+            c = (c + HA_PGROUPS) % h.nbc;
         }
     } else if (warp == HA_LOAD_WARP) {
         // ------------------------------------------------------------ bulk loads of E chunks
@@ -732,7 +751,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                 const int f = it / h.D, d = it % h.D;
                 for (int mt = 0; mt < nmta; ++mt) {
                     if (ewrapped && !mbar_wait_ab<64>(eempty0 + 8 * se, eph ^ 1u, abort_flag)) goto eload_done;
-                    const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + 2 * mt) * h.A * HA_EW;
+                    const float2 *src = h.Ea + (((size_t)f * h.D + d) * h.nbc + 2 * mt) * h.A * HA_EW;
                     const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes;
                     mbar_expect_tx(efull0 + 8 * se, 2 * echunk);
                     bulk_g2s(dst, src, echunk, efull0 + 8 * se);
@@ -907,7 +926,7 @@ HaDev make_dev(const Ctx &c)
     h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.Ly = s.Ly; h.Jc = s.Jc;
     h.nchunk = c.D * s.nbc; h.nmt = s.nmt; h.nkq = s.nkq; h.J = s.J;
     h.Q = (long long)s.nmt * c.F * h.nchunk;
-    h.E = s.E; h.uij = s.uij;
+    h.E = s.E; h.Ea = s.Ea; h.uij = s.uij;
     return h;
 }
 
@@ -921,10 +940,10 @@ uint32_t adj_scratch_bytes(const Ctx &c)
 }
 
 // TMEM columns of both kernels: the accumulators (two sets, and the forward's running sum),
-// then HA_NSTAGE A stages of 32 columns per part
-void tmem_layout(const Ctx &c, bool x3, int nacc_sets, HaLayout &L)
+// then `nstage` A stages of 32 columns per part
+void tmem_layout(const Ctx &c, bool x3, int nacc_sets, int nstage, HaLayout &L)
 {
-    L.nstage = HA_NSTAGE;
+    L.nstage = nstage;
     L.acols = (x3 ? 2 : 1) * 32;
     L.abase = (nacc_sets * c.ha.npad + 31) / 32 * 32;
     L.ncols = 512;
@@ -935,7 +954,7 @@ void tmem_layout(const Ctx &c, bool x3, int nacc_sets, HaLayout &L)
 bool make_layout_fwd(const Ctx &c, bool x3, HaLayout &L)
 {
     const int nt = x3 ? 2 : 1;
-    tmem_layout(c, x3, 3, L);
+    tmem_layout(c, x3, 3, HA_NSTAGE_FWD, L);
     if (L.abase + L.nstage * L.acols > L.ncols) return false;
     L.b_bytes = 0;
     L.stage_bytes = 0;
@@ -959,7 +978,7 @@ bool make_layout_fwd(const Ctx &c, bool x3, HaLayout &L)
 bool make_layout_adj(const Ctx &c, bool x3, HaLayout &L)
 {
     const int nt = x3 ? 2 : 1;
-    tmem_layout(c, x3, 2, L);
+    tmem_layout(c, x3, 2, HA_NSTAGE, L);
     if (L.abase + L.nstage * L.acols > L.ncols) return false;
     L.b_bytes = (uint32_t)c.ha.npad * 128u;
     L.stage_bytes = (uint32_t)nt * L.b_bytes;
@@ -1203,12 +1222,13 @@ fm_status ha_setup(Ctx &c)
     const size_t vp_n = (size_t)s.nmt * c.F * s.J * 128 * s.npad;
     const size_t q_n = (size_t)c.F * c.T * s.U * 2;
     const size_t qi_n = (size_t)c.F * s.nkq * 2 * s.npad * 128;
-    const size_t need = e_n * 8 + ys_n * 2 + vp_n * 4 + q_n * 4 + qi_n + (size_t)c.B * 16 + (size_t)s.nmt * 64 * 8;
+    const size_t need = 2 * e_n * 8 + ys_n * 2 + vp_n * 4 + q_n * 4 + qi_n + (size_t)c.B * 16 + (size_t)s.nmt * 64 * 8;
     size_t fr = 0, tot = 0;
     FM_CK(cudaMemGetInfo(&fr, &tot));
     if (need > fr / 2) return FM_OK;
 
     FM_TRY(ha_alloc(c, &s.E, e_n));
+    FM_TRY(ha_alloc(c, &s.Ea, e_n));
     FM_TRY(ha_alloc(c, &s.uij, (size_t)s.nmt * 64));
     FM_TRY(ha_alloc(c, &s.bmap, (size_t)c.B));
     FM_TRY(ha_alloc(c, &s.moff, (size_t)s.U + 1));
@@ -1251,7 +1271,9 @@ fm_status ha_setup(Ctx &c)
     a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D;
     a.lat = c.cfg.latitude_rad; a.amp_scale = std::ldexp(1.0, e2 / 2);
     a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
-    k_ha_table<<<2048, 256>>>(a, s.E);
+    k_ha_table<<<2048, 256>>>(a, 1, reinterpret_cast<float *>(s.E));
+    FM_CK_LAUNCH();
+    k_ha_table<<<2048, 256>>>(a, 0, reinterpret_cast<float *>(s.Ea));
     FM_CK_LAUNCH();
     FM_CK(cudaDeviceSynchronize());
     s.on = true;

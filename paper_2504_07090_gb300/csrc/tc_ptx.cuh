@@ -229,6 +229,15 @@ template <> struct Elem<0> {
         hi = u32_of(&h);
         lo = u32_of(&l);
     }
+    // v = (low, high) element of one packed column; the residual in one packed FMA
+    static __device__ __forceinline__ void split2(float2 v, uint32_t &hi, uint32_t &lo)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        const float2 r = __ffma2_rn(__bfloat1622float2(h), make_float2(-1.f, -1.f), v);
+        __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
+        hi = u32_of(&h);
+        lo = u32_of(&l);
+    }
     static __device__ __forceinline__ float2 unpack(uint32_t w)
     {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
@@ -241,6 +250,14 @@ template <> struct Elem<1> {
         __half2 h = __floats2half2_rn(a, b);
         float2 hf = __half22float2(h);
         __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = u32_of(&h);
+        lo = u32_of(&l);
+    }
+    static __device__ __forceinline__ void split2(float2 v, uint32_t &hi, uint32_t &lo)
+    {
+        __half2 h = __floats2half2_rn(v.x, v.y);
+        const float2 r = __ffma2_rn(__half22float2(h), make_float2(-1.f, -1.f), v);
+        __half2 l = __floats2half2_rn(r.x, r.y);
         hi = u32_of(&h);
         lo = u32_of(&l);
     }
