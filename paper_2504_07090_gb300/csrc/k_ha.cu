@@ -44,7 +44,8 @@ constexpr int HA_MMA_WARP = 20;
 constexpr int HA_LOAD_WARP = 21;          // bulk copies of the phasor table (and sky strips)
 constexpr int HA_QLOAD_WARP = 22;         // adjoint only: bulk copies of the residual tiles
 constexpr int HA_THREADS = 22 * 32;       // forward
-constexpr int HA_ADJ_THREADS = 23 * 32;   // adjoint
+constexpr int HA_EPI2_WARP0 = 23;         // adjoint only: warps 23..26, the second epilogue set
+constexpr int HA_ADJ_THREADS = 27 * 32;   // adjoint
 constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulation chain
 constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
 constexpr int HA_EW = 66;                 // float2 entries per table row: 64 cells + 16 bytes of padding
@@ -671,7 +672,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + misc + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int2 *suij = reinterpret_cast<int2 *>(gbase + L.v_off + (size_t)32 * 129 * 4);
+    int2 *suij = reinterpret_cast<int2 *>(gbase + L.v_off + ((size_t)2 * 32 * (128 + 64 * h.k + 1) + 4 * 128) * 4);
     for (int e = tid; e < 32 * h.nkq; e += blockDim.x) suij[e] = h.uij[e];
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
@@ -685,7 +686,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(accf0 + 8 * q, 1);
-            mbar_init(acce0 + 8 * q, 4);
+            mbar_init(acce0 + 8 * q, 8);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -845,60 +846,95 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
         mma_done:
             if (*abort_flag && last_s >= 0) mbar_drain(empty0 + 8 * last_s, last_ph);
         }
-    } else if (warp >= HA_EPI_WARP0 && warp < HA_EPI_WARP0 + 4) {
-        // ------------------------------------------------------------ epilogue (warps 16-19)
-        // Per M-tile, the accumulator D[n][t] goes through shared memory in two halves of
-        // 32 LSTs (sk[t][n], row stride 129); thread et then adds, for its outputs
-        // r = et + 128 j, the entries on the diagonal n = t k + R - 1 - r - 128 mt
-        // in LST order.  Named barrier 1 spans the four epilogue warps; its OR-reduced
-        // form decides a wind-down for all four at once.
-        const int quarter = warp & 3, et = tid - 32 * HA_EPI_WARP0;     // 0..127
-        float *sk = reinterpret_cast<float *>(gbase + L.v_off);          // [32][129]
+    } else if ((warp >= HA_EPI_WARP0 && warp < HA_EPI_WARP0 + 4) || warp >= HA_EPI2_WARP0) {
+        // ------------------------------------------------------------ epilogue (warps 16-19, 23-26)
+        // Two sets of four warps, set eh for the LSTs [32 eh, 32 eh + 32).  Per M-tile a set
+        // moves its half of the accumulator D[n][t] into its shared tile sk[t][pk + n] (row
+        // stride skw = 128 + 2 pk + 1, pk = 32 k zero cells on both sides of each row); thread
+        // et then adds, for its outputs r = et + 128 j, the entries on the diagonal
+        // n = t k + R - 1 - r - 128 mt: 32 unconditional loads (the diagonal leaves [0, 128)
+        // only into the zero margins) into four partial sums, added in a fixed order.  At the
+        // end of an item set 1 hands its sums to set 0 through shared memory, which adds them
+        // and stores x-bar.  Named barrier 1 + eh spans a set, barrier 3 both sets; the
+        // OR-reduced form of barrier 3 decides a wind-down for all eight warps at once.
+        const int eh = warp >= HA_EPI2_WARP0;
+        const int quarter = warp & 3, et = 32 * quarter + lane;          // TMEM lane = n = et
+        const int pk = 32 * h.k, skw = 128 + 2 * pk + 1;
+        float *sk = reinterpret_cast<float *>(gbase + L.v_off) + (size_t)eh * 32 * skw;   // [32][skw]
+        float *xs1 = reinterpret_cast<float *>(gbase + L.v_off) + (size_t)2 * 32 * skw;  // [4][128]
+        for (int e = et; e < 32 * skw; e += 128) sk[e] = 0.f;
+        bar_or(1 + eh, 128, false);
+        const int t0 = 32 * eh;
         long long nacc = 0;
         for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
             const int f = it / h.D, d = it % h.D;
             float xr[4] = {0.f, 0.f, 0.f, 0.f};      // outputs r = et + 128 j (R <= 512)
             bool stop = false;
-            for (int mt = 0; mt < nmta && !stop; ++mt, ++nacc) {
+            for (int mt = 0; mt < nmta; ++mt, ++nacc) {
                 const int qa = (int)(nacc & 1);
                 mbar_wait_ab<128>(accf0 + 8 * qa, (uint32_t)((nacc >> 1) & 1), abort_flag);
                 __syncwarp();
-                if (bar_or(1, 128, *abort_flag != 0)) { stop = true; break; }
+                if (bar_or(3, 256, *abort_flag != 0)) { stop = true; break; }
                 tc_fence_after();
                 const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
                 const int c0 = h.R - 1 - 128 * mt;                           // n = t k + c0 - r
-                for (int t0 = 0; t0 < h.T; t0 += 32) {
+                if (t0 < h.T) {
+                    // LST columns t >= T hold zeros (zero residual rows); those past npad are
+                    // not loaded and set to zero here
                     float v[32];
                     tmem_ld16(taddr + (uint32_t)t0, v);
-                    if (t0 + 16 < h.npad) tmem_ld16(taddr + (uint32_t)(t0 + 16), v + 16);
+                    if (t0 + 16 < h.npad) {
+                        tmem_ld16(taddr + (uint32_t)(t0 + 16), v + 16);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) sk[q * 129 + et] = v[q];
-                    bar_or(1, 128, false);
-                    const int tn = min(32, h.T - t0);
+                        for (int q = 16; q < 32; ++q) v[q] = 0.f;
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acce0 + 8 * qa);   // the accumulator is read
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) sk[q * skw + pk + et] = v[q];
+                    bar_or(1 + eh, 128, false);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         if (et + 128 * j >= h.R) break;
-                        // n = nb0 + q kst must lie in [0, 128): q in [q_lo, q_hi)
+                        // entry (q, nb0 + q k), q < 32; nothing of [0, 128) on the diagonal when
+                        // nb0 + 31 k < 0 or nb0 >= 128, otherwise every entry lies in the row
+                        // or its margins
                         const int nb0 = t0 * h.k + c0 - et - 128 * j;
-                        const int q_lo = nb0 >= 0 ? 0 : (-nb0 + h.k - 1) / h.k;
-                        const int q_hi = nb0 >= 128 ? 0 : min(tn, (128 - nb0 + h.k - 1) / h.k);
-                        float a = 0.f;
-                        const float *col = sk + nb0;              // entry (q, nb0 + q kst)
-                        for (int q = q_lo; q < q_hi; ++q) a += col[q * (129 + h.k)];
-                        xr[j] += a;
+                        if (nb0 + 31 * h.k < 0 || nb0 >= 128) continue;
+                        const float *col = sk + pk + nb0;
+                        const int st = skw + h.k;
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4) {
+                            a0 += col[q * st];
+                            a1 += col[(q + 1) * st];
+                            a2 += col[(q + 2) * st];
+                            a3 += col[(q + 3) * st];
+                        }
+                        xr[j] += (a0 + a1) + (a2 + a3);
                     }
-                    bar_or(1, 128, false);
+                    bar_or(1 + eh, 128, false);
+                } else {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acce0 + 8 * qa);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acce0 + 8 * qa);
             }
             if (stop) break;
-            const float sc = 1.f / (sp * qscale[f]);
-            float *xo = xbar + ((size_t)f * h.D + d) * h.R;
+            if (eh) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (et + 128 * j < h.R) xo[et + 128 * j] = xr[j] * sc;
+                for (int j = 0; j < 4; ++j) xs1[j * 128 + et] = xr[j];
+            }
+            bar_or(3, 256, false);
+            if (!eh) {
+                const float sc = 1.f / (sp * qscale[f]);
+                float *xo = xbar + ((size_t)f * h.D + d) * h.R;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (et + 128 * j < h.R) xo[et + 128 * j] = (xr[j] + xs1[j * 128 + et]) * sc;
+            }
+            bar_or(3, 256, false);
         }
     }
 done:
@@ -933,10 +969,11 @@ HaDev make_dev(const Ctx &c)
 bool x3_of(int prec) { return prec == FM_PREC_BF16X3 || prec == FM_PREC_FP16X3; }
 bool f16_of(int prec) { return prec == FM_PREC_FP16X1 || prec == FM_PREC_FP16X3; }
 
-// adjoint scratch: the epilogue's half tile sk [32][129] and the group pairs [32 nkq]
+// adjoint scratch: the two epilogue sets' tiles sk [32][128 + 64 k + 1] (32 k zero cells on
+// each side of a row), set 1's partial sums [4][128] and the group pairs [32 nkq]
 uint32_t adj_scratch_bytes(const Ctx &c)
 {
-    return 32u * 129u * 4u + 32u * (uint32_t)c.ha.nkq * 8u;
+    return (2u * 32u * (128u + 64u * (uint32_t)c.ha.k + 1u) + 4u * 128u) * 4u + 32u * (uint32_t)c.ha.nkq * 8u;
 }
 
 // TMEM columns of both kernels: the accumulators (two sets, and the forward's running sum),
