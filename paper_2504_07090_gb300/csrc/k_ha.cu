@@ -25,6 +25,7 @@
 // fill 128-byte-swizzled operand tiles, one thread issues tcgen05.mma into TMEM, four
 // warps drain the accumulators and one thread issues bulk copies.  Every wait is
 // bounded; a timeout records FM_ERR_TIMEOUT and the CTA winds down in order.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -188,6 +189,65 @@ __global__ void k_ha_yprep(HaDev h, const float *__restrict__ x, const unsigned 
     }
 }
 
+// Hankel image of one (channel, declination) sky strip, per part (hi, lo):
+// img[part][j][rho][e] = ys[part][8 j + rho k + e], 16 bytes per (j, rho), j < Jc.
+// K known at compile time: thread task (part, j) loads the strip words it needs with
+// 16-byte loads and forms the eight chunks in registers (byte permutes for odd shifts).
+template <int K, int NT>
+__device__ __forceinline__ void build_image(const uint32_t *strip, int Ly, int Jc, uint32_t img_bytes, uint8_t *img,
+                                            int t0, int nthr)
+{
+    constexpr int NW4 = ((7 * K + 7) / 2 + 5) / 4;   // 16-byte words covering elements 8 j .. 8 j + 7 K + 8
+    for (int task = t0; task < NT * Jc; task += nthr) {
+        const int part = task >= Jc, j = task - part * Jc;
+        const uint4 *src = reinterpret_cast<const uint4 *>(strip + part * (Ly / 2)) + j;
+        uint32_t w[4 * NW4];
+#pragma unroll
+        for (int q = 0; q < NW4; ++q) {
+            const uint4 v = src[q];
+            w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(img + (size_t)part * img_bytes + (size_t)j * 128);
+#pragma unroll
+        for (int rho = 0; rho < 8; ++rho) {
+            const int sft = rho * K, ws = sft >> 1;
+            uint4 o;
+            if (sft & 1) {
+                o.x = __byte_perm(w[ws], w[ws + 1], 0x5432);
+                o.y = __byte_perm(w[ws + 1], w[ws + 2], 0x5432);
+                o.z = __byte_perm(w[ws + 2], w[ws + 3], 0x5432);
+                o.w = __byte_perm(w[ws + 3], w[ws + 4], 0x5432);
+            } else {
+                o = make_uint4(w[ws], w[ws + 1], w[ws + 2], w[ws + 3]);
+            }
+            dst[rho] = o;
+        }
+    }
+}
+
+// the same for any k: one 16-byte chunk per thread task
+template <int NT>
+__device__ __forceinline__ void build_image_any(const uint32_t *strip, int Ly, int Jc, int k, uint32_t img_bytes,
+                                                uint8_t *img, int t0, int nthr)
+{
+    const int nch = Jc * 8;
+    for (int e = t0; e < NT * nch; e += nthr) {
+        const int part = e >= nch, r = e - part * nch, j = r >> 3, rho = r & 7;
+        const int s0 = 8 * j + rho * k;
+        const uint32_t *w = strip + part * (Ly / 2) + (s0 >> 1);
+        uint4 o;
+        if (s0 & 1) {
+            o.x = __byte_perm(w[0], w[1], 0x5432);
+            o.y = __byte_perm(w[1], w[2], 0x5432);
+            o.z = __byte_perm(w[2], w[3], 0x5432);
+            o.w = __byte_perm(w[3], w[4], 0x5432);
+        } else {
+            o = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        *reinterpret_cast<uint4 *>(img + (size_t)part * img_bytes + (size_t)j * 128 + rho * 16) = o;
+    }
+}
+
 // ------------------------------------------------------------ forward kernel
 // GEMM D[rho][t] = sum_{d, m} A[rho][m] B[t][m] per (M-tile, channel), K = (d, m) with the
 // hour-angle cells taken in the order m = nhp - 1 - n.
@@ -299,23 +359,10 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
                 __syncwarp();
                 if (*abort_flag) goto done;
                 const uint32_t *strip = reinterpret_cast<const uint32_t *>(eslot + eb);
-                const int nch = h.Jc * 8;
-                for (int e = gt; e < NT * nch; e += 128) {
-                    const int part = e >= nch, r = e - part * nch, j = r >> 3, rho = r & 7;
-                    const int s0 = 8 * j + rho * h.k;
-                    const uint32_t *w = strip + part * (h.Ly / 2) + (s0 >> 1);
-                    uint4 o;
-                    if (s0 & 1) {
-                        o.x = __byte_perm(w[0], w[1], 0x5432);
-                        o.y = __byte_perm(w[1], w[2], 0x5432);
-                        o.z = __byte_perm(w[2], w[3], 0x5432);
-                        o.w = __byte_perm(w[3], w[4], 0x5432);
-                    } else {
-                        o = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                    *reinterpret_cast<uint4 *>(gbase + (size_t)(gb * NT + part) * L.img_bytes + (size_t)j * 128 +
-                                               rho * 16) = o;
-                }
+                uint8_t *img = gbase + (size_t)(gb * NT) * L.img_bytes;
+                if (h.k == 1) build_image<1, NT>(strip, h.Ly, h.Jc, L.img_bytes, img, gt, 128);
+                else if (h.k == 2) build_image<2, NT>(strip, h.Ly, h.Jc, L.img_bytes, img, gt, 128);
+                else build_image_any<NT>(strip, h.Ly, h.Jc, h.k, L.img_bytes, img, gt, 128);
             }
             {
                 const uint8_t *ei = eslot + (size_t)ij.x * (HA_EW * 8), *ej = eslot + (size_t)ij.y * (HA_EW * 8);
@@ -1226,11 +1273,10 @@ fm_status ha_setup(Ctx &c)
         const int rflip = rb & 1;   // representative reversed w.r.t. the group's first member
         rep_i[u] = pos[bi[rb >> 1]];
         rep_j[u] = pos[bj[rb >> 1]];
-        for (int &m : members[u]) {
-            m ^= rflip;
-            bmap[m >> 1] = 2 * u + (m & 1);
-        }
+        for (int &m : members[u]) m ^= rflip;
     }
+    for (int u = 0; u < s.U; ++u)
+        for (int m : members[u]) bmap[m >> 1] = 2 * u + (m & 1);
 
     // partition of the forward work units over the CTAs
     const int nchunk = c.D * s.nbc;
