@@ -157,6 +157,38 @@ FM_API int64_t fm_precond_size(fm_handle h);   /* doubles written by fm_get_prec
 FM_API fm_status fm_leapfrog(fm_handle h, void *dev_q, void *dev_p, double eps, int n_steps, double u_accept,
                       double *dev_h_out, int *dev_accepted_out, fm_stream stream);
 
+/* Batched trajectories over independent problems (one HMC chain per handle; App. B for each
+ * chain, the chains independent of one another).
+ *
+ * fm_create_batch: fm_create for cfgs[0..n-1] into out[0..n-1]; on a failure the handles
+ * already created are destroyed, out[] is all NULL and the failing status is returned.
+ *
+ * fm_batch_create: captures, once, one fm_leapfrog trajectory of n_steps for every handle
+ * hs[k] on its own state (dev_q[k], dev_p[k], dev_h_out[k], dev_accepted_out[k]: the same
+ * meaning, types and sizes as in fm_leapfrog) as parallel branches of one CUDA graph.  Every
+ * handle must have had fm_set_data and fm_build_precond (FM_ERR_STATE otherwise); no handle
+ * may appear twice.  Before the capture it runs one chi^2 + gradient evaluation per handle
+ * at dev_q[k] (so that every buffer the trajectory needs exists) and synchronises; the call
+ * allocates the batch's streams, events, graph and a device array of 2 n doubles.  The
+ * handles and the four device buffers of every chain must stay valid, and must not be used
+ * by other calls while a batch launch runs, until fm_batch_destroy.
+ *
+ * fm_batch_leapfrog: one launch of the captured graph on `stream`: chain k runs with step
+ * eps[k] > 0 and accept uniform u_accept[k] in [0, 1) (host arrays of n; copied before the
+ * call returns), from the q and p its buffers hold, with exactly the arithmetic of
+ * fm_leapfrog on that handle.  Stream-ordered and asynchronous like fm_leapfrog.
+ *
+ * fm_batch_destroy: synchronises the device and frees the batch (not the handles). */
+typedef struct fm_batch_s *fm_batch;
+FM_API fm_status fm_create_batch(int n, const fm_config *cfgs, fm_handle *out);
+FM_API fm_status fm_batch_create(int n, const fm_handle *hs, void *const *dev_q, void *const *dev_p,
+                                 double *const *dev_h_out, int *const *dev_accepted_out, int n_steps,
+                                 fm_batch *out);
+FM_API fm_status fm_batch_leapfrog(fm_batch b, const double *eps, const double *u_accept, fm_stream stream);
+/* number of kernel launches one fm_batch_leapfrog call makes (kernel nodes of the graph) */
+FM_API fm_status fm_batch_kernels(fm_batch b, int64_t *out);
+FM_API fm_status fm_batch_destroy(fm_batch b);
+
 /* Apply the preconditioner's block Cholesky factor L (M = L L^T, App. B) to a device
  * vector [n_params]: op 0: out = L in (momentum draw p = L p0);  op 1: out = L^-1 in
  * (z of the kinetic energy);  op 2: out = L^-T in (Laplace-approximation draw from

@@ -484,10 +484,13 @@ fm_status fm_leapfrog(fm_handle h, void *dev_q, void *dev_p, double eps, int n_s
     Ctx &c = *reinterpret_cast<Ctx *>(h);
     if (!c.have_data) { set_error("fm_set_data has not been called"); return FM_ERR_STATE; }
     if (!c.pc_chol) { set_error("fm_build_precond has not been called"); return FM_ERR_STATE; }
-    if (c.prec == FM_PREC_FP64_SIMT)
-        return run_leapfrog<double>(c, (double *)dev_q, (double *)dev_p, eps, n_steps, u_accept, dev_h_out,
+    if (c.prec == FM_PREC_FP64_SIMT) {
+        FM_TRY(set_leapfrog_params<double>(c, eps, u_accept, stream));
+        return run_leapfrog<double>(c, (double *)dev_q, (double *)dev_p, c.lf_prm, n_steps, dev_h_out,
                                     dev_accepted_out, stream);
-    return run_leapfrog<float>(c, (float *)dev_q, (float *)dev_p, eps, n_steps, u_accept, dev_h_out, dev_accepted_out,
+    }
+    FM_TRY(set_leapfrog_params<float>(c, eps, u_accept, stream));
+    return run_leapfrog<float>(c, (float *)dev_q, (float *)dev_p, c.lf_prm, n_steps, dev_h_out, dev_accepted_out,
                                stream);
 }
 

@@ -150,6 +150,7 @@ struct Ctx {
     void *lf_q0 = nullptr, *lf_g = nullptr, *lf_z = nullptr;
     void *lf_y = nullptr;             // [gain-block order] intermediate of the dense solves
     double *lf_scal = nullptr;
+    double *lf_prm = nullptr;         // [2] eps, accept uniform of fm_leapfrog (read by the kernels)
 };
 
 // --------------------------------------------------------------------- errors
@@ -273,7 +274,11 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st);
 template <typename R>
 fm_status run_precond_apply(Ctx &c, int op, const R *in, R *out, cudaStream_t st);
 template <typename R>
-fm_status run_leapfrog(Ctx &c, R *q, R *p, double eps, int n_steps, double u, double *h_out, int *acc_out,
+fm_status set_leapfrog_params(Ctx &c, double eps, double u, cudaStream_t st);
+template <typename R>
+fm_status prepare_leapfrog(Ctx &c);
+template <typename R>
+fm_status run_leapfrog(Ctx &c, R *q, R *p, const double *prm, int n_steps, double *h_out, int *acc_out,
                        cudaStream_t st);
 
 // gradient / hvp drivers (fm_api.cu)

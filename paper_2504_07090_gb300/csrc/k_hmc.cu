@@ -554,6 +554,22 @@ __global__ void k_axpy(long long n, double alpha, const R *__restrict__ x, R *__
         y[k] += (R)alpha * x[k];
 }
 
+// momentum half-kick p -= (eps / 2) g with eps = prm[0] read on the device, so that a
+// captured trajectory can be replayed with a new step size
+template <typename R>
+__global__ void k_kick(long long n, const double *__restrict__ prm, const R *__restrict__ g, R *__restrict__ p)
+{
+    const R a = (R)(-0.5 * prm[0]);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        p[k] += a * g[k];
+}
+
+__global__ void k_set_lf_params(double *prm, double eps, double u)
+{
+    prm[0] = eps;
+    prm[1] = u;
+}
+
 template <typename R>
 __global__ void k_copy(long long n, const R *__restrict__ x, R *__restrict__ y)
 {
@@ -632,10 +648,12 @@ __device__ __forceinline__ void lower_mv(const R *S, const R *vs, R &y0, R &y1)
 template <typename R>
 __global__ void __launch_bounds__(256) k_lf_dense(int n, const R *__restrict__ M, int lower,
                                                   const R *__restrict__ x, R *__restrict__ y, double *__restrict__ kin,
-                                                  R *__restrict__ q, double eps, R *__restrict__ out)
+                                                  R *__restrict__ q, const double *__restrict__ peps,
+                                                  R *__restrict__ out)
 {
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (r >= n) return;
+    const double eps = q ? *peps : 0.0;
     const R *row = M + (size_t)r * n;
     R a = 0;
     for (int cc = lane; cc < n; cc += 32)
@@ -652,12 +670,14 @@ __global__ void __launch_bounds__(256) k_lf_dense(int n, const R *__restrict__ M
 template <typename R>
 __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const R *__restrict__ Li,
                                                           const R *__restrict__ L, const R *__restrict__ in, int fwd,
-                                                          int bwd, int mul, R *__restrict__ q, double eps,
+                                                          int bwd, int mul, R *__restrict__ q,
+                                                          const double *__restrict__ peps,
                                                           R *__restrict__ out, double *__restrict__ kin)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const double eps = q ? *peps : 0.0;
     {
         // ------------------------------------------------ one 64 x 64 block per warp
         const long long blk = (long long)blockIdx.x * LF_WARPS + w;
@@ -717,11 +737,13 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
 // Diagonal mass matrix (block = 1): the same operations elementwise with l = L[k].
 template <typename R>
 __global__ void __launch_bounds__(256) k_lf_solve_diag(long long n, const R *__restrict__ L, const R *__restrict__ in,
-                                                       int fwd, int bwd, int mul, R *__restrict__ q, double eps,
+                                                       int fwd, int bwd, int mul, R *__restrict__ q,
+                                                       const double *__restrict__ peps,
                                                        R *__restrict__ out, double *__restrict__ kin)
 {
     __shared__ double red[256];
     double s = 0.0;
+    const double eps = q ? *peps : 0.0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const double l = (double)L[k];
         double v = (double)in[k];
@@ -755,7 +777,8 @@ __global__ void __launch_bounds__(256) k_sum_to(int n, const double *__restrict_
 }
 
 // H0 = U0 + K0, H1 = U1 + K1, accept iff u < exp(H0 - H1); non-finite -> reject.
-__global__ void k_lf_finish(const double *__restrict__ sc, double u, double *__restrict__ h_out, int *__restrict__ acc,
+__global__ void k_lf_finish(const double *__restrict__ sc, const double *__restrict__ prm, double *__restrict__ h_out,
+                            int *__restrict__ acc,
                             int *__restrict__ status)
 {
     double H0 = sc[0] + sc[2], H1 = sc[1] + sc[3];
@@ -766,7 +789,7 @@ __global__ void k_lf_finish(const double *__restrict__ sc, double u, double *__r
         a = 0;
         atomicExch(status, (int)FM_ERR_NONFINITE);
     } else {
-        a = (H1 <= H0) ? 1 : (u < exp(H0 - H1) ? 1 : 0);
+        a = (H1 <= H0) ? 1 : (prm[1] < exp(H0 - H1) ? 1 : 0);
     }
     *acc = a;
 }
@@ -780,8 +803,8 @@ __global__ void k_lf_restore(long long n, const int *__restrict__ acc, const R *
 }
 
 template <typename R>
-static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q, double eps, R *out, double *kin_out,
-                           cudaStream_t st)
+static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q, const double *peps, R *out,
+                           double *kin_out, cudaStream_t st)
 {
     const int bs = c.pc_block;
     const R *L = (const R *)c.pc_chol;
@@ -793,7 +816,7 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
         FM_CK(cudaFuncSetAttribute(k_lf_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
         k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
-                                                                eps, out, kin_out ? part : nullptr);
+                                                                peps, out, kin_out ? part : nullptr);
         FM_CK_LAUNCH();
         if (ng > 0) {
             // the gain block: matrix-vector products with L_g (mul), L_g^-1 (fwd), L_g^-T (bwd)
@@ -802,20 +825,20 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
             const unsigned dg = cdiv(ng, 8);
             R *y = (R *)c.lf_y;
             if (mul) {
-                k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Lg, 1, in + base, nullptr, nullptr, nullptr, 0.0, out + base);
+                k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Lg, 1, in + base, nullptr, nullptr, nullptr, nullptr, out + base);
                 FM_CK_LAUNCH();
             } else {
                 const R *src = in + base;
                 if (fwd) {
                     const bool last = !bwd;
                     k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi, 1, src, y, kin_out ? part + nb : nullptr,
-                                                      last && q ? q + base : nullptr, eps,
+                                                      last && q ? q + base : nullptr, peps,
                                                       last && out ? out + base : nullptr);
                     FM_CK_LAUNCH();
                     src = y;
                 }
                 if (bwd) {
-                    k_lf_dense<R><<<dg, 256, 0, st>>>(ng, GiT, 0, src, nullptr, nullptr, q ? q + base : nullptr, eps,
+                    k_lf_dense<R><<<dg, 256, 0, st>>>(ng, GiT, 0, src, nullptr, nullptr, q ? q + base : nullptr, peps,
                                                       out ? out + base : nullptr);
                     FM_CK_LAUNCH();
                 }
@@ -826,7 +849,7 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
             FM_CK_LAUNCH();
         }
     } else {
-        k_lf_solve_diag<R><<<512, 256, 0, st>>>(c.n_par, L, in, fwd, bwd, mul, q, eps, out, kin_out ? part : nullptr);
+        k_lf_solve_diag<R><<<512, 256, 0, st>>>(c.n_par, L, in, fwd, bwd, mul, q, peps, out, kin_out ? part : nullptr);
         FM_CK_LAUNCH();
         if (kin_out) {
             k_sum_to<<<1, 256, 0, st>>>(512, part, kin_out);
@@ -858,14 +881,20 @@ static fm_status lf_ensure(Ctx &c)
         return FM_ERR_ALLOC;
     }
     c.allocs.push_back(c.lf_y);
+    if (cudaMalloc(&c.lf_prm, sizeof(double) * 2) != cudaSuccess) {
+        set_error("cudaMalloc leapfrog parameters");
+        return FM_ERR_ALLOC;
+    }
+    c.allocs.push_back(c.lf_prm);
     return FM_OK;
 }
 
-// kinetic energy K = z.z/2 (L z = p) into *kin_out; with q != NULL also q += eps L^-T z
+// kinetic energy K = z.z/2 (L z = p) into *kin_out; with q != NULL also q += eps L^-T z,
+// eps = *peps (device)
 template <typename R>
-static fm_status lf_kinetic_drift(Ctx &c, const R *p, R *q, double eps, double *kin_out, cudaStream_t st)
+static fm_status lf_kinetic_drift(Ctx &c, const R *p, R *q, const double *peps, double *kin_out, cudaStream_t st)
 {
-    return lf_blocks<R>(c, p, 1, q ? 1 : 0, 0, q, eps, nullptr, kin_out, st);
+    return lf_blocks<R>(c, p, 1, q ? 1 : 0, 0, q, peps, nullptr, kin_out, st);
 }
 
 template <typename R>
@@ -873,18 +902,20 @@ fm_status run_precond_apply(Ctx &c, int op, const R *in, R *out, cudaStream_t st
 {
     FM_TRY(lf_ensure<R>(c));
     switch (op) {
-    case 0: return lf_blocks<R>(c, in, 0, 0, 1, nullptr, 0.0, out, nullptr, st);
-    case 1: return lf_blocks<R>(c, in, 1, 0, 0, nullptr, 0.0, out, nullptr, st);
-    case 2: return lf_blocks<R>(c, in, 0, 1, 0, nullptr, 0.0, out, nullptr, st);
-    case 3: return lf_blocks<R>(c, in, 1, 1, 0, nullptr, 0.0, out, nullptr, st);
+    case 0: return lf_blocks<R>(c, in, 0, 0, 1, nullptr, nullptr, out, nullptr, st);
+    case 1: return lf_blocks<R>(c, in, 1, 0, 0, nullptr, nullptr, out, nullptr, st);
+    case 2: return lf_blocks<R>(c, in, 0, 1, 0, nullptr, nullptr, out, nullptr, st);
+    case 3: return lf_blocks<R>(c, in, 1, 1, 0, nullptr, nullptr, out, nullptr, st);
     default: set_error("op must be 0..3"); return FM_ERR_INVALID_ARG;
     }
 }
 template fm_status run_precond_apply<float>(Ctx &, int, const float *, float *, cudaStream_t);
 template fm_status run_precond_apply<double>(Ctx &, int, const double *, double *, cudaStream_t);
 
+// One trajectory: the kernels read eps = prm[0] and the accept uniform u = prm[1] from device
+// memory (a captured trajectory is replayed with new values by rewriting prm).
 template <typename R>
-fm_status run_leapfrog(Ctx &c, R *q, R *p, double eps, int n_steps, double u, double *h_out, int *acc_out,
+fm_status run_leapfrog(Ctx &c, R *q, R *p, const double *prm, int n_steps, double *h_out, int *acc_out,
                        cudaStream_t st)
 {
     const long long n = c.n_par;
@@ -894,29 +925,50 @@ fm_status run_leapfrog(Ctx &c, R *q, R *p, double eps, int n_steps, double u, do
     k_copy<R><<<512, 256, 0, st>>>(n, q, q0);
     FM_CK_LAUNCH();
     FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 0, g, st));
-    FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, 0.0, sc + 2, st));
+    FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, nullptr, sc + 2, st));
     for (int s = 0; s < n_steps; ++s) {
-        k_axpy<R><<<512, 256, 0, st>>>(n, -0.5 * eps, g, p);
+        k_kick<R><<<512, 256, 0, st>>>(n, prm, g, p);
         FM_CK_LAUNCH();
-        FM_TRY(lf_kinetic_drift<R>(c, p, q, eps, nullptr, st));
+        FM_TRY(lf_kinetic_drift<R>(c, p, q, prm, nullptr, st));
         FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 1, g, st));
-        k_axpy<R><<<512, 256, 0, st>>>(n, -0.5 * eps, g, p);
+        k_kick<R><<<512, 256, 0, st>>>(n, prm, g, p);
         FM_CK_LAUNCH();
     }
     if (n_steps == 0) {
         k_copy<double><<<1, 32, 0, st>>>(1, sc + 0, sc + 1);
         FM_CK_LAUNCH();
     }
-    FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, 0.0, sc + 3, st));
-    k_lf_finish<<<1, 1, 0, st>>>(sc, u, h_out, acc_out, c.status);
+    FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, nullptr, sc + 3, st));
+    k_lf_finish<<<1, 1, 0, st>>>(sc, prm, h_out, acc_out, c.status);
     FM_CK_LAUNCH();
     k_lf_restore<R><<<512, 256, 0, st>>>(n, acc_out, q0, q);
     FM_CK_LAUNCH();
     return FM_OK;
 }
 
-template fm_status run_leapfrog<float>(Ctx &, float *, float *, double, int, double, double *, int *, cudaStream_t);
-template fm_status run_leapfrog<double>(Ctx &, double *, double *, double, int, double, double *, int *, cudaStream_t);
+// the per-handle parameter slot written in stream order (fm_leapfrog)
+template <typename R>
+fm_status set_leapfrog_params(Ctx &c, double eps, double u, cudaStream_t st)
+{
+    FM_TRY(lf_ensure<R>(c));
+    k_set_lf_params<<<1, 1, 0, st>>>(c.lf_prm, eps, u);
+    FM_CK_LAUNCH();
+    return FM_OK;
+}
+template fm_status set_leapfrog_params<float>(Ctx &, double, double, cudaStream_t);
+template fm_status set_leapfrog_params<double>(Ctx &, double, double, cudaStream_t);
+
+// allocations a trajectory needs, made outside any stream capture
+template <typename R>
+fm_status prepare_leapfrog(Ctx &c)
+{
+    return lf_ensure<R>(c);
+}
+template fm_status prepare_leapfrog<float>(Ctx &);
+template fm_status prepare_leapfrog<double>(Ctx &);
+
+template fm_status run_leapfrog<float>(Ctx &, float *, float *, const double *, int, double *, int *, cudaStream_t);
+template fm_status run_leapfrog<double>(Ctx &, double *, double *, const double *, int, double *, int *, cudaStream_t);
 
 template fm_status run_build_precond<float>(Ctx &, const float *, int, cudaStream_t);
 template fm_status run_build_precond<double>(Ctx &, const double *, int, cudaStream_t);

@@ -31,7 +31,8 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_dat
            "fm_forward_pixels", "fm_sky_pixels", "fm_chi2_grad", "fm_hvp", "fm_build_precond", "fm_get_precond_blocks",
            "fm_precond_size", "fm_leapfrog", "fm_precond_apply", "fm_set_profiling", "fm_get_profile",
            "fm_contraction_info", "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status",
-           "fm_last_error"]
+           "fm_last_error", "fm_create_batch", "fm_batch_create", "fm_batch_leapfrog", "fm_batch_kernels",
+           "fm_batch_destroy"]
 CONTRACTION_FORMS = {0: "direct", 1: "antenna", 2: "hour_angle"}
 
 
@@ -93,6 +94,12 @@ def load(path: str = LIB_PATH):
     L.fm_kernel_launches.argtypes = []
     L.fm_kernel_launches.restype = c_int64
     L.fm_last_error.restype = ctypes.c_char_p
+    L.fm_create_batch.argtypes = [c_int, POINTER(FmConfig), POINTER(vp)]
+    L.fm_batch_create.argtypes = [c_int, POINTER(vp), POINTER(vp), POINTER(vp), POINTER(vp), POINTER(vp), c_int,
+                                  POINTER(vp)]
+    L.fm_batch_leapfrog.argtypes = [vp, POINTER(c_double), POINTER(c_double), vp]
+    L.fm_batch_kernels.argtypes = [vp, POINTER(c_int64)]
+    L.fm_batch_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("fm_num_params", "fm_num_vis", "fm_precond_size", "fm_last_error", "fm_kernel_launches"):
             getattr(L, name).restype = c_int
@@ -276,3 +283,50 @@ class _Chi2Fn(torch.autograd.Function):
 def chi2_potential(theta: torch.Tensor, model: ForwardModel) -> torch.Tensor:
     """U(theta) = chi^2/2 + prior as a differentiable scalar; backward uses the CUDA adjoint."""
     return _Chi2Fn.apply(theta, model)
+
+
+class Batch:
+    """One leapfrog trajectory per ForwardModel over independent problems, captured once as a
+    single CUDA graph (fm_batch_create) and replayed by run() (fm_batch_leapfrog).  Each chain
+    works in place on its own q and p tensors, exactly as ForwardModel.leapfrog does."""
+
+    def __init__(self, models, qs, ps, n_steps: int):
+        self.lib = load()
+        self.models = list(models)
+        n = len(self.models)
+        self.n = n
+        self.qs, self.ps = list(qs), list(ps)
+        self.h_out = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in range(n)]
+        self.acc_out = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in range(n)]
+        arr = c_void_p * n
+        hs = arr(*[m.h for m in self.models])
+        qp = arr(*[m._t(q, m.n_params, "q") for m, q in zip(self.models, self.qs)])
+        pp = arr(*[m._t(p, m.n_params, "p") for m, p in zip(self.models, self.ps)])
+        hp = arr(*[_ptr(t) for t in self.h_out])
+        ap = arr(*[_ptr(t) for t in self.acc_out])
+        b = c_void_p()
+        _check(self.lib.fm_batch_create(n, hs, qp, pp, hp, ap, int(n_steps), byref(b)), "fm_batch_create")
+        self.b = b
+
+    def run(self, eps, u):
+        """One trajectory per chain with steps eps[k] and accept uniforms u[k]."""
+        e = (c_double * self.n)(*[float(x) for x in eps])
+        v = (c_double * self.n)(*[float(x) for x in u])
+        _check(self.lib.fm_batch_leapfrog(self.b, e, v, _stream()), "fm_batch_leapfrog")
+        return self.h_out, self.acc_out
+
+    def kernels(self) -> int:
+        out = c_int64()
+        _check(self.lib.fm_batch_kernels(self.b, byref(out)), "fm_batch_kernels")
+        return int(out.value)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
