@@ -42,9 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg1")
-    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--precision", default=None, help="default: fp16x3 (cfg1), bf16x3 (cfg2)")
+    ap.add_argument("--problems", type=int, default=64, help="cfg2: number of independent problems")
     ap.add_argument("--traj", type=int, default=20, help="leapfrog steps per trajectory")
-    ap.add_argument("--eps", type=float, default=0.1)
+    ap.add_argument("--eps", type=float, default=None, help="leapfrog step: default 0.1 (cfg1), 0.02 (cfg2)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -180,11 +181,122 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def main_batch(args):
+    """cfg2: independent HMC chains on problems of uneven size (antennas 7/19/37, 16/32/64
+    channels, 512..16384 modes per channel, 20 LSTs).  One step = for every chain p = L z,
+    then one launch of the CUDA graph holding every chain's trajectory (fm_batch_leapfrog)."""
+    import torch
+    from paper_2504_07090_gb300 import build, fm, synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    prec = args.precision or "bf16x3"
+    probs = synth.batch_problems(args.problems)
+    dev = "cuda"
+    K, W = args.steps, args.warmup
+    models, qs, ps, zs, forms = [], [], [], [], {}
+    for k, prob in enumerate(probs):
+        tr = synth.draw_truth(prob)
+        h0 = fm.ForwardModel(prob, prec, sigma=1.0)
+        th = torch.tensor(tr.theta, dtype=torch.float32, device=dev)
+        m = h0.forward(th)
+        sigma = 0.01 * float(torch.linalg.norm(m, dim=-1).mean())
+        h0.close()
+        prob.sigma = sigma
+        h = fm.ForwardModel(prob, prec, sigma=sigma)
+        h.set_data((m + sigma * torch.tensor(tr.noise, dtype=torch.float32, device=dev)).contiguous())
+        mu, lam = synth.prior_for(prob, tr.theta)
+        h.set_prior(torch.tensor(mu, dtype=torch.float32, device=dev), torch.tensor(lam, dtype=torch.float32, device=dev))
+        nk = prob.n_mode_ra * prob.n_mode_dec
+        h.build_precond(th, 64 if nk % 64 == 0 else 1)
+        models.append(h)
+        qs.append(th.clone())
+        ps.append(torch.empty_like(th))
+        zs.append(torch.tensor(synth.random_vectors(h.n_params, K + W, 20250430 + k), dtype=torch.float32, device=dev))
+        f = h.contraction_info()["form"]
+        forms[f] = forms.get(f, 0) + 1
+    torch.cuda.synchronize()
+    batch = fm.Batch(models, qs, ps, args.traj)
+    n = len(models)
+    eps = [args.eps or 0.02] * n
+    us = np.random.default_rng(20250431).random((K + W, n))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def draw(i):
+        for k in range(n):
+            models[k].precond_apply(0, zs[k][i], out=ps[k])
+
+    for i in range(W):
+        flush.zero_()
+        draw(i)
+        batch.run(eps, us[i])
+    torch.cuda.synchronize()
+    for h in models:
+        h.sync_status()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    l0 = fm.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()
+        evs[i][0].record(st)
+        draw(W + i)
+        batch.run(eps, us[W + i])
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = fm.kernel_launches() - l0 + K * batch.kernels()
+    for h in models:
+        h.sync_status()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    # the same trajectories launched one chain after another (fm_leapfrog, no graph)
+    seq_ms = 0.0
+    for i in range(min(K, 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        draw(W + i)
+        for k in range(n):
+            models[k].leapfrog(qs[k], ps[k], eps[k], args.traj, float(us[W + i][k]), batch.h_out[k], batch.acc_out[k])
+        b.record(st)
+        torch.cuda.synchronize()
+        seq_ms += a.elapsed_time(b)
+    seq_ms /= min(K, 2)
+    evals = n * (args.traj + 1)
+    value = K * evals / (total_ms / 1000.0)
+    n_par = sum(h.n_params for h in models)
+    line = {
+        "metric": METRIC, "value": value, "unit": "chi2+grad evals/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "precision": prec, "data": "synthetic",
+        "config": {"workload": f"cfg2: {n} independent problems (antennas 7/19/37, 16/32/64 channels, 20 LSTs, "
+                               f"512..16384 modes per channel; {n_par} parameters in all; contraction forms {forms}); "
+                               f"one step = p = L z per chain + one graph launch of {n} {args.traj}-step trajectories "
+                               f"({evals} chi2+grad evals)",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU, concurrent graph branches"},
+        "leapfrog_steps_per_s": K * n * args.traj / (total_ms / 1000.0),
+        "sequential_launch_ms_per_step": seq_ms,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for h in models:
+        h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.config == "cfg2":
+        main_batch(args)
+        return
+    args.precision = args.precision or "fp16x3"
+    args.eps = args.eps or 0.1
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

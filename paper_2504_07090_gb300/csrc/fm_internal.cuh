@@ -170,6 +170,23 @@ extern long long g_launches;     // kernels launched by the library (relaxed cou
         FM_CK(cudaGetLastError());                                          \
     } while (0)
 
+// Lets kernel `fn` launch with up to the device's opt-in shared memory per block (less its
+// static shared memory).  The limit
+// is an attribute of the function, shared by every handle in the process, so it is raised to
+// the device maximum instead of being set to one handle's size (a smaller size set for one
+// handle would make another handle's launches, or graph nodes captured from them, fail).
+template <typename F>
+inline cudaError_t smem_opt_in(F fn)
+{
+    int dev = 0, mx = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);   // the kernel's static shared memory counts too
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+}
+
 #define FM_TRY(expr)                                                        \
     do {                                                                    \
         fm_status _s = (expr);                                              \

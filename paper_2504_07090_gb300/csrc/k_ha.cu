@@ -1098,7 +1098,7 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
     FM_CK_LAUNCH();
     k_ha_yprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, ys_hi, ys_lo);
     FM_CK_LAUNCH();
-    FM_CK(cudaFuncSetAttribute(k_vis_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    FM_CK(smem_opt_in(k_vis_ha<ET, X3>));
     FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
         k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(h, L, ys_hi, ys_lo, s.vpart, c.status);
         FM_CK_LAUNCH();
@@ -1128,7 +1128,7 @@ fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar,
     FM_CK_LAUNCH();
     int grid = sm_count();
     if (grid > c.F * c.D) grid = c.F * c.D;
-    FM_CK(cudaFuncSetAttribute(k_adj_ha<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    FM_CK(smem_opt_in(k_adj_ha<ET, X3>));
     FM_TRY(profiled(c, 1, st, [&]() -> fm_status {
         k_adj_ha<ET, X3><<<grid, HA_ADJ_THREADS, L.smem, st>>>(h, L, s.qimg, s.qscale, s.sp, xbar, c.status);
         FM_CK_LAUNCH();

@@ -508,8 +508,7 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
                 }
                 c.allocs.push_back(c.pc_linv);
             }
-            cudaFuncSetAttribute(k_pc_blk_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * 64 * 65 * sizeof(double)));
+            smem_opt_in(k_pc_blk_inv<R>);
             k_pc_blk_inv<R><<<(unsigned)nsky_blk, 64, 2 * 64 * 65 * sizeof(double), st>>>(Lf, (R *)c.pc_linv);
             if (ng > 0) {
                 if (!c.pc_ginv) {
@@ -813,7 +812,7 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
         const long long nb = c.n_sky / bs;
         const int ng = 2 * c.A * c.NG;
         const size_t smem = sizeof(R) * (size_t)LF_WARPS * (4096 + 64);
-        FM_CK(cudaFuncSetAttribute(k_lf_tri<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FM_CK(smem_opt_in(k_lf_tri<R>));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
         k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
                                                                 peps, out, kin_out ? part : nullptr);

@@ -521,8 +521,8 @@ fm_status modes_tc_setup(Ctx &c)
     k_md_image<<<256, 256>>>(c.g.leg64, c.D, c.N, 1, 0, z.Np, z.Dp, MD_CSCALE, s.legt_img);
     FM_CK_LAUNCH();
     const size_t sf = md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp), sa = md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np);
-    FM_CK(cudaFuncSetAttribute(k_modes_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-    FM_CK(cudaFuncSetAttribute(k_modes_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+    FM_CK(smem_opt_in(k_modes_fwd));
+    FM_CK(smem_opt_in(k_modes_adj));
     FM_CK(cudaDeviceSynchronize());
     s.on = true;
     return FM_OK;

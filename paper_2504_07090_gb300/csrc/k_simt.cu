@@ -373,7 +373,7 @@ static fm_status vis_simt_launch(Ctx &c, const R *x, R *vis, cudaStream_t st)
     size_t sm_r = (size_t)ngrp * ntile * 32 * sizeof(R);
     size_t smem = sm_e > sm_r ? sm_e : sm_r;
     if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
-    FM_CK(cudaFuncSetAttribute(k_vis_simt<R, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CK(smem_opt_in(k_vis_simt<R, TPT>));
     k_vis_simt<R, TPT><<<c.F * c.T, 256, smem, st>>>(c.g, x, vis, nbk, ntile, tpg, ngrp, pc);
     FM_CK_LAUNCH();
     return FM_OK;
@@ -630,7 +630,7 @@ fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart,
 {
     const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
     if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
-    FM_CK(cudaFuncSetAttribute(k_chi2_ft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CK(smem_opt_in(k_chi2_ft<R>));
     k_chi2_ft<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p, c.ha.U,
                                                 c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft);
     FM_CK_LAUNCH();
@@ -651,7 +651,7 @@ fm_status launch_chi2_mid(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, 
 {
     size_t smem = 256 * sizeof(double) + (c.A + 2 * (size_t)c.B) * 2 * sizeof(R);
     if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
-    FM_CK(cudaFuncSetAttribute(k_chi2_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CK(smem_opt_in(k_chi2_mid<R>));
     k_chi2_mid<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p);
     FM_CK_LAUNCH();
     return FM_OK;
@@ -732,7 +732,7 @@ fm_status launch_hvp_mid(Ctx &c, const R *vis, const R *dvis, const R *g, const 
 {
     size_t smem = (2 * (size_t)c.A + 4 * (size_t)c.B) * 2 * sizeof(R);
     if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
-    FM_CK(cudaFuncSetAttribute(k_hvp_mid<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CK(smem_opt_in(k_hvp_mid<R>));
     k_hvp_mid<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, dvis, (const R *)c.data, g, dg, full, omega, zpart);
     FM_CK_LAUNCH();
     return FM_OK;
@@ -796,7 +796,7 @@ fm_status launch_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st)
 {
     size_t smem = ((size_t)c.A * 128 + c.B) * 2 * sizeof(R);
     if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
-    FM_CK(cudaFuncSetAttribute(k_adj_simt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CK(smem_opt_in(k_adj_simt<R>));
     dim3 grid(cdiv(c.npix, 128), c.F);
     k_adj_simt<R><<<grid, 128, smem, st>>>(c.g, omega, xbar);
     FM_CK_LAUNCH();

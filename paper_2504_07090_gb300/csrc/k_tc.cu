@@ -765,8 +765,8 @@ template <int ET, bool X3>
 static fm_status vis_tc_launch(Ctx &c, const FwdLayout &L, int rch, int sub, size_t smem, int grid, const float *x,
                                float *vis, cudaStream_t st)
 {
-    if (c.A <= 48) FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else FM_CK(cudaFuncSetAttribute(k_vis_tc<ET, X3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (c.A <= 48) FM_CK(smem_opt_in(k_vis_tc<ET, X3, 3>));
+    else FM_CK(smem_opt_in(k_vis_tc<ET, X3, 4>));
     return profiled(c, 0, st, [&]() -> fm_status {
         if (c.A <= 48) k_vis_tc<ET, X3, 3><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
         else k_vis_tc<ET, X3, 4><<<grid, FWD_THREADS, smem, st>>>(c.g, L, rch, sub, x, c.tc_scale, vis);
@@ -834,7 +834,7 @@ template <int ET, bool X3>
 static fm_status adj_tc_launch(Ctx &c, const AdjLayout &L, size_t smem, int grid, const float *omega, float *wbar,
                                cudaStream_t st)
 {
-    FM_CK(cudaFuncSetAttribute(k_adj_tc<ET, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CK(smem_opt_in(k_adj_tc<ET, X3>));
     return profiled(c, 1, st, [&]() -> fm_status {
         k_adj_tc<ET, X3><<<grid, ADJ_THREADS, smem, st>>>(c.g, L, omega, wbar);
         FM_CK_LAUNCH();

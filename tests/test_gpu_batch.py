@@ -120,3 +120,19 @@ def test_batch_first_chain_matches_oracle(chains):
     assert rel_l2(qs[0].cpu().numpy() - q0, qw - q0) < 3e-4
     assert rel_l2(ps[0].cpu().numpy(), pw) < 1e-4
     b.close()
+
+
+def test_handles_of_different_sizes_coexist():
+    """A handle created after a larger one (smaller tiles, smaller shared-memory needs) must
+    not break the larger handle's launches: per-kernel launch limits are process-wide."""
+    import torch
+    big_p, big_o, big_th, *_ = make_case("mid")
+    small_p, *_ = make_case("ha37")
+    big = handle(big_p, "fp16x3")
+    v1 = big.forward(torch.tensor(big_th, dtype=torch.float32, device="cuda")).clone()
+    small = handle(small_p, "fp16x3")
+    v2 = big.forward(torch.tensor(big_th, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(v1, v2)
+    small.close()
+    big.close()
