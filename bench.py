@@ -412,7 +412,7 @@ def main():
     # of one ncu capture of these kernels at cfg1, fp16x3); None for other workloads
     traffic = None
     if args.config == "cfg1" and args.precision == "fp16x3" and info["form"] == "hour_angle":
-        traffic = (305.466368e6 + 4.553472e6) if fwd_dom else (296.288512e6 + 7.201024e6)
+        traffic = (305.315328e6 + 4.527104e6) if fwd_dom else (296.304384e6 + 7.579392e6)
     roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
