@@ -228,12 +228,13 @@ FM_API fm_status fm_sky_pixels_noalloc(int n_freq, int n_ra, int n_dec, int n_mo
  * out[4] (host int32):
  *   out[0]  0 = direct per-baseline SIMT sum (FP64 / FP32 precisions),
  *           1 = antenna form on the tensor cores (V = E W E^H per channel and LST),
- *           2 = hour-angle form on the tensor cores (drift scan with the LST step a whole
- *               number of RA pixels: one phasor table per channel, the sky as a Toeplitz
- *               operand, baselines with equal vectors up to sign computed once);
+ *           2 = hour-angle form on the tensor cores (drift scan with the LST step k / q RA
+ *               pixels, q <= 4: one phasor table per channel over hour-angle cells of
+ *               1 / q pixel, the sky as a Toeplitz operand, baselines with equal vectors up
+ *               to sign computed once);
  *   out[1]  distinct fringes computed per channel and LST (form 2: baseline groups;
  *           otherwise the number of baselines);
- *   out[2]  LST step in RA pixels (form 2), else 0;
+ *   out[2]  LST step in hour-angle cells, k (form 2), else 0;
  *   out[3]  hour-angle cells per declination row, padded (form 2), else 0.
  * The form is fixed at fm_create; the environment variable FM_HA=0 read there
  * disables form 2 and FM_HA_GROUPS=0 makes it compute every baseline separately. */

@@ -66,7 +66,8 @@ template <> struct Tab<float> {
 // LST t depends on n = t k - r + R - 1 only.
 struct HaState {
     bool on = false;
-    int k = 1;                 // LST step in RA pixels
+    int k = 1;                 // LST step in hour-angle cells
+    int q = 1;                 // hour-angle cells per RA pixel (the LST step is k / q pixels)
     int nh = 0, nhp = 0;       // hour-angle indices used, padded to a multiple of 128
     int nbc = 0;               // 64-index chunks per declination row (nhp / 64)
     int U = 0;                 // fringe groups: baselines with equal vectors up to sign

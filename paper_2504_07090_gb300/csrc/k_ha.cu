@@ -3,12 +3,13 @@
 // Eq. (rime_discrete) with K_ij = E_i conj(E_j) sums, for every baseline, channel and
 // LST, the beam- and solid-angle-weighted sky times the fringe over all pixels.  In a
 // drift scan (Sec. 2.1: the array points at a fixed topocentric direction) with LSTs
-// spaced by a whole number k of RA pixels, LST_t - RA_r = LST_0 - RA_{R-1} + (t k - r + R - 1) dRA,
+// spaced by k / q RA pixels (q <= 4), LST_t - RA_r = LST_0 - RA_{R-1} + (t k - r q + (R - 1) q) dRA / q,
 // so the direction of pixel (r, d) at LST t depends on the hour-angle index
-// n = t k - r + R - 1 only.  With one primary beam for all antennas (Sec. 3.4), baselines
+// n = t k - r q + (R - 1) q only (cells of dRA / q; q = 1 when the step is a whole number of
+// pixels).  With one primary beam for all antennas (Sec. 3.4), baselines
 // with equal vectors b = r_i - r_j (up to sign) also have equal (or conjugate) fringes.
 // For one channel and one fringe group u the visibility is then
-//   V_u(t) = sum_{d, n} P_u(n, d) x(t k + R - 1 - n, d),
+//   V_u(t) = sum_{d, n} P_u(n, d) x((t k + (R - 1) q - n) / q, d)   (terms with q | t k - n),
 //   P_u(n, d) = E_i(n, d) conj(E_j(n, d)),  E_i = sqrt(dOmega_d A(n, d)) exp(-2 pi i nu r_i . s(n, d) / c),
 // a real GEMM  D[rho][t] = sum_K A[rho][K] B[t][K],  rho = (u, Re | Im), K = (d, n),
 // whose A operand is generated tile by tile from a per-channel table of E (computed once
@@ -19,7 +20,7 @@
 //   xbar(r, d) = sum_t sum_rho P_rho(n(r, t), d) Q_rho(t),   Q_u = sum_{b in u} omega_b,
 // (conj(omega_b) for baselines reversed with respect to the group's representative): the
 // GEMM X[n][t] = sum_rho P^T[n][rho] Q[t][rho], then sums along the diagonals
-// n = t k + R - 1 - r, done with warp shuffles in the TMEM epilogue.
+// n = t k + (R - 1 - r) q, done in the epilogue.
 //
 // Both kernels are warp-specialised like the antenna-form kernels: 16 producer warps
 // fill 128-byte-swizzled operand tiles, one thread issues tcgen05.mma into TMEM, four
@@ -56,7 +57,7 @@ constexpr int HA_PGROUPS = 4;             // forward producer groups of HA_PROD_
 
 // kernel parameters, by value
 struct HaDev {
-    int F, D, T, R, A, U, k, nhp, nbc, npad, Ly, Jc, nchunk, nmt, nkq, J;
+    int F, D, T, R, A, U, k, q, nhp, nbc, npad, Ly, Jc, nchunk, nmt, nkq, J;   // k: LST step, q: cells per pixel
     long long Q;                          // forward work units: nmt * F * nchunk
     const float2 *E;                      // phasor table, cells paired (forward)
     const float2 *Ea;                     // the same, one (Re, Im) per cell (adjoint)
@@ -106,7 +107,7 @@ __device__ __forceinline__ void st32(uint8_t *p, uint32_t v) { *reinterpret_cast
 // at hour angle H(n) = LST_0 - (ra_min + (R - 1 - n + 1/2) dRA); zero below the horizon
 // and for n >= nh.  FP64 throughout, stored as FP32.
 struct HaTabArgs {
-    int F, D, R, A, A_all, nh, nhp, nbc;
+    int F, D, R, A, A_all, nh, nhp, nbc, q;
     int ant[64];                          // table entry -> antenna index
     double lst0, ra_min, dra, dec_min, ddec, lat, amp_scale;
     const double *kap64, *bcoef64, *domega64;
@@ -128,7 +129,7 @@ __global__ void k_ha_table(HaTabArgs a, int paired, float *__restrict__ E)
         const int n = 64 * nb + nl;
         float2 out = make_float2(0.f, 0.f);
         if (nl < 64 && n < a.nh && i < a.A - 1) {     // entry A - 1 is the zero antenna of padded pairs
-            const double H = a.lst0 - (a.ra_min + ((double)(a.R - 1 - n) + 0.5) * a.dra);
+            const double H = a.lst0 - (a.ra_min + ((double)((a.R - 1) * a.q - n) + 0.5 * a.q) * (a.dra / a.q));
             const double dec = a.dec_min + (d + 0.5) * a.ddec;
             double sd, cd, sh, ch, sl, cl;
             sincos(dec, &sd, &cd);
@@ -179,7 +180,9 @@ __global__ void k_ha_yprep(HaDev h, const float *__restrict__ x, const unsigned 
         float v[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int r = jp + q + h.R - h.nhp;
+            // element j holds pixel r when j - (nhp - 1 - (R - 1) qc) = r qc (qc cells per pixel)
+            const int rr = jp + q - (h.nhp - 1 - (h.R - 1) * h.q);
+            const int r = rr >= 0 && rr % h.q == 0 ? rr / h.q : -1;
             v[q] = (r >= 0 && r < h.R) ? sc * x[fd * h.R + r] : 0.f;
         }
         uint32_t hi, lo;
@@ -924,7 +927,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                 if (bar_or(3, 256, *abort_flag != 0)) { stop = true; break; }
                 tc_fence_after();
                 const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
-                const int c0 = h.R - 1 - 128 * mt;                           // n = t k + c0 - r
+                const int c0 = (h.R - 1) * h.q - 128 * mt;                   // n = t k + c0 - r q
                 if (t0 < h.T) {
                     // LST columns t >= T hold zeros (zero residual rows); those past npad are
                     // not loaded and set to zero here
@@ -948,7 +951,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                         // entry (q, nb0 + q k), q < 32; nothing of [0, 128) on the diagonal when
                         // nb0 + 31 k < 0 or nb0 >= 128, otherwise every entry lies in the row
                         // or its margins
-                        const int nb0 = t0 * h.k + c0 - et - 128 * j;
+                        const int nb0 = t0 * h.k + c0 - (et + 128 * j) * h.q;
                         if (nb0 + 31 * h.k < 0 || nb0 >= 128) continue;
                         const float *col = sk + pk + nb0;
                         const int st = skw + h.k;
@@ -1005,7 +1008,7 @@ HaDev make_dev(const Ctx &c)
 {
     const HaState &s = c.ha;
     HaDev h;
-    h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = s.nant + 1; h.U = s.U; h.k = s.k;
+    h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = s.nant + 1; h.U = s.U; h.k = s.k; h.q = s.q;
     h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.Ly = s.Ly; h.Jc = s.Jc;
     h.nchunk = c.D * s.nbc; h.nmt = s.nmt; h.nkq = s.nkq; h.J = s.J;
     h.Q = (long long)s.nmt * c.F * h.nchunk;
@@ -1163,17 +1166,24 @@ fm_status ha_setup(Ctx &c)
         if (atoi(e) == 0) return FM_OK;
     if (c.A < 2 || c.A > 64 || c.T > 64 || c.R > 512) return FM_OK;
     const double dra = (c.cfg.ra_max - c.cfg.ra_min) / c.R;
-    int k = 1;
+    // LST step = k / q RA pixels (q <= 4): hour-angle cells of 1 / q pixel, k cells per LST
+    int k = 1, q = 1;
     if (c.T > 1) {
         const double dl = c.lst[1] - c.lst[0];
         for (int t = 1; t < c.T; ++t)
             if (std::fabs(c.lst[t] - c.lst[0] - t * dl) > 1e-9 * dra) return FM_OK;
         const double kr = dl / dra;
-        k = (int)std::llround(kr);
-        if (k < 1 || k > 32 || std::fabs(kr - k) > 1e-9 * k) return FM_OK;
+        bool found = false;
+        for (q = 1; q <= 4 && !found; ++q) {
+            k = (int)std::llround(kr * q);
+            if (k >= 1 && k <= 32 && std::fabs(kr * q - k) <= 1e-9 * k) found = true;
+        }
+        --q;
+        if (!found) return FM_OK;
     }
     s.k = k;
-    s.nh = c.R + (c.T - 1) * k;
+    s.q = q;
+    s.nh = (c.R - 1) * q + (c.T - 1) * k + 1;
     s.nhp = (s.nh + 127) / 128 * 128;
     s.nbc = s.nhp / 64;
     s.npad = (c.T + 15) / 16 * 16;
@@ -1349,6 +1359,7 @@ fm_status ha_setup(Ctx &c)
     s.sp = (float)std::ldexp(1.0, e2);
     HaTabArgs a;
     a.F = c.F; a.D = c.D; a.R = c.R; a.A = s.nant + 1; a.A_all = c.A; a.nh = s.nh; a.nhp = s.nhp; a.nbc = s.nbc;
+    a.q = s.q;
     for (int q = 0; q < s.nant; ++q) a.ant[q] = s.ant_of[q];
     a.lst0 = c.lst[0]; a.ra_min = c.cfg.ra_min; a.dra = dra;
     a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D;

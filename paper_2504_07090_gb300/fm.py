@@ -260,7 +260,7 @@ class ForwardModel:
         """Form of the fringe contraction this handle runs (fm_contraction_info)."""
         out = (ctypes.c_int32 * 4)()
         _check(self.lib.fm_contraction_info(self.h, out), "fm_contraction_info")
-        return {"form": CONTRACTION_FORMS[int(out[0])], "fringes": int(out[1]), "lst_step_pixels": int(out[2]),
+        return {"form": CONTRACTION_FORMS[int(out[0])], "fringes": int(out[1]), "lst_step_cells": int(out[2]),
                 "hour_angle_cells": int(out[3])}
 
     def sync_status(self):

@@ -178,6 +178,14 @@ def config(name: str) -> Problem:
         # the cfg1 array (666 baselines, 63 distinct vectors) with the LST step equal to
         # one RA pixel (10 LSTs, 32 RA cells of 1.5 deg)
         return drift_scan_problem("ha37", 4, 3, 148e6, 152e6, 10, 7, 32, 8, 4, 20, 23)
+    if name == "hafrac2":
+        # LST step of 2.5 RA pixels (5 LSTs 3 deg apart, 40 RA cells of 1.2 deg): hour-angle
+        # cells of half a pixel, 5 cells per LST step; 7-antenna hexagon
+        return drift_scan_problem("hafrac2", 2, 4, 150e6, 156e6, 5, 9, 40, 8, 4, 20, 31)
+    if name == "hafrac4":
+        # LST step of 0.75 RA pixel (20 LSTs 0.75 deg apart, 48 RA cells of 1 deg, as in the
+        # uneven-problem batch): cells of a quarter pixel, 3 per LST step; 19-antenna hexagon
+        return drift_scan_problem("hafrac4", 3, 3, 150e6, 155e6, 20, 6, 48, 8, 4, 20, 37)
     if name == "harand":
         # 12 antennas at seeded random east/north/up offsets (66 distinct baselines: two
         # forward M-tiles, the second ragged), LST step equal to one RA pixel

@@ -1,11 +1,13 @@
-"""Hour-angle form of the tensor-core contraction (drift scans whose LST step is a whole
-number of RA pixels) against the FP64 oracle, element by element.
+"""Hour-angle form of the tensor-core contraction (drift scans whose LST step is k / q RA
+pixels, q <= 4) against the FP64 oracle, element by element.
 
 ha7: 7-antenna hexagon, LST step 2 pixels (9 baseline groups); ha37: the 37-antenna
 hexagon, step 1 (63 groups, 666 baselines); harand: 12 antennas at random 3-D offsets
-(66 groups: two forward M-tiles, three adjoint K chunks).  Each runs with baseline
-grouping on and off (FM_HA_GROUPS=0: every baseline its own group, 11 M-tiles and 21 K
-chunks for ha37), at the tolerances of the antenna form."""
+(66 groups: two forward M-tiles, three adjoint K chunks); hafrac2: step 2.5 pixels (cells of
+half a pixel, 5 per step); hafrac4: 19-antenna hexagon, step 0.75 pixel (cells of a quarter
+pixel, 3 per step).  Each runs with baseline grouping on and off (FM_HA_GROUPS=0: every
+baseline its own group, 11 M-tiles and 21 K chunks for ha37), at the tolerances of the
+antenna form."""
 import numpy as np
 import pytest
 
@@ -13,7 +15,9 @@ from gpu_cases import TOL_GRAD, TOL_VIS, as_complex, handle, make_case, perturbe
 
 pytestmark = pytest.mark.gpu
 
-CASES = {"ha7": (9, 21, 2), "ha37": (63, 666, 1), "harand": (66, 66, 1)}
+# groups, baselines, LST step in hour-angle cells k, cells per RA pixel q
+CASES = {"ha7": (9, 21, 2, 1), "ha37": (63, 666, 1, 1), "harand": (66, 66, 1, 1), "hafrac2": (9, 21, 5, 2),
+         "hafrac4": (30, 171, 3, 4)}
 PRECS = ["bf16x1", "bf16x3", "fp16x1", "fp16x3"]
 
 
@@ -40,11 +44,12 @@ def test_handle_runs_the_hour_angle_form(name, grouped, monkeypatch):
     _groups(monkeypatch, grouped)
     p, o, th, d, mu, lam = make_case(name)
     info = handle(p, "fp16x3").contraction_info()
-    ng, nb, k = CASES[name]
+    ng, nb, k, q = CASES[name]
     assert info["form"] == "hour_angle"
     assert info["fringes"] == (ng if grouped else nb)
-    assert info["lst_step_pixels"] == k
-    assert info["hour_angle_cells"] % 128 == 0 and info["hour_angle_cells"] >= p.n_ra + (p.n_lst - 1) * k
+    assert info["lst_step_cells"] == k
+    assert info["hour_angle_cells"] % 128 == 0
+    assert info["hour_angle_cells"] >= (p.n_ra - 1) * q + (p.n_lst - 1) * k + 1
 
 
 @pytest.mark.parametrize("name", list(CASES))
