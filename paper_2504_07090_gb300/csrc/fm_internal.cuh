@@ -75,8 +75,9 @@ struct HaState {
     int ant_of[64] = {};       // table entry -> antenna
     int nmt = 0;               // forward M-tiles, ceil(U / 64)
     int nkq = 0;               // adjoint K-chunks, ceil(U / 32)
-    int npad = 0;              // n_lst rounded up to 16 (MMA N)
+    int npad = 0;              // LSTs per pass (at most 64) rounded up to 16 (MMA N)
     int Jc = 0, Ly = 0;        // forward sky image chunks; sky-strip length (16-bit elements)
+    int Lyc = 0;               // strip elements one pass of at most 64 LSTs reads
     int grid = 0, J = 0;       // forward CTAs; most CTAs sharing one (M-tile, channel) segment
     float sp = 1.f;            // response scale 2^e (e even): the table holds sqrt(dOmega A) 2^(e/2)
     float2 *E = nullptr;       // [F][D][nbc][nant + 1][66] phasor table, cells paired (entry nant is zero; 2 pad cells)

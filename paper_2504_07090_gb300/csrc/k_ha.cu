@@ -52,12 +52,14 @@ constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulat
 constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
 constexpr int HA_EW = 66;                 // float2 entries per table row: 64 cells + 16 bytes of padding
 constexpr int HA_NSTAGE = 4;              // adjoint operand stages (A in TMEM, B in shared memory)
+constexpr int HA_TCHUNK = 64;             // LSTs per pass (the GEMM's N); more run as several passes
 constexpr int HA_NSTAGE_FWD = 5;          // forward A stages in TMEM
 constexpr int HA_PGROUPS = 4;             // forward producer groups of HA_PROD_WARPS / 4 warps, one unit each
 
 // kernel parameters, by value
 struct HaDev {
     int F, D, T, R, A, U, k, q, nhp, nbc, npad, Ly, Jc, nchunk, nmt, nkq, J;   // k: LST step, q: cells per pixel
+    int Tt, t0, Lyc;                      // all LSTs; this LST chunk: [t0, t0 + T); strip bytes / 2 it reads
     long long Q;                          // forward work units: nmt * F * nchunk
     const float2 *E;                      // phasor table, cells paired (forward)
     const float2 *Ea;                     // the same, one (Re, Im) per cell (adjoint)
@@ -320,7 +322,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
     const int G = gridDim.x;
     const long long q0 = range_lo(h.Q, G, blockIdx.x), q1 = range_lo(h.Q, G, blockIdx.x + 1);
     const uint32_t eb = (uint32_t)h.A * (uint32_t)(HA_EW * 8);    // E chunk bytes
-    const uint32_t sb = (uint32_t)h.Ly * 2u;                      // bytes of one strip part
+    const uint32_t sb = (uint32_t)h.Lyc * 2u;                     // bytes of one strip part (this chunk)
 
     if (warp < HA_PROD_WARPS) {
         // ------------------------------------------------------------ producers
@@ -363,9 +365,9 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
                 if (*abort_flag) goto done;
                 const uint32_t *strip = reinterpret_cast<const uint32_t *>(eslot + eb);
                 uint8_t *img = gbase + (size_t)(gb * NT) * L.img_bytes;
-                if (h.k == 1) build_image<1, NT>(strip, h.Ly, h.Jc, L.img_bytes, img, gt, 128);
-                else if (h.k == 2) build_image<2, NT>(strip, h.Ly, h.Jc, L.img_bytes, img, gt, 128);
-                else build_image_any<NT>(strip, h.Ly, h.Jc, h.k, L.img_bytes, img, gt, 128);
+                if (h.k == 1) build_image<1, NT>(strip, h.Lyc, h.Jc, L.img_bytes, img, gt, 128);
+                else if (h.k == 2) build_image<2, NT>(strip, h.Lyc, h.Jc, L.img_bytes, img, gt, 128);
+                else build_image_any<NT>(strip, h.Lyc, h.Jc, h.k, L.img_bytes, img, gt, 128);
             }
             {
                 const uint8_t *ei = eslot + (size_t)ij.x * (HA_EW * 8), *ej = eslot + (size_t)ij.y * (HA_EW * 8);
@@ -416,7 +418,8 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
                 const bool gstart = (q == q0) || (c == 0);
                 const float2 *src = h.E + (((size_t)f * h.D + d) * h.nbc + (h.nbc - 1 - c)) * h.A * HA_EW;
                 const uint32_t dst = base + L.e_off + (uint32_t)se * L.eslot_bytes;
-                const size_t row = ((size_t)f * h.D + d) * h.Ly;
+                // the chunk's LSTs start t0 k elements into the strip (t0 a multiple of 64)
+                const size_t row = ((size_t)f * h.D + d) * h.Ly + (size_t)h.t0 * h.k;
                 mbar_expect_tx(efull0 + 8 * se, eb + (gstart ? (uint32_t)NT * sb : 0u));
                 bulk_g2s(dst, src, eb, efull0 + 8 * se);
                 if (gstart) {
@@ -584,7 +587,7 @@ __global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float 
         const int row = 2 * (u & 63);
         const float sgn = (code & 1) ? -1.f : 1.f;
         for (int tl = 0; tl < tn; ++tl) {
-            const size_t e = ((size_t)f * h.T + t0 + tl) * B + b;
+            const size_t e = ((size_t)f * h.Tt + h.t0 + t0 + tl) * B + b;
             float2 v = make_float2(sv[row][tl] * sc, sgn * sv[row + 1][tl] * sc);
             if (dc) {
                 const float2 u2 = reinterpret_cast<const float2 *>(U)[e];
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(256) k_ha_qsum(HaDev h, int B, const float *__
     // sums the members of its groups, and the CTA records its maximum
     extern __shared__ float som[];                  // [2 B]
     __shared__ float red[256];
-    const int ft = blockIdx.x, f = ft / h.T;
+    const int ft = blockIdx.x, f = ft / h.Tt;
     const float *om = omega + (size_t)ft * B * 2;
     for (int e = threadIdx.x; e < 2 * B; e += blockDim.x) som[e] = om[e];
     __syncthreads();
@@ -652,7 +655,8 @@ __global__ void __launch_bounds__(256) k_ha_qsum(HaDev h, int B, const float *__
 }
 
 // One CTA per (channel, K chunk): the swizzled B tile [npad rows t][64 rho] of the
-// adjoint, hi then (x3) lo, ready for one bulk copy.
+// adjoint for the LSTs t0 + t, t < T, of the current chunk, hi then (x3) lo, ready for one
+// bulk copy; the power-of-two scale is the chunk's.
 template <int ET, bool X3>
 __global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const float *__restrict__ qmax_ft,
                           float *__restrict__ qscale, uint8_t *__restrict__ qimg)
@@ -662,7 +666,7 @@ __global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const float *_
     __shared__ float smx;
     if (threadIdx.x < 32) {
         float m = 0.f;
-        for (int t = threadIdx.x; t < h.T; t += 32) m = fmaxf(m, qmax_ft[(size_t)f * h.T + t]);
+        for (int t = threadIdx.x; t < h.T; t += 32) m = fmaxf(m, qmax_ft[(size_t)f * h.Tt + h.t0 + t]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (threadIdx.x == 0) smx = m;
@@ -680,7 +684,7 @@ __global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const float *_
             const int u = 32 * kq + 4 * ch + q;
             float re = 0.f, im = 0.f;
             if (t < h.T && u < h.U) {
-                const float *p = q32 + (((size_t)f * h.T + t) * h.U + u) * 2;
+                const float *p = q32 + (((size_t)f * h.Tt + h.t0 + t) * h.U + u) * 2;
                 re = p[0] * sc;
                 im = p[1] * sc;
             }
@@ -927,7 +931,7 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                 if (bar_or(3, 256, *abort_flag != 0)) { stop = true; break; }
                 tc_fence_after();
                 const uint32_t taddr = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(qa * h.npad);
-                const int c0 = (h.R - 1) * h.q - 128 * mt;                   // n = t k + c0 - r q
+                const int c0 = (h.R - 1) * h.q - 128 * mt + h.t0 * h.k;      // n = t k + c0 - r q (t in the chunk)
                 if (t0 < h.T) {
                     // LST columns t >= T hold zeros (zero residual rows); those past npad are
                     // not loaded and set to zero here
@@ -982,7 +986,11 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                 float *xo = xbar + ((size_t)f * h.D + d) * h.R;
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (et + 128 * j < h.R) xo[et + 128 * j] = (xr[j] + xs1[j * 128 + et]) * sc;
+                    if (et + 128 * j < h.R) {
+                        // later LST chunks add to the earlier ones' sum (stream order)
+                        const float v = (xr[j] + xs1[j * 128 + et]) * sc;
+                        xo[et + 128 * j] = h.t0 > 0 ? xo[et + 128 * j] + v : v;
+                    }
             }
             bar_or(3, 256, false);
         }
@@ -1010,6 +1018,7 @@ HaDev make_dev(const Ctx &c)
     HaDev h;
     h.F = c.F; h.D = c.D; h.T = c.T; h.R = c.R; h.A = s.nant + 1; h.U = s.U; h.k = s.k; h.q = s.q;
     h.nhp = s.nhp; h.nbc = s.nbc; h.npad = s.npad; h.Ly = s.Ly; h.Jc = s.Jc;
+    h.Tt = c.T; h.t0 = 0; h.Lyc = s.Lyc; h.T = c.T < HA_TCHUNK ? c.T : HA_TCHUNK;
     h.nchunk = c.D * s.nbc; h.nmt = s.nmt; h.nkq = s.nkq; h.J = s.J;
     h.Q = (long long)s.nmt * c.F * h.nchunk;
     h.E = s.E; h.Ea = s.Ea; h.uij = s.uij;
@@ -1046,7 +1055,7 @@ bool make_layout_fwd(const Ctx &c, bool x3, HaLayout &L)
     L.b_bytes = 0;
     L.stage_bytes = 0;
     L.img_bytes = (uint32_t)c.ha.Jc * 128u;
-    L.eslot_bytes = (uint32_t)(c.ha.nant + 1) * (uint32_t)(HA_EW * 8) + (uint32_t)nt * (uint32_t)c.ha.Ly * 2u;
+    L.eslot_bytes = (uint32_t)(c.ha.nant + 1) * (uint32_t)(HA_EW * 8) + (uint32_t)nt * (uint32_t)c.ha.Lyc * 2u;
     L.e_off = 2u * (uint32_t)nt * L.img_bytes;
     const size_t bars = 16 * (size_t)L.nstage + 48 + 16;
     L.neslot = 8;
@@ -1102,14 +1111,20 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
     k_ha_yprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, ys_hi, ys_lo);
     FM_CK_LAUNCH();
     FM_CK(smem_opt_in(k_vis_ha<ET, X3>));
-    FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
-        k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(h, L, ys_hi, ys_lo, s.vpart, c.status);
+    // one pass per chunk of at most HA_TCHUNK LSTs (the partial sums are reused)
+    for (int t0 = 0; t0 < c.T; t0 += HA_TCHUNK) {
+        HaDev hc = h;
+        hc.t0 = t0;
+        hc.T = c.T - t0 < HA_TCHUNK ? c.T - t0 : HA_TCHUNK;
+        FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
+            k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(hc, L, ys_hi, ys_lo, s.vpart, c.status);
+            FM_CK_LAUNCH();
+            return FM_OK;
+        }));
+        k_ha_vfinish<<<dim3(s.nmt * c.F, cdiv(hc.T, HA_VF_T)), 256, 0, st>>>(hc, c.B, s.vpart, s.ncontrib, s.bmap,
+                                                                             s.xmax, s.sp, dc, dcs, c.dc_u, vis);
         FM_CK_LAUNCH();
-        return FM_OK;
-    }));
-    k_ha_vfinish<<<dim3(s.nmt * c.F, cdiv(c.T, HA_VF_T)), 256, 0, st>>>(h, c.B, s.vpart, s.ncontrib, s.bmap,
-                                                                        s.xmax, s.sp, dc, dcs, c.dc_u, vis);
-    FM_CK_LAUNCH();
+    }
     return FM_OK;
 }
 
@@ -1127,16 +1142,22 @@ fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar,
                                                                             s.qmax_ft);
         FM_CK_LAUNCH();
     }
-    k_ha_qimg<ET, X3><<<c.F * s.nkq, 256, 0, st>>>(h, s.q32, s.qmax_ft, s.qscale, s.qimg);
-    FM_CK_LAUNCH();
     int grid = sm_count();
     if (grid > c.F * c.D) grid = c.F * c.D;
     FM_CK(smem_opt_in(k_adj_ha<ET, X3>));
-    FM_TRY(profiled(c, 1, st, [&]() -> fm_status {
-        k_adj_ha<ET, X3><<<grid, HA_ADJ_THREADS, L.smem, st>>>(h, L, s.qimg, s.qscale, s.sp, xbar, c.status);
+    // one pass per chunk of at most HA_TCHUNK LSTs; passes after the first add to xbar
+    for (int t0 = 0; t0 < c.T; t0 += HA_TCHUNK) {
+        HaDev hc = h;
+        hc.t0 = t0;
+        hc.T = c.T - t0 < HA_TCHUNK ? c.T - t0 : HA_TCHUNK;
+        k_ha_qimg<ET, X3><<<c.F * s.nkq, 256, 0, st>>>(hc, s.q32, s.qmax_ft, s.qscale, s.qimg);
         FM_CK_LAUNCH();
-        return FM_OK;
-    }));
+        FM_TRY(profiled(c, 1, st, [&]() -> fm_status {
+            k_adj_ha<ET, X3><<<grid, HA_ADJ_THREADS, L.smem, st>>>(hc, L, s.qimg, s.qscale, s.sp, xbar, c.status);
+            FM_CK_LAUNCH();
+            return FM_OK;
+        }));
+    }
     return FM_OK;
 }
 
@@ -1164,7 +1185,7 @@ fm_status ha_setup(Ctx &c)
     if (c.prec < FM_PREC_BF16X1) return FM_OK;
     if (const char *e = getenv("FM_HA"))
         if (atoi(e) == 0) return FM_OK;
-    if (c.A < 2 || c.A > 64 || c.T > 64 || c.R > 512) return FM_OK;
+    if (c.A < 2 || c.R > 512) return FM_OK;
     const double dra = (c.cfg.ra_max - c.cfg.ra_min) / c.R;
     // LST step = k / q RA pixels (q <= 4): hour-angle cells of 1 / q pixel, k cells per LST
     int k = 1, q = 1;
@@ -1186,12 +1207,14 @@ fm_status ha_setup(Ctx &c)
     s.nh = (c.R - 1) * q + (c.T - 1) * k + 1;
     s.nhp = (s.nh + 127) / 128 * 128;
     s.nbc = s.nhp / 64;
-    s.npad = (c.T + 15) / 16 * 16;
+    const int tc = c.T < HA_TCHUNK ? c.T : HA_TCHUNK;       // LSTs per pass
+    s.npad = (tc + 15) / 16 * 16;
     if (s.npad < 16) s.npad = 16;
     // forward image: chunks j < Jc of 8 cells; the sky strip holds the Ly >= 8 Jc + 7 k + 8
     // elements the image reads (a multiple of 8, so strips stay 16-byte aligned)
     s.Jc = 8 * s.nbc + (s.npad / 8 - 1) * k;
-    s.Ly = 8 * s.Jc + 8 * k + 8;
+    s.Lyc = 8 * s.Jc + 8 * k + 8;
+    s.Ly = s.Lyc + ((c.T - 1) / HA_TCHUNK) * HA_TCHUNK * k;   // later passes start t0 k further in
 
     // fringe groups: equal baseline vectors (to 1 nm) up to sign
     bool group = true;
@@ -1270,6 +1293,10 @@ fm_status ha_setup(Ctx &c)
         }
     }
     std::vector<int> pos(c.A, -1);
+    // the table holds at most 63 antennas plus its zero entry
+    int n_in = 0;
+    for (int a = 0; a < c.A; ++a) n_in += in_s[a] ? 1 : 0;
+    if (n_in > 63) return FM_OK;
     s.nant = 0;
     for (int a = 0; a < c.A; ++a)
         if (in_s[a]) { pos[a] = s.nant; s.ant_of[s.nant] = a; ++s.nant; }

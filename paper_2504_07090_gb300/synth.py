@@ -186,6 +186,10 @@ def config(name: str) -> Problem:
         # LST step of 0.75 RA pixel (20 LSTs 0.75 deg apart, 48 RA cells of 1 deg, as in the
         # uneven-problem batch): cells of a quarter pixel, 3 per LST step; 19-antenna hexagon
         return drift_scan_problem("hafrac4", 3, 3, 150e6, 155e6, 20, 6, 48, 8, 4, 20, 37)
+    if name == "hachunk":
+        # 91-antenna hexagon (more antennas than the phasor table's 64 entries; its covering
+        # subset fits), 70 LSTs (two passes of at most 64), LST step of half an RA pixel
+        return drift_scan_problem("hachunk", 6, 2, 150e6, 153e6, 70, 4, 112, 16, 4, 20, 41)
     if name == "harand":
         # 12 antennas at seeded random east/north/up offsets (66 distinct baselines: two
         # forward M-tiles, the second ragged), LST step equal to one RA pixel
