@@ -366,13 +366,18 @@ static fm_status vis_simt_launch(Ctx &c, const R *x, R *vis, cudaStream_t st)
 {
     int nbk = (c.A + 3) / 4, ntile = nbk * (nbk + 1) / 2;
     int tpg = ((cdiv(ntile, TPT) + 31) / 32) * 32;
-    if (tpg > 256) return FM_ERR_UNSUPPORTED;
+    if (tpg > 256) { set_error("direct forward: %d antennas exceed the tile layout", c.A); return FM_ERR_UNSUPPORTED; }
     int ngrp = 256 / tpg;
+    // pixels staged per round: 64, halved while the phasor tiles exceed shared memory
     int pc = 64;
-    size_t sm_e = 2 * (size_t)pc * c.g.apad * 2 * sizeof(R) + pc * sizeof(R);
-    size_t sm_r = (size_t)ngrp * ntile * 32 * sizeof(R);
-    size_t smem = sm_e > sm_r ? sm_e : sm_r;
-    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    size_t sm_e = 0, smem = 0;
+    const size_t sm_r = (size_t)ngrp * ntile * 32 * sizeof(R);
+    for (;; pc /= 2) {
+        sm_e = 2 * (size_t)pc * c.g.apad * 2 * sizeof(R) + pc * sizeof(R);
+        smem = sm_e > sm_r ? sm_e : sm_r;
+        if (smem <= 227 * 1024 || pc <= 8) break;
+    }
+    if (smem > 227 * 1024) { set_error("direct forward: tiles exceed shared memory"); return FM_ERR_UNSUPPORTED; }
     FM_CK(smem_opt_in(k_vis_simt<R, TPT>));
     k_vis_simt<R, TPT><<<c.F * c.T, 256, smem, st>>>(c.g, x, vis, nbk, ntile, tpg, ngrp, pc);
     FM_CK_LAUNCH();
