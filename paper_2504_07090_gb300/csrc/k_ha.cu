@@ -13,8 +13,9 @@
 //   P_u(n, d) = E_i(n, d) conj(E_j(n, d)),  E_i = sqrt(dOmega_d A(n, d)) exp(-2 pi i nu r_i . s(n, d) / c),
 // a real GEMM  D[rho][t] = sum_K A[rho][K] B[t][K],  rho = (u, Re | Im), K = (d, n),
 // whose A operand is generated tile by tile from a per-channel table of E (computed once
-// per handle with FP64 phases) and whose B operand is the Toeplitz matrix of the sky,
-// built per tile from a reversed copy of each declination row.
+// per handle with FP64 phases) and whose B operand is the Toeplitz matrix of the sky (a
+// Hankel matrix once the cells are taken in reverse order), read by the tensor core from
+// one shared-memory image per (channel, declination).
 //
 // The adjoint (the pixel gradient through the same response) is
 //   xbar(r, d) = sum_t sum_rho P_rho(n(r, t), d) Q_rho(t),   Q_u = sum_{b in u} omega_b,
@@ -22,10 +23,11 @@
 // GEMM X[n][t] = sum_rho P^T[n][rho] Q[t][rho], then sums along the diagonals
 // n = t k + (R - 1 - r) q, done in the epilogue.
 //
-// Both kernels are warp-specialised like the antenna-form kernels: 16 producer warps
-// fill 128-byte-swizzled operand tiles, one thread issues tcgen05.mma into TMEM, four
-// warps drain the accumulators and one thread issues bulk copies.  Every wait is
-// bounded; a timeout records FM_ERR_TIMEOUT and the CTA winds down in order.
+// Both kernels are warp-specialised: 16 producer warps write the P operand into TMEM,
+// one thread issues tcgen05.mma (A from TMEM, B from shared memory) into TMEM
+// accumulators, epilogue warps drain them, and single threads issue bulk copies.  LSTs
+// beyond 64 run as further passes over the same table.  Every wait is bounded; a timeout
+// records FM_ERR_TIMEOUT and the CTA winds down in order.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -268,7 +270,7 @@ __device__ __forceinline__ void build_image_any(const uint32_t *strip, int Ly, i
 // CTA g takes the contiguous range [Q g / G, Q (g+1) / G).  A segment is the part of one
 // (M-tile, channel) pair inside a CTA's range; its partial sum goes to
 // vpart[segment][j] with j the CTA's rank among the segment's contributors.
-//   load warp (21): per unit, the E chunk [A][HA_EW] (and, at the first unit of a
+//   load warp (21): per unit, the E chunk [A][HA_EW] (cells paired) (and, at the first unit of a
 //     (channel, declination) group, the two sky strips) by bulk copies;  efull[se] (tx)
 //   producers (warps 0-15): four groups of four warps take turns by unit; warp w fills TMEM
 //     lanes 32 (w & 3) .. +31 of stage s over all 64 cells (hi, lo), and at the start of a
@@ -705,8 +707,8 @@ __global__ void k_ha_qimg(HaDev h, const float *__restrict__ q32, const float *_
 //     8 quarter .. +7 of row n into TMEM lane n (A operand of stage s: 8 columns hi, 8 lo);
 //     then full[s]
 //   MMA warp (20): D[n][t] of the M-tile into TMEM set (M-tile count & 1);  accf[q]
-//   epilogue (16-19): the diagonal sums over the M-tiles of the item (see below), one
-//     output row xbar(., d) per item.
+//   epilogue (16-19 and 23-26, one set per 32-LST half): the diagonal sums over the
+//     M-tiles of the item (see below), one output row xbar(., d) per item.
 template <int ET, bool X3>
 __global__ void __launch_bounds__(HA_ADJ_THREADS, 1)
 k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__restrict__ qscale, float sp,
