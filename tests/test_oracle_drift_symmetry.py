@@ -2,7 +2,8 @@
 relies on, checked on the oracle's own geometry and visibilities (no GPU).
 
 1. With LSTs spaced by k RA pixels, pixel (r, d) at LST t points where pixel (r - k, d)
-   pointed at LST t - 1 (the direction depends on the hour angle LST - RA only, Sec. 2.1).
+   pointed at LST t - 1 (the direction depends on the hour angle LST - RA only, Sec. 2.1);
+   with a spacing of k / q pixels the same holds for a shift of q LSTs and k pixels.
 2. With one beam for all antennas (Sec. 3.4), baselines with equal vectors have equal
    visibilities and reversed vectors give the complex conjugate (Eq. rime_discrete)."""
 import numpy as np
@@ -24,6 +25,22 @@ def test_directions_shift_by_k_pixels_per_lst(name, k):
     assert np.max(np.abs(a - b)) < 1e-12
     # and not for a shift by a different number of pixels
     assert np.max(np.abs(s[1:, :, k + 1:, :] - s[:-1, :, : o.R - k - 1, :])) > 1e-4
+
+
+@pytest.mark.parametrize("name,k,q", [("hafrac2", 5, 2), ("hafrac4", 3, 4), ("hachunk", 1, 2)])
+def test_directions_shift_by_k_pixels_per_q_lsts(name, k, q):
+    """LST step of k / q pixels: pixel (r, d) at LST t points where pixel (r - k, d) pointed at
+    LST t - q (the hour angle t k / q - r is unchanged), and no shift by fewer LSTs does so."""
+    p = synth.config(name)
+    dra = (p.ra_max - p.ra_min) / p.n_ra
+    assert abs((p.lst_rad[1] - p.lst_rad[0]) / dra * q - k) < 1e-9
+    o = oracle.Oracle(p)
+    s = o.s.reshape(o.T, o.D, o.R, 3)
+    assert np.max(np.abs(s[q:, :, k:, :] - s[:-q, :, :-k, :])) < 1e-12
+    for tq in range(1, q):
+        # a shift of tq < q LSTs moves the hour angle by tq k / q pixels, not a whole number
+        kk = (tq * k) // q
+        assert np.max(np.abs(s[tq:, :, kk:, :] - s[:-tq, :, : o.R - kk, :])) > 1e-4
 
 
 def _groups(ant):
