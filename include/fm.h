@@ -240,6 +240,14 @@ FM_API fm_status fm_sky_pixels_noalloc(int n_freq, int n_ra, int n_dec, int n_mo
  * disables form 2 and FM_HA_GROUPS=0 makes it compute every baseline separately. */
 FM_API fm_status fm_contraction_info(fm_handle h, int32_t *out);
 
+/* Diagnostic of the device-side failure path (no counterpart in the paper): one CTA waits,
+ * with the bounded mbarrier wait of the tensor-core kernels and a limit of limit_cycles SM
+ * clocks (1 .. the kernels' own limit of 4e9), on a barrier that nothing arrives at, then
+ * writes FM_ERR_TIMEOUT (or FM_OK had the wait completed) to dev_status_out (device int[1])
+ * and returns; nothing faults or hangs and the context stays usable.  Used by the tests of
+ * the failure handling. */
+FM_API fm_status fm_diag_bounded_wait(int64_t limit_cycles, int *dev_status_out, fm_stream stream);
+
 /* Kernels launched by this library in this process so far (all handles). */
 FM_API int64_t fm_kernel_launches(void);
 

@@ -32,7 +32,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // SLEEP_NS > 0 backs off between polls (for roles that mostly wait: the MMA issuer,
 // the bulk-copy issuer and the epilogue), keeping the issue slots for the producers
 template <int SLEEP_NS = 0>
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                             long long limit = WAIT_CYCLES)
 {
     long long t0 = clock64();
     while (true) {
@@ -46,7 +47,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
             : "memory");
         if (ok) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }

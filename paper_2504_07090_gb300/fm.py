@@ -32,7 +32,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_dat
            "fm_precond_size", "fm_leapfrog", "fm_precond_apply", "fm_set_profiling", "fm_get_profile",
            "fm_contraction_info", "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status",
            "fm_last_error", "fm_create_batch", "fm_batch_create", "fm_batch_leapfrog", "fm_batch_kernels",
-           "fm_batch_destroy"]
+           "fm_batch_destroy", "fm_diag_bounded_wait"]
 CONTRACTION_FORMS = {0: "direct", 1: "antenna", 2: "hour_angle"}
 
 
@@ -100,11 +100,19 @@ def load(path: str = LIB_PATH):
     L.fm_batch_leapfrog.argtypes = [vp, POINTER(c_double), POINTER(c_double), vp]
     L.fm_batch_kernels.argtypes = [vp, POINTER(c_int64)]
     L.fm_batch_destroy.argtypes = [vp]
+    L.fm_diag_bounded_wait.argtypes = [c_int64, vp, vp]
     for name in EXPORTS:
         if name not in ("fm_num_params", "fm_num_vis", "fm_precond_size", "fm_last_error", "fm_kernel_launches"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
+
+
+def diag_bounded_wait(limit_cycles: int) -> int:
+    """Run the bounded-wait diagnostic (fm_diag_bounded_wait); returns the device status."""
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(load().fm_diag_bounded_wait(int(limit_cycles), _ptr(out), _stream()), "fm_diag_bounded_wait")
+    return int(out.item())
 
 
 def kernel_launches() -> int:

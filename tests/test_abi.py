@@ -55,3 +55,23 @@ def test_invalid_config_rejected_before_device_work(lib):
     assert lib.fm_forward(None, None, None, None) == fm.FM_ERR_INVALID_ARG
     assert lib.fm_num_params(None) == -1
     assert lib.fm_destroy(None) == fm.FM_OK
+
+
+def test_batch_and_diagnostic_arguments_rejected_before_device_work(lib):
+    import ctypes
+    from paper_2504_07090_gb300 import fm
+    out = ctypes.c_void_p()
+    # batches: no handles, a NULL handle, n_steps out of range
+    assert lib.fm_batch_create(0, None, None, None, None, None, 20, ctypes.byref(out)) == fm.FM_ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.fm_batch_create(1, arr, arr, arr, arr, arr, 20, ctypes.byref(out)) == fm.FM_ERR_INVALID_ARG
+    assert lib.fm_batch_create(1, arr, arr, arr, arr, arr, 0, ctypes.byref(out)) == fm.FM_ERR_INVALID_ARG
+    assert out.value is None
+    assert lib.fm_batch_leapfrog(None, None, None, None) == fm.FM_ERR_INVALID_ARG
+    assert lib.fm_batch_destroy(None) == fm.FM_OK
+    assert lib.fm_create_batch(0, None, None) == fm.FM_ERR_INVALID_ARG
+    # the bounded-wait diagnostic: status pointer required, limit within the kernels' own
+    dummy = ctypes.c_int(0)
+    assert lib.fm_diag_bounded_wait(1000, None, None) == fm.FM_ERR_INVALID_ARG
+    assert lib.fm_diag_bounded_wait(0, ctypes.byref(dummy), None) == fm.FM_ERR_INVALID_ARG
+    assert lib.fm_diag_bounded_wait(5_000_000_000, ctypes.byref(dummy), None) == fm.FM_ERR_INVALID_ARG
