@@ -412,7 +412,7 @@ def main():
     # of one ncu capture of these kernels at cfg1, fp16x3); None for other workloads
     traffic = None
     if args.config == "cfg1" and args.precision == "fp16x3" and info["form"] == "hour_angle":
-        traffic = (305.315328e6 + 4.527104e6) if fwd_dom else (296.304384e6 + 7.579392e6)
+        traffic = (305.316352e6 + 4.327936e6) if fwd_dom else (296.293888e6 + 7.27936e6)
     roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
