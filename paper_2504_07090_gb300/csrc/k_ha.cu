@@ -186,7 +186,7 @@ __global__ void k_ha_yprep(HaDev h, const float *__restrict__ x, const unsigned 
         for (int q = 0; q < 2; ++q) {
             // element j holds pixel r when j - (nhp - 1 - (R - 1) qc) = r qc (qc cells per pixel)
             const int rr = jp + q - (h.nhp - 1 - (h.R - 1) * h.q);
-            const int r = rr >= 0 && rr % h.q == 0 ? rr / h.q : -1;
+            const int r = h.q == 1 ? rr : (rr >= 0 && rr % h.q == 0 ? rr / h.q : -1);
             v[q] = (r >= 0 && r < h.R) ? sc * x[fd * h.R + r] : 0.f;
         }
         uint32_t hi, lo;

@@ -553,12 +553,13 @@ __global__ void k_axpy(long long n, double alpha, const R *__restrict__ x, R *__
         y[k] += (R)alpha * x[k];
 }
 
-// momentum half-kick p -= (eps / 2) g with eps = prm[0] read on the device, so that a
-// captured trajectory can be replayed with a new step size
+// momentum kick p -= (frac eps) g with eps = prm[0] read on the device, so that a captured
+// trajectory can be replayed with a new step size
 template <typename R>
-__global__ void k_kick(long long n, const double *__restrict__ prm, const R *__restrict__ g, R *__restrict__ p)
+__global__ void k_kick(long long n, const double *__restrict__ prm, double frac, const R *__restrict__ g,
+                       R *__restrict__ p)
 {
-    const R a = (R)(-0.5 * prm[0]);
+    const R a = (R)(-frac * prm[0]);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         p[k] += a * g[k];
 }
@@ -925,12 +926,14 @@ fm_status run_leapfrog(Ctx &c, R *q, R *p, const double *prm, int n_steps, doubl
     FM_CK_LAUNCH();
     FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 0, g, st));
     FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, nullptr, sc + 2, st));
+    // the closing half-kick of a step and the opening one of the next use the same gradient
+    // and run as one full kick
+    k_kick<R><<<512, 256, 0, st>>>(n, prm, 0.5, g, p);
+    FM_CK_LAUNCH();
     for (int s = 0; s < n_steps; ++s) {
-        k_kick<R><<<512, 256, 0, st>>>(n, prm, g, p);
-        FM_CK_LAUNCH();
         FM_TRY(lf_kinetic_drift<R>(c, p, q, prm, nullptr, st));
         FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 1, g, st));
-        k_kick<R><<<512, 256, 0, st>>>(n, prm, g, p);
+        k_kick<R><<<512, 256, 0, st>>>(n, prm, s + 1 < n_steps ? 1.0 : 0.5, g, p);
         FM_CK_LAUNCH();
     }
     if (n_steps == 0) {
