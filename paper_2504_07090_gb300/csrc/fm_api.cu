@@ -281,7 +281,8 @@ template fm_status vis_of_modes<float>(Ctx &, const float *, float *, float *, c
 template fm_status vis_of_modes<double>(Ctx &, const double *, double *, double *, cudaStream_t);
 
 template <typename R>
-fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out, R *grad, cudaStream_t st)
+fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out, R *grad, cudaStream_t st,
+                        R *kick_p, const double *kick_prm, double kick_frac)
 {
     if (!c.have_data) { set_error("fm_set_data has not been called"); return FM_ERR_STATE; }
     R *x = (R *)c.x, *vis = (R *)c.vis, *om = (R *)c.omega, *zp = (R *)c.zpart, *gn = (R *)c.gains;
@@ -293,7 +294,8 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
     FM_TRY(run_adjoint<R>(c, om, (R *)c.xbar, st, groups));
     FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, grad, st));
     FM_TRY(launch_gain_reduce_chan<R>(c, zp, grad + c.n_sky, st));
-    return launch_prior_and_total<R>(c, theta, grad, c.chi2p, c.F * c.T, chi2_out, u_out, st);
+    return launch_prior_and_total<R>(c, theta, grad, c.chi2p, c.F * c.T, chi2_out, u_out, st, kick_p, kick_prm,
+                                     kick_frac);
 }
 
 template <typename R>
@@ -313,8 +315,10 @@ static fm_status run_hvp(Ctx &c, const R *theta, const R *v, R *hv, int full, cu
     return launch_prior_hvp<R>(c, v, hv, st);
 }
 
-template fm_status run_chi2_grad<float>(Ctx &, const float *, double *, double *, float *, cudaStream_t);
-template fm_status run_chi2_grad<double>(Ctx &, const double *, double *, double *, double *, cudaStream_t);
+template fm_status run_chi2_grad<float>(Ctx &, const float *, double *, double *, float *, cudaStream_t, float *,
+                                        const double *, double);
+template fm_status run_chi2_grad<double>(Ctx &, const double *, double *, double *, double *, cudaStream_t, double *,
+                                         const double *, double);
 
 }  // namespace fm
 

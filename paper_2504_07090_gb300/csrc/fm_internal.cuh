@@ -256,8 +256,10 @@ fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart,
 template <typename R>
 fm_status launch_gain_reduce_chan(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
 template <typename R>
+// with kick_p != NULL also the momentum kick kick_p -= kick_frac eps grad, eps = kick_prm[0] (device)
 fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, int nchi2, double *chi2_out,
-                                 double *u_out, cudaStream_t st);
+                                 double *u_out, cudaStream_t st, R *kick_p = nullptr,
+                                 const double *kick_prm = nullptr, double kick_frac = 0.0);
 template <typename R>
 fm_status launch_prior_hvp(Ctx &c, const R *v, R *hv, cudaStream_t st);
 template <typename R>
@@ -301,7 +303,10 @@ fm_status run_leapfrog(Ctx &c, R *q, R *p, const double *prm, int n_steps, doubl
                        cudaStream_t st);
 
 // gradient / hvp drivers (fm_api.cu)
+// with kick_p != NULL the evaluation ends with the leapfrog kick kick_p -= kick_frac eps grad,
+// eps = kick_prm[0] (device), fused into its last pass over the gradient
 template <typename R>
-fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out, R *grad, cudaStream_t st);
+fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out, R *grad, cudaStream_t st,
+                        R *kick_p = nullptr, const double *kick_prm = nullptr, double kick_frac = 0.0);
 
 }  // namespace fm

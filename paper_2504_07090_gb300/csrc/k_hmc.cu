@@ -546,24 +546,6 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
 }
 
 // ------------------------------------------------------------------ leapfrog
-template <typename R>
-__global__ void k_axpy(long long n, double alpha, const R *__restrict__ x, R *__restrict__ y)
-{
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        y[k] += (R)alpha * x[k];
-}
-
-// momentum kick p -= (frac eps) g with eps = prm[0] read on the device, so that a captured
-// trajectory can be replayed with a new step size
-template <typename R>
-__global__ void k_kick(long long n, const double *__restrict__ prm, double frac, const R *__restrict__ g,
-                       R *__restrict__ p)
-{
-    const R a = (R)(-frac * prm[0]);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        p[k] += a * g[k];
-}
-
 __global__ void k_set_lf_params(double *prm, double eps, double u)
 {
     prm[0] = eps;
@@ -922,23 +904,20 @@ fm_status run_leapfrog(Ctx &c, R *q, R *p, const double *prm, int n_steps, doubl
     FM_TRY(lf_ensure<R>(c));
     R *q0 = (R *)c.lf_q0, *g = (R *)c.lf_g;
     double *sc = c.lf_scal;            // U0, U1, K0, K1, chi2
+    if (n_steps < 1) {
+        set_error("n_steps must be at least 1");
+        return FM_ERR_INVALID_ARG;
+    }
     k_copy<R><<<512, 256, 0, st>>>(n, q, q0);
     FM_CK_LAUNCH();
-    FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 0, g, st));
-    FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, nullptr, sc + 2, st));
-    // the closing half-kick of a step and the opening one of the next use the same gradient
-    // and run as one full kick
-    k_kick<R><<<512, 256, 0, st>>>(n, prm, 0.5, g, p);
-    FM_CK_LAUNCH();
+    FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, nullptr, sc + 2, st));     // K0, before any kick
+    // every gradient evaluation ends with the kick that uses its gradient, fused into its last
+    // pass: a half kick after the first and the last, and between steps one full kick (the
+    // closing half kick of a step and the opening one of the next use the same gradient)
+    FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 0, g, st, p, prm, 0.5));
     for (int s = 0; s < n_steps; ++s) {
         FM_TRY(lf_kinetic_drift<R>(c, p, q, prm, nullptr, st));
-        FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 1, g, st));
-        k_kick<R><<<512, 256, 0, st>>>(n, prm, s + 1 < n_steps ? 1.0 : 0.5, g, p);
-        FM_CK_LAUNCH();
-    }
-    if (n_steps == 0) {
-        k_copy<double><<<1, 32, 0, st>>>(1, sc + 0, sc + 1);
-        FM_CK_LAUNCH();
+        FM_TRY(run_chi2_grad<R>(c, q, sc + 4, sc + 1, g, st, p, prm, s + 1 < n_steps ? 1.0 : 0.5));
     }
     FM_TRY(lf_kinetic_drift<R>(c, p, nullptr, nullptr, sc + 3, st));
     k_lf_finish<<<1, 1, 0, st>>>(sc, prm, h_out, acc_out, c.status);

@@ -473,27 +473,30 @@ __global__ void __launch_bounds__(256) k_chi2_mid(DevGeom g, const R *__restrict
 // One CTA per (channel, LST): model, residual, chi^2 partial (a warp's terms summed in the
 // working type, the warps' sums in FP64), the adjoint weights
 // omega_pq = conj(g_p) g_q r_pq / sigma^2 and the per-antenna gain partials
-// Z_a = [sum_{q>a} r_aq g_q conj(V_aq) + sum_{p<a} conj(r_pa) g_p V_pa] / sigma^2 (a warp per
-// antenna, lanes over its partners, shuffle sums in a fixed order).  With q32 != NULL
-// (hour-angle form) omega is not written: its sums over the baseline groups go to
-// q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].
+// Z_a = [sum_{q>a} r_aq g_q conj(V_aq) + sum_{p<a} conj(r_pa) g_p V_pa] / sigma^2.  The two
+// terms of every baseline are formed once, with its residual; Z_a then sums its A - 1 terms
+// in CF_THREADS / A interleaved chunks (one thread each) and adds the chunks in order.  With
+// q32 != NULL (hour-angle form) omega is not written: its sums over the baseline groups go to
+// q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].  Needs A <= CF_THREADS.
+constexpr int CF_THREADS = 256;
 template <typename R>
-__global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict__ vis, const R *__restrict__ data,
-                                                 const R *__restrict__ gains, R *__restrict__ omega,
-                                                 R *__restrict__ zpart, double *__restrict__ chi2p, int U,
-                                                 const int *__restrict__ moff, const int *__restrict__ mem,
-                                                 float *__restrict__ q32, float *__restrict__ qmax_ft)
+__global__ void __launch_bounds__(CF_THREADS) k_chi2_ft(DevGeom g, const R *__restrict__ vis, const R *__restrict__ data,
+                                                        const R *__restrict__ gains, R *__restrict__ omega,
+                                                        R *__restrict__ zpart, double *__restrict__ chi2p, int U,
+                                                        const int *__restrict__ moff, const int *__restrict__ mem,
+                                                        float *__restrict__ q32, float *__restrict__ qmax_ft)
 {
     using C2 = typename V2<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *sG = reinterpret_cast<C2 *>(smem_raw);            // [A]
-    C2 *sV = sG + g.A;                                     // [B]
-    C2 *sR = sV + g.B;                                     // [B] residuals
-    C2 *sW = sR + g.B;                                     // [B] omega (hour-angle form)
-    __shared__ double dred[8];
-    __shared__ float fred[8];
+    C2 *sTi = sG + g.A;                                    // [B] term of baseline (i, j) in Z_i
+    C2 *sTj = sTi + g.B;                                   // [B] term of baseline (i, j) in Z_j
+    C2 *sW = sTj + g.B;                                    // [B] omega (hour-angle form)
+    __shared__ C2 sZ[CF_THREADS];                          // chunk sums of Z_a
+    __shared__ double dred[CF_THREADS / 32];
+    __shared__ float fred[CF_THREADS / 32];
     const int ft = blockIdx.x, f = ft / g.T, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < g.A; i += blockDim.x) {
+    for (int i = tid; i < g.A; i += CF_THREADS) {
         sG[i].x = gains[2 * (f * g.A + i)];
         sG[i].y = gains[2 * (f * g.A + i) + 1];
     }
@@ -503,11 +506,11 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
     const C2 *drow = reinterpret_cast<const C2 *>(data) + (size_t)ft * g.B;
     C2 *orow = reinterpret_cast<C2 *>(omega) + (size_t)ft * g.B;
     R c2 = 0;   // a warp's terms in the working type; FP64 across warps
-    for (int b = tid; b < g.B; b += blockDim.x) {
+    for (int b = tid; b < g.B; b += CF_THREADS) {
         const int i = g.bl_i[b], j = g.bl_j[b];
         const C2 V = vrow[b], d = drow[b], gi = sG[i], gj = sG[j];
         const R ggr = gi.x * gj.x + gi.y * gj.y, ggi = gi.y * gj.x - gi.x * gj.y;     // g_i conj(g_j)
-        C2 r, om;
+        C2 r, om, ti, tj;
         r.x = ggr * V.x - ggi * V.y - d.x;
         r.y = ggr * V.y + ggi * V.x - d.y;
         c2 += r.x * r.x + r.y * r.y;
@@ -515,8 +518,18 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
         om.y = (ggr * r.y - ggi * r.x) * is2;
         if (q32) sW[b] = om;
         else orow[b] = om;
-        sV[b] = V;
-        sR[b] = r;
+        {   // r g_j conj(V), the term in Z_i
+            const R pr = r.x * gj.x - r.y * gj.y, pi = r.x * gj.y + r.y * gj.x;
+            ti.x = pr * V.x + pi * V.y;
+            ti.y = pi * V.x - pr * V.y;
+        }
+        {   // conj(r) g_i V, the term in Z_j
+            const R pr = r.x * gi.x + r.y * gi.y, pi = r.x * gi.y - r.y * gi.x;
+            tj.x = pr * V.x - pi * V.y;
+            tj.y = pr * V.y + pi * V.x;
+        }
+        sTi[b] = ti;
+        sTj[b] = tj;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
@@ -524,12 +537,12 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
     __syncthreads();
     if (tid == 0) {
         double a = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += dred[k];
+        for (int k = 0; k < CF_THREADS / 32; ++k) a += dred[k];
         chi2p[ft] = a * g.inv_sigma2;
     }
     if (q32) {
         float qm = 0.f;
-        for (int u = tid; u < U; u += blockDim.x) {
+        for (int u = tid; u < U; u += CF_THREADS) {
             float qr = 0.f, qi = 0.f;
             for (int m = moff[u]; m < moff[u + 1]; ++m) {
                 const int code = mem[m], b = code >> 1;
@@ -544,41 +557,36 @@ __global__ void __launch_bounds__(256) k_chi2_ft(DevGeom g, const R *__restrict_
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) qm = fmaxf(qm, __shfl_xor_sync(0xffffffffu, qm, o));
         if (lane == 0) fred[w] = qm;
-        __syncthreads();
-        if (tid == 0) {
-            float m = 0.f;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, fred[k]);
-            qmax_ft[ft] = m;
-        }
     }
-    for (int a = w; a < g.A; a += (int)(blockDim.x >> 5)) {
+    // Z_a, chunk c: partners j = c, c + nc, ... (j != a); pair_index(a, j) = rowa + j for j > a
+    const int nc = CF_THREADS / g.A;
+    if (tid < nc * g.A) {
+        const int a = tid / nc, c = tid - a * nc;
+        const int rowa = a * g.A - (a * (a + 1)) / 2 - a - 1;
         R zr = 0, zi = 0;
-        for (int j = lane; j < g.A; j += 32) {
+        for (int j = c; j < g.A; j += nc) {
             if (j == a) continue;
-            const C2 gq = sG[j];
-            if (j > a) {          // r_aq g_q conj(V_aq)
-                const int b = pair_index(a, j, g.A);
-                const C2 r = sR[b], V = sV[b];
-                const R tr = r.x * gq.x - r.y * gq.y, ti = r.x * gq.y + r.y * gq.x;
-                zr += tr * V.x + ti * V.y;
-                zi += ti * V.x - tr * V.y;
-            } else {              // conj(r_pa) g_p V_pa
-                const int b = pair_index(j, a, g.A);
-                const C2 r = sR[b], V = sV[b];
-                const R tr = r.x * gq.x + r.y * gq.y, ti = r.x * gq.y - r.y * gq.x;
-                zr += tr * V.x - ti * V.y;
-                zi += tr * V.y + ti * V.x;
-            }
+            const C2 t = j > a ? sTi[rowa + j] : sTj[pair_index(j, a, g.A)];
+            zr += t.x;
+            zi += t.y;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            zr += __shfl_xor_sync(0xffffffffu, zr, o);
-            zi += __shfl_xor_sync(0xffffffffu, zi, o);
+        sZ[tid].x = zr;
+        sZ[tid].y = zi;
+    }
+    __syncthreads();
+    if (q32 && tid == 0) {
+        float m = 0.f;
+        for (int k = 0; k < CF_THREADS / 32; ++k) m = fmaxf(m, fred[k]);
+        qmax_ft[ft] = m;
+    }
+    if (tid < g.A) {
+        R zr = 0, zi = 0;
+        for (int c = 0; c < nc; ++c) {
+            zr += sZ[tid * nc + c].x;
+            zi += sZ[tid * nc + c].y;
         }
-        if (lane == 0) {
-            zpart[((size_t)ft * g.A + a) * 2] = zr * is2;
-            zpart[((size_t)ft * g.A + a) * 2 + 1] = zi * is2;
-        }
+        zpart[((size_t)ft * g.A + tid) * 2] = zr * is2;
+        zpart[((size_t)ft * g.A + tid) * 2 + 1] = zi * is2;
     }
 }
 
@@ -634,9 +642,12 @@ fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart,
                            cudaStream_t st)
 {
     const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
-    if (smem > 227 * 1024) return FM_ERR_UNSUPPORTED;
+    if (smem > 227 * 1024 || c.A > CF_THREADS) {
+        set_error("chi^2 epilogue: %d antennas (at most %d, %zu bytes of shared memory)", c.A, CF_THREADS, smem);
+        return FM_ERR_UNSUPPORTED;
+    }
     FM_CK(smem_opt_in(k_chi2_ft<R>));
-    k_chi2_ft<R><<<c.F * c.T, 256, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p, c.ha.U,
+    k_chi2_ft<R><<<c.F * c.T, CF_THREADS, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p, c.ha.U,
                                                 c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft);
     FM_CK_LAUNCH();
     return FM_OK;
@@ -864,21 +875,26 @@ struct __align__(16) Pack16 { R v[16 / sizeof(R)]; };
 // partials (FP64, loads batched so that their latencies overlap) and U = chi^2 / 2 + prior.
 // Each CTA writes its partial; the CTA that takes the last ticket adds the partials in
 // index order (so the result does not depend on which CTA that is) and resets the ticket
-// for the next launch.  vec: the four arrays are 16-byte aligned.
+// for the next launch.  With p != NULL the pass also applies the leapfrog momentum kick
+// p -= frac eps grad with the finished gradient (eps = prm[0], read on the device).  vec: the
+// arrays are 16-byte aligned.
 constexpr int PT_THREADS = 256;
 template <typename R>
 __global__ void __launch_bounds__(PT_THREADS) k_prior_total(long long n, int vec, const R *__restrict__ theta,
                                                             const R *__restrict__ mu, const R *__restrict__ lam,
                                                             R *__restrict__ grad, double *part, int nft,
                                                             const double *__restrict__ chi2p, double *chi2_out,
-                                                            double *u_out, int *status, unsigned *ticket)
+                                                            double *u_out, int *status, unsigned *ticket,
+                                                            R *__restrict__ p, const double *__restrict__ prm,
+                                                            double frac)
 {
     constexpr int W = 16 / sizeof(R);
     __shared__ double wred[8];
     __shared__ int last;
     const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x, gstride = (long long)gridDim.x * blockDim.x;
     R acc = 0;
-    if (lam) {
+    if (lam || p) {
+        const R ak = p ? (R)(-frac * prm[0]) : (R)0;      // the kick's factor, as in a separate kick
         long long head = 0;
         if (vec) {
             const long long np = n / W;
@@ -887,22 +903,36 @@ __global__ void __launch_bounds__(PT_THREADS) k_prior_total(long long n, int vec
             const Pack16<R> *mp = reinterpret_cast<const Pack16<R> *>(mu);
             const Pack16<R> *lp = reinterpret_cast<const Pack16<R> *>(lam);
             Pack16<R> *gp = reinterpret_cast<Pack16<R> *>(grad);
+            Pack16<R> *pp = reinterpret_cast<Pack16<R> *>(p);
             for (long long k = gtid; k < np; k += gstride) {
-                const Pack16<R> t = th[k], m = mp[k], l = lp[k];
                 Pack16<R> gr = gp[k];
+                if (lam) {
+                    const Pack16<R> t = th[k], m = mp[k], l = lp[k];
 #pragma unroll
-                for (int e = 0; e < W; ++e) {
-                    const R dv = t.v[e] - m.v[e], ld = l.v[e] * dv;
-                    gr.v[e] += ld;
-                    acc += ld * dv;
+                    for (int e = 0; e < W; ++e) {
+                        const R dv = t.v[e] - m.v[e], ld = l.v[e] * dv;
+                        gr.v[e] += ld;
+                        acc += ld * dv;
+                    }
+                    gp[k] = gr;
                 }
-                gp[k] = gr;
+                if (p) {
+                    Pack16<R> pv = pp[k];
+#pragma unroll
+                    for (int e = 0; e < W; ++e) pv.v[e] += ak * gr.v[e];
+                    pp[k] = pv;
+                }
             }
         }
         for (long long k = head + gtid; k < n; k += gstride) {
-            const R l = lam[k], dv = theta[k] - mu[k], ld = l * dv;
-            grad[k] += ld;
-            acc += ld * dv;
+            R gk = grad[k];
+            if (lam) {
+                const R l = lam[k], dv = theta[k] - mu[k], ld = l * dv;
+                gk += ld;
+                grad[k] = gk;
+                acc += ld * dv;
+            }
+            if (p) p[k] += ak * gk;
         }
     }
     const double blk = cta256_sum<R>((R)0.5 * acc, wred);
@@ -937,15 +967,15 @@ __global__ void __launch_bounds__(PT_THREADS) k_prior_total(long long n, int vec
 
 template <typename R>
 fm_status launch_prior_and_total(Ctx &c, const R *theta, R *grad, const double *chi2p, int nchi2, double *chi2_out,
-                                 double *u_out, cudaStream_t st)
+                                 double *u_out, cudaStream_t st, R *kick_p, const double *kick_prm, double kick_frac)
 {
     const R *mu = (const R *)c.mu, *lam = c.have_prior ? (const R *)c.lam : nullptr;
     auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-    const int vec = al(theta) && al(mu) && al(c.lam) && al(grad);
+    const int vec = al(theta) && al(mu) && al(c.lam) && al(grad) && al(kick_p);
     const long long units = vec ? c.n_par / (16 / (long long)sizeof(R)) : c.n_par;
     const int nblk = (int)std::max(1LL, std::min<long long>(4 * 152, (long long)cdiv(units, PT_THREADS)));
     k_prior_total<R><<<nblk, PT_THREADS, 0, st>>>(c.n_par, vec, theta, mu, lam, grad, c.red, nchi2, chi2p, chi2_out,
-                                                 u_out, c.status, c.ticket);
+                                                 u_out, c.status, c.ticket, kick_p, kick_prm, kick_frac);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -1045,7 +1075,7 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
                                          cudaStream_t);                                                  \
     template fm_status launch_gain_reduce<R>(Ctx &, const R *, R *, cudaStream_t);                       \
     template fm_status launch_prior_and_total<R>(Ctx &, const R *, R *, const double *, int, double *, double *, \
-                                                 cudaStream_t);                                          \
+                                                 cudaStream_t, R *, const double *, double);             \
     template fm_status launch_prior_hvp<R>(Ctx &, const R *, R *, cudaStream_t);                         \
     template fm_status launch_add_dc<R>(Ctx &, const R *, long long, R *, cudaStream_t);                \
     template fm_status launch_center<R>(Ctx &, const R *, R *, R *, cudaStream_t);
