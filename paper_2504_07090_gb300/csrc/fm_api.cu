@@ -243,11 +243,12 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 // x -> V; with dc != nullptr the monopole visibilities dc[f * dcs] U[f][t][b] are added
 // (inside the last kernel of the hour-angle form, as a separate pass otherwise)
 template <typename R>
-static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st, const R *dc = nullptr, long long dcs = 0)
+static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st, const R *dc = nullptr, long long dcs = 0,
+                         bool xmax_ready = false)
 {
     // the tensor-core launchers time their main kernel themselves
     if constexpr (std::is_same<R, float>::value) {
-        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs);
+        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs, xmax_ready);
         if (c.prec >= FM_PREC_BF16X1) {
             FM_TRY(launch_vis_tc(c, x, vis, st));
             return dc ? launch_add_dc<R>(c, dc, dcs, vis, st) : FM_OK;
@@ -270,12 +271,20 @@ static fm_status run_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st, b
 template <typename R>
 fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st)
 {
+    // hour-angle form after the tensor-core transform: the transform forms the channel maxima
+    // of x that scale the sky strip
+    unsigned *xmax = nullptr;
+    if constexpr (std::is_same<R, float>::value)
+        if (c.ha.on && c.mtc.on) {
+            FM_CK(cudaMemsetAsync(c.ha.xmax, 0, sizeof(unsigned) * c.F, st));
+            xmax = c.ha.xmax;
+        }
     if (c.dc_split) {
-        FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 1));
-        return run_vis<R>(c, xbuf, vis, st, a, c.nk);
+        FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 1, xmax));
+        return run_vis<R>(c, xbuf, vis, st, a, c.nk, xmax != nullptr);
     }
-    FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 0));
-    return run_vis<R>(c, xbuf, vis, st);
+    FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 0, xmax));
+    return run_vis<R>(c, xbuf, vis, st, nullptr, 0, xmax != nullptr);
 }
 template fm_status vis_of_modes<float>(Ctx &, const float *, float *, float *, cudaStream_t);
 template fm_status vis_of_modes<double>(Ctx &, const double *, double *, double *, cudaStream_t);
@@ -285,12 +294,11 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
                         R *kick_p, const double *kick_prm, double kick_frac)
 {
     if (!c.have_data) { set_error("fm_set_data has not been called"); return FM_ERR_STATE; }
-    R *x = (R *)c.x, *vis = (R *)c.vis, *om = (R *)c.omega, *zp = (R *)c.zpart, *gn = (R *)c.gains;
-    FM_TRY(launch_gains<R>(c, theta + c.n_sky, gn, st));
+    R *x = (R *)c.x, *vis = (R *)c.vis, *om = (R *)c.omega, *zp = (R *)c.zpart;
     FM_TRY(vis_of_modes<R>(c, theta, x, vis, st));
     // hour-angle form: the epilogue forms the group sums of omega itself
     const bool groups = std::is_same<R, float>::value && c.ha.on;
-    FM_TRY(launch_chi2_chan<R>(c, vis, gn, om, zp, c.chi2p, groups, st));
+    FM_TRY(launch_chi2_chan<R>(c, vis, theta + c.n_sky, om, zp, c.chi2p, groups, st));   // gains formed inside
     FM_TRY(run_adjoint<R>(c, om, (R *)c.xbar, st, groups));
     FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, grad, st));
     FM_TRY(launch_gain_reduce_chan<R>(c, zp, grad + c.n_sky, st));

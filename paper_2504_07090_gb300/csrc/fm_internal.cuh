@@ -228,7 +228,9 @@ fm_status profiled(Ctx &c, int cls, cudaStream_t st, F fn)
 fm_status launch_precompute(Ctx &c, cudaStream_t st);
 
 template <typename R>
-fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc = 0);   // a -> x
+// a -> x; xmax != NULL (tensor-core transform only): also atomicMax of each channel's largest
+// |x| (as float bits) into xmax[f], which the caller has zeroed
+fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc = 0, unsigned *xmax = nullptr);
 template <typename R>
 fm_status launch_modes_adjoint(Ctx &c, const R *xbar, R *abar, cudaStream_t st);  // xbar -> abar
 template <typename R>
@@ -248,9 +250,10 @@ fm_status launch_hvp_mid(Ctx &c, const R *vis, const R *dvis, const R *g, const 
 template <typename R>
 fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
 // per-(channel, LST) form of the chi^2 epilogue (gradient path): chi2p[f][t], the gain
-// partials zpart[f][t][a][2], omega, or (groups) the hour-angle group sums of omega
+// partials zpart[f][t][a][2], omega, or (groups) the hour-angle group sums of omega; the
+// gains are formed inside from the coefficients gamma [A][NG][2]
 template <typename R>
-fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p, bool groups,
+fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zpart, double *chi2p, bool groups,
                            cudaStream_t st);
 // grad_gain from zpart in one pass over (channel, LST)
 template <typename R>
@@ -281,11 +284,12 @@ fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_
 fm_status ha_setup(Ctx &c);
 // tensor-core mode transforms (float handles of the split precisions)
 fm_status modes_tc_setup(Ctx &c);
-fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc);
+fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax);
 fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st);
-// dc != nullptr: also adds the monopole visibilities dc[f * dcs] U[f][t][b]
+// dc != nullptr: also adds the monopole visibilities dc[f * dcs] U[f][t][b]; xmax_ready: the
+// channel maxima of x are already in c.ha.xmax (formed by the mode transform)
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc = nullptr,
-                        long long dcs = 0);
+                        long long dcs = 0, bool xmax_ready = false);
 // q_ready: the group sums q32 / qmax_ft were already formed from omega (by the chi^2 epilogue)
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready = false);
 

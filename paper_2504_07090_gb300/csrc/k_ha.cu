@@ -1098,7 +1098,7 @@ bool make_layout_adj(const Ctx &c, bool x3, HaLayout &L)
 
 template <int ET, bool X3>
 fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cudaStream_t st, const float *dc,
-                        long long dcs)
+                        long long dcs, bool xmax_ready)
 {
     HaState &s = c.ha;
     HaLayout L;
@@ -1107,9 +1107,11 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
         return FM_ERR_UNSUPPORTED;
     }
     uint16_t *ys_hi = s.ys, *ys_lo = s.ys + (size_t)c.F * c.D * s.Ly;
-    FM_CK(cudaMemsetAsync(s.xmax, 0, sizeof(unsigned) * c.F, st));
-    k_ha_xmax<<<dim3(cdiv(c.npix, 256 * 8), c.F), 256, 0, st>>>(c.npix, x, s.xmax);
-    FM_CK_LAUNCH();
+    if (!xmax_ready) {
+        FM_CK(cudaMemsetAsync(s.xmax, 0, sizeof(unsigned) * c.F, st));
+        k_ha_xmax<<<dim3(cdiv(c.npix, 256 * 8), c.F), 256, 0, st>>>(c.npix, x, s.xmax);
+        FM_CK_LAUNCH();
+    }
     k_ha_yprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, ys_hi, ys_lo);
     FM_CK_LAUNCH();
     FM_CK(smem_opt_in(k_vis_ha<ET, X3>));
@@ -1403,13 +1405,16 @@ fm_status ha_setup(Ctx &c)
     return FM_OK;
 }
 
-fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc, long long dcs)
+fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc, long long dcs,
+                        bool xmax_ready)
 {
     const HaDev h = make_dev(c);
     const bool x3 = x3_of(c.prec);
     if (f16_of(c.prec))
-        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs) : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs);
-    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs) : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs);
+        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs, xmax_ready)
+                  : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs, xmax_ready);
+    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs, xmax_ready)
+              : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs, xmax_ready);
 }
 
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready)

@@ -366,10 +366,34 @@ __global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restr
     }
 }
 
+// Packed storage of a lower-triangular 64 x 64 block in 16-byte pieces of PER = 16 /
+// sizeof(R) entries: row r keeps its first ceil((r + 1) / PER) pieces (entries past the
+// diagonal in the last piece are zero), rows one after another.  With r = PER a + b, row r
+// starts at piece PER a (a + 1) / 2 + b (a + 1); a block takes 544 pieces in FP32 and 1056 in
+// FP64 instead of 1024, and every row starts on a 16-byte boundary.
+template <typename R>
+__host__ __device__ constexpr int tri_row_pieces(int r)
+{
+    return (r + (int)(16 / sizeof(R))) / (int)(16 / sizeof(R));
+}
+template <typename R>
+__host__ __device__ constexpr int tri_row_start(int r)
+{
+    return (int)(16 / sizeof(R)) * (r / (int)(16 / sizeof(R))) * (r / (int)(16 / sizeof(R)) + 1) / 2 +
+           (r % (int)(16 / sizeof(R))) * (r / (int)(16 / sizeof(R)) + 1);
+}
+template <typename R>
+__host__ __device__ constexpr int tri_block_elems()
+{
+    return tri_row_start<R>(64) * (int)(16 / sizeof(R));
+}
+static_assert(tri_row_start<float>(64) == 544 && tri_row_start<double>(64) == 1056, "packed block size");
+static_assert(tri_row_start<float>(5) == 6 && tri_row_start<float>(4) == 4, "packed row start");
+
 // Inverses of the stored 64 x 64 sky-block factors (one CTA of 64 threads per block):
 // the factor, as stored in the working type, is read into FP64 shared memory and thread
-// j solves L x = e_j by forward substitution; Linv[r][j] = x_r.  Inverting the stored
-// factor keeps L^-1 (L z) = z to FP64 rounding before the final store.
+// j solves L x = e_j by forward substitution; Linv[r][j] = x_r, stored packed (above).
+// Inverting the stored factor keeps L^-1 (L z) = z to FP64 rounding before the final store.
 template <typename R>
 __global__ void __launch_bounds__(64) k_pc_blk_inv(const R *__restrict__ L, R *__restrict__ Linv)
 {
@@ -391,8 +415,10 @@ __global__ void __launch_bounds__(64) k_pc_blk_inv(const R *__restrict__ L, R *_
         }
         x[r] = v;
     }
-    R *Ib = Linv + (size_t)blockIdx.x * 4096;
-    for (int r = 0; r < 64; ++r) Ib[r * 64 + j] = (R)x[r];
+    R *Ib = Linv + (size_t)blockIdx.x * tri_block_elems<R>();
+    constexpr int PER = 16 / sizeof(R);
+    for (int r = 0; r < 64; ++r)
+        if (j < tri_row_pieces<R>(r) * PER) Ib[tri_row_start<R>(r) * PER + j] = (R)x[r];
 }
 
 // Sky prior on the block diagonals: blocks[k/bs][k%bs][k%bs] += lam[k]
@@ -501,7 +527,7 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
             k_pc_chol_big<R><<<1, 256, 0, st>>>(ng, c.pc_blocks + sky_sz, (const R *)c.lam, c.n_sky,
                                                 c.have_prior ? 1 : 0, W, Lf + sky_sz, c.status);
             if (!c.pc_linv) {
-                if (cudaMalloc(&c.pc_linv, c.rsz * (size_t)sky_sz) != cudaSuccess) {
+                if (cudaMalloc(&c.pc_linv, sizeof(R) * (size_t)nsky_blk * tri_block_elems<R>()) != cudaSuccess) {
                     rc = FM_ERR_ALLOC;
                     set_error("cudaMalloc sky-block inverses");
                     break;
@@ -567,10 +593,10 @@ __global__ void k_copy(long long n, const R *__restrict__ x, R *__restrict__ y)
 // The solves use the explicit inverses of the factors (computed in FP64 from the stored
 // factors when the preconditioner is built), so every operation is a triangular
 // matrix-vector product without a serial dependency.  One warp per 64 x 64 sky block:
-// the block (L^-1, or L for mul) is copied to shared memory with cp.async (16-byte
-// pieces, XOR-permuted within each row), lane l owns entries l and l + 32, and the
-// vector entries are broadcast by shuffles.  CTA 0 (when n_dense > 0) handles the dense
-// gain block of order n_dense the same way from global memory, overlapping the sky blocks.
+// the block (L^-1 from its packed rows, with zeros written above the diagonal; or L,
+// stored full, for mul) is copied to shared memory with cp.async (16-byte pieces,
+// XOR-permuted within each row), lane l owns entries l and l + 32, and the vector is read
+// from shared memory.  The dense gain block follows in k_lf_dense.
 constexpr int LF_WARPS = 4;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
@@ -666,11 +692,21 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
         if (blk >= nblk) return;
         R *S = sm + (size_t)w * (4096 + 64);            // block image, then the 64-vector
         R *vs = S + 4096;
-        const R *Lb = (mul ? L : Li) + blk * 4096;      // the factor for mul, its inverse for the solves
         constexpr int PER = 16 / sizeof(R), NP = 64 / PER;     // elements per 16-byte piece, pieces per row
-        for (int e = lane; e < 64 * NP; e += 32) {
-            const int r = e / NP, pc = e % NP;
-            cp_async16(S + r * 64 + ((pc ^ (r & (NP - 1))) * PER), Lb + r * 64 + pc * PER);
+        if (mul) {                                      // the factor, stored full
+            const R *Lb = L + blk * 4096;
+            for (int e = lane; e < 64 * NP; e += 32) {
+                const int r = e / NP, pc = e % NP;
+                cp_async16(S + r * 64 + ((pc ^ (r & (NP - 1))) * PER), Lb + r * 64 + pc * PER);
+            }
+        } else {                                        // its inverse, stored packed; zeros above
+            const R *Lb = Li + blk * tri_block_elems<R>();
+            for (int e = lane; e < 64 * NP; e += 32) {
+                const int r = e / NP, pc = e % NP;
+                R *dst = S + r * 64 + ((pc ^ (r & (NP - 1))) * PER);
+                if (pc < tri_row_pieces<R>(r)) cp_async16(dst, Lb + (tri_row_start<R>(r) + pc) * PER);
+                else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
         const long long off = blk * 64;
         vs[lane] = in[off + lane];

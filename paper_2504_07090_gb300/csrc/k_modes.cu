@@ -289,9 +289,12 @@ __device__ __forceinline__ float md_tmem_max(uint32_t tmem, int c0, int ncols, f
 // ---------------------------------------------------------------- forward
 // CTA (f, d tile): stage 1 D1[d][m] (TMEM columns 0 .. Mp) = Leg_tile a_f^T over n;
 // stage 2 D2[d][r] (columns Mp .. Mp + Rp) = W Phi^T over m; x[f][d][r] = D2 / scales.
+// xmax != NULL: the largest |x| the CTA wrote goes to xmax[f] by atomicMax on its float bits
+// (non-negative floats order like their bit patterns, so the result is independent of order).
 __global__ void __launch_bounds__(MD_THREADS, 1)
 k_modes_fwd(MdDims z, const float *__restrict__ a_all, int skip_dc, const uint8_t *__restrict__ leg_img,
-            const uint8_t *__restrict__ phi_img, float *__restrict__ x_all, int *__restrict__ status, int ncols)
+            const uint8_t *__restrict__ phi_img, float *__restrict__ x_all, int *__restrict__ status, int ncols,
+            unsigned *__restrict__ xmax)
 {
     const int f = blockIdx.x, dt = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -348,6 +351,7 @@ k_modes_fwd(MdDims z, const float *__restrict__ a_all, int skip_dc, const uint8_
     tc_fence_after();
 
     // x = D2 / (g 2^28 sa)
+    float xm = 0.f;
     if (ok) {
         const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sa);
         const int quarter = warp & 3, half = warp >> 2, lane = tid & 31;
@@ -360,8 +364,16 @@ k_modes_fwd(MdDims z, const float *__restrict__ a_all, int skip_dc, const uint8_
             if (d < z.D)
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    if (cg + q < z.R) xr[cg + q] = v[q] * inv;
+                    if (cg + q < z.R) {
+                        const float xv = v[q] * inv;
+                        xr[cg + q] = xv;
+                        xm = fmaxf(xm, fabsf(xv));
+                    }
         }
+    }
+    if (xmax) {                                 // uniform: every thread takes part
+        const float bm = block_max(xm, m.red);
+        if (tid == 0 && ok) atomicMax(xmax + f, __float_as_uint(bm));
     }
     tc_fence_before();
     __syncthreads();
@@ -528,12 +540,12 @@ fm_status modes_tc_setup(Ctx &c)
     return FM_OK;
 }
 
-fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc)
+fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax)
 {
     const MdDims z = md_dims(c);
     const int ndt = (c.D + 127) / 128;
     k_modes_fwd<<<dim3(c.F, ndt), MD_THREADS, md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp), st>>>(
-        z, a, skip_dc, c.mtc.leg_img, c.mtc.phi_img, x, c.status, md_cols(z.Mp + z.Rp));
+        z, a, skip_dc, c.mtc.leg_img, c.mtc.phi_img, x, c.status, md_cols(z.Mp + z.Rp), xmax);
     FM_CK_LAUNCH();
     return FM_OK;
 }

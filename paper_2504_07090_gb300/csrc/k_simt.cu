@@ -156,10 +156,14 @@ template <> const float *tab_leg<float>(const Ctx &c) { return c.g.leg32; }
 
 // x[f][d][r] = sum_n P[d][n] sum_m Phi[r][m] a[f][m][n]   (Eq. fg_separable)
 template <typename R>
-fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc)
+fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc, unsigned *xmax)
 {
     if constexpr (std::is_same<R, float>::value)
-        if (c.mtc.on) return launch_modes_tc_forward(c, a, x, st, skip_dc);
+        if (c.mtc.on) return launch_modes_tc_forward(c, a, x, st, skip_dc, xmax);
+    if (xmax) {
+        set_error("channel maxima are formed only by the tensor-core mode transform");
+        return FM_ERR_STATE;
+    }
     R *t1 = (R *)c.tmp;
     GemmArgs s1{c.R, c.N, c.M, 0, c.M, 1, c.nk, c.N, 1, (long long)c.R * c.N, c.N, 1, skip_dc};
     FM_TRY(gemm<R>(s1, c.F, tab_phi<R>(c), a, t1, st));
@@ -475,13 +479,15 @@ __global__ void __launch_bounds__(256) k_chi2_mid(DevGeom g, const R *__restrict
 // omega_pq = conj(g_p) g_q r_pq / sigma^2 and the per-antenna gain partials
 // Z_a = [sum_{q>a} r_aq g_q conj(V_aq) + sum_{p<a} conj(r_pa) g_p V_pa] / sigma^2.  The two
 // terms of every baseline are formed once, with its residual; Z_a then sums its A - 1 terms
-// in CF_THREADS / A interleaved chunks (one thread each) and adds the chunks in order.  With
-// q32 != NULL (hour-angle form) omega is not written: its sums over the baseline groups go to
-// q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].  Needs A <= CF_THREADS.
+// in CF_THREADS / A interleaved chunks (one thread each) and adds the chunks in order.  The
+// gains g_i(nu_f) = sum_k X_k(nu_f) gamma_ik are formed from the coefficients gamma in the
+// prologue.  With q32 != NULL (hour-angle form) omega is not written: its sums over the
+// baseline groups go to q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].  Needs
+// A <= CF_THREADS.
 constexpr int CF_THREADS = 256;
 template <typename R>
-__global__ void __launch_bounds__(CF_THREADS) k_chi2_ft(DevGeom g, const R *__restrict__ vis, const R *__restrict__ data,
-                                                        const R *__restrict__ gains, R *__restrict__ omega,
+__global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(DevGeom g, const R *__restrict__ vis, const R *__restrict__ data,
+                                                        const R *__restrict__ gamma, R *__restrict__ omega,
                                                         R *__restrict__ zpart, double *__restrict__ chi2p, int U,
                                                         const int *__restrict__ moff, const int *__restrict__ mem,
                                                         float *__restrict__ q32, float *__restrict__ qmax_ft)
@@ -496,9 +502,17 @@ __global__ void __launch_bounds__(CF_THREADS) k_chi2_ft(DevGeom g, const R *__re
     __shared__ double dred[CF_THREADS / 32];
     __shared__ float fred[CF_THREADS / 32];
     const int ft = blockIdx.x, f = ft / g.T, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < g.A; i += CF_THREADS) {
-        sG[i].x = gains[2 * (f * g.A + i)];
-        sG[i].y = gains[2 * (f * g.A + i) + 1];
+    {
+        const R *X = Tab<R>::gleg(g) + (size_t)f * g.NG;
+        for (int i = tid; i < g.A; i += CF_THREADS) {     // as k_gains
+            R re = 0, im = 0;
+            for (int k = 0; k < g.NG; ++k) {
+                re += X[k] * gamma[(i * g.NG + k) * 2];
+                im += X[k] * gamma[(i * g.NG + k) * 2 + 1];
+            }
+            sG[i].x = re;
+            sG[i].y = im;
+        }
     }
     __syncthreads();
     const R is2 = (R)g.inv_sigma2;
@@ -638,7 +652,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gain_reduce_ft(DevGeom g, const 
 }
 
 template <typename R>
-fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart, double *chi2p, bool groups,
+fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zpart, double *chi2p, bool groups,
                            cudaStream_t st)
 {
     const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
@@ -647,7 +661,7 @@ fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *g, R *omega, R *zpart,
         return FM_ERR_UNSUPPORTED;
     }
     FM_CK(smem_opt_in(k_chi2_ft<R>));
-    k_chi2_ft<R><<<c.F * c.T, CF_THREADS, smem, st>>>(c.g, vis, (const R *)c.data, g, omega, zpart, chi2p, c.ha.U,
+    k_chi2_ft<R><<<c.F * c.T, CF_THREADS, smem, st>>>(c.g, vis, (const R *)c.data, gamma, omega, zpart, chi2p, c.ha.U,
                                                 c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft);
     FM_CK_LAUNCH();
     return FM_OK;
@@ -1064,7 +1078,7 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
 #define FM_INST(R)                                                                                       \
     template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t); \
     template fm_status launch_gain_reduce_chan<R>(Ctx &, const R *, R *, cudaStream_t);                 \
-    template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int);                \
+    template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int, unsigned *);    \
     template fm_status launch_modes_adjoint<R>(Ctx &, const R *, R *, cudaStream_t);                     \
     template fm_status launch_gains<R>(Ctx &, const R *, R *, cudaStream_t);                             \
     template fm_status launch_vis<R>(Ctx &, const R *, R *, cudaStream_t);                               \
