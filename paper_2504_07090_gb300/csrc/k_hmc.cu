@@ -593,9 +593,9 @@ __global__ void k_copy(long long n, const R *__restrict__ x, R *__restrict__ y)
 // The solves use the explicit inverses of the factors (computed in FP64 from the stored
 // factors when the preconditioner is built), so every operation is a triangular
 // matrix-vector product without a serial dependency.  One warp per 64 x 64 sky block:
-// the block (L^-1 from its packed rows, with zeros written above the diagonal; or L,
-// stored full, for mul) is copied to shared memory with cp.async (16-byte pieces,
-// XOR-permuted within each row), lane l owns entries l and l + 32, and the vector is read
+// the block is copied to shared memory with cp.async in 16-byte pieces (L^-1 packed as it
+// is stored, 8.7 KB in FP32, so that twice as many warps fit on an SM; L, stored full, for
+// mul into an XOR-permuted image), lane l owns entries l and l + 32, and the vector is read
 // from shared memory.  The dense gain block follows in k_lf_dense.
 constexpr int LF_WARPS = 4;
 
@@ -614,19 +614,10 @@ __device__ __forceinline__ R warp_sum(R a)
     return a;
 }
 
-// Shared-memory image of a 64 x 64 block: row-major, the 16-byte pieces of row r
-// permuted by XOR with (r mod pieces per row), so that a column read (32 lanes, 32 rows)
-// touches few banks and a row read none twice.
-template <typename R>
-__device__ __forceinline__ int swz(int r, int c)
-{
-    constexpr int PER = 16 / sizeof(R), NP = 64 / PER;
-    return r * 64 + (((c / PER) ^ (r & (NP - 1))) * PER) + (c % PER);
-}
-
 // y = T v for a 64 x 64 lower-triangular T stored with zeros above the diagonal in the
-// XOR-permuted image S: lane l forms rows l and l + 32 from whole 16-byte pieces of its
-// rows and broadcast pieces of v (vs, shared)
+// image S (row-major, the 16-byte pieces of row r permuted by XOR with r mod pieces per row,
+// so that a row read touches no bank twice): lane l forms rows l and l + 32 from whole
+// 16-byte pieces of its rows and broadcast pieces of v (vs, shared)
 template <typename R>
 __device__ __forceinline__ void lower_mv(const R *S, const R *vs, R &y0, R &y1)
 {
@@ -643,6 +634,35 @@ __device__ __forceinline__ void lower_mv(const R *S, const R *vs, R &y0, R &y1)
             const R vq = vs[pc * PER + q];
             a0 += r0[ph + q] * vq;
             a1 += r1[ph + q] * vq;
+        }
+    }
+    y0 = a0;
+    y1 = a1;
+}
+
+// The same product for T in the packed form (tri_row_start): lane l reads only the stored
+// pieces of rows l and l + 32, in the order of lower_mv, so the sums are the same
+template <typename R>
+__device__ __forceinline__ void lower_mv_packed(const R *P, const R *vs, R &y0, R &y1)
+{
+    constexpr int PER = 16 / sizeof(R), NP = 64 / PER;
+    struct alignas(16) Piece { R v[PER]; };
+    const int lane = threadIdx.x & 31;
+    const Piece *r0 = reinterpret_cast<const Piece *>(P) + tri_row_start<R>(lane);
+    const Piece *r1 = reinterpret_cast<const Piece *>(P) + tri_row_start<R>(lane + 32);
+    const int n0 = tri_row_pieces<R>(lane), n1 = tri_row_pieces<R>(lane + 32);
+    R a0 = 0, a1 = 0;
+#pragma unroll
+    for (int pc = 0; pc < NP; ++pc) {
+        if (pc < n0) {
+            const Piece t = r0[pc];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) a0 += t.v[q] * vs[pc * PER + q];
+        }
+        if (pc < n1) {
+            const Piece t = r1[pc];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) a1 += t.v[q] * vs[pc * PER + q];
         }
     }
     y0 = a0;
@@ -690,23 +710,19 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
         // ------------------------------------------------ one 64 x 64 block per warp
         const long long blk = (long long)blockIdx.x * LF_WARPS + w;
         if (blk >= nblk) return;
-        R *S = sm + (size_t)w * (4096 + 64);            // block image, then the 64-vector
-        R *vs = S + 4096;
         constexpr int PER = 16 / sizeof(R), NP = 64 / PER;     // elements per 16-byte piece, pieces per row
-        if (mul) {                                      // the factor, stored full
+        const int wsz = mul ? 4096 : tri_block_elems<R>();      // block image, then the 64-vector
+        R *S = sm + (size_t)w * (wsz + 64);
+        R *vs = S + wsz;
+        if (mul) {                                      // the factor, stored full: XOR-permuted image
             const R *Lb = L + blk * 4096;
             for (int e = lane; e < 64 * NP; e += 32) {
                 const int r = e / NP, pc = e % NP;
                 cp_async16(S + r * 64 + ((pc ^ (r & (NP - 1))) * PER), Lb + r * 64 + pc * PER);
             }
-        } else {                                        // its inverse, stored packed; zeros above
+        } else {                                        // its inverse, packed, copied as it is stored
             const R *Lb = Li + blk * tri_block_elems<R>();
-            for (int e = lane; e < 64 * NP; e += 32) {
-                const int r = e / NP, pc = e % NP;
-                R *dst = S + r * 64 + ((pc ^ (r & (NP - 1))) * PER);
-                if (pc < tri_row_pieces<R>(r)) cp_async16(dst, Lb + (tri_row_start<R>(r) + pc) * PER);
-                else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-            }
+            for (int e = lane; e < tri_row_start<R>(64); e += 32) cp_async16(S + e * PER, Lb + e * PER);
         }
         const long long off = blk * 64;
         vs[lane] = in[off + lane];
@@ -722,26 +738,27 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
         }
         R v0 = vs[lane], v1 = vs[lane + 32];
         if (fwd) {
-            lower_mv<R>(S, vs, v0, v1);
+            lower_mv_packed<R>(S, vs, v0, v1);
             if (kin) {
                 double sq = warp_sum((double)v0 * (double)v0 + (double)v1 * (double)v1);
                 if (lane == 0) kin[blk] = sq;
             }
         }
         if (bwd) {
-            // v = T^T v: lane l forms entries l and l + 32 from rows r (column reads)
+            // v = T^T v: lane l forms entries l and l + 32 from the rows r that store them
+            // (consecutive entries of row r across the lanes)
             __syncwarp();
             vs[lane] = v0;
             vs[lane + 32] = v1;
             __syncwarp();
             R b0 = 0, b1 = 0;
-            const int c0 = lane / PER, c1 = (lane + 32) / PER, q0 = lane % PER;
 #pragma unroll 8
             for (int r = 0; r < 64; ++r) {
                 const R zr = vs[r];
-                const int x = r & (NP - 1);
-                b0 += S[r * 64 + ((c0 ^ x) * PER) + q0] * zr;
-                b1 += S[r * 64 + ((c1 ^ x) * PER) + q0] * zr;
+                const R *row = S + tri_row_start<R>(r) * PER;
+                const int len = tri_row_pieces<R>(r) * PER;
+                if (lane < len) b0 += row[lane] * zr;
+                if (lane + 32 < len) b1 += row[lane + 32] * zr;
             }
             v0 = b0;
             v1 = b1;
@@ -830,7 +847,7 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
     if (bs > 1) {
         const long long nb = c.n_sky / bs;
         const int ng = 2 * c.A * c.NG;
-        const size_t smem = sizeof(R) * (size_t)LF_WARPS * (4096 + 64);
+        const size_t smem = sizeof(R) * (size_t)LF_WARPS * ((mul ? 4096 : tri_block_elems<R>()) + 64);
         FM_CK(smem_opt_in(k_lf_tri<R>));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
         k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
