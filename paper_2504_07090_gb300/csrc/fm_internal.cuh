@@ -128,7 +128,7 @@ struct Ctx {
     int pc_block = 0;
     double *pc_blocks = nullptr;      // FP64 GN blocks (sky then gain)
     void *pc_chol = nullptr;          // factors in the working real type
-    void *pc_ginv = nullptr;          // inverse of the dense gain-block factor and its transpose (block 64 only)
+    void *pc_ginv = nullptr;          // gain block (block 64 only): L_g^-1, its transpose, and L_g^-T L_g^-1
     void *pc_linv = nullptr;          // inverses of the 64 x 64 sky-block factors (block 64 only)
     double *pc_tmp = nullptr;         // FP64 scratch of the gain-block inverse
     int64_t pc_size = 0;

@@ -366,6 +366,22 @@ __global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restr
     }
 }
 
+// The gain block of the inverse mass matrix, Gm = L_g^-T L_g^-1 (symmetric), from the FP64
+// inverse columns Xd[j][k] = (L_g^-1)[k][j]: Gm[r][c] = sum over k >= max(r, c) of
+// Xd[r][k] Xd[c][k], in FP64, rounded once.  A drift then needs one product with Gm.
+template <typename R>
+__global__ void k_pc_gm(int n, const double *__restrict__ Xd, R *__restrict__ Gm)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        const double *xr = Xd + (size_t)r * n, *xc = Xd + (size_t)c * n;
+        double a = 0.0;
+        for (int k = r > c ? r : c; k < n; ++k) a += xr[k] * xc[k];
+        Gm[e] = (R)a;
+    }
+}
+
 // Packed storage of a lower-triangular 64 x 64 block in 16-byte pieces of PER = 16 /
 // sizeof(R) entries: row r keeps its first ceil((r + 1) / PER) pieces (entries past the
 // diagonal in the last piece are zero), rows one after another.  With r = PER a + b, row r
@@ -538,7 +554,7 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
             k_pc_blk_inv<R><<<(unsigned)nsky_blk, 64, 2 * 64 * 65 * sizeof(double), st>>>(Lf, (R *)c.pc_linv);
             if (ng > 0) {
                 if (!c.pc_ginv) {
-                    if (cudaMalloc(&c.pc_ginv, 2 * c.rsz * (size_t)ng * ng) != cudaSuccess ||
+                    if (cudaMalloc(&c.pc_ginv, 3 * c.rsz * (size_t)ng * ng) != cudaSuccess ||
                         cudaMalloc(&c.pc_tmp, sizeof(double) * (size_t)ng * ng) != cudaSuccess) {
                         rc = FM_ERR_ALLOC;
                         set_error("cudaMalloc gain-block inverse");
@@ -549,6 +565,8 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
                 }
                 k_pc_tri_inv<R><<<cdiv(ng, 128), 128, 0, st>>>(ng, W, c.pc_tmp, (R *)c.pc_ginv,
                                                                (R *)c.pc_ginv + (size_t)ng * ng);
+                k_pc_gm<R><<<cdiv((long long)ng * ng, 256), 256, 0, st>>>(ng, c.pc_tmp,
+                                                                         (R *)c.pc_ginv + 2 * (size_t)ng * ng);
             }
         } else {
             k_pc_chol_diag<R><<<cdiv(need, 256), 256, 0, st>>>(need, c.pc_blocks, (const R *)c.lam,
@@ -695,20 +713,50 @@ __global__ void __launch_bounds__(256) k_lf_dense(int n, const R *__restrict__ M
     }
 }
 
+// The dense gain block as the first nctas CTAs of k_lf_tri (so that they run in its first
+// wave): one warp per row r of the n x n row-major matrix M (mode 0: entries c >= r, 1: c <= r,
+// 2: all), x = in + base, each lane taking c = lane, lane + 32, ... as k_lf_dense does;
+// outputs at base + r and the kinetic partial kin[r] = y_r^2 (when kin != NULL).
+template <typename R>
+struct LfDense {
+    const R *M;
+    int n, mode;
+    long long base;
+    unsigned nctas;
+    double *kin;
+};
+
 template <typename R>
 __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const R *__restrict__ Li,
                                                           const R *__restrict__ L, const R *__restrict__ in, int fwd,
                                                           int bwd, int mul, R *__restrict__ q,
                                                           const double *__restrict__ peps,
-                                                          R *__restrict__ out, double *__restrict__ kin)
+                                                          R *__restrict__ out, double *__restrict__ kin,
+                                                          LfDense<R> dn)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const double eps = q ? *peps : 0.0;
+    if (blockIdx.x < dn.nctas) {
+        // ------------------------------------------------ dense gain rows, one warp per row
+        const int r = (int)blockIdx.x * LF_WARPS + w;
+        if (r >= dn.n) return;
+        const R *row = dn.M + (size_t)r * dn.n, *x = in + dn.base;
+        R a = 0;
+        for (int cc = lane; cc < dn.n; cc += 32)
+            if (dn.mode == 2 || (dn.mode == 1 ? cc <= r : cc >= r)) a += row[cc] * x[cc];
+        a = warp_sum(a);
+        if (lane == 0) {
+            if (dn.kin) dn.kin[r] = (double)a * (double)a;
+            if (q && !mul) q[dn.base + r] += (R)(eps * a);
+            if (out) out[dn.base + r] = a;
+        }
+        return;
+    }
     {
         // ------------------------------------------------ one 64 x 64 block per warp
-        const long long blk = (long long)blockIdx.x * LF_WARPS + w;
+        const long long blk = (long long)(blockIdx.x - dn.nctas) * LF_WARPS + w;
         if (blk >= nblk) return;
         constexpr int PER = 16 / sizeof(R), NP = 64 / PER;     // elements per 16-byte piece, pieces per row
         const int wsz = mul ? 4096 : tri_block_elems<R>();      // block image, then the 64-vector
@@ -850,34 +898,30 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
         const size_t smem = sizeof(R) * (size_t)LF_WARPS * ((mul ? 4096 : tri_block_elems<R>()) + 64);
         FM_CK(smem_opt_in(k_lf_tri<R>));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
-        k_lf_tri<R><<<(unsigned)grid, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
-                                                                peps, out, kin_out ? part : nullptr);
-        FM_CK_LAUNCH();
+        // the gain block runs as extra warps of the same launch: one product with L_g (mul),
+        // L_g^-1 (fwd), L_g^-T (bwd) or L_g^-T L_g^-1 (fwd and bwd, no kinetic energy)
+        const R *Gi = (const R *)c.pc_ginv;
+        LfDense<R> dn{nullptr, ng, 0, c.n_sky, 0u, nullptr};
         if (ng > 0) {
-            // the gain block: matrix-vector products with L_g (mul), L_g^-1 (fwd), L_g^-T (bwd)
+            if (mul) { dn.M = L + (size_t)nb * bs * bs; dn.mode = 1; }
+            else if (fwd && bwd) { if (!kin_out) { dn.M = Gi + 2 * (size_t)ng * ng; dn.mode = 2; } }
+            else if (fwd) { dn.M = Gi; dn.mode = 1; dn.kin = kin_out ? part + nb : nullptr; }
+            else if (bwd) { dn.M = Gi + (size_t)ng * ng; dn.mode = 0; }
+        }
+        if (dn.M) dn.nctas = cdiv(ng, LF_WARPS);
+        const long long gtot = grid + dn.nctas;
+        k_lf_tri<R><<<(unsigned)gtot, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
+                                                                peps, out, kin_out ? part : nullptr, dn);
+        FM_CK_LAUNCH();
+        if (ng > 0 && !dn.M && fwd && bwd) {     // both solves with the kinetic energy: two products
             const long long base = c.n_sky;
-            const R *Lg = L + (size_t)nb * bs * bs, *Gi = (const R *)c.pc_ginv, *GiT = Gi + (size_t)ng * ng;
             const unsigned dg = cdiv(ng, 8);
             R *y = (R *)c.lf_y;
-            if (mul) {
-                k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Lg, 1, in + base, nullptr, nullptr, nullptr, nullptr, out + base);
-                FM_CK_LAUNCH();
-            } else {
-                const R *src = in + base;
-                if (fwd) {
-                    const bool last = !bwd;
-                    k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi, 1, src, y, kin_out ? part + nb : nullptr,
-                                                      last && q ? q + base : nullptr, peps,
-                                                      last && out ? out + base : nullptr);
-                    FM_CK_LAUNCH();
-                    src = y;
-                }
-                if (bwd) {
-                    k_lf_dense<R><<<dg, 256, 0, st>>>(ng, GiT, 0, src, nullptr, nullptr, q ? q + base : nullptr, peps,
-                                                      out ? out + base : nullptr);
-                    FM_CK_LAUNCH();
-                }
-            }
+            k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi, 1, in + base, y, part + nb, nullptr, peps, nullptr);
+            FM_CK_LAUNCH();
+            k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi + (size_t)ng * ng, 0, y, nullptr, nullptr,
+                                              q ? q + base : nullptr, peps, out ? out + base : nullptr);
+            FM_CK_LAUNCH();
         }
         if (kin_out) {
             k_sum_to<<<1, 256, 0, st>>>((int)(nb + ng), part, kin_out);
