@@ -232,3 +232,20 @@ def test_global_gain_phase_is_a_gauge_and_gain_scale_is_quadratic():
     th3 = th.copy()
     th3[o.n_sky:] *= 1.7
     np.testing.assert_allclose(o.model(th3), 1.7 ** 2 * m0, atol=1e-12 * np.abs(m0).max())
+
+
+def test_prior_inflation_takes_the_first_spd_factor():
+    # M = H_lik + c diag(lam) for the first c in 1, 1.1, 1.21, ... that is SPD: with
+    # H_lik = diag(-2, 1) and lam = 1 that needs c > 2, first reached at c = 1.1^8
+    H = np.diag([-2.0, 1.0])
+    lam = np.array([1.0, 1.0])
+    L, c = oracle.cholesky_with_inflation(H, lam)
+    want = 1.0
+    for _ in range(8):
+        want *= 1.1
+    assert c == want and want > 2.0 and want / 1.1 < 2.0
+    np.testing.assert_allclose(L @ L.T, H + c * np.diag(lam), rtol=1e-14)
+    # an SPD H_lik is factorised with c = 1 (no inflation)
+    L1, c1 = oracle.cholesky_with_inflation(np.array([[4.0, 1.0], [1.0, 3.0]]), lam)
+    assert c1 == 1.0
+    np.testing.assert_allclose(L1 @ L1.T, [[5.0, 1.0], [1.0, 4.0]], rtol=1e-14)
