@@ -38,7 +38,7 @@ N_PRODUCTS = {"bf16x1": 1, "fp16x1": 1, "bf16x3": 3, "fp16x3": 3}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg1")
@@ -71,23 +71,71 @@ def workload_desc(prob, traj):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms, started before the warm-up; stop() keeps the samples
+    whose own timestamps fall inside the window marked by begin() / end() (all samples,
+    and "window": "run", when none do, e.g. for a window shorter than the interval)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
         self.gpu = gpu_index
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 3.0              # until the first sample is written
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def parse(lines, t0=None, t1=None, slack=0.06):
+        """Samples of nvidia-smi csv lines (FIELDS order); with t0 / t1 (epoch seconds) only
+        those stamped within [t0 - slack, t1 + slack], if there are any."""
+        import datetime
+        rows = []
+        for line in lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                sm, smax = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            act = {nm for nm, v in zip(ClockSampler.NAMES, parts[6:10]) if v.lower().startswith("active")}
+            rows.append((ts, sm, smax, act))
+        window = "run"
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if r[0] is not None and t0 - slack <= r[0] <= t1 + slack]
+            if inside:
+                rows, window = inside, "timed region"
+        sm = [r[1] for r in rows]
+        reasons = set().union(*[r[3] for r in rows]) if rows else set()
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+                "samples": len(sm), "window": window, "reasons": sorted(reasons)}
 
     def stop(self):
         if self.proc is None:
@@ -98,24 +146,10 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
-            for line in fh:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
+            out = self.parse(fh.readlines(), self.t0, self.t1)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        return out
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -229,6 +263,8 @@ def main_batch(args):
         for k in range(n):
             models[k].precond_apply(0, zs[k][i], out=ps[k])
 
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     for i in range(W):
         flush.zero_()
         draw(i)
@@ -236,10 +272,9 @@ def main_batch(args):
     torch.cuda.synchronize()
     for h in models:
         h.sync_status()
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start()
     l0 = fm.kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks.begin()
     for i in range(K):
         flush.zero_()
         evs[i][0].record(st)
@@ -247,6 +282,7 @@ def main_batch(args):
         batch.run(eps, us[W + i])
         evs[i][1].record(st)
     torch.cuda.synchronize()
+    clocks.end()
     clk = clocks.stop()
     launches = fm.kernel_launches() - l0 + K * batch.kernels()
     for h in models:
@@ -341,19 +377,20 @@ def main():
         h.precond_apply(0, zs[i], out=p)
         h.leapfrog(q, p, args.eps, args.traj, float(us[i]), h_out, acc)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for i in range(W):
         flush.zero_()
         step(i)
     torch.cuda.synchronize()
     h.sync_status()
 
-    clocks = ClockSampler(local)
     h.get_profile()
     h.set_profiling(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     launches0 = fm.kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     n_acc = 0
@@ -364,6 +401,7 @@ def main():
         step(W + i)
         evs[i][1].record(st)
     torch.cuda.synchronize()
+    clocks.end()
     torch.cuda.nvtx.range_pop()
     launches = fm.kernel_launches() - launches0
     clk = clocks.stop()
