@@ -69,6 +69,20 @@ def workload_desc(prob, traj):
             f"{prob.n_params} params; one HMC iteration = p = L z + {traj}-step leapfrog ({traj + 1} chi2+grad evals)")
 
 
+# ------------------------------------------------------------------ ranks
+def job_rate(local_ms: float, units_per_rank: float, world: int, dist=None, device=None):
+    """Whole-job rate over `world` ranks that each process units_per_rank units: the job's time
+    is the slowest rank's (an all-reduce MAX of local_ms when dist is given).  Returns
+    (units per second of the whole job, that time in ms)."""
+    ms = float(local_ms)
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1000.0), ms
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples every 50 ms, started before the warm-up; stop() keeps the samples
@@ -413,12 +427,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
     n_acc = int(acc.item())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     evals_per_step = args.traj + 1
-    value = world * K * evals_per_step / (total_ms / 1000.0)
+    value, total_ms = job_rate(total_ms, K * evals_per_step, world, dist, dev)
 
     # roofline of the dominant contraction kernel (live CUDA events around each launch)
     info = h.contraction_info()
@@ -489,11 +499,8 @@ def main():
             b.record(st)
             torch.cuda.synchronize()
             e_ms += a.elapsed_time(b)
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * K * evals_per_step / (e_ms / 1000.0), "unit": "chi2+grad evals/s",
+        e_rate, e_ms = job_rate(e_ms, K * evals_per_step, world, dist, dev)
+        e2e = {"value": e_rate, "unit": "chi2+grad evals/s",
                "h2d_bytes_per_step": 2 * 4 * h.n_params, "d2h_bytes_per_step": 4 * h.n_params + 16 + 4}
 
     cpu = None
