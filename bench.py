@@ -87,32 +87,43 @@ def job_rate(local_ms: float, units_per_rank: float, world: int, dist=None, devi
 class ClockSampler:
     """nvidia-smi samples every 50 ms, started before the warm-up; stop() keeps the samples
     whose own timestamps fall inside the window marked by begin() / end() (all samples,
-    and "window": "run", when none do, e.g. for a window shorter than the interval)."""
-    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    and "window": "run", when none do, e.g. for a window shorter than the interval, or when
+    nvidia-smi does not take the timestamp field and is restarted without it)."""
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
         self.gpu = gpu_index
+        self.stamped = True
         self.t0 = self.t1 = None
+
+    def _launch(self, fields: str) -> bool:
+        """Start nvidia-smi; True once it has written a sample (waits up to 3 s)."""
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={fields}",
+                                      "--format=csv,noheader,nounits", "-lms", "50"],
+                                     stdout=self.fh, stderr=subprocess.DEVNULL)
+        deadline = time.time() + 3.0
+        while time.time() < deadline:
+            if os.path.getsize(self.path) > 0:
+                return True
+            if self.proc.poll() is not None:
+                break
+            time.sleep(0.02)
+        return os.path.getsize(self.path) > 0
 
     def start(self):
         try:
-            self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            if not self._launch("timestamp,index," + self.QUERY) and self.proc.poll() is not None:
+                self.fh.close()
+                self.stamped = False
+                self._launch("index," + self.QUERY)
         except Exception:
             self.proc = None
-            return
-        deadline = time.time() + 3.0              # until the first sample is written
-        while time.time() < deadline and self.proc.poll() is None:
-            if os.path.getsize(self.path) > 0:
-                break
-            time.sleep(0.02)
 
     def begin(self):
         self.t0 = time.time()
@@ -121,24 +132,28 @@ class ClockSampler:
         self.t1 = time.time()
 
     @staticmethod
-    def parse(lines, t0=None, t1=None, slack=0.06):
-        """Samples of nvidia-smi csv lines (FIELDS order); with t0 / t1 (epoch seconds) only
-        those stamped within [t0 - slack, t1 + slack], if there are any."""
+    def parse(lines, t0=None, t1=None, stamped=True, slack=0.06):
+        """Samples of nvidia-smi csv lines ([timestamp,] index, then QUERY); with t0 / t1
+        (epoch seconds) only those stamped within [t0 - slack, t1 + slack], if any."""
         import datetime
+        off = 1 if stamped else 0
         rows = []
         for line in lines:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 10:
+            if len(parts) < 9 + off:
                 continue
             try:
-                sm, smax = float(parts[2]), float(parts[3])
+                sm, smax = float(parts[1 + off]), float(parts[2 + off])
             except ValueError:
                 continue
-            try:
-                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-            except ValueError:
-                ts = None
-            act = {nm for nm, v in zip(ClockSampler.NAMES, parts[6:10]) if v.lower().startswith("active")}
+            ts = None
+            if stamped:
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+            flags = parts[5 + off:9 + off]
+            act = {nm for nm, v in zip(ClockSampler.NAMES, flags) if v.lower().startswith("active")}
             rows.append((ts, sm, smax, act))
         window = "run"
         if t0 is not None and t1 is not None:
@@ -161,7 +176,7 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         with open(self.path) as fh:
-            out = self.parse(fh.readlines(), self.t0, self.t1)
+            out = self.parse(fh.readlines(), self.t0, self.t1, self.stamped)
         os.unlink(self.path)
         return out
 
