@@ -52,7 +52,7 @@ typedef enum {
     FM_ERR_NONFINITE = 4,     /* chi^2 or the Hamiltonian was NaN/Inf (trajectory rejected) */
     FM_ERR_TIMEOUT = 5,       /* a device-side wait exceeded its iteration limit */
     FM_ERR_NOT_SPD = 6,       /* a preconditioner block stayed indefinite after inflation */
-    FM_ERR_UNSUPPORTED = 7,   /* shape or precision not supported by this build */
+    FM_ERR_UNSUPPORTED = 7,   /* shape or precision the library does not support */
     FM_ERR_STATE = 8          /* call order: e.g. leapfrog before data were set */
 } fm_status;
 
