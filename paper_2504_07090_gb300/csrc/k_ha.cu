@@ -98,8 +98,6 @@ __device__ __forceinline__ float pow2_scale(float mx)
     return sc;
 }
 
-__device__ __forceinline__ void st32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
-
 // ------------------------------------------------------------ per-handle phasor table
 // E[f][d][nb][i][row], n = 64 nb + nl, i over the table's antenna subset plus one all-zero
 // entry (padding pairs point at it).  A row of 132 floats holds the 64 cells, then 16 bytes
