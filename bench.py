@@ -234,10 +234,11 @@ def run_reference(args):
             rates.append(r)
     v = float(np.mean(rates))
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "chi2+grad evals/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "chi2+grad evals/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", str(args.gpus))),         # the launch's N (host cores)
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(prob, args.traj).split(";")[0] + "; one chi2+grad evaluation"},
+        "config": {"workload": workload_desc(prob, args.traj)},      # the GPU arm's workload and unit
         "cpu_baseline": {"value": v, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "chi2+grad evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
