@@ -215,7 +215,8 @@ FM_API fm_status fm_get_profile(fm_handle h, double *out_ms, int64_t *out_count)
  * a[f][m][n] without allocating anything.  The intermediate sum over m lives in a
  * file-scope device array of 2^21 floats (8 MiB) that every GPU loading the library
  * holds until the process exits; n_freq*n_ra*n_mode_dec above 2^21 is rejected with
- * FM_ERR_INVALID_ARG.  The first call on each device looks up the array's device
+ * FM_ERR_INVALID_ARG, and so are n_freq > 65535 and n_ra or n_dec > 65535 * 32 (the
+ * launch grid), before anything is launched.  The first call on each device looks up the array's device
  * address with that device current (make that first call before any stream capture).
  * Every call shares the array, which keeps the last call's contents: calls that
  * overlap on the GPU (other streams, or a second call before the first finished on a

@@ -50,7 +50,7 @@ constexpr int HA_QLOAD_WARP = 22;         // adjoint only: bulk copies of the re
 constexpr int HA_THREADS = 22 * 32;       // forward
 constexpr int HA_EPI2_WARP0 = 23;         // adjoint only: warps 23..26, the second epilogue set
 constexpr int HA_ADJ_THREADS = 27 * 32;   // adjoint
-constexpr int HA_SUB = 16;                // 64-cell K chunks per TMEM accumulation chain
+constexpr int HA_SUB = 4;                 // 64-cell K chunks per TMEM accumulation chain (shorter chains: less FP32 accumulation bias)
 constexpr int HA_SMEM_BUDGET = 227 * 1024 - 1024 - 512;
 constexpr int HA_EW = 66;                 // float2 entries per table row: 64 cells + 16 bytes of padding
 constexpr int HA_NSTAGE = 4;              // adjoint operand stages (A in TMEM, B in shared memory)

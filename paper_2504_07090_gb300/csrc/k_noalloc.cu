@@ -92,6 +92,14 @@ extern "C" fm_status fm_sky_pixels_noalloc(int n_freq, int n_ra, int n_dec, int 
         set_error("invalid argument: grid too large");
         return FM_ERR_INVALID_ARG;
     }
+    // both launches put n_freq on gridDim.z and 32-row tiles of n_ra (first) or n_dec (second)
+    // on gridDim.y, each limited to 65535: checked here, before the first launch writes the
+    // shared scratch
+    if (n_freq > 65535 || cdiv(n_ra, 32) > 65535 || cdiv(n_dec, 32) > 65535) {
+        set_error("invalid argument: n_freq = %d, n_ra = %d or n_dec = %d exceeds the launch grid limits "
+                  "(n_freq <= 65535, n_ra and n_dec <= 65535 * 32)", n_freq, n_ra, n_dec);
+        return FM_ERR_INVALID_ARG;
+    }
     float *t1 = nullptr;
     FM_TRY(scratch_ptr(&t1));
     const long long npix = (long long)n_ra * n_dec, nk = (long long)n_mode_ra * n_mode_dec;

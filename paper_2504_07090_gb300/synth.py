@@ -178,6 +178,10 @@ def config(name: str) -> Problem:
         # the cfg1 array (666 baselines, 63 distinct vectors) with the LST step equal to
         # one RA pixel (10 LSTs, 32 RA cells of 1.5 deg)
         return drift_scan_problem("ha37", 4, 3, 148e6, 152e6, 10, 7, 32, 8, 4, 20, 23)
+    if name == "ha37m":
+        # ha37 with 16 x 4 = 64 modes per channel (one 64-block of the mass matrix per
+        # channel): the hour-angle leapfrog case
+        return drift_scan_problem("ha37m", 4, 3, 148e6, 152e6, 10, 7, 32, 16, 4, 20, 23)
     if name == "hafrac2":
         # LST step of 2.5 RA pixels (5 LSTs 3 deg apart, 40 RA cells of 1.2 deg): hour-angle
         # cells of half a pixel, 5 cells per LST step; 7-antenna hexagon

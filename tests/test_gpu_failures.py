@@ -7,7 +7,7 @@ check and the handle keeps working once the status has been read."""
 import numpy as np
 import pytest
 
-from gpu_cases import TOL_VIS, as_complex, handle, make_case, quant, rel_l2
+from gpu_cases import as_complex, bound, handle, make_case, quant, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def test_bounded_wait_times_out_and_the_context_stays_usable():
     p, o, th, d, mu, lam = make_case("small")
     h = handle(p, "fp32")
     v = h.forward(torch.tensor(quant("fp32", th), dtype=torch.float32, device="cuda"))
-    assert rel_l2(as_complex(v), o.model(quant("fp32", th))) < TOL_VIS["fp32"]
+    assert rel_l2(as_complex(v), o.model(quant("fp32", th))) < bound("direct", "V", "fp32")
     h.sync_status()
 
 
