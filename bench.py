@@ -33,6 +33,14 @@ if ROOT not in sys.path:
 METRIC = "χ²+grad evals/s & vis-pixel terms/s at stated err vs FP64; leapfrog steps/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 N_PRODUCTS = {"bf16x1": 1, "fp16x1": 1, "bf16x3": 3, "fp16x3": 3}
+# leapfrog step per workload: the largest with acceptance above 90 % (Sec. 4.2); at cfg1 the
+# energy error of a 20-step trajectory grows as eps^4 (median |dH| 0.43 at 0.01, 7.4 at 0.02)
+EPS_DEFAULT = {"cfg1": 0.007, "cfg3": 0.007}
+A_MIN = 0.2                 # acceptance threshold of the step-size rule (App. B)
+# DRAM read + write bytes per launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum), from the ncu capture of profiles/k_vis_ha_k_adj_ha_cfg1_fp16x3.md,
+# keyed (workload, precision, form, kernel); a kernel changed since its capture has no entry
+TRAFFIC = {}
 
 
 def parse():
@@ -45,7 +53,10 @@ def parse():
     ap.add_argument("--precision", default=None, help="default: fp16x3 (cfg1), bf16x3 (cfg2)")
     ap.add_argument("--problems", type=int, default=64, help="cfg2: number of independent problems")
     ap.add_argument("--traj", type=int, default=20, help="leapfrog steps per trajectory")
-    ap.add_argument("--eps", type=float, default=None, help="leapfrog step: default 0.1 (cfg1), 0.02 (cfg2)")
+    ap.add_argument("--eps", type=float, default=None, help="leapfrog step: default 0.007 (cfg1), 0.02 (cfg2)")
+    ap.add_argument("--block", type=int, default=64, help="preconditioner block (64, or 1 for the diagonal)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the bf16x3 / fp32 comparison and the errors")
+    ap.add_argument("--no-err", action="store_true", help="skip the errors against the FP64 oracle")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -62,11 +73,13 @@ def peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
-def workload_desc(prob, traj):
+def workload_desc(prob, traj, block=64):
+    pc = "64-block" if block > 1 else "diagonal"
     return (f"{prob.name}: {prob.n_ant}-antenna hexagon ({prob.n_bl} baselines), {prob.n_freq} ch "
             f"{prob.freq_hz[0] / 1e6:.0f}-{prob.freq_hz[-1] / 1e6:.0f} MHz, {prob.n_lst} LSTs, "
             f"{prob.n_dec}x{prob.n_ra} px, {prob.n_mode_ra}x{prob.n_mode_dec} modes/ch, "
-            f"{prob.n_params} params; one HMC iteration = p = L z + {traj}-step leapfrog ({traj + 1} chi2+grad evals)")
+            f"{prob.n_params} params; one HMC iteration = p = L z + {traj}-step leapfrog ({traj + 1} chi2+grad evals), "
+            f"{pc} Gauss-Newton mass matrix")
 
 
 # ------------------------------------------------------------------ ranks
@@ -241,6 +254,9 @@ def run_reference(args):
         "config": {"workload": workload_desc(prob, args.traj)},      # the GPU arm's workload and unit
         "cpu_baseline": {"value": v, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "chi2+grad evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "the FP64 oracle timed on a bounded sample of every step and extrapolated linearly to the whole "
+                "evaluation (the work is linear in channels and (channel, LST) pairs), so ms_per_step x steps is "
+                "far longer than this run's wall clock by design",
     }), flush=True)
 
 
@@ -353,6 +369,69 @@ def main_batch(args):
         h.close()
 
 
+def errors_vs_fp64(prob, tr, handles, d_dev, f0):
+    """Relative l2 errors of the GPU forms against the FP64 oracle on channel f0 of the timed
+    workload: the visibilities of all its LSTs at the truth, and its sky gradient at sky modes
+    perturbed by 1 % of the channel rms.  For the gradient each handle gets, for the duration
+    of the check, data that are the oracle model plus seeded noise on channel f0 and zero on
+    the others (the sky modes are per channel, so that slice of the gradient depends on f0
+    alone); the oracle's restricted gradient plus the prior's is the expected value."""
+    import torch
+    import oracle
+    o = oracle.Oracle(prob)
+    o.sigma = prob.sigma
+    th = tr.theta.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    pairs = [(f0, t) for t in range(prob.n_lst)]
+    m0 = o.model(th, fts=pairs)[f0]
+    a, _ = o.split(th)
+    sc = np.zeros(o.n_par)
+    sc[: o.n_sky] = np.repeat(np.sqrt(np.mean(a ** 2, axis=1)), o.nk)
+    th_e = (th + 0.01 * sc * np.random.default_rng(6).standard_normal(o.n_par)).astype(np.float32).astype(np.float64)
+    d1 = np.zeros((prob.n_freq, prob.n_lst, prob.n_bl, 2))
+    d1[f0] = np.stack([m0.real, m0.imag], -1) + prob.sigma * tr.noise[f0]
+    d1 = d1.astype(np.float32).astype(np.float64)
+    _, _, g = o.chi2_grad(th_e, d1[..., 0] + 1j * d1[..., 1], fts=pairs)
+    from paper_2504_07090_gb300 import synth
+    mu, lam = synth.prior_for(prob, tr.theta)
+    sl = slice(f0 * o.nk, (f0 + 1) * o.nk)
+    g_sl = g[sl] + (lam * (th_e - mu.astype(np.float32).astype(np.float64)))[sl]
+    t_or = time.perf_counter() - t0
+    out = {}
+    d1_dev = torch.tensor(d1, dtype=torch.float32, device="cuda").contiguous()
+    for name, h in handles.items():
+        V = h.forward(torch.tensor(th, dtype=torch.float32, device="cuda"))[f0].double().cpu().numpy()
+        ev = float(np.linalg.norm(V[..., 0] + 1j * V[..., 1] - m0) / np.linalg.norm(m0))
+        h.set_data(d1_dev)
+        _, grad = h.chi2_grad(torch.tensor(th_e, dtype=torch.float32, device="cuda"))
+        eg = float(np.linalg.norm(grad[sl].double().cpu().numpy() - g_sl) / np.linalg.norm(g_sl))
+        h.set_data(d_dev)
+        out[name] = {"V": ev, "grad": eg}
+    return out, {"channel": int(f0), "pairs": len(pairs), "oracle_s": t_or,
+                 "what": f"relative l2 vs the FP64 oracle: all {prob.n_lst}x{prob.n_bl} visibilities of channel {f0} "
+                         f"at the truth; its {o.nk} sky-gradient entries at a 1 % sky perturbation"}
+
+
+def time_chi2_grad(h, theta, n_eval, reps, flush, st):
+    """chi^2 + gradient evaluations/s of one handle: reps x n_eval back-to-back fm_chi2_grad
+    calls, L2 flushed before each batch, CUDA events around each batch."""
+    import torch
+    scal = torch.empty(2, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(theta)
+    h.chi2_grad(theta, grad, scal)
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(n_eval):
+            h.chi2_grad(theta, grad, scal)
+        b.record(st)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return reps * n_eval / (tot / 1000.0), tot / (reps * n_eval)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -362,7 +441,7 @@ def main():
         main_batch(args)
         return
     args.precision = args.precision or "fp16x3"
-    args.eps = args.eps or 0.1
+    args.eps = args.eps or EPS_DEFAULT.get(args.config, 0.01)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -387,25 +466,30 @@ def main():
     prob.sigma = sigma
     h = fm.ForwardModel(prob, args.precision, sigma=sigma)
     d = (m + sigma * torch.tensor(tr.noise, dtype=torch.float32, device=dev)).contiguous()
+    del m
     h.set_data(d)
     mu, lam = synth.prior_for(prob, tr.theta)
-    h.set_prior(torch.tensor(mu, dtype=torch.float32, device=dev), torch.tensor(lam, dtype=torch.float32, device=dev))
+    mu_d = torch.tensor(mu, dtype=torch.float32, device=dev)
+    lam_d = torch.tensor(lam, dtype=torch.float32, device=dev)
+    h.set_prior(mu_d, lam_d)
     q = th_true.clone()
-    h.build_precond(q, 64)
+    t_pc = time.perf_counter()
+    h.build_precond(q, args.block)
     torch.cuda.synchronize()
+    t_pc = time.perf_counter() - t_pc
 
     K, W = args.steps, args.warmup
-    zs = torch.tensor(synth.random_vectors(h.n_params, K + W, 20250420 + rank), dtype=torch.float32, device=dev)
-    us = np.random.default_rng(20250421 + rank).random(K + W)
-    p = torch.empty_like(q)
-    h_out = torch.empty(2, dtype=torch.float64, device=dev)
-    acc = torch.empty(1, dtype=torch.int32, device=dev)
+    # the chain runs on the device (fm_hmc_chain): momentum z ~ N(0, 1) from the counter-based
+    # generator, p = L z, the trajectory, the Metropolis test and the step-size rule of App. B,
+    # one captured graph launch per HMC iteration
+    seed = 20250420 + rank
+    state = torch.tensor([args.eps, 0.0], dtype=torch.float64, device=dev)
+    trace = torch.zeros((W + K, 5), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
     st = torch.cuda.current_stream()
 
     def step(i):
-        h.precond_apply(0, zs[i], out=p)
-        h.leapfrog(q, p, args.eps, args.traj, float(us[i]), h_out, acc)
+        h.hmc_chain(q, 1, args.traj, args.eps, A_MIN, seed, state, trace[i])
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -415,15 +499,13 @@ def main():
     torch.cuda.synchronize()
     h.sync_status()
 
-    h.get_profile()
-    h.set_profiling(True)
+    # ---- timed region: profiling off
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.begin()
     launches0 = fm.kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    n_acc = 0
     torch.cuda.nvtx.range_push("bench_timed")
     for i in range(K):
         flush.zero_()
@@ -433,20 +515,45 @@ def main():
     torch.cuda.synchronize()
     clocks.end()
     torch.cuda.nvtx.range_pop()
-    launches = fm.kernel_launches() - launches0
+    # kernels of the library in the timed region: one graph per iteration (fm_kernel_launches
+    # counts launches made outside graphs, here the chain's call-setup kernel)
+    launches = fm.kernel_launches() - launches0 + K * h.chain_kernels()
     clk = clocks.stop()
     if dist:
         dist.barrier()
-    h.set_profiling(False)
-    (fwd_ms, adj_ms), (fwd_n, adj_n) = h.get_profile()
     h.sync_status()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
-    n_acc = int(acc.item())
     evals_per_step = args.traj + 1
     value, total_ms = job_rate(total_ms, K * evals_per_step, world, dist, dev)
+    rec = trace.cpu().numpy()[W:]
+    dH = rec[:, 2] - rec[:, 1]
+    sampler = {"eps0": args.eps, "a_min": A_MIN, "n_steps": args.traj, "trajectories": K,
+               "accepted": int(rec[:, 3].sum()), "acceptance_rate": float(rec[:, 3].mean()),
+               "mean_accept_prob": float(rec[:, 4].mean()), "median_abs_dH": float(np.median(np.abs(dH))),
+               "eps_used": {"min": float(rec[:, 0].min()), "max": float(rec[:, 0].max())},
+               "eps_after": float(state[0].item()),
+               "rule": "Philox4x32-10 momentum and accept draws on the device; eps <- eps/1.2 if a < a_min else "
+                       "min(eps0, 1.2 eps) (App. B); eps0 the largest step with acceptance above 90 % (Sec. 4.2)"}
 
-    # roofline of the dominant contraction kernel (live CUDA events around each launch)
+    # ---- roofline of the dominant contraction kernel: a separate, untimed pass with the
+    # per-launch events on (fm_set_profiling), over the same kind of steps
+    h.get_profile()
+    h.set_profiling(True)
+    q_keep, state_keep = q.clone(), state.clone()
+    p = torch.empty_like(q)
+    hp = torch.empty(2, dtype=torch.float64, device=dev)
+    ap = torch.empty(1, dtype=torch.int32, device=dev)
+    zp = torch.tensor(synth.random_vectors(h.n_params, 1, seed)[0], dtype=torch.float32, device=dev)
+    for i in range(min(K, 5)):
+        # the same trajectories launched directly (fm_leapfrog), so that the events record
+        flush.zero_()
+        h.precond_apply(0, zp, out=p)
+        h.leapfrog(q, p, args.eps, args.traj, 0.5, hp, ap)
+    (fwd_ms, adj_ms), (fwd_n, adj_n) = h.get_profile()
+    h.set_profiling(False)
+    q.copy_(q_keep)
+    state.copy_(state_keep)
     info = h.contraction_info()
     pk, pk_src = peaks()
     nprod = N_PRODUCTS.get(args.precision, 1)
@@ -458,11 +565,12 @@ def main():
         flops_launch = 4.0 * info["fringes"] * prob.n_pix * prob.n_freq * prob.n_lst
         formula = "4 n_groups n_pix n_freq n_lst"
         names = ("forward contraction (k_vis_ha)", "adjoint contraction (k_adj_ha)")
-        npad = (prob.n_lst + 15) // 16 * 16
+        npad = (min(prob.n_lst, 64) + 15) // 16 * 16
+        n_pass = (prob.n_lst + 63) // 64
         nhp = info["hour_angle_cells"]
         n_mt, n_kq = (info["fringes"] + 63) // 64, (info["fringes"] + 31) // 32
-        exe = (nprod * 2.0 * 128 * n_mt * npad * nhp * prob.n_dec * prob.n_freq,
-               nprod * 2.0 * nhp * npad * 64 * n_kq * prob.n_dec * prob.n_freq)
+        exe = (n_pass * nprod * 2.0 * 128 * n_mt * npad * nhp * prob.n_dec * prob.n_freq,
+               n_pass * nprod * 2.0 * nhp * npad * 64 * n_kq * prob.n_dec * prob.n_freq)
     else:
         flops_launch = 8.0 * prob.n_ant ** 2 * prob.n_pix * prob.n_freq * prob.n_lst
         formula = "8 n_ant^2 n_pix n_freq n_lst"
@@ -472,11 +580,7 @@ def main():
     dom = names[0] if fwd_dom else names[1]
     dom_ms1, dom_n = (fwd_ms1, fwd_n) if fwd_dom else (adj_ms1, adj_n)
     achieved = flops_launch / (dom_ms1 / 1000.0) / 1e12 if dom_n else None
-    # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
-    # of one ncu capture of these kernels at cfg1, fp16x3); None for other workloads
-    traffic = None
-    if args.config == "cfg1" and args.precision == "fp16x3" and info["form"] == "hour_angle":
-        traffic = (305.316352e6 + 4.327936e6) if fwd_dom else (296.293888e6 + 7.27936e6)
+    traffic = TRAFFIC.get((args.config, args.precision, info["form"], "fwd" if fwd_dom else "adj"))
     roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
@@ -484,21 +588,20 @@ def main():
                                f"= {formula} = {flops_launch:.4g}",
                 "form": info["form"], "fringes": info["fringes"],
                 "forward_ms_per_launch": fwd_ms1, "adjoint_ms_per_launch": adj_ms1,
-                "launches": {"forward": fwd_n, "adjoint": adj_n}}
+                "launches": {"forward": fwd_n, "adjoint": adj_n},
+                "timing": "CUDA events around every contraction launch on its stream, in an untimed pass of "
+                          f"{min(K, 5)} steps after the timed region"}
     if exe[0] is not None and dom_n:
         e_dom = exe[0] if fwd_dom else exe[1]
         roofline["tensor_executed_tflops"] = e_dom / (dom_ms1 / 1000.0) / 1e12
         roofline["tensor_executed_frac_of_bf16_sustained"] = roofline["tensor_executed_tflops"] / pk["bf16_tflops_sustained"]
 
-    # end to end through the C ABI with host buffers: H2D (q, z) -> step -> D2H (q, H, accepted)
+    # ---- end to end through the C ABI with host buffers: H2D (q, z) -> step -> D2H (q, H, accepted)
     e2e = None
     if not args.no_e2e:
         qh = q.detach().cpu().pin_memory()
-        zh = zs[:K].detach().cpu().pin_memory()
         q_back = torch.empty_like(qh).pin_memory()
-        hh = torch.empty(2, dtype=torch.float64).pin_memory()
-        ah = torch.empty(1, dtype=torch.int32).pin_memory()
-        zdev = torch.empty_like(q)
+        rec_h = torch.empty(5, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         e_ms = 0.0
         for i in range(K):
@@ -506,18 +609,41 @@ def main():
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
             q.copy_(qh, non_blocking=True)
-            zdev.copy_(zh[i], non_blocking=True)
-            h.precond_apply(0, zdev, out=p)
-            h.leapfrog(q, p, args.eps, args.traj, float(us[W + i]), h_out, acc)
+            h.hmc_chain(q, 1, args.traj, args.eps, A_MIN, seed, state, trace[W + i])
             q_back.copy_(q, non_blocking=True)
-            hh.copy_(h_out, non_blocking=True)
-            ah.copy_(acc, non_blocking=True)
+            rec_h.copy_(trace[W + i], non_blocking=True)
             b.record(st)
             torch.cuda.synchronize()
             e_ms += a.elapsed_time(b)
         e_rate, e_ms = job_rate(e_ms, K * evals_per_step, world, dist, dev)
         e2e = {"value": e_rate, "unit": "chi2+grad evals/s",
-               "h2d_bytes_per_step": 2 * 4 * h.n_params, "d2h_bytes_per_step": 4 * h.n_params + 16 + 4}
+               "h2d_bytes_per_step": 4 * h.n_params, "d2h_bytes_per_step": 4 * h.n_params + 5 * 8}
+
+    # ---- the other forms on the same workload (chi^2 + gradient alone) and every form's
+    # error against the FP64 oracle
+    forms, err, err_info = None, None, None
+    if rank == 0 and not args.no_forms:
+        q.copy_(th_true)
+        handles = {args.precision: h}
+        for pr in [x for x in ("fp16x3", "bf16x3", "fp32") if x != args.precision]:
+            hx = fm.ForwardModel(prob, pr, sigma=sigma)
+            hx.set_data(d)
+            hx.set_prior(mu_d, lam_d)
+            handles[pr] = hx
+        forms = {}
+        for pr, hx in handles.items():
+            n_eval = evals_per_step if pr != "fp32" else 3
+            rate, ms = time_chi2_grad(hx, q, n_eval, 3, flush, st)
+            forms[pr] = {"chi2_grad_evals_per_s": rate, "ms_per_eval": ms, "form": hx.contraction_info()["form"]}
+        if not args.no_err:
+            f0 = int(np.random.default_rng(3).integers(prob.n_freq))
+            err_all, err_info = errors_vs_fp64(prob, tr, handles, d, f0)
+            for pr in forms:
+                forms[pr]["err_vs_fp64"] = err_all[pr]
+            err = dict(err_all[args.precision], **err_info)
+        for pr, hx in handles.items():
+            if hx is not h:
+                hx.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -530,11 +656,14 @@ def main():
             "metric": METRIC, "value": value, "unit": "chi2+grad evals/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "precision": args.precision, "data": "synthetic",
-            "config": {"workload": workload_desc(prob, args.traj), "l2": "flushed between steps (256 MB write)",
+            "config": {"workload": workload_desc(prob, args.traj, args.block), "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "terms_per_s": value * prob.terms_per_forward(),
             "leapfrog_steps_per_s": world * K * args.traj / (total_ms / 1000.0),
-            "accepted_last": n_acc,
+            "err_vs_fp64": err,
+            "sampler": sampler,
+            "precond_build_s": t_pc,
+            "forms": forms,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line), flush=True)

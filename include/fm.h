@@ -157,6 +157,45 @@ FM_API int64_t fm_precond_size(fm_handle h);   /* doubles written by fm_get_prec
 FM_API fm_status fm_leapfrog(fm_handle h, void *dev_q, void *dev_p, double eps, int n_steps, double u_accept,
                       double *dev_h_out, int *dev_accepted_out, fm_stream stream);
 
+/* A Markov chain of Hessian-preconditioned HMC iterations run on the device (App. B: the
+ * momentum p = L z with z ~ N(0, 1), one leapfrog trajectory, the Metropolis test, and the
+ * adaptive step size of App. B).  Each of the n_iter iterations:
+ *   1. draws z (n_params normals) and the accept uniform u from the counter-based generator
+ *      Philox4x32-10 (Salmon et al., SC 2011) keyed by `seed`, at the iteration number
+ *      it = dev_state[1]: see fm_draw_normal and fm_draw_accept_uniform for the exact draws;
+ *   2. p = L z (fm_precond_apply op 0) and one fm_leapfrog trajectory of n_steps with step
+ *      eps = dev_state[0] and uniform u, in place on dev_q;
+ *   3. with a = min(1, exp(H0 - H1)) (0 when H0 or H1 is not finite): eps <- eps / 1.2 if
+ *      a < a_min, else eps <- min(eps0, 1.2 eps) (the paper's threshold is a_min = 0.2);
+ *      writes {eps used, H0, H1, accepted (0/1), a} to dev_trace[k][0..4] for the k-th
+ *      iteration of this call (dev_trace may be NULL), and advances dev_state[1] by 1.
+ * dev_q: device [n_params] (the chain state, updated in place); dev_state: device double[2]
+ * {step size > 0, iteration number (a whole number)}, read and updated by the device, so a
+ * chain continues across calls; dev_trace: device double[n_iter][5] or NULL.
+ * The first call for a given (dev_q, dev_state, n_steps) captures one iteration as a CUDA
+ * graph (after one chi^2 + gradient evaluation and a synchronisation of `stream`); every
+ * iteration is one launch of that graph on `stream`, and nothing is read back to the host.
+ * Needs fm_set_data and fm_build_precond first (FM_ERR_STATE otherwise).  A trajectory with a
+ * non-finite energy is rejected and raises FM_ERR_NONFINITE at the next fm_sync_status. */
+FM_API fm_status fm_hmc_chain(fm_handle h, void *dev_q, int n_iter, int n_steps, double eps0, double a_min,
+                              uint64_t seed, double *dev_state, double *dev_trace, fm_stream stream);
+/* kernel launches one iteration of the handle's captured chain makes (0 before the first call) */
+FM_API fm_status fm_chain_kernels(fm_handle h, int64_t *out);
+
+/* The chain's draws, for use and for checking: element i of the momentum draw at iteration
+ * `iteration` comes from the Philox4x32-10 block of counter (i / 4, iteration mod 2^32,
+ * iteration / 2^32, 0) and key (seed mod 2^32, seed / 2^32): its four output words w_j give
+ * u_j = (floor(w_j / 256) + 1/2) 2^-24, and elements 4g .. 4g+3 are
+ * r0 cos(2 pi u1), r0 sin(2 pi u1), r2 cos(2 pi u3), r2 sin(2 pi u3) with r_j = sqrt(-2 ln u_j)
+ * (Box-Muller), computed in FP32 and stored as float (fp64 = 0) or double (fp64 = 1) in
+ * dev_out[n].  The accept uniform of iteration it is (w_0 + 1/2) 2^-32 of counter
+ * (0, it mod 2^32, it / 2^32, 1); fm_draw_accept_uniform writes those of iterations
+ * iteration0 .. iteration0 + n - 1 to dev_out[n] (double). */
+FM_API fm_status fm_draw_normal(uint64_t seed, uint64_t iteration, int64_t n, void *dev_out, int fp64,
+                                fm_stream stream);
+FM_API fm_status fm_draw_accept_uniform(uint64_t seed, uint64_t iteration0, int64_t n, double *dev_out,
+                                        fm_stream stream);
+
 /* Batched trajectories over independent problems (one HMC chain per handle; App. B for each
  * chain, the chains independent of one another).
  *

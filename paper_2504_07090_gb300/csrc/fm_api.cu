@@ -60,6 +60,7 @@ static fm_status dalloc_bytes(Ctx &c, void **p, size_t bytes)
 static void free_ctx(Ctx *c)
 {
     if (!c) return;
+    chain_release(*c);
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
     delete c;

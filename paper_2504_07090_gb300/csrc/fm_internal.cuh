@@ -106,6 +106,15 @@ struct ModesTc {
     uint8_t *legt_img = nullptr;   // Leg^T [N][D]               (adjoint, second product)
 };
 
+// Device parameter block of the HMC chain (k_chain.cu), rewritten before every call.
+struct ChainDev {
+    double eps0, a_min;               // initial (and largest) step, acceptance threshold of the step rule
+    uint32_t k0, k1;                  // Philox key: the seed
+    double it0;                       // iteration number at the start of the call (trace index origin)
+    double *trace;                    // [ntrace][5] per iteration: eps used, H0, H1, accepted, a (or NULL)
+    long long ntrace;
+};
+
 // Device workspace and state of one handle.
 struct Ctx {
     fm_config cfg;
@@ -128,7 +137,7 @@ struct Ctx {
     int pc_block = 0;
     double *pc_blocks = nullptr;      // FP64 GN blocks (sky then gain)
     void *pc_chol = nullptr;          // factors in the working real type
-    void *pc_ginv = nullptr;          // gain block (block 64 only): L_g^-1, its transpose, and L_g^-T L_g^-1
+    void *pc_ginv = nullptr;          // gain block (block 64 only), FP64: L_g, L_g^-1, L_g^-T and L_g^-T L_g^-1
     void *pc_linv = nullptr;          // inverses of the 64 x 64 sky-block factors (block 64 only)
     double *pc_tmp = nullptr;         // FP64 scratch of the gain-block inverse
     int64_t pc_size = 0;
@@ -150,10 +159,23 @@ struct Ctx {
     ModesTc mtc;
     // leapfrog scratch
     void *lf_q0 = nullptr, *lf_g = nullptr, *lf_z = nullptr;
-    void *lf_y = nullptr;             // [gain-block order] intermediate of the dense solves
+    void *lf_y = nullptr;             // [gain-block order] FP64 intermediate of the dense solves
     double *lf_scal = nullptr;
     double *lf_prm = nullptr;         // [2] eps, accept uniform of fm_leapfrog (read by the kernels)
+    // HMC chain (fm_hmc_chain): momentum buffers, device parameter block, the captured iteration
+    void *ch_z = nullptr, *ch_p = nullptr;
+    ChainDev *ch_dev = nullptr;
+    ChainDev ch_host{};
+    double *ch_h = nullptr;           // [2] H0, H1 of the last trajectory
+    int *ch_acc = nullptr;
+    cudaGraph_t ch_graph = nullptr;
+    cudaGraphExec_t ch_exec = nullptr;
+    void *ch_q = nullptr;
+    double *ch_state = nullptr;
+    int ch_steps = 0;
 };
+
+void chain_release(Ctx &c);           // the chain's graph (k_chain.cu)
 
 // --------------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);

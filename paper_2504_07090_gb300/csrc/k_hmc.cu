@@ -297,7 +297,8 @@ __global__ void __launch_bounds__(64) k_pc_chol_small(int n, const double *__res
 template <typename R>
 __global__ void __launch_bounds__(256) k_pc_chol_big(int n, const double *__restrict__ H, const R *__restrict__ lam,
                                                      long long lam_off, int have_prior, double *__restrict__ W,
-                                                     R *__restrict__ L, int *__restrict__ status)
+                                                     R *__restrict__ L, double *__restrict__ L64,
+                                                     int *__restrict__ status)
 {
     __shared__ int bad;
     const int tid = threadIdx.x;
@@ -338,16 +339,18 @@ __global__ void __launch_bounds__(256) k_pc_chol_big(int n, const double *__rest
     for (int e = tid; e < n * n; e += blockDim.x) {
         int r = e / n, q = e % n;
         L[e] = (q <= r) ? (R)W[e] : R(0);
+        if (L64) L64[e] = (q <= r) ? W[e] : 0.0;
     }
 }
 
 // Inverse of the dense lower-triangular gain-block factor W (FP64, row-major): thread j
 // solves W x = e_j by forward substitution in FP64 (x kept in Xd[j][.]), then stores
-// Ginv[r][j] = x_r in the working type.  Used by the leapfrog's dense solves, which then
-// become triangular matrix-vector products.
-template <typename R>
+// Ginv[r][j] = x_r.  Used by the leapfrog's dense solves, which then become triangular
+// matrix-vector products.  The gain block keeps FP64 throughout (factor, inverses, products):
+// the global gain phase is held by the prior alone, so the block's condition number
+// reaches 1e6 and a rounded inverse would misplace the data-constrained directions.
 __global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restrict__ W, double *__restrict__ Xd,
-                                                    R *__restrict__ Ginv, R *__restrict__ GinvT)
+                                                    double *__restrict__ Ginv, double *__restrict__ GinvT)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         double *x = Xd + (size_t)j * n;
@@ -360,17 +363,16 @@ __global__ void __launch_bounds__(128) k_pc_tri_inv(int n, const double *__restr
             x[r] = -a / row[r];
         }
         for (int r = 0; r < n; ++r) {
-            Ginv[(size_t)r * n + j] = (R)x[r];
-            GinvT[(size_t)j * n + r] = (R)x[r];
+            Ginv[(size_t)r * n + j] = x[r];
+            GinvT[(size_t)j * n + r] = x[r];
         }
     }
 }
 
 // The gain block of the inverse mass matrix, Gm = L_g^-T L_g^-1 (symmetric), from the FP64
 // inverse columns Xd[j][k] = (L_g^-1)[k][j]: Gm[r][c] = sum over k >= max(r, c) of
-// Xd[r][k] Xd[c][k], in FP64, rounded once.  A drift then needs one product with Gm.
-template <typename R>
-__global__ void k_pc_gm(int n, const double *__restrict__ Xd, R *__restrict__ Gm)
+// Xd[r][k] Xd[c][k], in FP64.  A drift then needs one product with Gm.
+__global__ void k_pc_gm(int n, const double *__restrict__ Xd, double *__restrict__ Gm)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
          e += (long long)gridDim.x * blockDim.x) {
@@ -378,7 +380,7 @@ __global__ void k_pc_gm(int n, const double *__restrict__ Xd, R *__restrict__ Gm
         const double *xr = Xd + (size_t)r * n, *xc = Xd + (size_t)c * n;
         double a = 0.0;
         for (int k = r > c ? r : c; k < n; ++k) a += xr[k] * xc[k];
-        Gm[e] = (R)a;
+        Gm[e] = a;
     }
 }
 
@@ -540,8 +542,20 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
         if (bs > 1) {
             k_pc_chol_small<R><<<(unsigned)nsky_blk, 64, 0, st>>>(bs, c.pc_blocks, (const R *)c.lam, 0,
                                                                   c.have_prior ? 1 : 0, Lf, c.status);
+            if (ng > 0 && !c.pc_ginv) {
+                if (cudaMalloc(&c.pc_ginv, 4 * sizeof(double) * (size_t)ng * ng) != cudaSuccess ||
+                    cudaMalloc(&c.pc_tmp, sizeof(double) * (size_t)ng * ng) != cudaSuccess) {
+                    rc = FM_ERR_ALLOC;
+                    set_error("cudaMalloc gain-block inverse");
+                    break;
+                }
+                c.allocs.push_back(c.pc_ginv);
+                c.allocs.push_back(c.pc_tmp);
+            }
+            // FP64 gain block: [0] L_g, [1] L_g^-1, [2] L_g^-T, [3] L_g^-T L_g^-1
+            double *G64 = (double *)c.pc_ginv;
             k_pc_chol_big<R><<<1, 256, 0, st>>>(ng, c.pc_blocks + sky_sz, (const R *)c.lam, c.n_sky,
-                                                c.have_prior ? 1 : 0, W, Lf + sky_sz, c.status);
+                                                c.have_prior ? 1 : 0, W, Lf + sky_sz, G64, c.status);
             if (!c.pc_linv) {
                 if (cudaMalloc(&c.pc_linv, sizeof(R) * (size_t)nsky_blk * tri_block_elems<R>()) != cudaSuccess) {
                     rc = FM_ERR_ALLOC;
@@ -553,20 +567,9 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
             smem_opt_in(k_pc_blk_inv<R>);
             k_pc_blk_inv<R><<<(unsigned)nsky_blk, 64, 2 * 64 * 65 * sizeof(double), st>>>(Lf, (R *)c.pc_linv);
             if (ng > 0) {
-                if (!c.pc_ginv) {
-                    if (cudaMalloc(&c.pc_ginv, 3 * c.rsz * (size_t)ng * ng) != cudaSuccess ||
-                        cudaMalloc(&c.pc_tmp, sizeof(double) * (size_t)ng * ng) != cudaSuccess) {
-                        rc = FM_ERR_ALLOC;
-                        set_error("cudaMalloc gain-block inverse");
-                        break;
-                    }
-                    c.allocs.push_back(c.pc_ginv);
-                    c.allocs.push_back(c.pc_tmp);
-                }
-                k_pc_tri_inv<R><<<cdiv(ng, 128), 128, 0, st>>>(ng, W, c.pc_tmp, (R *)c.pc_ginv,
-                                                               (R *)c.pc_ginv + (size_t)ng * ng);
-                k_pc_gm<R><<<cdiv((long long)ng * ng, 256), 256, 0, st>>>(ng, c.pc_tmp,
-                                                                         (R *)c.pc_ginv + 2 * (size_t)ng * ng);
+                k_pc_tri_inv<<<cdiv(ng, 128), 128, 0, st>>>(ng, W, c.pc_tmp, G64 + (size_t)ng * ng,
+                                                            G64 + 2 * (size_t)ng * ng);
+                k_pc_gm<<<cdiv((long long)ng * ng, 256), 256, 0, st>>>(ng, c.pc_tmp, G64 + 3 * (size_t)ng * ng);
             }
         } else {
             k_pc_chol_diag<R><<<cdiv(need, 256), 256, 0, st>>>(need, c.pc_blocks, (const R *)c.lam,
@@ -691,25 +694,25 @@ __device__ __forceinline__ void lower_mv_packed(const R *P, const R *vs, R &y0, 
 // (upper) of M[r][c] x_c with M = L_g, L_g^-1 or L_g^-T (row-major), one warp per row so
 // that all rows' loads are in flight together.  Outputs: y (scratch), kin[r] = y_r^2,
 // q[r] += eps y_r, out[r] = y_r (each when non-NULL).
-template <typename R>
-__global__ void __launch_bounds__(256) k_lf_dense(int n, const R *__restrict__ M, int lower,
-                                                  const R *__restrict__ x, R *__restrict__ y, double *__restrict__ kin,
+template <typename R, typename X>
+__global__ void __launch_bounds__(256) k_lf_dense(int n, const double *__restrict__ M, int lower,
+                                                  const X *__restrict__ x, double *__restrict__ y, double *__restrict__ kin,
                                                   R *__restrict__ q, const double *__restrict__ peps,
                                                   R *__restrict__ out)
 {
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (r >= n) return;
     const double eps = q ? *peps : 0.0;
-    const R *row = M + (size_t)r * n;
-    R a = 0;
+    const double *row = M + (size_t)r * n;
+    double a = 0;
     for (int cc = lane; cc < n; cc += 32)
-        if (lower ? cc <= r : cc >= r) a += row[cc] * x[cc];
+        if (lower ? cc <= r : cc >= r) a += row[cc] * (double)x[cc];
     a = warp_sum(a);
     if (lane == 0) {
         if (y) y[r] = a;
-        if (kin) kin[r] = (double)a * (double)a;
+        if (kin) kin[r] = a * a;
         if (q) q[r] += (R)(eps * a);
-        if (out) out[r] = a;
+        if (out) out[r] = (R)a;
     }
 }
 
@@ -719,7 +722,7 @@ __global__ void __launch_bounds__(256) k_lf_dense(int n, const R *__restrict__ M
 // outputs at base + r and the kinetic partial kin[r] = y_r^2 (when kin != NULL).
 template <typename R>
 struct LfDense {
-    const R *M;
+    const double *M;                  // FP64 (the gain block keeps FP64 throughout)
     int n, mode;
     long long base;
     unsigned nctas;
@@ -742,15 +745,16 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
         // ------------------------------------------------ dense gain rows, one warp per row
         const int r = (int)blockIdx.x * LF_WARPS + w;
         if (r >= dn.n) return;
-        const R *row = dn.M + (size_t)r * dn.n, *x = in + dn.base;
-        R a = 0;
+        const double *row = dn.M + (size_t)r * dn.n;
+        const R *x = in + dn.base;
+        double a = 0;
         for (int cc = lane; cc < dn.n; cc += 32)
-            if (dn.mode == 2 || (dn.mode == 1 ? cc <= r : cc >= r)) a += row[cc] * x[cc];
+            if (dn.mode == 2 || (dn.mode == 1 ? cc <= r : cc >= r)) a += row[cc] * (double)x[cc];
         a = warp_sum(a);
         if (lane == 0) {
-            if (dn.kin) dn.kin[r] = (double)a * (double)a;
+            if (dn.kin) dn.kin[r] = a * a;
             if (q && !mul) q[dn.base + r] += (R)(eps * a);
-            if (out) out[dn.base + r] = a;
+            if (out) out[dn.base + r] = (R)a;
         }
         return;
     }
@@ -898,12 +902,12 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
         const size_t smem = sizeof(R) * (size_t)LF_WARPS * ((mul ? 4096 : tri_block_elems<R>()) + 64);
         FM_CK(smem_opt_in(k_lf_tri<R>));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
-        // the gain block runs as extra warps of the same launch: one product with L_g (mul),
+        // the gain block runs as extra warps of the same launch: one FP64 product with L_g (mul),
         // L_g^-1 (fwd), L_g^-T (bwd) or L_g^-T L_g^-1 (fwd and bwd, no kinetic energy)
-        const R *Gi = (const R *)c.pc_ginv;
+        const double *G64 = (const double *)c.pc_ginv, *Gi = G64 + (size_t)ng * ng;
         LfDense<R> dn{nullptr, ng, 0, c.n_sky, 0u, nullptr};
         if (ng > 0) {
-            if (mul) { dn.M = L + (size_t)nb * bs * bs; dn.mode = 1; }
+            if (mul) { dn.M = G64; dn.mode = 1; }
             else if (fwd && bwd) { if (!kin_out) { dn.M = Gi + 2 * (size_t)ng * ng; dn.mode = 2; } }
             else if (fwd) { dn.M = Gi; dn.mode = 1; dn.kin = kin_out ? part + nb : nullptr; }
             else if (bwd) { dn.M = Gi + (size_t)ng * ng; dn.mode = 0; }
@@ -916,10 +920,10 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
         if (ng > 0 && !dn.M && fwd && bwd) {     // both solves with the kinetic energy: two products
             const long long base = c.n_sky;
             const unsigned dg = cdiv(ng, 8);
-            R *y = (R *)c.lf_y;
-            k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi, 1, in + base, y, part + nb, nullptr, peps, nullptr);
+            double *y = (double *)c.lf_y;
+            k_lf_dense<R, R><<<dg, 256, 0, st>>>(ng, Gi, 1, in + base, y, part + nb, nullptr, peps, nullptr);
             FM_CK_LAUNCH();
-            k_lf_dense<R><<<dg, 256, 0, st>>>(ng, Gi + (size_t)ng * ng, 0, y, nullptr, nullptr,
+            k_lf_dense<R, double><<<dg, 256, 0, st>>>(ng, Gi + (size_t)ng * ng, 0, y, nullptr, nullptr,
                                               q ? q + base : nullptr, peps, out ? out + base : nullptr);
             FM_CK_LAUNCH();
         }
@@ -955,7 +959,7 @@ static fm_status lf_ensure(Ctx &c)
         return FM_ERR_ALLOC;
     }
     c.allocs.push_back(c.lf_scal);
-    if (cudaMalloc(&c.lf_y, c.rsz * (size_t)(2 * c.A * c.NG + 1)) != cudaSuccess) {
+    if (cudaMalloc(&c.lf_y, sizeof(double) * (size_t)(2 * c.A * c.NG + 1)) != cudaSuccess) {
         set_error("cudaMalloc leapfrog scratch");
         return FM_ERR_ALLOC;
     }

@@ -32,7 +32,8 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_dat
            "fm_precond_size", "fm_leapfrog", "fm_precond_apply", "fm_set_profiling", "fm_get_profile",
            "fm_contraction_info", "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status",
            "fm_last_error", "fm_create_batch", "fm_batch_create", "fm_batch_leapfrog", "fm_batch_kernels",
-           "fm_batch_destroy", "fm_diag_bounded_wait"]
+           "fm_batch_destroy", "fm_diag_bounded_wait", "fm_hmc_chain", "fm_chain_kernels", "fm_draw_normal",
+           "fm_draw_accept_uniform"]
 CONTRACTION_FORMS = {0: "direct", 1: "antenna", 2: "hour_angle"}
 
 
@@ -101,6 +102,10 @@ def load(path: str = LIB_PATH):
     L.fm_batch_kernels.argtypes = [vp, POINTER(c_int64)]
     L.fm_batch_destroy.argtypes = [vp]
     L.fm_diag_bounded_wait.argtypes = [c_int64, vp, vp]
+    L.fm_hmc_chain.argtypes = [vp, vp, c_int, c_int, c_double, c_double, ctypes.c_uint64, vp, vp, vp]
+    L.fm_chain_kernels.argtypes = [vp, POINTER(c_int64)]
+    L.fm_draw_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64, c_int64, vp, c_int, vp]
+    L.fm_draw_accept_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, c_int64, vp, vp]
     for name in EXPORTS:
         if name not in ("fm_num_params", "fm_num_vis", "fm_precond_size", "fm_last_error", "fm_kernel_launches"):
             getattr(L, name).restype = c_int
@@ -113,6 +118,22 @@ def diag_bounded_wait(limit_cycles: int) -> int:
     out = torch.zeros(1, dtype=torch.int32, device="cuda")
     _check(load().fm_diag_bounded_wait(int(limit_cycles), _ptr(out), _stream()), "fm_diag_bounded_wait")
     return int(out.item())
+
+
+def draw_normal(seed: int, iteration: int, n: int, dtype=torch.float32) -> torch.Tensor:
+    """n standard normals of the chain's momentum draw (fm_draw_normal)."""
+    out = torch.empty(n, dtype=dtype, device="cuda")
+    _check(load().fm_draw_normal(int(seed), int(iteration), int(n), _ptr(out), 1 if dtype == torch.float64 else 0,
+                                 _stream()), "fm_draw_normal")
+    return out
+
+
+def draw_accept_uniform(seed: int, iteration0: int, n: int) -> torch.Tensor:
+    """Accept uniforms of iterations iteration0 .. iteration0 + n - 1 (fm_draw_accept_uniform)."""
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(load().fm_draw_accept_uniform(int(seed), int(iteration0), int(n), _ptr(out), _stream()),
+           "fm_draw_accept_uniform")
+    return out
 
 
 def kernel_launches() -> int:
@@ -246,6 +267,26 @@ class ForwardModel:
                                     float(eps), int(n_steps), float(u), _ptr(h_out), _ptr(acc_out), _stream()),
                "fm_leapfrog")
         return h_out, acc_out
+
+    def hmc_chain(self, q: torch.Tensor, n_iter: int, n_steps: int, eps0: float, a_min: float, seed: int,
+                  state: torch.Tensor, trace: torch.Tensor | None = None) -> torch.Tensor | None:
+        """n_iter device-side HMC iterations with the adaptive step (fm_hmc_chain); state is a
+        CUDA float64 tensor [2] = (step size, iteration number), updated in place; returns
+        trace [n_iter][5] = (eps used, H0, H1, accepted, a) when one is passed."""
+        if not (state.is_cuda and state.dtype == torch.float64 and state.numel() == 2 and state.is_contiguous()):
+            raise ValueError("state: need a contiguous CUDA float64 tensor of 2 elements")
+        if trace is not None and not (trace.is_cuda and trace.dtype == torch.float64 and trace.is_contiguous()
+                                      and trace.numel() >= 5 * n_iter):
+            raise ValueError("trace: need a contiguous CUDA float64 tensor of at least 5 n_iter elements")
+        _check(self.lib.fm_hmc_chain(self.h, self._t(q, self.n_params, "q"), int(n_iter), int(n_steps), float(eps0),
+                                     float(a_min), int(seed), _ptr(state), _ptr(trace), _stream()), "fm_hmc_chain")
+        return trace
+
+    def chain_kernels(self) -> int:
+        """Kernel launches one iteration of the captured chain makes (fm_chain_kernels)."""
+        out = c_int64()
+        _check(self.lib.fm_chain_kernels(self.h, byref(out)), "fm_chain_kernels")
+        return int(out.value)
 
     def precond_apply(self, op: int, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """op 0: L x, 1: L^-1 x, 2: L^-T x, 3: M^-1 x."""

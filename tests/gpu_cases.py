@@ -96,8 +96,9 @@ def to_pairs(z: np.ndarray) -> np.ndarray:
     return np.stack([z.real, z.imag], axis=-1)
 
 
-def make_case(name: str, noise: bool = True):
-    """Problem, oracle, truth, data d (oracle model + seeded noise), prior."""
+def make_case(name: str, noise: bool = True, prior=(0.05, 0.05)):
+    """Problem, oracle, truth, data d (oracle model + seeded noise), prior (sky width as a
+    fraction of the channel rms, gain width)."""
     p = synth.config(name)
     tr = synth.draw_truth(p)
     o = oracle.Oracle(p)
@@ -105,7 +106,7 @@ def make_case(name: str, noise: bool = True):
     p.sigma = 0.01 * float(np.mean(np.abs(m)))
     o.sigma = p.sigma
     d = m + (p.sigma * (tr.noise[..., 0] + 1j * tr.noise[..., 1]) if noise else 0.0)
-    mu, lam = synth.prior_for(p, tr.theta)
+    mu, lam = synth.prior_for(p, tr.theta, sky_frac=prior[0], gain_std=prior[1])
     return p, o, tr.theta.copy(), d, mu, lam
 
 
