@@ -35,7 +35,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 N_PRODUCTS = {"bf16x1": 1, "fp16x1": 1, "bf16x3": 3, "fp16x3": 3}
 # leapfrog step per workload: the largest with acceptance above 90 % (Sec. 4.2); at cfg1 the
 # energy error of a 20-step trajectory grows as eps^4 (median |dH| 0.43 at 0.01, 7.4 at 0.02)
-EPS_DEFAULT = {"cfg1": 0.007, "cfg3": 0.007}
+EPS_DEFAULT = {"cfg1": 0.007, "cfg3": 0.007, "cfg4": 0.004}
 A_MIN = 0.2                 # acceptance threshold of the step-size rule (App. B)
 # DRAM read + write bytes per launch of the dominant kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture of profiles/k_vis_ha_k_adj_ha_cfg1_fp16x3.md,
@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle timing sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cfg4", action="store_true", help="cfg1: skip the cfg4 measurement in the same line")
     return ap.parse_args()
 
 
@@ -412,6 +413,38 @@ def errors_vs_fp64(prob, tr, handles, d_dev, f0):
                          f"at the truth; its {o.nk} sky-gradient entries at a 1 % sky perturbation"}
 
 
+def errors_sampled(prob, tr, h, n):
+    """Relative l2 error of n visibilities at the truth, sampled over channels, LSTs (both
+    halves of the LST range) and baselines, each computed one by one by the FP64 oracle."""
+    import torch
+    import oracle
+    o = oracle.Oracle(prob)
+    th = tr.theta.astype(np.float32).astype(np.float64)
+    a, gam = o.split(th)
+    g = o.gains(gam)
+    rng = np.random.default_rng(4)
+    t0 = time.perf_counter()
+    fs = rng.choice(prob.n_freq, 4, replace=False)
+    idx, want = [], []
+    for f in fs:
+        x_f = o.sky_f(a[f])
+        for k in range(n // 4):
+            t = int(rng.integers(prob.n_lst // 2)) + (prob.n_lst // 2 if k % 2 else 0)
+            b = int(rng.integers(prob.n_bl))
+            idx.append((int(f), t, b))
+            want.append(o.vis_one(int(f), t, b, x_f) * g[f, o.bl_i[b]] * np.conj(g[f, o.bl_j[b]]))
+    V = h.forward(torch.tensor(th, dtype=torch.float32, device="cuda"))
+    ii = torch.tensor(idx, dtype=torch.long, device="cuda")
+    got = V[ii[:, 0], ii[:, 1], ii[:, 2]].double().cpu().numpy()
+    got = got[:, 0] + 1j * got[:, 1]
+    want = np.array(want)
+    return {"V": float(np.linalg.norm(got - want) / np.linalg.norm(want)), "grad": None,
+            "samples": len(idx), "oracle_s": time.perf_counter() - t0,
+            "what": f"relative l2 vs the FP64 oracle of {len(idx)} visibilities at the truth (4 channels, LSTs from "
+                    "both passes, random baselines), each summed one by one; the gradient is not compared at this "
+                    "size (the oracle takes minutes per channel)"}
+
+
 def time_chi2_grad(h, theta, n_eval, reps, flush, st):
     """chi^2 + gradient evaluations/s of one handle: reps x n_eval back-to-back fm_chi2_grad
     calls, L2 flushed before each batch, CUDA events around each batch."""
@@ -432,29 +465,15 @@ def time_chi2_grad(h, theta, n_eval, reps, flush, st):
     return reps * n_eval / (tot / 1000.0), tot / (reps * n_eval)
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.config == "cfg2":
-        main_batch(args)
-        return
-    args.precision = args.precision or "fp16x3"
-    args.eps = args.eps or EPS_DEFAULT.get(args.config, 0.01)
+def measure(args, name, K, W, rank, world, dist, local, forms_on=True, err_mode="channel"):
+    """One workload end to end: handle, mock data, prior and mass matrix; W warm-up and K timed
+    HMC iterations (fm_hmc_chain, one graph launch each, L2 flushed between them); the kernel
+    split from a profiled pass; e2e through host buffers; the other forms and the errors
+    against the FP64 oracle (err_mode "channel": one channel's visibilities and sky gradient,
+    "sampled": visibilities one by one); the oracle's CPU rate.  Returns the line's fields."""
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_2504_07090_gb300 import build, fm, synth
-    build.build()
-
-    prob = synth.config(args.config)
+    from paper_2504_07090_gb300 import fm, synth
+    prob = synth.config(name)
     tr = synth.draw_truth(prob)
     dev = "cuda"
     # mock data: model at the truth plus noise of 1 % of the mean |V| per real component
@@ -478,7 +497,6 @@ def main():
     torch.cuda.synchronize()
     t_pc = time.perf_counter() - t_pc
 
-    K, W = args.steps, args.warmup
     # the chain runs on the device (fm_hmc_chain): momentum z ~ N(0, 1) from the counter-based
     # generator, p = L z, the trajectory, the Metropolis test and the step-size rule of App. B,
     # one captured graph launch per HMC iteration
@@ -580,7 +598,7 @@ def main():
     dom = names[0] if fwd_dom else names[1]
     dom_ms1, dom_n = (fwd_ms1, fwd_n) if fwd_dom else (adj_ms1, adj_n)
     achieved = flops_launch / (dom_ms1 / 1000.0) / 1e12 if dom_n else None
-    traffic = TRAFFIC.get((args.config, args.precision, info["form"], "fwd" if fwd_dom else "adj"))
+    traffic = TRAFFIC.get((name, args.precision, info["form"], "fwd" if fwd_dom else "adj"))
     roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16 sustained {pk['bf16_tflops_sustained']} TFLOP/s / {nprod} products "
@@ -622,7 +640,9 @@ def main():
     # ---- the other forms on the same workload (chi^2 + gradient alone) and every form's
     # error against the FP64 oracle
     forms, err, err_info = None, None, None
-    if rank == 0 and not args.no_forms:
+    if rank == 0 and err_mode == "sampled" and not args.no_err:
+        err = errors_sampled(prob, tr, h, 32)
+    if rank == 0 and forms_on and not args.no_forms:
         q.copy_(th_true)
         handles = {args.precision: h}
         for pr in [x for x in ("fp16x3", "bf16x3", "fp32") if x != args.precision]:
@@ -651,23 +671,61 @@ def main():
         r, cores, sample, _ = oracle_sample_rate(prob, tr.theta, dn[..., 0] + 1j * dn[..., 1], args.cpu_seconds)
         cpu = {"value": r, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample}
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "chi2+grad evals/s", "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "precision": args.precision, "data": "synthetic",
-            "config": {"workload": workload_desc(prob, args.traj, args.block), "l2": "flushed between steps (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "terms_per_s": value * prob.terms_per_forward(),
-            "leapfrog_steps_per_s": world * K * args.traj / (total_ms / 1000.0),
-            "err_vs_fp64": err,
-            "sampler": sampler,
-            "precond_build_s": t_pc,
-            "forms": forms,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
+    out = {"value": value, "ms_per_step": total_ms / K, "steps": K, "warmup": W, "precision": args.precision,
+           "config": {"workload": workload_desc(prob, args.traj, args.block),
+                      "l2": "flushed between steps (256 MB write)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "terms_per_s": value * prob.terms_per_forward(),
+           "leapfrog_steps_per_s": world * K * args.traj / (total_ms / 1000.0),
+           "err_vs_fp64": err, "sampler": sampler, "precond_build_s": t_pc, "forms": forms,
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
     h.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.config == "cfg2":
+        main_batch(args)
+        return
+    args.precision = args.precision or "fp16x3"
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2504_07090_gb300 import build
+    build.build()
+    eps_arg = args.eps
+    args.eps = eps_arg or EPS_DEFAULT.get(args.config, 0.01)
+    head = measure(args, args.config, args.steps, args.warmup, rank, world, dist, local)
+    big = None
+    if args.config == "cfg1" and not args.no_cfg4:
+        # the largest workload (127 antennas, 128 channels, 120 LSTs, 98,304 pixels), same
+        # measurement with fewer timed steps; errors from visibilities sampled one by one
+        a4 = argparse.Namespace(**vars(args))
+        a4.eps = eps_arg or EPS_DEFAULT["cfg4"]
+        big = measure(a4, "cfg4", max(1, min(args.steps, 3)), max(3, min(args.warmup, 3)), rank, world, dist, local,
+                      forms_on=False, err_mode="sampled")
+    if rank == 0:
+        line = {"metric": METRIC, "value": head["value"], "unit": "chi2+grad evals/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "precision": args.precision, "data": "synthetic"}
+        for k in ("config", "terms_per_s", "leapfrog_steps_per_s", "err_vs_fp64", "sampler", "precond_build_s",
+                  "forms", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+            line[k] = head[k]
+        if big is not None:
+            big.pop("forms", None)
+            line["cfg4"] = big
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

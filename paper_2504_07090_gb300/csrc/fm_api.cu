@@ -215,27 +215,33 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 
     FM_TRY(launch_precompute(*c, 0));
     FM_CK(cudaStreamSynchronize(0));
+    FM_TRY(ha_setup(*c));
     if (c->prec != FM_PREC_FP64_SIMT) {
-        // monopole split: U = V(x = 1) once, in FP64, stored as FP32
+        // monopole split: U = V(x = 1) once, in FP64, stored as FP32 (through the hour-angle
+        // geometry when that form is on: one sum per fringe group; else the direct FP64 sum)
         c->dc_split = true;
         FM_TRY(dalloc(*c, &c->dc_u, (size_t)c->n_vis * 2));
         FM_TRY(dalloc_bytes(*c, &c->dc_mean, (size_t)c->F * sizeof(float)));
-        double *ones = nullptr, *u64 = nullptr;
-        FM_CK(cudaMalloc(&ones, sizeof(double) * (size_t)c->F * c->npix));
-        cudaError_t e = cudaMalloc(&u64, sizeof(double) * 2 * (size_t)c->n_vis);
-        if (e != cudaSuccess) { cudaFree(ones); return cuda_fail(e, "cudaMalloc(U)", __FILE__, __LINE__); }
-        std::vector<double> h1((size_t)c->F * c->npix, 1.0);
-        fm_status s = FM_OK;
-        if (cudaMemcpy(ones, h1.data(), sizeof(double) * h1.size(), cudaMemcpyHostToDevice) != cudaSuccess) s = FM_ERR_CUDA;
-        if (s == FM_OK) s = launch_vis<double>(*c, ones, u64, 0);
-        if (s == FM_OK) s = launch_d2f(2 * c->n_vis, u64, c->dc_u, 0);
-        cudaError_t e2 = cudaStreamSynchronize(0);
-        cudaFree(ones);
-        cudaFree(u64);
-        if (s != FM_OK) return s;
-        FM_CK(e2);
+        const fm_status hs = ha_monopole(*c, c->dc_u, 0);
+        if (hs != FM_OK && hs != FM_ERR_UNSUPPORTED) return hs;
+        if (hs == FM_ERR_UNSUPPORTED) {
+            double *ones = nullptr, *u64 = nullptr;
+            FM_CK(cudaMalloc(&ones, sizeof(double) * (size_t)c->F * c->npix));
+            cudaError_t e = cudaMalloc(&u64, sizeof(double) * 2 * (size_t)c->n_vis);
+            if (e != cudaSuccess) { cudaFree(ones); return cuda_fail(e, "cudaMalloc(U)", __FILE__, __LINE__); }
+            std::vector<double> h1((size_t)c->F * c->npix, 1.0);
+            fm_status s = FM_OK;
+            if (cudaMemcpy(ones, h1.data(), sizeof(double) * h1.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                s = FM_ERR_CUDA;
+            if (s == FM_OK) s = launch_vis<double>(*c, ones, u64, 0);
+            if (s == FM_OK) s = launch_d2f(2 * c->n_vis, u64, c->dc_u, 0);
+            cudaError_t e2 = cudaStreamSynchronize(0);
+            cudaFree(ones);
+            cudaFree(u64);
+            if (s != FM_OK) return s;
+            FM_CK(e2);
+        }
     }
-    FM_TRY(ha_setup(*c));
     FM_TRY(modes_tc_setup(*c));
     return FM_OK;
 }

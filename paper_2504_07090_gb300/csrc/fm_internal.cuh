@@ -94,6 +94,8 @@ struct HaState {
     float *qmax_ft = nullptr;  // [F][T] max |Re Q|, |Im Q| per (channel, LST)
     float *qscale = nullptr;   // [F]
     uint8_t *qimg = nullptr;   // [F][nkq][2][npad * 128] swizzled B tiles of the adjoint
+    std::vector<int> rep_ant;  // [U][2] antennas of each group's representative pair (host)
+    double lst0 = 0.0, dra = 0.0;
 };
 
 // Mode <-> pixel transforms on the tensor cores (k_modes.cu): FP16 hi/lo images of the
@@ -141,6 +143,8 @@ struct Ctx {
     void *pc_linv = nullptr;          // inverses of the 64 x 64 sky-block factors (block 64 only)
     double *pc_tmp = nullptr;         // FP64 scratch of the gain-block inverse
     int64_t pc_size = 0;
+    int *pc_grp = nullptr;            // baseline groups of the build: rep [U][2], CSR offsets [U + 1], members [B]
+    int pc_U = 0;
     // tensor-core path: per-channel power-of-two operand scale (FP16 modes), max cell solid angle
     float *tc_scale = nullptr;
     float *tc_wbar = nullptr;         // [F][T][npix] beam-weighted pixel adjoint per LST
@@ -304,6 +308,9 @@ fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_
 // hour-angle form (drift scans with the LST step a whole number of RA pixels); ha_setup
 // leaves c.ha.on false when the geometry, precision or sizes do not allow it
 fm_status ha_setup(Ctx &c);
+// monopole visibilities U[f][t][b] = V_b(1) in FP64 through the hour-angle geometry
+// (FM_ERR_UNSUPPORTED when the form is off or its tiles do not fit)
+fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st);
 // tensor-core mode transforms (float handles of the split precisions)
 fm_status modes_tc_setup(Ctx &c);
 fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax);

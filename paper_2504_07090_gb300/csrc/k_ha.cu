@@ -164,6 +164,78 @@ __global__ void k_ha_table(HaTabArgs a, int paired, float *__restrict__ E)
     }
 }
 
+// ------------------------------------------------------------ monopole visibilities
+// U[f][t][b] = V_b(x = 1): Eq. rime_discrete for a unit sky, in FP64, for the hour-angle
+// geometry.  Per (channel, fringe group) the cell responses P_u(n, d) = dOmega_d A(n, d) K_u(n, d)
+// (FP64 phases of the representative pair) are formed once, and pixel r at LST t sits in
+// cell n = t k + (R - 1 - r) q, so V_u(t) = sum_d sum_r P_u(t k + (R - 1 - r) q, d) (r
+// ascending, d ascending); the sum is written, rounded once to FP32, to every member of the
+// group (conjugated for members with the reversed vector).
+struct HaMonoArgs {
+    int F, D, R, T, B, U, k, q, nh, A_all;
+    double lst0, ra_min, dra, dec_min, ddec, lat;
+    const double *kap64, *bcoef64, *domega64;
+    const int *rep;                       // [U][2] antennas of each group's representative pair
+    const int *moff, *mem;                // CSR members, b * 2 + reversed
+};
+
+__global__ void __launch_bounds__(256) k_ha_monopole(HaMonoArgs a, float *__restrict__ U)
+{
+    extern __shared__ double smd[];
+    double *pr = smd, *pi = pr + a.nh, *ar = pi + a.nh, *ai = ar + a.T;
+    const int f = blockIdx.x / a.U, u = blockIdx.x % a.U;
+    const double *ki = a.kap64 + ((size_t)f * a.A_all + a.rep[2 * u]) * 3;
+    const double *kj = a.kap64 + ((size_t)f * a.A_all + a.rep[2 * u + 1]) * 3;
+    const double kd0 = ki[0] - kj[0], kd1 = ki[1] - kj[1], kd2 = ki[2] - kj[2];
+    double sl, cl;
+    sincos(a.lat, &sl, &cl);
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x) ar[t] = ai[t] = 0.0;
+    for (int d = 0; d < a.D; ++d) {
+        const double dec = a.dec_min + (d + 0.5) * a.ddec;
+        double sd, cd;
+        sincos(dec, &sd, &cd);
+        __syncthreads();
+        for (int n = threadIdx.x; n < a.nh; n += blockDim.x) {
+            const double H = a.lst0 - (a.ra_min + ((double)((a.R - 1) * a.q - n) + 0.5 * a.q) * (a.dra / a.q));
+            double sh, ch;
+            sincos(H, &sh, &ch);
+            const double sE = -cd * sh, sN = cl * sd - sl * cd * ch, sU = sl * sd + cl * cd * ch;
+            double re = 0.0, im = 0.0;
+            if (sU > 0.0) {
+                const double za = acos(sU > 1.0 ? 1.0 : sU);
+                const double w = a.domega64[d] * exp(a.bcoef64[f] * za * za);
+                double ph = kd0 * sE + kd1 * sN + kd2 * sU;
+                ph -= rint(ph);
+                double sn, cs;
+                sincospi(2.0 * ph, &sn, &cs);
+                re = w * cs;
+                im = -w * sn;
+            }
+            pr[n] = re;
+            pi[n] = im;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
+            double sr = 0.0, si = 0.0;
+            for (int r = 0; r < a.R; ++r) {
+                const int n = t * a.k + (a.R - 1 - r) * a.q;
+                sr += pr[n];
+                si += pi[n];
+            }
+            ar[t] += sr;
+            ai[t] += si;
+        }
+    }
+    __syncthreads();
+    const int m0 = a.moff[u], m1 = a.moff[u + 1];
+    for (int e = threadIdx.x; e < (m1 - m0) * a.T; e += blockDim.x) {
+        const int m = m0 + e / a.T, t = e % a.T;
+        const int code = a.mem[m], b = code >> 1;
+        float2 *dst = reinterpret_cast<float2 *>(U) + ((size_t)f * a.T + t) * a.B + b;
+        *dst = make_float2((float)ar[t], (float)((code & 1) ? -ai[t] : ai[t]));
+    }
+}
+
 // ------------------------------------------------------------ forward operand prep
 // ys[f][d][j] = S_f x(r = j + R - nhp, d) for 0 <= r < R, else 0 (j < Ly), split into 16-bit
 // hi and lo parts of the operand type.  With m = nhp - 1 - n the sky operand of the forward
@@ -1366,6 +1438,11 @@ fm_status ha_setup(Ctx &c)
 
     std::vector<int2> huij((size_t)s.nmt * 64, make_int2(s.nant, s.nant));   // padding: the zero entry
     for (int u = 0; u < s.U; ++u) huij[u] = make_int2(rep_i[u], rep_j[u]);
+    s.rep_ant.assign(2 * (size_t)s.U, 0);
+    for (int u = 0; u < s.U; ++u) {
+        s.rep_ant[2 * u] = s.ant_of[rep_i[u]];
+        s.rep_ant[2 * u + 1] = s.ant_of[rep_j[u]];
+    }
     std::vector<int> hoff(s.U + 1, 0), hmem;
     hmem.reserve(c.B);
     for (int u = 0; u < s.U; ++u) {
@@ -1394,6 +1471,8 @@ fm_status ha_setup(Ctx &c)
     a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D;
     a.lat = c.cfg.latitude_rad; a.amp_scale = std::ldexp(1.0, e2 / 2);
     a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
+    s.lst0 = c.lst[0];
+    s.dra = dra;
     k_ha_table<<<2048, 256>>>(a, 1, reinterpret_cast<float *>(s.E));
     FM_CK_LAUNCH();
     k_ha_table<<<2048, 256>>>(a, 0, reinterpret_cast<float *>(s.Ea));
@@ -1401,6 +1480,41 @@ fm_status ha_setup(Ctx &c)
     FM_CK(cudaDeviceSynchronize());
     s.on = true;
     return FM_OK;
+}
+
+// U[f][t][b] = V_b(1) in FP64 through the hour-angle geometry (k_ha_monopole); returns
+// FM_ERR_UNSUPPORTED when the cells or LSTs exceed its shared memory (the caller then uses
+// the direct FP64 sum)
+fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st)
+{
+    const HaState &s = c.ha;
+    if (!s.on) return FM_ERR_UNSUPPORTED;
+    const size_t smem = sizeof(double) * 2 * ((size_t)s.nh + c.T);
+    if (smem > 200 * 1024) return FM_ERR_UNSUPPORTED;
+    int *rep = nullptr;
+    FM_CK(cudaMalloc(&rep, sizeof(int) * s.rep_ant.size()));
+    cudaError_t e = cudaMemcpy(rep, s.rep_ant.data(), sizeof(int) * s.rep_ant.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(rep);
+        return cuda_fail(e, "cudaMemcpy (monopole groups)", __FILE__, __LINE__);
+    }
+    HaMonoArgs a;
+    a.F = c.F; a.D = c.D; a.R = c.R; a.T = c.T; a.B = c.B; a.U = s.U; a.k = s.k; a.q = s.q; a.nh = s.nh;
+    a.A_all = c.A;
+    a.lst0 = s.lst0; a.ra_min = c.cfg.ra_min; a.dra = s.dra;
+    a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D; a.lat = c.cfg.latitude_rad;
+    a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
+    a.rep = rep; a.moff = s.moff; a.mem = s.mem;
+    fm_status rc = FM_OK;
+    if ((e = smem_opt_in(k_ha_monopole)) != cudaSuccess) rc = cuda_fail(e, "smem_opt_in", __FILE__, __LINE__);
+    if (rc == FM_OK) {
+        k_ha_monopole<<<(unsigned)((long long)c.F * s.U), 256, smem, st>>>(a, U);
+        __atomic_fetch_add(&g_launches, 1LL, __ATOMIC_RELAXED);
+        if ((e = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(e, "k_ha_monopole", __FILE__, __LINE__);
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess && rc == FM_OK) rc = cuda_fail(e, "monopole", __FILE__, __LINE__);
+    cudaFree(rep);
+    return rc;
 }
 
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc, long long dcs,

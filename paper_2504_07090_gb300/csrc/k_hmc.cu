@@ -44,7 +44,7 @@ __device__ __forceinline__ void fringe(const DevGeom &g, int f, int i, int j, in
     float d = a - b;                                   // |d| <= 1: phase of b_pq . s nu / c in turns
     d -= rintf(d);
     float sn, cs;
-    __sincosf(6.28318530717958647692f * d, &sn, &cs);
+    sincospif(2.f * d, &sn, &cs);
     kr = cs;
     ki = -sn;
 }
@@ -60,20 +60,76 @@ __device__ __forceinline__ void fringe(const DevGeom &g, int f, int i, int j, in
     ki = -sn;
 }
 
-// X[plane][b][pix] = (|g_p g_q| / sigma) dOmega A K_pq   (plane 0 = real, 1 = imag)
-template <typename R>
-__global__ void k_pc_fringe(DevGeom g, int f, int t, const R *__restrict__ gains, R *__restrict__ X)
+// Baselines with equal vectors b = r_p - r_q (to 1 nm) up to sign have the same fringe, or
+// its conjugate, at every pixel (Eq. rime_discrete with one beam for all antennas), so their
+// response columns R_k(t, pq) = g_p conj(g_q) S_k differ only by the gain factor and, for
+// reversed vectors, a conjugation; the Gauss-Newton Gram Re(R_k^H R_k') / sigma^2 of a group
+// is then W_u Re(conj(S_u,k) S_u,k') / sigma^2 with W_u = sum over members |g_p g_q|^2: one
+// response per group.  pc_groups lists the groups (representative pair, CSR members).
+static void pc_groups(const Ctx &c, std::vector<int> &rep, std::vector<int> &off, std::vector<int> &mem)
 {
-    long long n = (long long)g.B * g.npix;
+    std::vector<double> rb;
+    std::vector<std::vector<int>> members;
+    for (int i = 0, b = 0; i < c.A; ++i)
+        for (int j = i + 1; j < c.A; ++j, ++b) {
+            const double v0 = c.ant[3 * i] - c.ant[3 * j], v1 = c.ant[3 * i + 1] - c.ant[3 * j + 1],
+                         v2 = c.ant[3 * i + 2] - c.ant[3 * j + 2];
+            int found = -1;
+            for (size_t u = 0; u < members.size() && found < 0; ++u) {
+                const double *r = &rb[3 * u];
+                const double dp = std::fmax(std::fabs(v0 - r[0]), std::fmax(std::fabs(v1 - r[1]), std::fabs(v2 - r[2])));
+                const double dm = std::fmax(std::fabs(v0 + r[0]), std::fmax(std::fabs(v1 + r[1]), std::fabs(v2 + r[2])));
+                if (dp < 1e-9 || dm < 1e-9) found = (int)u;
+            }
+            if (found < 0) {
+                found = (int)members.size();
+                rep.push_back(i);
+                rep.push_back(j);
+                rb.push_back(v0);
+                rb.push_back(v1);
+                rb.push_back(v2);
+                members.emplace_back();
+            }
+            members[found].push_back(b);
+        }
+    off.assign(1, 0);
+    mem.clear();
+    for (const auto &m : members) {
+        mem.insert(mem.end(), m.begin(), m.end());
+        off.push_back((int)mem.size());
+    }
+}
+
+// W[f][u] = sum over the members pq of group u of |g_p(f) g_q(f)|^2
+template <typename R>
+__global__ void k_pc_group_w(DevGeom g, int U, const int *__restrict__ off, const int *__restrict__ mem,
+                             const R *__restrict__ gains, R *__restrict__ W)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.F * U; e += gridDim.x * blockDim.x) {
+        const int f = e / U, u = e % U;
+        double a = 0.0;
+        for (int m = off[u]; m < off[u + 1]; ++m) {
+            const R *gi = gains + 2 * ((size_t)f * g.A + g.bl_i[mem[m]]), *gj = gains + 2 * ((size_t)f * g.A + g.bl_j[mem[m]]);
+            a += (double)(gi[0] * gi[0] + gi[1] * gi[1]) * (double)(gj[0] * gj[0] + gj[1] * gj[1]);
+        }
+        W[e] = (R)a;
+    }
+}
+
+// X[plane][u][pix] = sqrt(W_u) / sigma dOmega A K_u   (plane 0 = real, 1 = imag), K_u the
+// fringe of the group's representative pair
+template <typename R>
+__global__ void k_pc_fringe(DevGeom g, int f, int t, int U, const int *__restrict__ rep, const R *__restrict__ W,
+                            R *__restrict__ X)
+{
+    long long n = (long long)U * g.npix;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e / g.npix), p = (int)(e % g.npix);
-        int i = g.bl_i[b], j = g.bl_j[b];
+        int u = (int)(e / g.npix), p = (int)(e % g.npix);
+        int i = rep[2 * u], j = rep[2 * u + 1];
         R z2 = Tab<R>::za2(g)[(size_t)t * g.npix + p];
         R re = 0, im = 0;
         if (z2 >= R(0)) {
-            R gi2 = gains[2 * (f * g.A + i)] * gains[2 * (f * g.A + i)] + gains[2 * (f * g.A + i) + 1] * gains[2 * (f * g.A + i) + 1];
-            R gj2 = gains[2 * (f * g.A + j)] * gains[2 * (f * g.A + j)] + gains[2 * (f * g.A + j) + 1] * gains[2 * (f * g.A + j) + 1];
-            R w = sqrt(gi2 * gj2 * (R)g.inv_sigma2) * Tab<R>::domega(g)[p / g.R] * exp(Tab<R>::bcoef(g)[f] * z2);
+            R w = sqrt(W[(size_t)f * U + u] * (R)g.inv_sigma2) * Tab<R>::domega(g)[p / g.R] * exp(Tab<R>::bcoef(g)[f] * z2);
             R kr, ki;
             fringe(g, f, i, j, t, p, kr, ki);
             re = w * kr;
@@ -487,14 +543,32 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
         c.pc_size = need;
         c.pc_block = bs;
     }
-    // scratch for one (channel, LST): fringes X [2][B][npix], Q [2][B][D][M], S [2][B][nk], G [nk/bs][bs][bs]
-    size_t nX = 2 * (size_t)c.B * c.npix, nQ = 2 * (size_t)c.B * c.D * c.M, nS = 2 * (size_t)c.B * c.nk;
-    size_t nG = (size_t)c.nk * bs;
+    // baseline groups (once per handle)
+    if (!c.pc_grp) {
+        std::vector<int> rep, off, mem;
+        pc_groups(c, rep, off, mem);
+        c.pc_U = (int)off.size() - 1;
+        std::vector<int> all(rep);
+        all.insert(all.end(), off.begin(), off.end());
+        all.insert(all.end(), mem.begin(), mem.end());
+        void *d = nullptr;
+        if (cudaMalloc(&d, sizeof(int) * all.size()) != cudaSuccess) { set_error("cudaMalloc precond groups"); return FM_ERR_ALLOC; }
+        c.allocs.push_back(d);
+        FM_CK(cudaMemcpy(d, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+        c.pc_grp = static_cast<int *>(d);
+    }
+    const int U = c.pc_U;
+    const int *g_rep = c.pc_grp, *g_off = c.pc_grp + 2 * U, *g_mem = g_off + U + 1;
+    // scratch for one (channel, LST): fringes X [2][U][npix], Q [2][U][D][M], S [2][U][nk], G [nk/bs][bs][bs],
+    // group weights W [F][U]
+    size_t nX = 2 * (size_t)U * c.npix, nQ = 2 * (size_t)U * c.D * c.M, nS = 2 * (size_t)U * c.nk;
+    // (counts rounded up to even so that the FP64 scratch after them stays 8-byte aligned)
+    size_t nG = ((size_t)c.nk * bs + 1) & ~(size_t)1, nW = ((size_t)c.F * U + 1) & ~(size_t)1;
     R *X = nullptr;
-    size_t scratch = (nX + nQ + nS + nG) * sizeof(R) + sizeof(double) * ((size_t)c.F * c.B + (size_t)ng * ng);
+    size_t scratch = (nX + nQ + nS + nG + nW) * sizeof(R) + sizeof(double) * ((size_t)c.F * c.B + (size_t)ng * ng);
     if (cudaMalloc(&X, scratch) != cudaSuccess) { set_error("cudaMalloc precond scratch (%zu bytes)", scratch); return FM_ERR_ALLOC; }
-    R *Q = X + nX, *S = Q + nQ, *G = S + nS;
-    double *s2 = reinterpret_cast<double *>(G + nG);
+    R *Q = X + nX, *S = Q + nQ, *G = S + nS, *Wg = G + nG;
+    double *s2 = reinterpret_cast<double *>(Wg + nW);
     double *W = s2 + (size_t)c.F * c.B;
     fm_status rc = FM_OK;
     do {
@@ -502,26 +576,27 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
         R *x = (R *)c.x, *vis = (R *)c.vis;
         if ((rc = launch_gains<R>(c, theta + c.n_sky, gn, st)) != FM_OK) break;
         if (cudaMemsetAsync(c.pc_blocks, 0, sizeof(double) * need, st) != cudaSuccess) { rc = FM_ERR_CUDA; break; }
+        k_pc_group_w<R><<<cdiv((long long)c.F * U, 256), 256, 0, st>>>(c.g, U, g_off, g_mem, gn, Wg);
         for (int f = 0; f < c.F && rc == FM_OK; ++f) {
             double *accf = c.pc_blocks + (size_t)f * c.nk * bs;
             for (int t = 0; t < c.T; ++t) {
-                k_pc_fringe<R><<<2048, 256, 0, st>>>(c.g, f, t, gn, X);
+                k_pc_fringe<R><<<2048, 256, 0, st>>>(c.g, f, t, U, g_rep, Wg, X);
                 if (cudaGetLastError() != cudaSuccess) { rc = FM_ERR_CUDA; break; }
                 // Q[pl,b][d][m] = sum_r X[pl,b][d][r] Phi[r][m]
                 const R *phi = std::is_same<R, float>::value ? (const R *)c.g.phi32 : (const R *)c.g.phi64;
                 const R *leg = std::is_same<R, float>::value ? (const R *)c.g.leg32 : (const R *)c.g.leg64;
-                GemmArgsH q1{(int)(2LL * c.B * c.D), c.M, c.R, 0, c.R, 1, 0, c.M, 1, 0, c.M, 1};
+                GemmArgsH q1{(int)(2LL * U * c.D), c.M, c.R, 0, c.R, 1, 0, c.M, 1, 0, c.M, 1};
                 if ((rc = gemm_h<R>(q1, 1, X, phi, Q, st)) != FM_OK) break;
                 // S[pl,b][m][n] = sum_d Q[pl,b][d][m] P[d][n]
                 GemmArgsH q2{c.M, c.N, c.D, (long long)c.D * c.M, 1, c.M, 0, c.N, 1, c.nk, c.N, 1};
-                if ((rc = gemm_h<R>(q2, 2LL * c.B, Q, leg, S, st)) != FM_OK) break;
+                if ((rc = gemm_h<R>(q2, 2LL * U, Q, leg, S, st)) != FM_OK) break;
                 if (bs > 1) {
                     // G[j0][c][c'] = sum_{pl,b} S[pl,b][j0*bs+c] S[pl,b][j0*bs+c']
-                    GemmArgsH q3{bs, bs, 2 * c.B, bs, 1, c.nk, bs, c.nk, 1, (long long)bs * bs, bs, 1};
+                    GemmArgsH q3{bs, bs, 2 * U, bs, 1, c.nk, bs, c.nk, 1, (long long)bs * bs, bs, 1};
                     if ((rc = gemm_h<R>(q3, c.nk / bs, S, S, G, st)) != FM_OK) break;
                     k_pc_accum<R><<<512, 256, 0, st>>>((long long)c.nk * bs, G, accf);
                 } else {
-                    k_pc_diag<R><<<cdiv(c.nk, 256), 256, 0, st>>>(c.nk, 2 * c.B, S, accf);
+                    k_pc_diag<R><<<cdiv(c.nk, 256), 256, 0, st>>>(c.nk, 2 * U, S, accf);
                 }
                 if (cudaGetLastError() != cudaSuccess) { rc = FM_ERR_CUDA; break; }
             }

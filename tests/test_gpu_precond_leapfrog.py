@@ -31,8 +31,10 @@ def _oracle_blocks(o, th, lam, bs):
     return np.stack([blocks[k] for k in sorted(blocks)]), Hg
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("name,bs", [("tiny", 1), ("small", 64)])
+# small (7 antennas: 21 baselines in 9 groups) and ha37m (666 baselines in 63 groups) check
+# the build's one response per group of redundant baselines
+@pytest.mark.parametrize("prec,name,bs", [(pr, n, b) for pr in ("fp64", "fp32") for n, b in (("tiny", 1), ("small", 64))]
+                         + [("fp32", "ha37m", 64), ("fp16x3", "ha37m", 64), ("fp16x3", "ha37m", 1)])
 def test_gn_blocks_match_oracle(prec, name, bs, check_err):
     p, o, th, d, mu, lam = make_case(name)
     d, mu, lam = quant(prec, d, mu, lam)
@@ -43,8 +45,8 @@ def test_gn_blocks_match_oracle(prec, name, bs, check_err):
     sky, gain = _oracle_blocks(o, th, lam, bs)
     n_sky = sky.size
     tol = 1e-10 if prec == "fp64" else 1e-4
-    check_err(rel_l2(got[:n_sky], sky.reshape(-1)), tol, key("direct", "gn_sky", prec), f"{name} bs{bs}")
-    check_err(rel_l2(got[n_sky:], gain.reshape(-1)), tol, key("direct", "gn_gain", prec), f"{name} bs{bs}")
+    check_err(rel_l2(got[:n_sky], sky.reshape(-1)), tol, key("precond", "gn_sky", prec), f"{name} bs{bs}")
+    check_err(rel_l2(got[n_sky:], gain.reshape(-1)), tol, key("precond", "gn_gain", prec), f"{name} bs{bs}")
 
 
 def _oracle_mass(o, th, lam, bs):
@@ -112,7 +114,11 @@ def test_leapfrog_trajectory_matches_oracle(name, prec, form, eps, prior, check_
     check_err(e_p, tol_q, key(form, "lf_p", prec), name)
     # H0 = U(q0) + z.z/2: U carries the chi^2 error that the visibility bound implies
     check_err(e_h0, 1e-12 if exact else 1e-5, key(form, "H0", prec), name)
-    check_err(e_dh, 1e-9 if exact else 2e-2, key(form, "dH", prec), name)
+    # H1 - H0: U falls by about 1e4 along this trajectory (q0 is 0.5 % off the truth), and the
+    # model's visibility error (about 1e-6 of |m|, times |m| / |m - d| ~ 100 in U) moves with
+    # it, so the split modes' energy change carries an absolute error of order one (measured
+    # 0.73 fp16x3, 0.97 bf16x3); the direct FP32 form's 2e-4
+    check_err(e_dh, 1e-9 if exact else (2e-2 if form == "direct" else 1.5), key(form, "dH", prec), name)
     assert int(aout.item()) == 1
     # rejection restores q0: u just above the acceptance probability
     a = math.exp(min(0.0, H0 - H1))
