@@ -40,7 +40,8 @@ A_MIN = 0.2                 # acceptance threshold of the step-size rule (App. B
 # DRAM read + write bytes per launch of the dominant kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture of profiles/k_vis_ha_k_adj_ha_cfg1_fp16x3.md,
 # keyed (workload, precision, form, kernel); a kernel changed since its capture has no entry
-TRAFFIC = {}
+TRAFFIC = {("cfg1", "fp16x3", "hour_angle", "fwd"): 305.325568e6 + 4.501248e6,
+           ("cfg1", "fp16x3", "hour_angle", "adj"): 296.293632e6 + 7.320576e6}
 
 
 def parse():
@@ -61,6 +62,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cfg4", action="store_true", help="cfg1: skip the cfg4 measurement in the same line")
+    ap.add_argument("--no-cfg3", action="store_true", help="cfg1: skip the preconditioner / HVP measurement")
+    ap.add_argument("--no-cfg2", action="store_true", help="cfg1: skip the batched uneven-problem measurement")
+    ap.add_argument("--hvps", type=int, default=1000, help="cfg3: Gauss-Newton HVPs timed")
     return ap.parse_args()
 
 
@@ -263,20 +267,27 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 def main_batch(args):
+    """cfg2 alone (`--config cfg2`): one JSON line."""
+    import torch
+    from paper_2504_07090_gb300 import build
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    line = measure_batch(args, args.steps, args.warmup)
+    print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, K, W):
     """cfg2: independent HMC chains on problems of uneven size (antennas 7/19/37, 16/32/64
     channels, 512..16384 modes per channel, 20 LSTs).  One step = for every chain p = L z,
     then one launch of the CUDA graph holding every chain's trajectory (fm_batch_leapfrog)."""
     import torch
-    from paper_2504_07090_gb300 import build, fm, synth
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
+    from paper_2504_07090_gb300 import fm, synth
     prec = args.precision or "bf16x3"
     probs = synth.batch_problems(args.problems)
     dev = "cuda"
-    K, W = args.steps, args.warmup
+    t_setup = time.perf_counter()
     models, qs, ps, zs, forms = [], [], [], [], {}
     for k, prob in enumerate(probs):
         tr = synth.draw_truth(prob)
@@ -300,8 +311,11 @@ def main_batch(args):
         forms[f] = forms.get(f, 0) + 1
     torch.cuda.synchronize()
     batch = fm.Batch(models, qs, ps, args.traj)
+    t_setup = time.perf_counter() - t_setup
     n = len(models)
-    eps = [args.eps or 0.02] * n
+    # step per chain: cfg1's 0.007 scaled by the parameter count to the power -1/4 (the energy
+    # error of a trajectory grows as n_params eps^4), at most 0.03
+    eps = [args.eps or min(0.03, 0.007 * (1048872.0 / h.n_params) ** 0.25) for h in models]
     us = np.random.default_rng(20250431).random((K + W, n))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
@@ -332,6 +346,7 @@ def main_batch(args):
     clocks.end()
     clk = clocks.stop()
     launches = fm.kernel_launches() - l0 + K * batch.kernels()
+    acc_last = int(sum(int(a.item()) for a in batch.acc_out))
     for h in models:
         h.sync_status()
     total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
@@ -361,13 +376,15 @@ def main_batch(args):
                                f"({evals} chi2+grad evals)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU, concurrent graph branches"},
         "leapfrog_steps_per_s": K * n * args.traj / (total_ms / 1000.0),
-        "sequential_launch_ms_per_step": seq_ms,
+        "sequential_launch_ms_per_step": seq_ms, "setup_s": t_setup,
+        "sampler": {"eps": {"min": min(eps), "max": max(eps)}, "n_steps": args.traj,
+                    "accepted_in_last_step": acc_last, "chains": n},
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     batch.close()
     for h in models:
         h.close()
+    return line
 
 
 def errors_vs_fp64(prob, tr, handles, d_dev, f0):
@@ -443,6 +460,59 @@ def errors_sampled(prob, tr, h, n):
             "what": f"relative l2 vs the FP64 oracle of {len(idx)} visibilities at the truth (4 channels, LSTs from "
                     "both passes, random baselines), each summed one by one; the gradient is not compared at this "
                     "size (the oracle takes minutes per channel)"}
+
+
+def measure_cfg3(h, q, prob, flush, st, n_hvp):
+    """cfg3 on the cfg1 handle: the Gauss-Newton mass-matrix builds (diagonal and 64-blocks,
+    FP64 accumulation) and n_hvp Hessian-vector products with N(0, 1) vectors drawn on the
+    device (Philox), CUDA events around the loop; the HVP's error is checked against central
+    differences of the device gradient along sky-only vectors (exact: U is quadratic there)."""
+    import torch
+    from paper_2504_07090_gb300 import fm
+    out = {"workload": "cfg3: cfg1 sizes (1048872 parameters); diagonal and 64 x 64 block Gauss-Newton builds, "
+                       f"{n_hvp} HVPs with N(0,1) vectors"}
+    for bs in (1, 64):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.build_precond(q, bs)
+        torch.cuda.synchronize()
+        out[f"build_s_block{bs}"] = time.perf_counter() - t0
+    hv = torch.empty_like(q)
+    for full in (False, True):
+        n = n_hvp if not full else max(1, n_hvp // 10)
+        vs = [fm.draw_normal(777, k, h.n_params) for k in range(4)]
+        h.hvp(q, vs[0], full=full, out=hv)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for k in range(n):
+            v = fm.draw_normal(777, k, h.n_params) if k < 4 else vs[k % 4]
+            h.hvp(q, v, full=full, out=hv)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out["gn" if not full else "full"] = {"hvps": n, "hvp_per_s": n / (ms / 1000.0), "ms_per_hvp": ms / n,
+                                             "note": "each iteration also draws its N(0,1) vector on the device"}
+    # full Hessian along sky-only vectors against central differences of the gradient
+    n_sky = prob.n_sky_params
+    errs = []
+    g1, g2 = torch.empty_like(q), torch.empty_like(q)
+    for k in range(3):
+        v = fm.draw_normal(991, k, h.n_params)
+        v[n_sky:] = 0.0
+        v /= torch.linalg.norm(v)
+        hvk = h.hvp(q, v, full=True).double()
+        h.chi2_grad(q, g1)
+        # a step whose gradient change is as large as the gradient itself (FP32 gradients)
+        step = float(torch.linalg.norm(g1.double())) / float(torch.linalg.norm(hvk))
+        h.chi2_grad(q + step * v, g1)
+        h.chi2_grad(q - step * v, g2)
+        fd = (g1.double() - g2.double()) / (2.0 * step)
+        errs.append(float(torch.linalg.norm(fd - hvk) / torch.linalg.norm(fd)))
+    out["hvp_vs_gradient_differences"] = {"max_rel_l2": max(errs), "vectors": 3,
+                                          "what": "full HVP along sky-only unit vectors vs central differences of "
+                                                  "the device gradient (exact for any step: U is quadratic in the sky)"}
+    return out
 
 
 def time_chi2_grad(h, theta, n_eval, reps, flush, st):
@@ -671,6 +741,10 @@ def measure(args, name, K, W, rank, world, dist, local, forms_on=True, err_mode=
         r, cores, sample, _ = oracle_sample_rate(prob, tr.theta, dn[..., 0] + 1j * dn[..., 1], args.cpu_seconds)
         cpu = {"value": r, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample}
 
+    cfg3 = None
+    if rank == 0 and name == "cfg1" and not args.no_cfg3:
+        q.copy_(th_true)
+        cfg3 = measure_cfg3(h, q, prob, flush, st, args.hvps)
     out = {"value": value, "ms_per_step": total_ms / K, "steps": K, "warmup": W, "precision": args.precision,
            "config": {"workload": workload_desc(prob, args.traj, args.block),
                       "l2": "flushed between steps (256 MB write)",
@@ -678,7 +752,8 @@ def measure(args, name, K, W, rank, world, dist, local, forms_on=True, err_mode=
            "terms_per_s": value * prob.terms_per_forward(),
            "leapfrog_steps_per_s": world * K * args.traj / (total_ms / 1000.0),
            "err_vs_fp64": err, "sampler": sampler, "precond_build_s": t_pc, "forms": forms,
-           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+           "cfg3": cfg3}
     h.close()
     return out
 
@@ -714,6 +789,13 @@ def main():
         a4.eps = eps_arg or EPS_DEFAULT["cfg4"]
         big = measure(a4, "cfg4", max(1, min(args.steps, 3)), max(3, min(args.warmup, 3)), rank, world, dist, local,
                       forms_on=False, err_mode="sampled")
+    batch = None
+    if args.config == "cfg1" and not args.no_cfg2 and rank == 0:
+        a2 = argparse.Namespace(**vars(args))
+        a2.precision, a2.eps = None, None
+        batch = measure_batch(a2, max(1, min(args.steps, 3)), 3)
+        for k in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data", "dtype"):
+            batch.pop(k, None)
     if rank == 0:
         line = {"metric": METRIC, "value": head["value"], "unit": "chi2+grad evals/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -722,9 +804,14 @@ def main():
         for k in ("config", "terms_per_s", "leapfrog_steps_per_s", "err_vs_fp64", "sampler", "precond_build_s",
                   "forms", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
             line[k] = head[k]
+        if head.get("cfg3") is not None:
+            line["cfg3"] = head["cfg3"]
         if big is not None:
             big.pop("forms", None)
+            big.pop("cfg3", None)
             line["cfg4"] = big
+        if batch is not None:
+            line["cfg2"] = batch
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
