@@ -228,6 +228,20 @@ FM_API fm_status fm_batch_leapfrog(fm_batch b, const double *eps, const double *
 FM_API fm_status fm_batch_kernels(fm_batch b, int64_t *out);
 FM_API fm_status fm_batch_destroy(fm_batch b);
 
+/* High-pass delay filter along frequency on the model and the data (Eq. rime_filter), the
+ * Gaussian-process filter of Eq. gpr: F = I - C_fg (C_fg + C_noise)^-1 with
+ * C_fg[k][l] = sinc(2 tau_max_s (nu_k - nu_l)) (sinc(x) = sin(pi x) / (pi x): a top-hat of
+ * half-width tau_max_s seconds in delay) and C_noise = noise_ratio I (the paper: 250 ns and
+ * 1e-8), built on the host in FP64 and applied to every (LST, baseline) column.  With it on,
+ * fm_chi2_grad (and every trajectory) uses chi^2 = sum |F (m - d)|^2 / N~_ff with the diagonal
+ * N~_ff = sigma^2 sum_g F_fg^2 of the filtered noise F N F^T (Eq. filtered_noise), and its
+ * gradient.  fm_forward still returns the unfiltered model; fm_hvp returns
+ * FM_ERR_UNSUPPORTED; fm_build_precond builds the unfiltered Gauss-Newton mass matrix (any
+ * SPD mass matrix keeps the sampler exact).  tau_max_s <= 0 switches the filter off.
+ * Synchronous (host build and upload).  FM_ERR_UNSUPPORTED when the channel count exceeds the
+ * filter kernel's shared memory (128 channels in FP32, 64 in FP64). */
+FM_API fm_status fm_set_delay_filter(fm_handle h, double tau_max_s, double noise_ratio);
+
 /* Apply the preconditioner's block Cholesky factor L (M = L L^T, App. B) to a device
  * vector [n_params]: op 0: out = L in (momentum draw p = L p0);  op 1: out = L^-1 in
  * (z of the kinetic energy);  op 2: out = L^-T in (Laplace-approximation draw from

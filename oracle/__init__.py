@@ -196,6 +196,49 @@ class Oracle:
         dv = np.asarray(theta, dtype=np.float64) - (0.0 if mu is None else np.asarray(mu, dtype=np.float64))
         return 0.5 * float(np.sum(lam * dv * dv)), lam * dv
 
+    def grad_from_weights(self, theta, s_w):
+        """Gradient of chi^2 / 2 for per-visibility residual weights s_w[f, t, b] (the derivative
+        of chi^2 / 2 with respect to the conjugate model visibility): the chain rule through the
+        gains and the sky of the RIME sum (Sec. 2.3), as in chi2_grad with s_w = r / sigma^2."""
+        a, gam = self.split(theta)
+        g = self.gains(gam)
+        grad = np.zeros(self.n_par)
+        ggain = np.zeros((self.A, self.NG, 2))
+        bi, bj = self.bl_i, self.bl_j
+        for f in range(self.F):
+            x_f = self.sky_f(a[f])
+            xbar = np.zeros(self.npix)
+            X = self.gleg[f]
+            for t in range(self.T):
+                V = self.vis_ft(f, t, x_f)
+                sw = s_w[f, t]
+                self.adjoint_ft(f, t, np.conj(g[f, bi]) * g[f, bj] * sw, xbar)
+                ti = np.conj(sw) * np.conj(g[f, bj]) * V
+                tj = np.conj(sw) * g[f, bi] * V
+                for k in range(self.NG):
+                    np.add.at(ggain[:, k, 0], bi, X[k] * ti.real)
+                    np.add.at(ggain[:, k, 1], bi, -X[k] * ti.imag)
+                    np.add.at(ggain[:, k, 0], bj, X[k] * tj.real)
+                    np.add.at(ggain[:, k, 1], bj, X[k] * tj.imag)
+            grad[f * self.nk:(f + 1) * self.nk] += self.sky_adjoint_f(xbar)
+        grad[self.n_sky:] += ggain.reshape(-1)
+        return grad
+
+    def chi2_grad_filtered(self, theta, d, Fm, mu=None, lam=None):
+        """chi^2, U and grad U with the delay filter applied along frequency to the model and the
+        data (Eq. rime_filter): r~ = F (m - d) for every (LST, baseline), chi^2 = sum |r~|^2 / N~_ff
+        with the diagonal of the filtered noise N~ = F N F^T, N = sigma^2 I (Eq. filtered_noise),
+        and the gradient through the residual weights F^T (r~ / N~)."""
+        r = self.model(theta) - d
+        rt = np.einsum("fg,gtb->ftb", Fm, r)
+        ntil = self.sigma ** 2 * np.sum(Fm * Fm, axis=1)
+        chi2 = float(np.sum((rt.real ** 2 + rt.imag ** 2) / ntil[:, None, None]))
+        s_w = np.einsum("gf,gtb->ftb", Fm, rt / ntil[:, None, None])
+        grad = self.grad_from_weights(theta, s_w)
+        U = 0.5 * chi2
+        pu, pg = self.prior_terms(theta, mu, lam)
+        return chi2, U + pu, grad + pg
+
     def chi2_grad(self, theta, d, mu=None, lam=None, fts=None):
         """chi^2, U = chi^2/2 + prior, and grad U.  With ``fts`` only those (channel, LST)
         pairs contribute (the prior is then left out)."""
@@ -351,6 +394,17 @@ class Oracle:
         if lam is not None:
             Hg += np.diag(lam[self.n_sky:])
         return out, Hg
+
+
+# ------------------------------------------------------------- Eq. gpr
+def delay_filter(freq_hz, tau_max_s: float, noise_ratio: float) -> np.ndarray:
+    """The Gaussian-process high-pass filter of Eq. gpr, F = I - C_fg (C_fg + C_noise)^-1, with
+    C_fg[k, l] = sinc(2 tau_max (nu_k - nu_l)) (a top-hat of half-width tau_max in delay;
+    numpy's sinc(x) = sin(pi x) / (pi x)) and C_noise = noise_ratio * C_fg(0) I."""
+    nu = np.asarray(freq_hz, dtype=np.float64)
+    C = np.sinc(2.0 * tau_max_s * (nu[:, None] - nu[None, :]))
+    N = noise_ratio * np.eye(nu.size)
+    return np.eye(nu.size) - C @ np.linalg.inv(C + N)
 
 
 # --------------------------------------------------------------------- App. B

@@ -305,10 +305,20 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
     FM_TRY(vis_of_modes<R>(c, theta, x, vis, st));
     // hour-angle form: the epilogue forms the group sums of omega itself
     const bool groups = std::is_same<R, float>::value && c.ha.on;
-    FM_TRY(launch_chi2_chan<R>(c, vis, theta + c.n_sky, om, zp, c.chi2p, groups, st));   // gains formed inside
+    if (c.df_on) {
+        // delay filter: the filtered chi^2 and the residual weights sigma^2 F^T W F r, which the
+        // epilogue then uses in place of m - d (its own chi^2 partials are not used)
+        FM_TRY(launch_delay_filter<R>(c, vis, theta + c.n_sky, st));
+        FM_TRY(launch_chi2_chan<R>(c, vis, theta + c.n_sky, om, zp, c.chi2p, groups, st, (const R *)c.df_r));
+    } else {
+        FM_TRY(launch_chi2_chan<R>(c, vis, theta + c.n_sky, om, zp, c.chi2p, groups, st));   // gains formed inside
+    }
     FM_TRY(run_adjoint<R>(c, om, (R *)c.xbar, st, groups));
     FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, grad, st));
     FM_TRY(launch_gain_reduce_chan<R>(c, zp, grad + c.n_sky, st));
+    if (c.df_on)
+        return launch_prior_and_total<R>(c, theta, grad, c.df_chi2p, c.df_nparts, chi2_out, u_out, st, kick_p,
+                                         kick_prm, kick_frac);
     return launch_prior_and_total<R>(c, theta, grad, c.chi2p, c.F * c.T, chi2_out, u_out, st, kick_p, kick_prm,
                                      kick_frac);
 }
@@ -317,6 +327,7 @@ template <typename R>
 static fm_status run_hvp(Ctx &c, const R *theta, const R *v, R *hv, int full, cudaStream_t st)
 {
     if (!c.have_data) { set_error("fm_set_data has not been called"); return FM_ERR_STATE; }
+    if (c.df_on) { set_error("Hessian-vector products with the delay filter are not implemented"); return FM_ERR_UNSUPPORTED; }
     R *x = (R *)c.x, *xv = (R *)c.xv;
     FM_TRY(launch_gains<R>(c, theta + c.n_sky, (R *)c.gains, st));
     FM_TRY(launch_gains<R>(c, v + c.n_sky, (R *)c.dgains, st));

@@ -177,6 +177,12 @@ struct Ctx {
     void *ch_q = nullptr;
     double *ch_state = nullptr;
     int ch_steps = 0;
+    // delay filter along frequency (Eq. rime_filter): F [F][F] and the weights 1 / N~_ff in the
+    // working type, the residual buffer and the chi^2 partials of the filter pass
+    bool df_on = false;
+    void *df_F = nullptr, *df_w = nullptr, *df_r = nullptr;
+    double *df_chi2p = nullptr;
+    int df_nparts = 0;
 };
 
 void chain_release(Ctx &c);           // the chain's graph (k_chain.cu)
@@ -280,7 +286,7 @@ fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t 
 // gains are formed inside from the coefficients gamma [A][NG][2]
 template <typename R>
 fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zpart, double *chi2p, bool groups,
-                           cudaStream_t st);
+                           cudaStream_t st, const R *rin = nullptr);
 // grad_gain from zpart in one pass over (channel, LST)
 template <typename R>
 fm_status launch_gain_reduce_chan(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
@@ -321,6 +327,11 @@ fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, con
                         long long dcs = 0, bool xmax_ready = false);
 // q_ready: the group sums q32 / qmax_ft were already formed from omega (by the chi^2 epilogue)
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready = false);
+
+// delay filter (k_filter.cu): r = g_p conj(g_q) V - d into c.df_r, then in place
+// r <- sigma^2 F^T W F r with the filtered chi^2 partials in c.df_chi2p
+template <typename R>
+fm_status launch_delay_filter(Ctx &c, const R *vis, const R *gamma, cudaStream_t st);
 
 // preconditioner and leapfrog
 template <typename R>

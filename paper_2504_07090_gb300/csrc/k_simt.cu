@@ -490,7 +490,8 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
                                                         const R *__restrict__ gamma, R *__restrict__ omega,
                                                         R *__restrict__ zpart, double *__restrict__ chi2p, int U,
                                                         const int *__restrict__ moff, const int *__restrict__ mem,
-                                                        float *__restrict__ q32, float *__restrict__ qmax_ft)
+                                                        float *__restrict__ q32, float *__restrict__ qmax_ft,
+                                                        const R *__restrict__ rin)
 {
     using C2 = typename V2<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -518,6 +519,8 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
     const R is2 = (R)g.inv_sigma2;
     const C2 *vrow = reinterpret_cast<const C2 *>(vis) + (size_t)ft * g.B;
     const C2 *drow = reinterpret_cast<const C2 *>(data) + (size_t)ft * g.B;
+    // rin != NULL (delay filter): the residual weights come in precomputed, sigma^2 F^T W F r
+    const C2 *rrow = rin ? reinterpret_cast<const C2 *>(rin) + (size_t)ft * g.B : nullptr;
     C2 *orow = reinterpret_cast<C2 *>(omega) + (size_t)ft * g.B;
     R c2 = 0;   // a warp's terms in the working type; FP64 across warps
     for (int b = tid; b < g.B; b += CF_THREADS) {
@@ -525,8 +528,12 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
         const C2 V = vrow[b], d = drow[b], gi = sG[i], gj = sG[j];
         const R ggr = gi.x * gj.x + gi.y * gj.y, ggi = gi.y * gj.x - gi.x * gj.y;     // g_i conj(g_j)
         C2 r, om, ti, tj;
-        r.x = ggr * V.x - ggi * V.y - d.x;
-        r.y = ggr * V.y + ggi * V.x - d.y;
+        if (rrow) {
+            r = rrow[b];
+        } else {
+            r.x = ggr * V.x - ggi * V.y - d.x;
+            r.y = ggr * V.y + ggi * V.x - d.y;
+        }
         c2 += r.x * r.x + r.y * r.y;
         om.x = (ggr * r.x + ggi * r.y) * is2;
         om.y = (ggr * r.y - ggi * r.x) * is2;
@@ -653,7 +660,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gain_reduce_ft(DevGeom g, const 
 
 template <typename R>
 fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zpart, double *chi2p, bool groups,
-                           cudaStream_t st)
+                           cudaStream_t st, const R *rin)
 {
     const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
     if (smem > 227 * 1024 || c.A > CF_THREADS) {
@@ -662,7 +669,7 @@ fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zp
     }
     FM_CK(smem_opt_in(k_chi2_ft<R>));
     k_chi2_ft<R><<<c.F * c.T, CF_THREADS, smem, st>>>(c.g, vis, (const R *)c.data, gamma, omega, zpart, chi2p, c.ha.U,
-                                                c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft);
+                                                c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft, rin);
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -1076,7 +1083,7 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
 }
 
 #define FM_INST(R)                                                                                       \
-    template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t); \
+    template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t, const R *); \
     template fm_status launch_gain_reduce_chan<R>(Ctx &, const R *, R *, cudaStream_t);                 \
     template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int, unsigned *);    \
     template fm_status launch_modes_adjoint<R>(Ctx &, const R *, R *, cudaStream_t);                     \

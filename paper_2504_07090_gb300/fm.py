@@ -33,7 +33,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_dat
            "fm_contraction_info", "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status",
            "fm_last_error", "fm_create_batch", "fm_batch_create", "fm_batch_leapfrog", "fm_batch_kernels",
            "fm_batch_destroy", "fm_diag_bounded_wait", "fm_hmc_chain", "fm_chain_kernels", "fm_draw_normal",
-           "fm_draw_accept_uniform"]
+           "fm_draw_accept_uniform", "fm_set_delay_filter"]
 CONTRACTION_FORMS = {0: "direct", 1: "antenna", 2: "hour_angle"}
 
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
     L.fm_diag_bounded_wait.argtypes = [c_int64, vp, vp]
     L.fm_hmc_chain.argtypes = [vp, vp, c_int, c_int, c_double, c_double, ctypes.c_uint64, vp, vp, vp]
     L.fm_chain_kernels.argtypes = [vp, POINTER(c_int64)]
+    L.fm_set_delay_filter.argtypes = [vp, c_double, c_double]
     L.fm_draw_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64, c_int64, vp, c_int, vp]
     L.fm_draw_accept_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, c_int64, vp, vp]
     for name in EXPORTS:
@@ -281,6 +282,10 @@ class ForwardModel:
         _check(self.lib.fm_hmc_chain(self.h, self._t(q, self.n_params, "q"), int(n_iter), int(n_steps), float(eps0),
                                      float(a_min), int(seed), _ptr(state), _ptr(trace), _stream()), "fm_hmc_chain")
         return trace
+
+    def set_delay_filter(self, tau_max_s: float = 250e-9, noise_ratio: float = 1e-8):
+        """High-pass delay filter of the likelihood (fm_set_delay_filter); tau_max_s <= 0: off."""
+        _check(self.lib.fm_set_delay_filter(self.h, float(tau_max_s), float(noise_ratio)), "fm_set_delay_filter")
 
     def chain_kernels(self) -> int:
         """Kernel launches one iteration of the captured chain makes (fm_chain_kernels)."""
