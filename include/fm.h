@@ -85,7 +85,14 @@ typedef struct {
     double beam_ref_hz;
     double sigma_noise;          /* noise standard deviation per real component (Jy) */
     int precision;               /* fm_precision */
+    int beam_type;               /* FM_BEAM_GAUSSIAN (0, the FWHM above) or FM_BEAM_AIRY (1) */
+    double dish_ew_m, dish_ns_m; /* FM_BEAM_AIRY: aperture diameters along east-west and north-south
+                                    (Eq. airy): power beam (2 J1(x) / x)^2 with
+                                    x = (D_ns + sin^2(az) (D_ew - D_ns)) sin(za) pi nu / c,
+                                    az the azimuth from north through east */
 } fm_config;
+
+enum { FM_BEAM_GAUSSIAN = 0, FM_BEAM_AIRY = 1 };
 
 /* Create a handle: validates the configuration, allocates the device workspace and
  * runs the once-per-handle precompute on the device ("cached mode" of App. C):

@@ -36,7 +36,8 @@ class _Problem(ctypes.Structure):
                 ("ant_enu", POINTER(c_double)), ("freq_hz", POINTER(c_double)), ("lst_rad", POINTER(c_double)),
                 ("lat_rad", c_double), ("ra_min", c_double), ("ra_max", c_double),
                 ("dec_min", c_double), ("dec_max", c_double),
-                ("beam_fwhm_ref_rad", c_double), ("beam_ref_hz", c_double)]
+                ("beam_fwhm_ref_rad", c_double), ("beam_ref_hz", c_double),
+                ("beam_type", c_int), ("dish_ew", c_double), ("dish_ns", c_double)]
 
 
 def _dp(a: np.ndarray):
@@ -53,6 +54,10 @@ def lib():
         L.orc_get_geometry.argtypes = [c_void_p] + [POINTER(c_double)] * 7
         L.orc_beam.restype = c_double
         L.orc_beam.argtypes = [c_void_p, c_double, c_double]
+        L.orc_beam_dir.restype = c_double
+        L.orc_beam_dir.argtypes = [c_void_p, c_double, c_double, c_double, c_double]
+        L.orc_bessel_j1.restype = c_double
+        L.orc_bessel_j1.argtypes = [c_double]
         L.orc_sky.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
         L.orc_sky_adjoint.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double)]
         L.orc_vis_ft.argtypes = [c_void_p, c_int, c_int, POINTER(c_double), POINTER(c_double)]
@@ -65,6 +70,11 @@ def lib():
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def bessel_j1(x: float) -> float:
+    """J1 by Bessel's integral (the oracle's own evaluation, for its pins)."""
+    return float(lib().orc_bessel_j1(float(x)))
 
 
 class Oracle:
@@ -91,7 +101,9 @@ class Oracle:
                            _dp(self._ant), _dp(self._freq), _dp(self._lst),
                            float(prob.lat_rad), float(prob.ra_min), float(prob.ra_max),
                            float(prob.dec_min), float(prob.dec_max),
-                           float(prob.beam_fwhm_ref_rad), float(prob.beam_ref_hz))
+                           float(prob.beam_fwhm_ref_rad), float(prob.beam_ref_hz),
+                           int(getattr(prob, "beam_type", 0)), float(getattr(prob, "dish_ew_m", 0.0)),
+                           float(getattr(prob, "dish_ns_m", 0.0)))
         self._g = L.orc_create(ctypes.byref(self._p))
         if not self._g:
             raise MemoryError("orc_create failed")
@@ -120,6 +132,10 @@ class Oracle:
     # ------------------------------------------------------------------ pieces
     def beam(self, nu: float, s_up: float) -> float:
         return float(lib().orc_beam(self._g, float(nu), float(s_up)))
+
+    def beam_dir(self, nu: float, e: float, n: float, u: float) -> float:
+        """Total-power beam at the unit direction (east, north, up): Gaussian or Airy."""
+        return float(lib().orc_beam_dir(self._g, float(nu), float(e), float(n), float(u)))
 
     def split(self, theta: np.ndarray):
         theta = np.asarray(theta, dtype=np.float64)

@@ -13,7 +13,8 @@
  *     RA x Dec grid (Sec. 2.1, discretised RIME, Eq. rime_discrete; grid of Sec. 3.2);
  *   - the separable cos/sin(RA) x Legendre(Dec) mode basis evaluated pixel by pixel
  *     (Eq. fg_separable, Eq. eor_model; azimuthal periodicity of App. A.2);
- *   - the Gaussian primary beam (total-power response A of Eq. rime_integral);
+ *   - the primary beam (total-power response A of Eq. rime_integral): a Gaussian in zenith
+ *     angle, or the modified Airy pattern of Eq. airy squared, with J1 from Bessel's integral;
  *   - V_pq(nu,t) = sum_j dOmega_j A_j K_jpq B_j with K = exp(-2 pi i b_pq . s nu / c),
  *     b_pq = r_p - r_q, one baseline at a time (Eq. rime_integral, Eq. rime_discrete);
  *   - its adjoint with respect to the pixel values, baseline by baseline.
@@ -36,6 +37,8 @@ typedef struct {
     const double *lst_rad;   /* [n_lst] */
     double lat_rad, ra_min, ra_max, dec_min, dec_max;
     double beam_fwhm_ref_rad, beam_ref_hz;  /* fwhm <= 0: isotropic above the horizon */
+    int beam_type;                          /* 0 Gaussian, 1 Airy (Eq. airy) */
+    double dish_ew, dish_ns;                /* Airy aperture diameters (m) */
 } orc_problem;
 
 typedef struct {
@@ -172,6 +175,51 @@ void orc_get_geometry(const orc_geom *G, double *ra_c, double *dec_c, double *do
     if (gleg) memcpy(gleg, G->gleg, sizeof(double) * (size_t)P->n_freq * P->n_gain);
 }
 
+double orc_bessel_j1(double x)
+{
+    /* Bessel's integral J1(x) = (1 / 2 pi) int_0^2pi cos(tau - x sin tau) d tau, by the
+     * trapezoidal rule over the full period (exponentially convergent for this periodic,
+     * analytic integrand; 2 |x| + 64 nodes). */
+    int n = 2 * (int)fabs(x) + 64;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double tau = 2.0 * ORC_PI * k / n;
+        acc += cos(tau - x * sin(tau));
+    }
+    return acc / n;
+}
+
+double orc_beam_dir(const orc_geom *G, double nu, double e, double n, double u)
+{
+    /* Total-power beam at unit direction (east, north, up).  Airy (Eq. airy): (2 J1(x) / x)^2,
+     * x = D_eff sin(za) pi nu / c with D_eff = D_ns + sin^2(az) (D_ew - D_ns), the azimuth
+     * measured from north through east (sin(az) = e / sqrt(e^2 + n^2)), sin(za) = sqrt(e^2 + n^2). */
+    if (G->P.beam_type != 1) {
+        extern double orc_beam(const orc_geom *G, double nu, double s_up);
+        return orc_beam(G, nu, u);
+    }
+    if (u <= 0.0) return 0.0;
+    double sinza = sqrt(e * e + n * n);
+    if (sinza == 0.0) return 1.0;
+    double sin2az = (e * e) / (sinza * sinza);
+    double deff = G->P.dish_ns + sin2az * (G->P.dish_ew - G->P.dish_ns);
+    double x = deff * sinza * ORC_PI * nu / ORC_C_LIGHT;
+    double a;
+    if (x < 0.1) {
+        /* near the zenith the quotient J1(x) / x of an absolutely accurate J1 is not: the
+         * series 2 J1(x) / x = sum_k (-1)^k (x / 2)^(2k) / (k! (k + 1)!) instead */
+        double h2 = 0.25 * x * x, term = 1.0;
+        a = 1.0;
+        for (int k = 1; k < 8; ++k) {
+            term *= -h2 / ((double)k * (k + 1));
+            a += term;
+        }
+    } else {
+        a = 2.0 * orc_bessel_j1(x) / x;
+    }
+    return a * a;
+}
+
 double orc_beam(const orc_geom *G, double nu, double s_up)
 {
     /* Gaussian total-power beam in zenith angle, FWHM = fwhm_ref * ref_hz / nu, zero at
@@ -224,7 +272,7 @@ static void orc_pixel_weights(const orc_geom *G, int f, int t, const double *x_f
     double nu = G->freq[f];
     const double *s = G->s + 3 * (size_t)t * G->n_pix;
     for (int p = 0; p < G->n_pix; ++p)
-        w[p] = G->domega[p / R] * orc_beam(G, nu, s[3 * p + 2]) * (x_f ? x_f[p] : 1.0);
+        w[p] = G->domega[p / R] * orc_beam_dir(G, nu, s[3 * p], s[3 * p + 1], s[3 * p + 2]) * (x_f ? x_f[p] : 1.0);
 }
 
 void orc_vis_ft(const orc_geom *G, int f, int t, const double *x_f, double *V)
@@ -262,7 +310,7 @@ void orc_vis_one(const orc_geom *G, int f, int t, int b, const double *x_f, doub
     double bx = ri[0] - rj[0], by = ri[1] - rj[1], bz = ri[2] - rj[2];
     double re = 0.0, im = 0.0;
     for (int p = 0; p < np_; ++p) {
-        double w = G->domega[p / R] * orc_beam(G, nu, s[3 * p + 2]) * x_f[p];
+        double w = G->domega[p / R] * orc_beam_dir(G, nu, s[3 * p], s[3 * p + 1], s[3 * p + 2]) * x_f[p];
         if (w == 0.0) continue;
         double ph = -2.0 * ORC_PI * nu * (bx * s[3 * p] + by * s[3 * p + 1] + bz * s[3 * p + 2]) / ORC_C_LIGHT;
         re += w * cos(ph);
@@ -281,7 +329,7 @@ void orc_adjoint_ft(const orc_geom *G, int f, int t, const double *omega, double
     const double *s = G->s + 3 * (size_t)t * np_;
 #pragma omp parallel for schedule(static)
     for (int p = 0; p < np_; ++p) {
-        double w = G->domega[p / R] * orc_beam(G, nu, s[3 * p + 2]);
+        double w = G->domega[p / R] * orc_beam_dir(G, nu, s[3 * p], s[3 * p + 1], s[3 * p + 2]);
         if (w == 0.0) continue;
         double acc = 0.0;
         for (int b = 0; b < G->n_bl; ++b) {

@@ -93,6 +93,11 @@ static fm_status validate(const fm_config *cfg)
     if (!std::isfinite(cfg->latitude_rad) || std::fabs(cfg->latitude_rad) > kPi / 2) return invalid("latitude");
     if (!(cfg->sigma_noise > 0.0) || !std::isfinite(cfg->sigma_noise)) return invalid("sigma_noise must be > 0");
     if (cfg->beam_fwhm_ref_rad > 0.0 && !(cfg->beam_ref_hz > 0.0)) return invalid("beam_ref_hz must be > 0");
+    if (cfg->beam_type != FM_BEAM_GAUSSIAN && cfg->beam_type != FM_BEAM_AIRY) return invalid("unknown beam_type");
+    if (cfg->beam_type == FM_BEAM_AIRY &&
+        (!(cfg->dish_ew_m > 0.0) || !(cfg->dish_ns_m > 0.0) || !std::isfinite(cfg->dish_ew_m) ||
+         !std::isfinite(cfg->dish_ns_m)))
+        return invalid("the Airy beam needs dish_ew_m and dish_ns_m > 0");
     if (cfg->precision < FM_PREC_FP64_SIMT || cfg->precision > FM_PREC_FP16X3) return invalid("precision");
     long long npix = (long long)cfg->n_ra * cfg->n_dec;
     if (npix > (1LL << 30) || (long long)cfg->n_mode_ra * cfg->n_mode_dec > (1LL << 30))
@@ -142,6 +147,20 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
     FM_TRY(dalloc(*c, &d64, (size_t)c->F * c->A * 3)); g.kap64 = d64;
     FM_TRY(dalloc(*c, &d32, (size_t)c->F * c->A * 6)); g.kap32 = d32;
     FM_TRY(dalloc(*c, &d64, c->F)); g.bcoef64 = d64;
+    if (cfg->beam_type == FM_BEAM_AIRY) {
+        g.dish_ew = cfg->dish_ew_m;
+        g.dish_ns = cfg->dish_ns_m;
+        const size_t nb = (size_t)c->F * tp;
+        FM_TRY(dalloc(*c, &d32, nb)); g.beam32 = d32;
+        // FP64 table: kept by FP64 handles; FP32 handles use it once, for the FP64 monopole
+        // visibilities at create time, and free it afterwards
+        if (c->prec == FM_PREC_FP64_SIMT) { FM_TRY(dalloc(*c, &d64, nb)); g.beam64 = d64; }
+        else {
+            void *b = nullptr;
+            FM_CK(cudaMalloc(&b, sizeof(double) * nb));
+            g.beam64 = static_cast<double *>(b);
+        }
+    }
     FM_TRY(dalloc(*c, &d32, c->F)); g.bcoef32 = d32;
     FM_TRY(dalloc(*c, &d32, (size_t)c->npix)); g.dompix32 = d32;
     int *bl;
@@ -240,6 +259,11 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
             cudaFree(u64);
             if (s != FM_OK) return s;
             FM_CK(e2);
+        }
+        if (c->g.beam64) {                      // the FP64 beam table of an FP32 handle
+            FM_CK(cudaDeviceSynchronize());
+            cudaFree(const_cast<double *>(c->g.beam64));
+            c->g.beam64 = nullptr;
         }
     }
     FM_TRY(modes_tc_setup(*c));

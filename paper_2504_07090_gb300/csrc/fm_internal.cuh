@@ -45,7 +45,67 @@ struct DevGeom {
     int flat_array;           // every antenna has up = 0: phases need only east and north
     const int *bl_i, *bl_j;   // [B]
     int *status;              // device status word (fm_status codes)
+    // Airy beam (Eq. airy): tables of the power beam per (channel, LST, pixel); NULL for the
+    // Gaussian beam, which the kernels form from za2 and bcoef
+    const float *beam32;      // [F][T][npix]
+    const double *beam64;     // [F][T][npix] (FP64 handles)
+    double dish_ew, dish_ns;  // metres
+    const double *freq64;     // [F] channel frequencies (Hz)
 };
+
+// Bessel function of the first kind of order 1 in FP64: its power series
+// sum_k (-1)^k (x/2)^(2k+1) / (k! (k+1)!) for |x| <= 12, and Hankel's asymptotic expansion
+// J1(x) ~ sqrt(2 / (pi x)) (P cos w - Q sin w), w = x - 3 pi / 4, with
+// P = sum_k (-1)^k a_2k / x^2k, Q = sum_k (-1)^k a_2k+1 / x^(2k+1),
+// a_k = a_(k-1) (4 - (2k - 1)^2) / (8 k), a_0 = 1 (summed while the terms decrease) above.
+__host__ __device__ inline double bessel_j1(double x)
+{
+    const double ax = x < 0.0 ? -x : x;
+    double r;
+    if (ax <= 12.0) {
+        const double h = 0.5 * ax, h2 = h * h;
+        double term = h, sum = h;
+        for (int k = 1; k < 60; ++k) {
+            term *= -h2 / ((double)k * (double)(k + 1));
+            sum += term;
+            if ((term < 0 ? -term : term) < 1e-18 * (sum < 0 ? -sum : sum)) break;
+        }
+        r = sum;
+    } else {
+        double p = 1.0, q = 0.0, a = 1.0, xp = 1.0, last = 1e300;
+        for (int k = 1; k < 40; ++k) {
+            a *= (4.0 - (double)(2 * k - 1) * (2 * k - 1)) / (8.0 * k);
+            xp *= ax;
+            const double t = a / xp, at = t < 0 ? -t : t;
+            if (at > last || at < 1e-18) break;
+            last = at;
+            // even k -> P (sign (-1)^(k/2)), odd k -> Q (sign (-1)^((k-1)/2))
+            const double sg = ((k / 2) % 2 == 0) ? 1.0 : -1.0;
+            if (k % 2 == 0) p += sg * t;
+            else q += sg * t;
+        }
+        const double w = ax - 0.75 * kPi;
+        r = sqrt(2.0 / (kPi * ax)) * (p * cos(w) - q * sin(w));
+    }
+    return x < 0.0 ? -r : r;
+}
+
+// Power beam (2 J1(x) / x)^2 of Eq. airy at frequency nu and unit direction (east, north,
+// up): x = (D_ns n^2 + D_ew e^2) / sqrt(e^2 + n^2) pi nu / c (the effective diameter
+// D_ns + sin^2(az) (D_ew - D_ns) times sin(za)); zero at and below the horizon
+__host__ __device__ inline double airy_power(double nu, double e, double n, double u, double dew, double dns)
+{
+    if (!(u > 0.0)) return 0.0;
+    const double rho2 = e * e + n * n;
+    if (rho2 == 0.0) return 1.0;
+    const double x = (dns * n * n + dew * e * e) / sqrt(rho2) * kPi * nu / kCLight;
+    if (x < 1e-4) {
+        const double a = 1.0 - x * x / 8.0;
+        return a * a;
+    }
+    const double a = 2.0 * bessel_j1(x) / x;
+    return a * a;
+}
 
 template <typename R> struct Tab;
 template <> struct Tab<double> {

@@ -113,6 +113,9 @@ struct HaTabArgs {
     int ant[64];                          // table entry -> antenna index
     double lst0, ra_min, dra, dec_min, ddec, lat, amp_scale;
     const double *kap64, *bcoef64, *domega64;
+    int airy;                             // Airy beam (Eq. airy) instead of the Gaussian
+    double dew, dns;
+    const double *freq;
 };
 
 __global__ void k_ha_table(HaTabArgs a, int paired, float *__restrict__ E)
@@ -140,7 +143,8 @@ __global__ void k_ha_table(HaTabArgs a, int paired, float *__restrict__ E)
             const double sE = -cd * sh, sN = cl * sd - sl * cd * ch, sU = sl * sd + cl * cd * ch;
             if (sU > 0.0) {
                 const double za = acos(sU > 1.0 ? 1.0 : sU);
-                const double beta = a.domega64[d] * exp(a.bcoef64[f] * za * za);
+                const double beta = a.domega64[d] * (a.airy ? airy_power(a.freq[f], sE, sN, sU, a.dew, a.dns)
+                                                            : exp(a.bcoef64[f] * za * za));
                 const double amp = sqrt(beta) * a.amp_scale;
                 const double *kp = a.kap64 + ((size_t)f * a.A_all + a.ant[i]) * 3;
                 double ph = kp[0] * sE + kp[1] * sN + kp[2] * sU;
@@ -175,6 +179,9 @@ struct HaMonoArgs {
     int F, D, R, T, B, U, k, q, nh, A_all;
     double lst0, ra_min, dra, dec_min, ddec, lat;
     const double *kap64, *bcoef64, *domega64;
+    int airy;
+    double dew, dns;
+    const double *freq;
     const int *rep;                       // [U][2] antennas of each group's representative pair
     const int *moff, *mem;                // CSR members, b * 2 + reversed
 };
@@ -203,7 +210,8 @@ __global__ void __launch_bounds__(256) k_ha_monopole(HaMonoArgs a, float *__rest
             double re = 0.0, im = 0.0;
             if (sU > 0.0) {
                 const double za = acos(sU > 1.0 ? 1.0 : sU);
-                const double w = a.domega64[d] * exp(a.bcoef64[f] * za * za);
+                const double w = a.domega64[d] * (a.airy ? airy_power(a.freq[f], sE, sN, sU, a.dew, a.dns)
+                                                         : exp(a.bcoef64[f] * za * za));
                 double ph = kd0 * sE + kd1 * sN + kd2 * sU;
                 ph -= rint(ph);
                 double sn, cs;
@@ -1471,6 +1479,7 @@ fm_status ha_setup(Ctx &c)
     a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D;
     a.lat = c.cfg.latitude_rad; a.amp_scale = std::ldexp(1.0, e2 / 2);
     a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
+    a.airy = c.g.beam32 != nullptr; a.dew = c.g.dish_ew; a.dns = c.g.dish_ns; a.freq = c.g.freq64;
     s.lst0 = c.lst[0];
     s.dra = dra;
     k_ha_table<<<2048, 256>>>(a, 1, reinterpret_cast<float *>(s.E));
@@ -1504,6 +1513,7 @@ fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st)
     a.lst0 = s.lst0; a.ra_min = c.cfg.ra_min; a.dra = s.dra;
     a.dec_min = c.cfg.dec_min; a.ddec = (c.cfg.dec_max - c.cfg.dec_min) / c.D; a.lat = c.cfg.latitude_rad;
     a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
+    a.airy = c.g.beam32 != nullptr; a.dew = c.g.dish_ew; a.dns = c.g.dish_ns; a.freq = c.g.freq64;
     a.rep = rep; a.moff = s.moff; a.mem = s.mem;
     fm_status rc = FM_OK;
     if ((e = smem_opt_in(k_ha_monopole)) != cudaSuccess) rc = cuda_fail(e, "smem_opt_in", __FILE__, __LINE__);

@@ -129,7 +129,9 @@ __global__ void k_pc_fringe(DevGeom g, int f, int t, int U, const int *__restric
         R z2 = Tab<R>::za2(g)[(size_t)t * g.npix + p];
         R re = 0, im = 0;
         if (z2 >= R(0)) {
-            R w = sqrt(W[(size_t)f * U + u] * (R)g.inv_sigma2) * Tab<R>::domega(g)[p / g.R] * exp(Tab<R>::bcoef(g)[f] * z2);
+            // Gaussian beam from the squared zenith angle; the Airy beam from its table
+            const R bm = g.beam32 ? (R)g.beam32[((size_t)f * g.T + t) * g.npix + p] : exp(Tab<R>::bcoef(g)[f] * z2);
+            R w = sqrt(W[(size_t)f * U + u] * (R)g.inv_sigma2) * Tab<R>::domega(g)[p / g.R] * bm;
             R kr, ki;
             fringe(g, f, i, j, t, p, kr, ki);
             re = w * kr;

@@ -132,6 +132,20 @@ __global__ void k_dompix(int npix, int R, const float *__restrict__ domega32, fl
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) dompix[p] = domega32[p / R];
 }
 
+// power beam of Eq. airy per (channel, LST, pixel), FP64, stored in both types
+__global__ void k_beam_airy(int F, long long tp, const double *__restrict__ freq, const double *__restrict__ s64,
+                            double dew, double dns, float *__restrict__ b32, double *__restrict__ b64)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)F * tp;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(e / tp);
+        const double *s = s64 + 3 * (e % tp);
+        const double v = airy_power(freq[f], s[0], s[1], s[2], dew, dns);
+        b32[e] = (float)v;
+        if (b64) b64[e] = v;
+    }
+}
+
 }  // namespace
 
 fm_status launch_precompute(Ctx &c, cudaStream_t st)
@@ -163,6 +177,13 @@ fm_status launch_precompute(Ctx &c, cudaStream_t st)
     FM_CK_LAUNCH();
     k_dompix<<<cdiv(c.npix, 256), 256, 0, st>>>(c.npix, c.R, c.g.domega32, const_cast<float *>(c.g.dompix32));
     FM_CK_LAUNCH();
+    c.g.freq64 = a.freq;
+    if (c.g.beam32) {
+        const long long tp = (long long)c.T * c.npix;
+        k_beam_airy<<<2048, 256, 0, st>>>(c.F, tp, a.freq, c.g.s64, c.g.dish_ew, c.g.dish_ns,
+                                          const_cast<float *>(c.g.beam32), const_cast<double *>(c.g.beam64));
+        FM_CK_LAUNCH();
+    }
     return FM_OK;
 }
 

@@ -63,9 +63,11 @@ template <> struct Phasor<double> {
 };
 
 // Beam-weighted solid angle dOmega_d A(za; nu) of pixel p at LST t.
+// (Gaussian beam from the squared zenith angle; the Airy beam from its table)
 template <typename R>
 __device__ __forceinline__ R pixel_weight(const DevGeom &g, int f, int t, int p)
 {
+    if (g.beam64) return Tab<R>::domega(g)[p / g.R] * (R)g.beam64[((size_t)f * g.T + t) * g.npix + p];
     R z2 = Tab<R>::za2(g)[(size_t)t * g.npix + p];
     if (z2 < R(0)) return R(0);
     return Tab<R>::domega(g)[p / g.R] * exp(Tab<R>::bcoef(g)[f] * z2);
@@ -73,6 +75,7 @@ __device__ __forceinline__ R pixel_weight(const DevGeom &g, int f, int t, int p)
 template <>
 __device__ __forceinline__ float pixel_weight<float>(const DevGeom &g, int f, int t, int p)
 {
+    if (g.beam32) return g.domega32[p / g.R] * g.beam32[((size_t)f * g.T + t) * g.npix + p];
     float z2 = g.za2_32[(size_t)t * g.npix + p];
     if (z2 < 0.f) return 0.f;
     return g.domega32[p / g.R] * __expf(g.bcoef32[f] * z2);

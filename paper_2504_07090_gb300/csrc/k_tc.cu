@@ -96,6 +96,7 @@ __device__ __forceinline__ void phasor_small(float d, float &er, float &ei)
 
 __device__ __forceinline__ float pixel_w(const DevGeom &g, int f, int t, int p)
 {
+    if (g.beam32) return g.domega32[p / g.R] * g.beam32[((size_t)f * g.T + t) * g.npix + p];
     float z2 = g.za2_32[(size_t)t * g.npix + p];
     if (z2 < 0.f) return 0.f;
     return g.domega32[p / g.R] * __expf(g.bcoef32[f] * z2);
@@ -237,8 +238,11 @@ k_vis_tc(DevGeom g, FwdLayout L, int rch, int sub, const float *__restrict__ x, 
                     const int f = f0 + r;
                     const float scale = ET == 1 ? chan_scale[f] : 1.f;
                     const float bc = g.bcoef32[f];
-                    const float wa = (za >= 0.f) ? da * __expf(bc * za) * x[(size_t)f * g.npix + pa] * scale : 0.f;
-                    const float wb = (zb >= 0.f) ? db * __expf(bc * zb) * x[(size_t)f * g.npix + pb] * scale : 0.f;
+                    const float *bt = g.beam32 ? g.beam32 + ((size_t)f * g.T + t) * g.npix : nullptr;
+                    const float ba = bt ? (va ? bt[pa] : 0.f) : ((za >= 0.f) ? __expf(bc * za) : 0.f);
+                    const float bb = bt ? (vb ? bt[pb] : 0.f) : ((zb >= 0.f) ? __expf(bc * zb) : 0.f);
+                    const float wa = va ? da * ba * x[(size_t)f * g.npix + pa] * scale : 0.f;
+                    const float wb = vb ? db * bb * x[(size_t)f * g.npix + pb] * scale : 0.f;
 #pragma unroll
                     for (int k = 0; k < KMAX; ++k) {
                         const int i = warp + FWD_PROD_WARPS * k;

@@ -52,7 +52,7 @@ class FmConfig(ctypes.Structure):
                 ("ra_min", c_double), ("ra_max", c_double), ("dec_min", c_double), ("dec_max", c_double),
                 ("n_mode_ra", c_int), ("n_mode_dec", c_int), ("n_gain_modes", c_int),
                 ("beam_fwhm_ref_rad", c_double), ("beam_ref_hz", c_double), ("sigma_noise", c_double),
-                ("precision", c_int)]
+                ("precision", c_int), ("beam_type", c_int), ("dish_ew_m", c_double), ("dish_ns_m", c_double)]
 
 
 _lib = None
@@ -169,7 +169,8 @@ def make_config(prob, precision: str | int = "fp32", sigma: float | None = None)
                    int(prob.n_ra), int(prob.n_dec), float(prob.ra_min), float(prob.ra_max), float(prob.dec_min),
                    float(prob.dec_max), int(prob.n_mode_ra), int(prob.n_mode_dec), int(prob.n_gain),
                    float(prob.beam_fwhm_ref_rad), float(prob.beam_ref_hz),
-                   float(prob.sigma if sigma is None else sigma), prec)
+                   float(prob.sigma if sigma is None else sigma), prec, int(getattr(prob, "beam_type", 0)),
+                   float(getattr(prob, "dish_ew_m", 0.0)), float(getattr(prob, "dish_ns_m", 0.0)))
     return cfg, (ant, freq, lst)
 
 

@@ -64,6 +64,9 @@ class Problem:
     sigma: float = 1.0             # noise std per real component (Jy)
     n_src: int = 200
     seed: int = 20250409
+    beam_type: int = 0             # 0 Gaussian, 1 modified Airy (Eq. airy)
+    dish_ew_m: float = 0.0         # Airy aperture diameters
+    dish_ns_m: float = 0.0
     extra: dict = field(default_factory=dict)
 
     @property
@@ -317,3 +320,12 @@ def random_data(prob: Problem, scale: float, seed: int) -> np.ndarray:
 
 def with_isotropic_beam(prob: Problem) -> Problem:
     return replace(prob, beam_fwhm_ref_rad=0.0)
+
+
+# modified Airy beam of a 14 m dish squashed along east-west (Eq. airy gives no diameters;
+# these are this library's choice)
+AIRY_DISH_EW_M, AIRY_DISH_NS_M = 12.0, 14.0
+
+
+def with_airy_beam(prob: Problem, dish_ew_m: float = AIRY_DISH_EW_M, dish_ns_m: float = AIRY_DISH_NS_M) -> Problem:
+    return replace(prob, beam_type=1, dish_ew_m=dish_ew_m, dish_ns_m=dish_ns_m)
