@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-cfg4", action="store_true", help="cfg1: skip the cfg4 measurement in the same line")
     ap.add_argument("--no-cfg3", action="store_true", help="cfg1: skip the preconditioner / HVP measurement")
     ap.add_argument("--no-cfg2", action="store_true", help="cfg1: skip the batched uneven-problem measurement")
+    ap.add_argument("--no-tune", action="store_true", help="cfg2: keep the default launch grids")
     ap.add_argument("--hvps", type=int, default=1000, help="cfg3: Gauss-Newton HVPs timed")
     return ap.parse_args()
 
@@ -310,12 +311,37 @@ def measure_batch(args, K, W):
         f = h.contraction_info()["form"]
         forms[f] = forms.get(f, 0) + 1
     torch.cuda.synchronize()
-    batch = fm.Batch(models, qs, ps, args.traj)
     t_setup = time.perf_counter() - t_setup
     n = len(models)
-    # step per chain: cfg1's 0.007 scaled by the parameter count to the power -1/4 (the energy
-    # error of a trajectory grows as n_params eps^4), at most 0.03
+    # launch grids per problem from the autotuner (timings cached by problem shape)
     eps = [args.eps or min(0.03, 0.007 * (1048872.0 / h.n_params) ** 0.25) for h in models]
+    tune = None
+    if not args.no_tune:
+        from paper_2504_07090_gb300 import autotune
+        st0 = torch.cuda.current_stream()
+
+        def run_step():
+            b = fm.Batch(models, qs, ps, args.traj)
+            u0 = [0.5] * n
+            for k in range(n):
+                models[k].precond_apply(0, zs[k][0], out=ps[k])
+            b.run(eps, u0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st0)
+            for _ in range(2):
+                for k in range(n):
+                    models[k].precond_apply(0, zs[k][0], out=ps[k])
+                b.run(eps, u0)
+            e1.record(st0)
+            torch.cuda.synchronize()
+            b.close()
+            return e0.elapsed_time(e1) / 2
+
+        tune = autotune.tune_batch(models, qs, run_step)
+    batch = fm.Batch(models, qs, ps, args.traj)
+    # step per chain (set above): cfg1's 0.007 scaled by the parameter count to the power -1/4
+    # (the energy error of a trajectory grows as n_params eps^4), at most 0.03
     us = np.random.default_rng(20250431).random((K + W, n))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
@@ -376,7 +402,7 @@ def measure_batch(args, K, W):
                                f"({evals} chi2+grad evals)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "single GPU, concurrent graph branches"},
         "leapfrog_steps_per_s": K * n * args.traj / (total_ms / 1000.0),
-        "sequential_launch_ms_per_step": seq_ms, "setup_s": t_setup,
+        "sequential_launch_ms_per_step": seq_ms, "setup_s": t_setup, "autotune": tune,
         "sampler": {"eps": {"min": min(eps), "max": max(eps)}, "n_steps": args.traj,
                     "accepted_in_last_step": acc_last, "chains": n},
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk,

@@ -301,6 +301,17 @@ FM_API fm_status fm_sky_pixels_noalloc(int n_freq, int n_ra, int n_dec, int n_mo
  * disables form 2 and FM_HA_GROUPS=0 makes it compute every baseline separately. */
 FM_API fm_status fm_contraction_info(fm_handle h, int32_t *out);
 
+/* Launch grids of the hour-angle contraction kernels (the knobs of the autotuner,
+ * paper_2504_07090_gb300/autotune.py; the paper has no counterpart): ctas_fwd CTAs for the
+ * forward contraction (its work units are re-partitioned over them) and ctas_adj for the
+ * adjoint, each in [1, number of SMs], or 0 for one CTA per SM (the default).  Fewer CTAs let
+ * independent handles (the batched schedule) run side by side on the GPU.  The results change
+ * only by the order of the partial sums.  FM_ERR_UNSUPPORTED when the handle does not run the
+ * hour-angle form.  fm_get_launch_grids writes the grids in use to out[2] (host int32; 0 when
+ * the form is off).  Not to be called while work of the handle is in flight or captured. */
+FM_API fm_status fm_set_launch_grids(fm_handle h, int ctas_fwd, int ctas_adj);
+FM_API fm_status fm_get_launch_grids(fm_handle h, int32_t *out);
+
 /* Diagnostic of the device-side failure path (no counterpart in the paper): one CTA waits,
  * with the bounded mbarrier wait of the tensor-core kernels and a limit of limit_cycles SM
  * clocks (1 .. the kernels' own limit of 4e9), on a barrier that nothing arrives at, then

@@ -138,7 +138,9 @@ struct HaState {
     int npad = 0;              // LSTs per pass (at most 64) rounded up to 16 (MMA N)
     int Jc = 0, Ly = 0;        // forward sky image chunks; sky-strip length (16-bit elements)
     int Lyc = 0;               // strip elements one pass of at most 64 LSTs reads
-    int grid = 0, J = 0;       // forward CTAs; most CTAs sharing one (M-tile, channel) segment
+    int grid = 0, J = 0;       // forward CTAs; partial sums per (M-tile, channel) segment (vpart stride)
+    int J_alloc = 0;           // J of the default grid (the allocation)
+    int grid_adj = 0;          // adjoint CTAs (0: one per SM)
     float sp = 1.f;            // response scale 2^e (e even): the table holds sqrt(dOmega A) 2^(e/2)
     float2 *E = nullptr;       // [F][D][nbc][nant + 1][66] phasor table, cells paired (entry nant is zero; 2 pad cells)
     float2 *Ea = nullptr;      // the same table with one (Re, Im) per cell, for the adjoint
@@ -377,6 +379,8 @@ fm_status ha_setup(Ctx &c);
 // monopole visibilities U[f][t][b] = V_b(1) in FP64 through the hour-angle geometry
 // (FM_ERR_UNSUPPORTED when the form is off or its tiles do not fit)
 fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st);
+// launch grids of the hour-angle contraction kernels (0: one CTA per SM)
+fm_status ha_set_grids(Ctx &c, int ctas_fwd, int ctas_adj);
 // tensor-core mode transforms (float handles of the split precisions)
 fm_status modes_tc_setup(Ctx &c);
 fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax);

@@ -1224,7 +1224,7 @@ fm_status adj_ha_launch(Ctx &c, const HaDev &h, const float *omega, float *xbar,
                                                                             s.qmax_ft);
         FM_CK_LAUNCH();
     }
-    int grid = sm_count();
+    int grid = s.grid_adj > 0 ? s.grid_adj : sm_count();
     if (grid > c.F * c.D) grid = c.F * c.D;
     FM_CK(smem_opt_in(k_adj_ha<ET, X3>));
     // one pass per chunk of at most HA_TCHUNK LSTs; passes after the first add to xbar
@@ -1260,6 +1260,52 @@ static fm_status ha_alloc(Ctx &c, T **p, size_t count)
 // path is used for the tensor-core precisions when the LSTs are equally spaced by
 // k = 1 .. 32 RA pixels, n_ant <= 64, n_lst <= 64, n_ra <= 512 and the buffers take at most half of
 // the free device memory; otherwise c.ha.on stays false and the antenna form runs.
+// CTAs contributing to each (M-tile, channel) segment when the forward's Q work units are cut
+// into G contiguous ranges; sets s.grid and s.J (the most contributors of any segment)
+static void ha_partition(Ctx &c, int G, std::vector<int> &ncontrib)
+{
+    HaState &s = c.ha;
+    const int nchunk = c.D * s.nbc;
+    const long long Q = (long long)s.nmt * c.F * nchunk;
+    if (G > Q) G = (int)Q;
+    if (G < 1) G = 1;
+    s.grid = G;
+    ncontrib.assign((size_t)s.nmt * c.F, 0);
+    s.J = 1;
+    for (size_t seg = 0; seg < ncontrib.size(); ++seg) {
+        const int g0 = cta_of((long long)seg * nchunk, Q, G), g1 = cta_of((long long)(seg + 1) * nchunk - 1, Q, G);
+        ncontrib[seg] = g1 - g0 + 1;
+        if (ncontrib[seg] > s.J) s.J = ncontrib[seg];
+    }
+}
+
+// Launch grids of the hour-angle contraction kernels (the autotuner's knobs): ctas_fwd for the
+// forward (its unit partition is recomputed; 0 = one CTA per SM), ctas_adj for the adjoint
+// (0 = one CTA per SM).  The partial-sum buffer holds the default grid's contributors, and a
+// smaller grid never has more; a larger one is rejected.
+fm_status ha_set_grids(Ctx &c, int ctas_fwd, int ctas_adj)
+{
+    HaState &s = c.ha;
+    if (!s.on) { set_error("the handle does not run the hour-angle form"); return FM_ERR_UNSUPPORTED; }
+    const int sm = sm_count();
+    if (ctas_fwd < 0 || ctas_adj < 0 || ctas_fwd > sm || ctas_adj > sm) {
+        set_error("launch grids must be in [0, %d] CTAs (0: one per SM)", sm);
+        return FM_ERR_INVALID_ARG;
+    }
+    std::vector<int> ncontrib;
+    const int Jmax = s.J_alloc;
+    ha_partition(c, ctas_fwd > 0 ? ctas_fwd : sm, ncontrib);
+    if (s.J > Jmax) {                      // cannot happen for G <= the default; kept as a guard
+        ha_partition(c, sm, ncontrib);
+        set_error("forward grid needs %d partial sums per segment, %d allocated", s.J, Jmax);
+        return FM_ERR_INVALID_ARG;
+    }
+    s.J = Jmax;                            // the buffer's stride stays that of the allocation
+    FM_CK(cudaMemcpy(s.ncontrib, ncontrib.data(), sizeof(int) * ncontrib.size(), cudaMemcpyHostToDevice));
+    s.grid_adj = ctas_adj;
+    return FM_OK;
+}
+
 fm_status ha_setup(Ctx &c)
 {
     HaState &s = c.ha;
@@ -1397,19 +1443,10 @@ fm_status ha_setup(Ctx &c)
     for (int u = 0; u < s.U; ++u)
         for (int m : members[u]) bmap[m >> 1] = 2 * u + (m & 1);
 
-    // partition of the forward work units over the CTAs
-    const int nchunk = c.D * s.nbc;
-    const long long Q = (long long)s.nmt * c.F * nchunk;
-    int G = sm_count();
-    if (G > Q) G = (int)Q;
-    s.grid = G;
-    std::vector<int> ncontrib((size_t)s.nmt * c.F);
-    s.J = 1;
-    for (size_t seg = 0; seg < ncontrib.size(); ++seg) {
-        const int g0 = cta_of((long long)seg * nchunk, Q, G), g1 = cta_of((long long)(seg + 1) * nchunk - 1, Q, G);
-        ncontrib[seg] = g1 - g0 + 1;
-        if (ncontrib[seg] > s.J) s.J = ncontrib[seg];
-    }
+    // partition of the forward work units over the CTAs (the default grid: one CTA per SM;
+    // the partial-sum buffer is sized for it, and a smaller grid needs no more contributors)
+    std::vector<int> ncontrib;
+    ha_partition(c, sm_count(), ncontrib);
 
     // both kernels' tiles must fit in shared memory
     {
@@ -1439,6 +1476,7 @@ fm_status ha_setup(Ctx &c)
     FM_TRY(ha_alloc(c, &s.ys, ys_n));
     FM_TRY(ha_alloc(c, &s.xmax, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.vpart, vp_n));
+    s.J_alloc = s.J;
     FM_TRY(ha_alloc(c, &s.q32, q_n));
     FM_TRY(ha_alloc(c, &s.qmax_ft, (size_t)c.F * c.T));
     FM_TRY(ha_alloc(c, &s.qscale, (size_t)c.F));
@@ -1551,3 +1589,26 @@ fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_
 }
 
 }  // namespace fm
+
+using namespace fm;
+
+extern "C" fm_status fm_set_launch_grids(fm_handle h, int ctas_fwd, int ctas_adj)
+{
+    if (!h) {
+        set_error("invalid argument: handle is NULL");
+        return FM_ERR_INVALID_ARG;
+    }
+    return ha_set_grids(*reinterpret_cast<Ctx *>(h), ctas_fwd, ctas_adj);
+}
+
+extern "C" fm_status fm_get_launch_grids(fm_handle h, int32_t *out)
+{
+    if (!h || !out) {
+        set_error("invalid argument: handle and out are required");
+        return FM_ERR_INVALID_ARG;
+    }
+    const Ctx &c = *reinterpret_cast<const Ctx *>(h);
+    out[0] = c.ha.on ? c.ha.grid : 0;
+    out[1] = c.ha.on ? (c.ha.grid_adj > 0 ? c.ha.grid_adj : (sm_count() < c.F * c.D ? sm_count() : c.F * c.D)) : 0;
+    return FM_OK;
+}

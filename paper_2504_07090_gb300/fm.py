@@ -33,7 +33,7 @@ EXPORTS = ["fm_create", "fm_destroy", "fm_num_params", "fm_num_vis", "fm_set_dat
            "fm_contraction_info", "fm_kernel_launches", "fm_sky_pixels_noalloc", "fm_sync_status",
            "fm_last_error", "fm_create_batch", "fm_batch_create", "fm_batch_leapfrog", "fm_batch_kernels",
            "fm_batch_destroy", "fm_diag_bounded_wait", "fm_hmc_chain", "fm_chain_kernels", "fm_draw_normal",
-           "fm_draw_accept_uniform", "fm_set_delay_filter"]
+           "fm_draw_accept_uniform", "fm_set_delay_filter", "fm_set_launch_grids", "fm_get_launch_grids"]
 CONTRACTION_FORMS = {0: "direct", 1: "antenna", 2: "hour_angle"}
 
 
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
     L.fm_hmc_chain.argtypes = [vp, vp, c_int, c_int, c_double, c_double, ctypes.c_uint64, vp, vp, vp]
     L.fm_chain_kernels.argtypes = [vp, POINTER(c_int64)]
     L.fm_set_delay_filter.argtypes = [vp, c_double, c_double]
+    L.fm_set_launch_grids.argtypes = [vp, c_int, c_int]
+    L.fm_get_launch_grids.argtypes = [vp, POINTER(ctypes.c_int32)]
     L.fm_draw_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64, c_int64, vp, c_int, vp]
     L.fm_draw_accept_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, c_int64, vp, vp]
     for name in EXPORTS:
@@ -180,6 +182,7 @@ class ForwardModel:
     def __init__(self, prob, precision: str = "fp32", sigma: float | None = None):
         self.lib = load()
         self.precision = precision
+        self.prob = prob
         cfg, self._keep = make_config(prob, precision, sigma)
         h = c_void_p()
         _check(self.lib.fm_create(byref(cfg), byref(h)), "fm_create")
@@ -287,6 +290,15 @@ class ForwardModel:
     def set_delay_filter(self, tau_max_s: float = 250e-9, noise_ratio: float = 1e-8):
         """High-pass delay filter of the likelihood (fm_set_delay_filter); tau_max_s <= 0: off."""
         _check(self.lib.fm_set_delay_filter(self.h, float(tau_max_s), float(noise_ratio)), "fm_set_delay_filter")
+
+    def set_launch_grids(self, ctas_fwd: int, ctas_adj: int):
+        """CTAs of the hour-angle forward / adjoint contraction kernels (0: one per SM)."""
+        _check(self.lib.fm_set_launch_grids(self.h, int(ctas_fwd), int(ctas_adj)), "fm_set_launch_grids")
+
+    def launch_grids(self) -> tuple[int, int]:
+        out = (ctypes.c_int32 * 2)()
+        _check(self.lib.fm_get_launch_grids(self.h, out), "fm_get_launch_grids")
+        return int(out[0]), int(out[1])
 
     def chain_kernels(self) -> int:
         """Kernel launches one iteration of the captured chain makes (fm_chain_kernels)."""
