@@ -37,6 +37,7 @@ N_PRODUCTS = {"bf16x1": 1, "fp16x1": 1, "bf16x3": 3, "fp16x3": 3}
 # energy error of a 20-step trajectory grows as eps^4 (median |dH| 0.43 at 0.01, 7.4 at 0.02)
 EPS_DEFAULT = {"cfg1": 0.007, "cfg3": 0.007, "cfg4": 0.004}
 A_MIN = 0.2                 # acceptance threshold of the step-size rule (App. B)
+LEGENDRE_ORDERS = 6          # cfg1 compressed: 64 channels onto 6 Legendre orders (98,600 parameters)
 # DRAM read + write bytes per launch of the dominant kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture of profiles/k_vis_ha_k_adj_ha_cfg1_fp16x3.md,
 # keyed (workload, precision, form, kernel); a kernel changed since its capture has no entry
@@ -64,6 +65,8 @@ def parse():
     ap.add_argument("--no-cfg4", action="store_true", help="cfg1: skip the cfg4 measurement in the same line")
     ap.add_argument("--no-cfg3", action="store_true", help="cfg1: skip the preconditioner / HVP measurement")
     ap.add_argument("--no-cfg2", action="store_true", help="cfg1: skip the batched uneven-problem measurement")
+    ap.add_argument("--no-legendre", action="store_true",
+                    help="cfg1: skip the measurement with the sky compressed onto Legendre orders in frequency")
     ap.add_argument("--no-tune", action="store_true", help="cfg2: keep the default launch grids")
     ap.add_argument("--hvps", type=int, default=1000, help="cfg3: Gauss-Newton HVPs timed")
     return ap.parse_args()
@@ -83,7 +86,8 @@ def workload_desc(prob, traj, block=64):
     pc = "64-block" if block > 1 else "diagonal"
     return (f"{prob.name}: {prob.n_ant}-antenna hexagon ({prob.n_bl} baselines), {prob.n_freq} ch "
             f"{prob.freq_hz[0] / 1e6:.0f}-{prob.freq_hz[-1] / 1e6:.0f} MHz, {prob.n_lst} LSTs, "
-            f"{prob.n_dec}x{prob.n_ra} px, {prob.n_mode_ra}x{prob.n_mode_dec} modes/ch, "
+            f"{prob.n_dec}x{prob.n_ra} px, {prob.n_mode_ra}x{prob.n_mode_dec} modes/"
+            f"{'ch' if not prob.n_freq_modes else f'Legendre order ({prob.n_freq_modes} orders in frequency)'}, "
             f"{prob.n_params} params; one HMC iteration = p = L z + {traj}-step leapfrog ({traj + 1} chi2+grad evals), "
             f"{pc} Gauss-Newton mass matrix")
 
@@ -561,15 +565,18 @@ def time_chi2_grad(h, theta, n_eval, reps, flush, st):
     return reps * n_eval / (tot / 1000.0), tot / (reps * n_eval)
 
 
-def measure(args, name, K, W, rank, world, dist, local, forms_on=True, err_mode="channel"):
+def measure(args, name, K, W, rank, world, dist, local, forms_on=True, err_mode="channel", freq_modes=0):
     """One workload end to end: handle, mock data, prior and mass matrix; W warm-up and K timed
     HMC iterations (fm_hmc_chain, one graph launch each, L2 flushed between them); the kernel
     split from a profiled pass; e2e through host buffers; the other forms and the errors
     against the FP64 oracle (err_mode "channel": one channel's visibilities and sky gradient,
-    "sampled": visibilities one by one); the oracle's CPU rate.  Returns the line's fields."""
+    "sampled": visibilities one by one); the oracle's CPU rate.  freq_modes > 0 compresses the
+    sky onto that many Legendre orders in frequency.  Returns the line's fields."""
     import torch
     from paper_2504_07090_gb300 import fm, synth
     prob = synth.config(name)
+    if freq_modes:
+        prob = synth.with_freq_modes(prob, freq_modes)
     tr = synth.draw_truth(prob)
     dev = "cuda"
     # mock data: model at the truth plus noise of 1 % of the mean |V| per real component
@@ -768,7 +775,7 @@ def measure(args, name, K, W, rank, world, dist, local, forms_on=True, err_mode=
         cpu = {"value": r, "unit": "chi2+grad evals/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     cfg3 = None
-    if rank == 0 and name == "cfg1" and not args.no_cfg3:
+    if rank == 0 and name == "cfg1" and not freq_modes and not args.no_cfg3:
         q.copy_(th_true)
         cfg3 = measure_cfg3(h, q, prob, flush, st, args.hvps)
     out = {"value": value, "ms_per_step": total_ms / K, "steps": K, "warmup": W, "precision": args.precision,
@@ -815,6 +822,15 @@ def main():
         a4.eps = eps_arg or EPS_DEFAULT["cfg4"]
         big = measure(a4, "cfg4", max(1, min(args.steps, 3)), max(3, min(args.warmup, 3)), rank, world, dist, local,
                       forms_on=False, err_mode="sampled")
+    comp = None
+    if args.config == "cfg1" and not args.no_legendre:
+        # cfg1 with the sky compressed onto 6 Legendre orders in frequency (Eq. fg_legendre):
+        # 98,600 parameters, the same contraction kernels on the expanded channel modes
+        ak = argparse.Namespace(**vars(args))
+        ak.eps = eps_arg or EPS_DEFAULT["cfg1"]
+        ak.no_cpu_baseline = True
+        comp = measure(ak, "cfg1", max(1, min(args.steps, 5)), max(3, min(args.warmup, 3)), rank, world, dist, local,
+                       forms_on=False, err_mode="sampled", freq_modes=LEGENDRE_ORDERS)
     batch = None
     if args.config == "cfg1" and not args.no_cfg2 and rank == 0:
         a2 = argparse.Namespace(**vars(args))
@@ -836,6 +852,11 @@ def main():
             big.pop("forms", None)
             big.pop("cfg3", None)
             line["cfg4"] = big
+        if comp is not None:
+            comp.pop("forms", None)
+            comp.pop("cfg3", None)
+            comp.pop("cpu_baseline", None)
+            line["cfg1_legendre"] = comp
         if batch is not None:
             line["cfg2"] = batch
         print(json.dumps(line), flush=True)

@@ -13,8 +13,9 @@
  *    (re, im) in that real type.
  *  - Visibility layout: [n_freq][n_lst][n_bl] complex, baseline b enumerates the
  *    antenna pairs (p, q), p < q, row-major (0,1), (0,2), ..., (1,2), ...
- *  - Parameter vector theta (n_params reals): sky modes a[freq][m_ra][n_dec] first,
- *    then gain coefficients gamma[ant][k][re/im].
+ *  - Parameter vector theta (n_params reals): sky modes a[freq][m_ra][n_dec] first (or, with
+ *    n_freq_modes = K > 0, their Legendre-in-frequency coefficients a~[k][m_ra][n_dec]), then
+ *    gain coefficients gamma[ant][k][re/im].
  *  - All work is enqueued on `stream` (NULL = legacy default stream) and is
  *    asynchronous; outputs are valid once the stream reaches that point.
  *  - A handle owns its device workspace and is not thread-safe: one host thread
@@ -86,6 +87,10 @@ typedef struct {
     double sigma_noise;          /* noise standard deviation per real component (Jy) */
     int precision;               /* fm_precision */
     int beam_type;               /* FM_BEAM_GAUSSIAN (0, the FWHM above) or FM_BEAM_AIRY (1) */
+    int n_freq_modes;            /* 0: independent sky modes per channel; K >= 1 (K <= n_freq): the sky
+                                    modes of every channel are sum_{k<K} P_k(nu^) a~_k, Legendre
+                                    polynomials of the normalised frequency (Eq. fg_legendre), and the
+                                    parameters are a~ [K][n_mode_ra][n_mode_dec] then the gains */
     double dish_ew_m, dish_ns_m; /* FM_BEAM_AIRY: aperture diameters along east-west and north-south
                                     (Eq. airy): power beam (2 J1(x) / x)^2 with
                                     x = (D_ns + sin^2(az) (D_ew - D_ns)) sin(za) pi nu / c,
@@ -103,7 +108,8 @@ FM_API fm_status fm_create(const fm_config *cfg, fm_handle *out);
 /* Release the handle and all its device memory.  NULL is accepted. */
 FM_API fm_status fm_destroy(fm_handle h);
 
-FM_API int64_t fm_num_params(fm_handle h);     /* n_freq*n_mode_ra*n_mode_dec + 2*n_ant*n_gain_modes */
+FM_API int64_t fm_num_params(fm_handle h);     /* K*n_mode_ra*n_mode_dec + 2*n_ant*n_gain_modes, K = n_freq_modes
+                                                   (n_freq when that is 0) */
 FM_API int64_t fm_num_vis(fm_handle h);        /* n_freq*n_lst*n_bl complex visibilities */
 
 /* Data visibilities d (device, [n_freq][n_lst][n_bl] complex) used by the chi^2 of

@@ -95,8 +95,15 @@ class Oracle:
         self.nk = self.M * self.N
         self.B = self.A * (self.A - 1) // 2
         self.sigma = float(prob.sigma)
-        self.n_sky = self.F * self.nk
+        # Legendre-in-frequency compression (Eq. fg_legendre): a(nu_f) = sum_k X_k(nu_f) a~_k
+        self.K = int(getattr(prob, "n_freq_modes", 0) or 0)
+        self.n_sky_m = self.F * self.nk
+        self.n_sky = self.K * self.nk if self.K else self.n_sky_m
         self.n_par = self.n_sky + 2 * self.A * self.NG
+        if self.K:
+            lo, hi = float(np.min(self._freq)), float(np.max(self._freq))
+            nuh = 2.0 * (self._freq - lo) / (hi - lo) - 1.0 if hi > lo else np.zeros(self.F)
+            self.Xf = np.polynomial.legendre.legvander(nuh, self.K - 1)     # [F, K]
         self._p = _Problem(self.A, self.F, self.T, self.R, self.D, self.M, self.N, self.NG,
                            _dp(self._ant), _dp(self._freq), _dp(self._lst),
                            float(prob.lat_rad), float(prob.ra_min), float(prob.ra_max),
@@ -138,10 +145,21 @@ class Oracle:
         return float(lib().orc_beam_dir(self._g, float(nu), float(e), float(n), float(u)))
 
     def split(self, theta: np.ndarray):
+        """Per-channel sky modes a[f, j] (expanded from the Legendre coefficients when the sky is
+        compressed in frequency) and the gain coefficients."""
         theta = np.asarray(theta, dtype=np.float64)
-        a = theta[: self.n_sky].reshape(self.F, self.nk)
+        if self.K:
+            a = self.Xf @ theta[: self.n_sky].reshape(self.K, self.nk)
+        else:
+            a = theta[: self.n_sky].reshape(self.F, self.nk)
         gam = theta[self.n_sky:].reshape(self.A, self.NG, 2)
         return a, gam
+
+    def sky_to_params(self, g_sky: np.ndarray) -> np.ndarray:
+        """A per-channel sky gradient [F, nk] in the parameters' coordinates (the transpose of
+        the expansion when the sky is compressed in frequency), flattened."""
+        g_sky = np.asarray(g_sky).reshape(self.F, self.nk)
+        return (self.Xf.T @ g_sky).reshape(-1) if self.K else g_sky.reshape(-1)
 
     def sky_f(self, a_f: np.ndarray) -> np.ndarray:
         a_f = np.ascontiguousarray(a_f, dtype=np.float64)
@@ -219,6 +237,7 @@ class Oracle:
         a, gam = self.split(theta)
         g = self.gains(gam)
         grad = np.zeros(self.n_par)
+        gsky = np.zeros((self.F, self.nk))
         ggain = np.zeros((self.A, self.NG, 2))
         bi, bj = self.bl_i, self.bl_j
         for f in range(self.F):
@@ -236,7 +255,8 @@ class Oracle:
                     np.add.at(ggain[:, k, 1], bi, -X[k] * ti.imag)
                     np.add.at(ggain[:, k, 0], bj, X[k] * tj.real)
                     np.add.at(ggain[:, k, 1], bj, X[k] * tj.imag)
-            grad[f * self.nk:(f + 1) * self.nk] += self.sky_adjoint_f(xbar)
+            gsky[f] += self.sky_adjoint_f(xbar)
+        grad[: self.n_sky] = self.sky_to_params(gsky)
         grad[self.n_sky:] += ggain.reshape(-1)
         return grad
 
@@ -261,6 +281,7 @@ class Oracle:
         a, gam = self.split(theta)
         g = self.gains(gam)
         grad = np.zeros(self.n_par)
+        gsky = np.zeros((self.F, self.nk))
         ggain = np.zeros((self.A, self.NG, 2))
         chi2 = 0.0
         s2 = self.sigma ** 2
@@ -286,7 +307,8 @@ class Oracle:
                     np.add.at(ggain[:, k, 1], bi, -X[k] * ti.imag)
                     np.add.at(ggain[:, k, 0], bj, X[k] * tj.real)
                     np.add.at(ggain[:, k, 1], bj, X[k] * tj.imag)
-            grad[f * self.nk:(f + 1) * self.nk] += self.sky_adjoint_f(xbar)
+            gsky[f] += self.sky_adjoint_f(xbar)
+        grad[: self.n_sky] = self.sky_to_params(gsky)
         grad[self.n_sky:] += ggain.reshape(-1)
         U = 0.5 * chi2
         if fts is None:
@@ -302,6 +324,7 @@ class Oracle:
         g = self.gains(gam)
         dg = self.gains(vgam)
         out = np.zeros(self.n_par)
+        osky = np.zeros((self.F, self.nk))
         ggain = np.zeros((self.A, self.NG, 2))
         s2 = self.sigma ** 2
         bi, bj = self.bl_i, self.bl_j
@@ -334,7 +357,8 @@ class Oracle:
                     np.add.at(ggain[:, k, 1], bi, -X[k] * ci.imag)
                     np.add.at(ggain[:, k, 0], bj, X[k] * cj.real)
                     np.add.at(ggain[:, k, 1], bj, X[k] * cj.imag)
-            out[f * self.nk:(f + 1) * self.nk] += self.sky_adjoint_f(xbar)
+            osky[f] += self.sky_adjoint_f(xbar)
+        out[: self.n_sky] = self.sky_to_params(osky)
         out[self.n_sky:] += ggain.reshape(-1)
         if lam is not None and fts is None:
             out += lam * np.asarray(v, dtype=np.float64)
@@ -358,7 +382,12 @@ class Oracle:
             Vf = np.stack([self.vis_ft(f, t, x_f) for t in range(self.T)])     # [T, B]
             gg = g[f, bi] * np.conj(g[f, bj])
             for k in range(self.nk):
-                J[f, :, :, f * self.nk + k] = gg[None, :] * self.sky_column_response(f, k)
+                col = gg[None, :] * self.sky_column_response(f, k)
+                if self.K:          # the coefficient a~[l, k] enters channel f with weight X_l(nu_f)
+                    for l in range(self.K):
+                        J[f, :, :, l * self.nk + k] = self.Xf[f, l] * col
+                else:
+                    J[f, :, :, f * self.nk + k] = col
             X = self.gleg[f]
             for kk in range(self.NG):
                 for c, unit in ((0, 1.0), (1, 1j)):
@@ -371,23 +400,37 @@ class Oracle:
 
     def gn_blocks(self, theta, lam=None, bs: int = 64, blocks=None):
         """Gauss-Newton Hessian of U, Re(J^H J)/sigma^2 + diag(lam), on the block-diagonal:
-        consecutive sky blocks of size bs inside each channel, then the dense gain block.
-        ``blocks`` restricts the sky blocks computed (list of block indices)."""
+        consecutive sky blocks of size bs inside each channel (inside each Legendre order when
+        the sky is compressed in frequency: there the block of order l sums the channels' blocks
+        with the weights X_l(nu_f)^2, since channels share no visibility), then the dense gain
+        block.  ``blocks`` restricts the sky blocks computed (list of block indices)."""
         a, gam = self.split(theta)
         g = self.gains(gam)
         bi, bj = self.bl_i, self.bl_j
         s2 = self.sigma ** 2
         nb_f = self.nk // bs
-        want = range(self.F * nb_f) if blocks is None else blocks
+        n_lead = self.K if self.K else self.F
+        want = range(n_lead * nb_f) if blocks is None else blocks
+
+        memo = {}
+
+        def channel_block(f, j0):
+            if (f, j0) not in memo:
+                gg = g[f, bi] * np.conj(g[f, bj])
+                cols = np.stack([(gg[None, :] * self.sky_column_response(f, j0 * bs + c)).reshape(-1)
+                                 for c in range(bs)], axis=1)                  # [T*B, bs]
+                memo[(f, j0)] = (cols.conj().T @ cols).real / s2
+            return memo[(f, j0)]
+
         out = {}
         for blk in want:
-            f, j0 = divmod(int(blk), nb_f)
-            gg = g[f, bi] * np.conj(g[f, bj])
-            cols = np.stack([(gg[None, :] * self.sky_column_response(f, j0 * bs + c)).reshape(-1)
-                             for c in range(bs)], axis=1)                  # [T*B, bs]
-            H = (cols.conj().T @ cols).real / s2
+            l, j0 = divmod(int(blk), nb_f)
+            if self.K:
+                H = sum(self.Xf[f, l] ** 2 * channel_block(f, j0) for f in range(self.F))
+            else:
+                H = channel_block(l, j0)
             if lam is not None:
-                base = f * self.nk + j0 * bs
+                base = l * self.nk + j0 * bs
                 H = H + np.diag(lam[base:base + bs])
             out[int(blk)] = H
         # dense gain block

@@ -99,6 +99,7 @@ static fm_status validate(const fm_config *cfg)
          !std::isfinite(cfg->dish_ns_m)))
         return invalid("the Airy beam needs dish_ew_m and dish_ns_m > 0");
     if (cfg->precision < FM_PREC_FP64_SIMT || cfg->precision > FM_PREC_FP16X3) return invalid("precision");
+    if (cfg->n_freq_modes < 0 || cfg->n_freq_modes > cfg->n_freq) return invalid("n_freq_modes must be in [0, n_freq]");
     long long npix = (long long)cfg->n_ra * cfg->n_dec;
     if (npix > (1LL << 30) || (long long)cfg->n_mode_ra * cfg->n_mode_dec > (1LL << 30))
         return invalid("grid too large");
@@ -114,7 +115,9 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
     c->B = c->A * (c->A - 1) / 2;
     c->prec = cfg->precision;
     c->rsz = c->prec == FM_PREC_FP64_SIMT ? 8 : 4;
-    c->n_sky = (int64_t)c->F * c->nk;
+    c->K = cfg->n_freq_modes;
+    c->n_sky_m = (int64_t)c->F * c->nk;
+    c->n_sky = c->K > 0 ? (int64_t)c->K * c->nk : c->n_sky_m;
     c->n_par = c->n_sky + 2LL * c->A * c->NG;
     c->n_vis = (int64_t)c->F * c->T * c->B;
     c->ant.assign(cfg->ant_enu_m, cfg->ant_enu_m + 3 * (size_t)c->A);
@@ -234,6 +237,7 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 
     FM_TRY(launch_precompute(*c, 0));
     FM_CK(cudaStreamSynchronize(0));
+    FM_TRY(freq_basis_setup(*c));
     FM_TRY(ha_setup(*c));
     if (c->prec != FM_PREC_FP64_SIMT) {
         // monopole split: U = V(x = 1) once, in FP64, stored as FP32 (through the hour-angle
@@ -326,7 +330,12 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
 {
     if (!c.have_data) { set_error("fm_set_data has not been called"); return FM_ERR_STATE; }
     R *x = (R *)c.x, *vis = (R *)c.vis, *om = (R *)c.omega, *zp = (R *)c.zpart;
-    FM_TRY(vis_of_modes<R>(c, theta, x, vis, st));
+    const R *sky = theta;
+    if (c.K > 0) {                          // Legendre-in-frequency coefficients -> channel modes
+        FM_TRY(launch_freq_expand<R>(c, theta, (R *)c.ax, st));
+        sky = (const R *)c.ax;
+    }
+    FM_TRY(vis_of_modes<R>(c, sky, x, vis, st));
     // hour-angle form: the epilogue forms the group sums of omega itself
     const bool groups = std::is_same<R, float>::value && c.ha.on;
     if (c.df_on) {
@@ -338,7 +347,8 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
         FM_TRY(launch_chi2_chan<R>(c, vis, theta + c.n_sky, om, zp, c.chi2p, groups, st));   // gains formed inside
     }
     FM_TRY(run_adjoint<R>(c, om, (R *)c.xbar, st, groups));
-    FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, grad, st));
+    FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, c.K > 0 ? (R *)c.gx : grad, st));
+    if (c.K > 0) FM_TRY(launch_freq_contract<R>(c, (const R *)c.gx, grad, st));
     FM_TRY(launch_gain_reduce_chan<R>(c, zp, grad + c.n_sky, st));
     if (c.df_on)
         return launch_prior_and_total<R>(c, theta, grad, c.df_chi2p, c.df_nparts, chi2_out, u_out, st, kick_p,
@@ -355,12 +365,20 @@ static fm_status run_hvp(Ctx &c, const R *theta, const R *v, R *hv, int full, cu
     R *x = (R *)c.x, *xv = (R *)c.xv;
     FM_TRY(launch_gains<R>(c, theta + c.n_sky, (R *)c.gains, st));
     FM_TRY(launch_gains<R>(c, v + c.n_sky, (R *)c.dgains, st));
-    FM_TRY(vis_of_modes<R>(c, theta, x, (R *)c.vis, st));
-    FM_TRY(vis_of_modes<R>(c, v, xv, (R *)c.dvis, st));
+    const R *sky = theta, *vsky = v;
+    if (c.K > 0) {
+        FM_TRY(launch_freq_expand<R>(c, theta, (R *)c.ax, st));
+        FM_TRY(launch_freq_expand<R>(c, v, (R *)c.avx, st));
+        sky = (const R *)c.ax;
+        vsky = (const R *)c.avx;
+    }
+    FM_TRY(vis_of_modes<R>(c, sky, x, (R *)c.vis, st));
+    FM_TRY(vis_of_modes<R>(c, vsky, xv, (R *)c.dvis, st));
     FM_TRY(launch_hvp_mid<R>(c, (R *)c.vis, (R *)c.dvis, (R *)c.gains, (R *)c.dgains, full, (R *)c.omega,
                              (R *)c.zpart, st));
     FM_TRY(run_adjoint<R>(c, (R *)c.omega, (R *)c.xbar, st));
-    FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, hv, st));
+    FM_TRY(launch_modes_adjoint<R>(c, (R *)c.xbar, c.K > 0 ? (R *)c.gx : hv, st));
+    if (c.K > 0) FM_TRY(launch_freq_contract<R>(c, (const R *)c.gx, hv, st));
     FM_TRY(launch_gain_reduce<R>(c, (R *)c.zpart, hv + c.n_sky, st));
     return launch_prior_hvp<R>(c, v, hv, st);
 }
@@ -442,14 +460,22 @@ fm_status fm_forward(fm_handle h, const void *dev_theta, void *dev_vis_out, fm_s
     if (!dev_theta || !dev_vis_out) return invalid("NULL device pointer");
     Ctx &c = *reinterpret_cast<Ctx *>(h);
     if (c.prec == FM_PREC_FP64_SIMT) {
-        const double *th = (const double *)dev_theta;
+        const double *th = (const double *)dev_theta, *sky = th;
+        if (c.K > 0) {
+            FM_TRY(launch_freq_expand<double>(c, th, (double *)c.ax, stream));
+            sky = (const double *)c.ax;
+        }
         FM_TRY(launch_gains<double>(c, th + c.n_sky, (double *)c.gains, stream));
-        FM_TRY(vis_of_modes<double>(c, th, (double *)c.x, (double *)c.vis, stream));
+        FM_TRY(vis_of_modes<double>(c, sky, (double *)c.x, (double *)c.vis, stream));
         return launch_apply_gains<double>(c, (double *)c.vis, (double *)c.gains, (double *)dev_vis_out, stream);
     }
-    const float *th = (const float *)dev_theta;
+    const float *th = (const float *)dev_theta, *sky = th;
+    if (c.K > 0) {
+        FM_TRY(launch_freq_expand<float>(c, th, (float *)c.ax, stream));
+        sky = (const float *)c.ax;
+    }
     FM_TRY(launch_gains<float>(c, th + c.n_sky, (float *)c.gains, stream));
-    FM_TRY(vis_of_modes<float>(c, th, (float *)c.x, (float *)c.vis, stream));
+    FM_TRY(vis_of_modes<float>(c, sky, (float *)c.x, (float *)c.vis, stream));
     return launch_apply_gains<float>(c, (float *)c.vis, (float *)c.gains, (float *)dev_vis_out, stream);
 }
 
@@ -471,9 +497,20 @@ fm_status fm_sky_pixels(fm_handle h, const void *dev_theta, void *dev_x_out, fm_
     FM_HANDLE_OK(h);
     if (!dev_theta || !dev_x_out) return invalid("NULL device pointer");
     Ctx &c = *reinterpret_cast<Ctx *>(h);
-    if (c.prec == FM_PREC_FP64_SIMT)
-        return launch_modes_forward<double>(c, (const double *)dev_theta, (double *)dev_x_out, stream, 0);
-    return launch_modes_forward<float>(c, (const float *)dev_theta, (float *)dev_x_out, stream, 0);
+    if (c.prec == FM_PREC_FP64_SIMT) {
+        const double *sky = (const double *)dev_theta;
+        if (c.K > 0) {
+            FM_TRY(launch_freq_expand<double>(c, sky, (double *)c.ax, stream));
+            sky = (const double *)c.ax;
+        }
+        return launch_modes_forward<double>(c, sky, (double *)dev_x_out, stream, 0);
+    }
+    const float *sky = (const float *)dev_theta;
+    if (c.K > 0) {
+        FM_TRY(launch_freq_expand<float>(c, sky, (float *)c.ax, stream));
+        sky = (const float *)c.ax;
+    }
+    return launch_modes_forward<float>(c, sky, (float *)dev_x_out, stream, 0);
 }
 
 fm_status fm_chi2_grad(fm_handle h, const void *dev_theta, double *dev_chi2_out, double *dev_u_out,

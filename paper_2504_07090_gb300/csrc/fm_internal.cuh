@@ -184,7 +184,15 @@ struct Ctx {
     fm_config cfg;
     std::vector<double> ant, freq, lst;
     int A, F, T, R, D, M, N, NG, npix, nk, B, prec;
-    int64_t n_sky, n_par, n_vis;
+    int64_t n_sky, n_par, n_vis;     // parameter space: sky modes (K x nk or F x nk) + gains
+    // Legendre-in-frequency compression (K > 0): the model runs on n_sky_m = F x nk expanded modes
+    int K = 0;
+    int64_t n_sky_m = 0;
+    void *fx64 = nullptr, *fx32 = nullptr;   // X[f][k] = P_k(nu^_f)
+    std::vector<double> fx_host;
+    void *ax = nullptr, *avx = nullptr, *gx = nullptr;   // expanded theta, v and gradient sky parts
+    double *pc_gacc = nullptr;               // preconditioner: one channel's blocks before spreading
+    size_t pc_gacc_n = 0;                    // its length in doubles
     size_t rsz;                       // bytes per real (4 or 8)
     DevGeom g;
     // owned device buffers
@@ -396,6 +404,15 @@ fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_
 // r <- sigma^2 F^T W F r with the filtered chi^2 partials in c.df_chi2p
 template <typename R>
 fm_status launch_delay_filter(Ctx &c, const R *vis, const R *gamma, cudaStream_t st);
+
+// Legendre-in-frequency compression (k_freq.cu): a[f][j] = sum_k X_k(nu_f) a~[k][j] and its
+// transpose; the preconditioner spreads a channel's FP64 blocks G into the K compressed ones
+fm_status freq_basis_setup(Ctx &c);
+template <typename R>
+fm_status launch_freq_expand(Ctx &c, const R *ap, R *am, cudaStream_t st);
+template <typename R>
+fm_status launch_freq_contract(Ctx &c, const R *gm, R *gp, cudaStream_t st);
+fm_status launch_freq_spread(Ctx &c, int f, long long n, const double *G, double *acc, cudaStream_t st);
 
 // preconditioner and leapfrog
 template <typename R>

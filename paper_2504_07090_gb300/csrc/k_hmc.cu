@@ -256,7 +256,7 @@ __global__ void k_pc_vis2(DevGeom g, const R *__restrict__ vis, double *__restri
 // u = (1, i) for the first antenna and u' = (1, -i) for the conjugated second one.
 template <typename R>
 __global__ void k_pc_gain_block(DevGeom g, const double *__restrict__ s2, const R *__restrict__ gains,
-                                const R *__restrict__ lam, int have_prior, int dense, double *__restrict__ out)
+                                const R *__restrict__ lam_gain, int have_prior, int dense, double *__restrict__ out)
 {
     const int ng = 2 * g.A * g.NG;
     long long n = dense ? (long long)ng * ng : ng;
@@ -294,7 +294,7 @@ __global__ void k_pc_gain_block(DevGeom g, const double *__restrict__ s2, const 
             }
         }
         h *= g.inv_sigma2;
-        if (r == cidx && have_prior) h += (double)lam[(size_t)g.F * g.nk + r];
+        if (r == cidx && have_prior) h += (double)lam_gain[r];
         out[e] = h;
     }
 }
@@ -579,8 +579,26 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
         if ((rc = launch_gains<R>(c, theta + c.n_sky, gn, st)) != FM_OK) break;
         if (cudaMemsetAsync(c.pc_blocks, 0, sizeof(double) * need, st) != cudaSuccess) { rc = FM_ERR_CUDA; break; }
         k_pc_group_w<R><<<cdiv((long long)c.F * U, 256), 256, 0, st>>>(c.g, U, g_off, g_mem, gn, Wg);
+        if (c.K > 0 && c.pc_gacc_n < (size_t)c.nk * bs) {
+            // (re)allocate for this block size: a previous buffer stays in c.allocs until destroy
+            if (cudaMalloc(&c.pc_gacc, sizeof(double) * (size_t)c.nk * bs) != cudaSuccess) {
+                c.pc_gacc = nullptr;
+                c.pc_gacc_n = 0;
+                rc = FM_ERR_ALLOC;
+                set_error("cudaMalloc precond channel blocks");
+                break;
+            }
+            c.allocs.push_back(c.pc_gacc);
+            c.pc_gacc_n = (size_t)c.nk * bs;
+        }
         for (int f = 0; f < c.F && rc == FM_OK; ++f) {
-            double *accf = c.pc_blocks + (size_t)f * c.nk * bs;
+            // Legendre-in-frequency compression: the channel's blocks are summed apart, then
+            // spread into the K compressed parameters' blocks with the weights X_k(nu_f)^2
+            double *accf = c.K > 0 ? c.pc_gacc : c.pc_blocks + (size_t)f * c.nk * bs;
+            if (c.K > 0 && cudaMemsetAsync(accf, 0, sizeof(double) * (size_t)c.nk * bs, st) != cudaSuccess) {
+                rc = FM_ERR_CUDA;
+                break;
+            }
             for (int t = 0; t < c.T; ++t) {
                 k_pc_fringe<R><<<2048, 256, 0, st>>>(c.g, f, t, U, g_rep, Wg, X);
                 if (cudaGetLastError() != cudaSuccess) { rc = FM_ERR_CUDA; break; }
@@ -602,14 +620,20 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
                 }
                 if (cudaGetLastError() != cudaSuccess) { rc = FM_ERR_CUDA; break; }
             }
+            if (rc == FM_OK && c.K > 0) rc = launch_freq_spread(c, f, (long long)c.nk * bs, accf, c.pc_blocks, st);
         }
         if (rc != FM_OK) break;
         // prior on the sky diagonal
         // (added by the Cholesky kernels' inflation logic through H + lam; store H + lam here)
         // gain block: needs V at theta
-        if ((rc = vis_of_modes<R>(c, theta, x, vis, st)) != FM_OK) break;
+        const R *sky = theta;
+        if (c.K > 0) {
+            if ((rc = launch_freq_expand<R>(c, theta, (R *)c.ax, st)) != FM_OK) break;
+            sky = (const R *)c.ax;
+        }
+        if ((rc = vis_of_modes<R>(c, sky, x, vis, st)) != FM_OK) break;
         k_pc_vis2<R><<<cdiv((long long)c.F * c.B, 256), 256, 0, st>>>(c.g, vis, s2);
-        k_pc_gain_block<R><<<512, 256, 0, st>>>(c.g, s2, gn, (const R *)c.lam, c.have_prior ? 1 : 0, bs > 1 ? 1 : 0,
+        k_pc_gain_block<R><<<512, 256, 0, st>>>(c.g, s2, gn, c.have_prior ? (const R *)c.lam + c.n_sky : nullptr, c.have_prior ? 1 : 0, bs > 1 ? 1 : 0,
                                                 c.pc_blocks + sky_sz);
         if (c.have_prior)
             k_pc_add_prior<R><<<cdiv(c.n_sky, 256), 256, 0, st>>>(c.n_sky, bs, (const R *)c.lam, c.pc_blocks);

@@ -52,7 +52,8 @@ class FmConfig(ctypes.Structure):
                 ("ra_min", c_double), ("ra_max", c_double), ("dec_min", c_double), ("dec_max", c_double),
                 ("n_mode_ra", c_int), ("n_mode_dec", c_int), ("n_gain_modes", c_int),
                 ("beam_fwhm_ref_rad", c_double), ("beam_ref_hz", c_double), ("sigma_noise", c_double),
-                ("precision", c_int), ("beam_type", c_int), ("dish_ew_m", c_double), ("dish_ns_m", c_double)]
+                ("precision", c_int), ("beam_type", c_int), ("n_freq_modes", c_int), ("dish_ew_m", c_double),
+                ("dish_ns_m", c_double)]
 
 
 _lib = None
@@ -172,7 +173,8 @@ def make_config(prob, precision: str | int = "fp32", sigma: float | None = None)
                    float(prob.dec_max), int(prob.n_mode_ra), int(prob.n_mode_dec), int(prob.n_gain),
                    float(prob.beam_fwhm_ref_rad), float(prob.beam_ref_hz),
                    float(prob.sigma if sigma is None else sigma), prec, int(getattr(prob, "beam_type", 0)),
-                   float(getattr(prob, "dish_ew_m", 0.0)), float(getattr(prob, "dish_ns_m", 0.0)))
+                   int(getattr(prob, "n_freq_modes", 0)), float(getattr(prob, "dish_ew_m", 0.0)),
+                   float(getattr(prob, "dish_ns_m", 0.0)))
     return cfg, (ant, freq, lst)
 
 
@@ -191,7 +193,7 @@ class ForwardModel:
         self.n_params = int(self.lib.fm_num_params(h))
         self.n_vis = int(self.lib.fm_num_vis(h))
         self.vis_shape = (prob.n_freq, prob.n_lst, prob.n_bl, 2)
-        self.n_sky = prob.n_freq * prob.n_mode_ra * prob.n_mode_dec
+        self.n_sky = (getattr(prob, "n_freq_modes", 0) or prob.n_freq) * prob.n_mode_ra * prob.n_mode_dec
         self.n_pix_total = prob.n_freq * prob.n_ra * prob.n_dec
 
     def close(self):

@@ -67,6 +67,7 @@ class Problem:
     beam_type: int = 0             # 0 Gaussian, 1 modified Airy (Eq. airy)
     dish_ew_m: float = 0.0         # Airy aperture diameters
     dish_ns_m: float = 0.0
+    n_freq_modes: int = 0          # > 0: sky modes compressed onto this many Legendre orders in frequency
     extra: dict = field(default_factory=dict)
 
     @property
@@ -94,8 +95,13 @@ class Problem:
         return self.n_mode_ra * self.n_mode_dec
 
     @property
+    def n_sky_rows(self) -> int:
+        """Leading extent of the sky parameters: channels, or Legendre orders when compressed."""
+        return self.n_freq_modes if self.n_freq_modes > 0 else self.n_freq
+
+    @property
     def n_sky_params(self) -> int:
-        return self.n_freq * self.n_modes
+        return self.n_sky_rows * self.n_modes
 
     @property
     def n_gain_params(self) -> int:
@@ -257,6 +263,8 @@ def draw_truth(prob: Problem, seed: int | None = None) -> Truth:
       * 21 cm signal: flat power 10 mK^2, independent per channel.
     Gains: g_i(nu) = sum_k gamma_ik P_k(nu_hat) with gamma_i0 = 1 + 0.05 CN(0,1),
     gamma_ik = 0.05 CN(0,1) for k >= 1.
+    With n_freq_modes > 0 the sky is drawn as Legendre-in-frequency coefficients instead
+    (_draw_compressed); the 21 cm part, white across channels, has no place there.
     """
     rng = np.random.default_rng(prob.seed if seed is None else seed)
     F, M, N = prob.n_freq, prob.n_mode_ra, prob.n_mode_dec
@@ -280,6 +288,8 @@ def draw_truth(prob: Problem, seed: int | None = None) -> Truth:
     z = rng.standard_normal((4, nk))
     u_q = (chol @ z) / (res_sr * math.sqrt(nk))           # [4, nk]
     theta = np.empty(prob.n_params, dtype=np.float64)
+    if prob.n_freq_modes > 0:
+        return _draw_compressed(prob, rng, theta, a_diff.reshape(nk), u_q)
     sky = theta[: F * nk].reshape(F, nk)
     for f, nu in enumerate(prob.freq_hz):
         lg = math.log(nu / NU0_HZ)
@@ -287,11 +297,38 @@ def draw_truth(prob: Problem, seed: int | None = None) -> Truth:
         sig21 = rayleigh_jeans_jy_per_sr(math.sqrt(10e-6), nu)
         a21 = sig21 * np.sqrt((2.0 * n_idx + 1.0) / nk) * rng.standard_normal((M, N))
         sky[f] = ((nu / NU0_HZ) ** -2.5 * a_diff + a21).reshape(nk) + ps
-    g = theta[F * nk:].reshape(prob.n_ant, prob.n_gain, 2)
+    return _draw_gains_and_noise(prob, rng, theta)
+
+
+def _draw_gains_and_noise(prob: Problem, rng, theta: np.ndarray) -> Truth:
+    g = theta[prob.n_sky_params:].reshape(prob.n_ant, prob.n_gain, 2)
     g[:] = 0.05 / math.sqrt(2.0) * rng.standard_normal((prob.n_ant, prob.n_gain, 2))
     g[:, 0, 0] += 1.0
     noise = rng.standard_normal((prob.n_freq, prob.n_lst, prob.n_bl, 2))
     return Truth(theta=theta, noise=noise)
+
+
+def _draw_compressed(prob: Problem, rng, theta: np.ndarray, a_diff: np.ndarray, u_q: np.ndarray) -> Truth:
+    """Sky coefficients of the Legendre-in-frequency model, drawn directly (no basis is
+    evaluated): order 0 holds the band's mean sky (the diffuse modes and the point sources'
+    flux at 150 MHz); order k >= 1 holds an independent draw of the same angular spectra,
+    scaled by 0.2^k, so that the spectra are smooth and the higher orders fall off as a
+    power law's expansion does over a narrow band."""
+    K, nk = prob.n_freq_modes, prob.n_modes
+    sky = theta[: K * nk].reshape(K, nk)
+    sky[0] = a_diff + u_q[0]
+    scale = np.abs(a_diff).copy()
+    scale[0] = 0.3 * abs(a_diff[0])
+    for k in range(1, K):
+        sky[k] = 0.2 ** k * (scale * rng.standard_normal(nk) + u_q[min(k, 3)])
+    return _draw_gains_and_noise(prob, rng, theta)
+
+
+def with_freq_modes(prob: Problem, n_freq_modes: int) -> Problem:
+    """The same problem with its sky compressed onto n_freq_modes Legendre orders in frequency."""
+    if not 0 <= n_freq_modes <= prob.n_freq:
+        raise ValueError("n_freq_modes must lie in [0, n_freq]")
+    return replace(prob, n_freq_modes=int(n_freq_modes), name=f"{prob.name}-K{n_freq_modes}")
 
 
 def prior_for(prob: Problem, theta_true: np.ndarray, sky_frac: float = 0.05,
@@ -300,7 +337,7 @@ def prior_for(prob: Problem, theta_true: np.ndarray, sky_frac: float = 0.05,
     (the ~5 % foreground prior of Sec. 3.2), 0.05 for gain coefficients."""
     mu = theta_true.copy()
     lam = np.empty_like(theta_true)
-    F, nk = prob.n_freq, prob.n_modes
+    F, nk = prob.n_sky_rows, prob.n_modes
     sky = theta_true[: F * nk].reshape(F, nk)
     rms = np.sqrt(np.mean(sky ** 2, axis=1))
     lam[: F * nk] = np.repeat(1.0 / (sky_frac * rms) ** 2, nk)

@@ -96,10 +96,13 @@ def to_pairs(z: np.ndarray) -> np.ndarray:
     return np.stack([z.real, z.imag], axis=-1)
 
 
-def make_case(name: str, noise: bool = True, prior=(0.05, 0.05)):
+def make_case(name: str, noise: bool = True, prior=(0.05, 0.05), freq_modes: int = 0):
     """Problem, oracle, truth, data d (oracle model + seeded noise), prior (sky width as a
-    fraction of the channel rms, gain width)."""
+    fraction of the channel rms, gain width); freq_modes > 0 compresses the sky onto that many
+    Legendre orders in frequency."""
     p = synth.config(name)
+    if freq_modes:
+        p = synth.with_freq_modes(p, freq_modes)
     tr = synth.draw_truth(p)
     o = oracle.Oracle(p)
     m = o.model(tr.theta)
@@ -111,7 +114,7 @@ def make_case(name: str, noise: bool = True, prior=(0.05, 0.05)):
 
 
 def perturbed(o, theta: np.ndarray, frac: float, seed: int) -> np.ndarray:
-    a, _ = o.split(theta)
+    a = np.asarray(theta[: o.n_sky]).reshape(-1, o.nk)     # channels, or Legendre orders
     sc = np.empty(o.n_par)
     sc[: o.n_sky] = np.repeat(np.sqrt(np.mean(a ** 2, axis=1)), o.nk)
     sc[o.n_sky:] = 1.0
