@@ -271,6 +271,39 @@ __device__ __forceinline__ void md_tmem_to_atom(uint32_t tmem, int c0, int ka, f
     }
 }
 
+// Result rows (TMEM lanes) to a row-major array out[row * ld + col], times `inv`: each warp
+// passes its 32 rows x 16 columns through a padded shared-memory tile (32 x 17 floats) so
+// that one store instruction writes 16 consecutive columns of two rows; rows >= nrows and
+// columns >= ncols are skipped.  Returns the largest |value| this thread stored.
+__device__ __forceinline__ float md_store_rows(uint32_t tmem, int c0, int cols_pad, int row_base, int nrows, int ncols,
+                                               float inv, float *__restrict__ out, size_t ld, float *tile)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = w & 3, half = w >> 2;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+    const int row0 = row_base + 32 * quarter;
+    float *t = tile + (size_t)w * (32 * 17);
+    float mx = 0.f;
+    for (int cg = 16 * half; cg < cols_pad; cg += 32) {
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)cg, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) t[lane * 17 + q] = v[q] * inv;
+        __syncwarp();
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+            const int rr = 2 * i + (lane >> 4), cc = lane & 15;
+            const int row = row0 + rr, col = cg + cc;
+            const float xv = t[rr * 17 + cc];
+            if (row < nrows && col < ncols) {
+                out[(size_t)row * ld + col] = xv;
+                mx = fmaxf(mx, fabsf(xv));
+            }
+        }
+        __syncwarp();
+    }
+    return mx;
+}
+
 // largest |value| of a TMEM accumulator (all threads receive it)
 __device__ __forceinline__ float md_tmem_max(uint32_t tmem, int c0, int ncols, float *red)
 {
@@ -350,26 +383,12 @@ k_modes_fwd(MdDims z, const float *__restrict__ a_all, int skip_dc, const uint8_
     }
     tc_fence_after();
 
-    // x = D2 / (g 2^28 sa)
+    // x = D2 / (g 2^28 sa), through the A atom's space (free once the last MMAs are complete)
     float xm = 0.f;
     if (ok) {
         const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sa);
-        const int quarter = warp & 3, half = warp >> 2, lane = tid & 31;
-        const int d = 128 * dt + 32 * quarter + lane;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)z.Mp;
-        float *xr = x_all + ((size_t)f * z.D + d) * z.R;
-        for (int cg = 16 * half; cg < z.Rp; cg += 32) {
-            float v[16];
-            tmem_ld16(taddr + (uint32_t)cg, v);
-            if (d < z.D)
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (cg + q < z.R) {
-                        const float xv = v[q] * inv;
-                        xr[cg + q] = xv;
-                        xm = fmaxf(xm, fabsf(xv));
-                    }
-        }
+        xm = md_store_rows(tmem, z.Mp, z.Rp, 128 * dt, z.D, z.R, inv, x_all + (size_t)f * z.D * z.R, (size_t)z.R,
+                           reinterpret_cast<float *>(m.a));
     }
     if (xmax) {                                 // uniform: every thread takes part
         const float bm = block_max(xm, m.red);
@@ -450,18 +469,8 @@ k_modes_adj(MdDims z, const float *__restrict__ xb_all, const uint8_t *__restric
 
     if (ok) {
         const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sx);
-        const int quarter = warp & 3, half = warp >> 2, lane = tid & 31;
-        const int mm = 128 * mtile + 32 * quarter + lane;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)z.Dp;
-        float *ar = abar_all + ((size_t)f * z.M + mm) * z.N;
-        for (int cg = 16 * half; cg < z.Np; cg += 32) {
-            float v[16];
-            tmem_ld16(taddr + (uint32_t)cg, v);
-            if (mm < z.M)
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (cg + q < z.N) ar[cg + q] = v[q] * inv;
-        }
+        md_store_rows(tmem, z.Dp, z.Np, 128 * mtile, z.M, z.N, inv, abar_all + (size_t)f * z.M * z.N, (size_t)z.N,
+                      reinterpret_cast<float *>(m.a));
     }
     tc_fence_before();
     __syncthreads();
