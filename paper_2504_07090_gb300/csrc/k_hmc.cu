@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
             vs[lane + 32] = v1;
             __syncwarp();
             R b0 = 0, b1 = 0;
-#pragma unroll 8
+#pragma unroll
             for (int r = 0; r < 64; ++r) {
                 const R zr = vs[r];
                 const R *row = S + tri_row_start<R>(r) * PER;
