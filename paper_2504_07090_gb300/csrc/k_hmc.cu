@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "fm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fm {
 
@@ -721,6 +722,13 @@ __global__ void k_copy(long long n, const R *__restrict__ x, R *__restrict__ y)
 // from shared memory.  The dense gain block follows in k_lf_dense.
 constexpr int LF_WARPS = 4;
 
+// shared bytes of one warp of k_lf_tri: the block image, the vector, an mbarrier and a flag
+template <typename R>
+__host__ __device__ constexpr size_t lf_warp_bytes(int mul)
+{
+    return sizeof(R) * (size_t)((mul ? 4096 : tri_block_elems<R>()) + 64) + 16;
+}
+
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -836,10 +844,9 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
                                                           int bwd, int mul, R *__restrict__ q,
                                                           const double *__restrict__ peps,
                                                           R *__restrict__ out, double *__restrict__ kin,
-                                                          LfDense<R> dn)
+                                                          LfDense<R> dn, int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sm = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const double eps = q ? *peps : 0.0;
     if (blockIdx.x < dn.nctas) {
@@ -865,22 +872,39 @@ __global__ void __launch_bounds__(LF_WARPS * 32) k_lf_tri(long long nblk, const 
         if (blk >= nblk) return;
         constexpr int PER = 16 / sizeof(R), NP = 64 / PER;     // elements per 16-byte piece, pieces per row
         const int wsz = mul ? 4096 : tri_block_elems<R>();      // block image, then the 64-vector
-        R *S = sm + (size_t)w * (wsz + 64);
+        // per warp: the image, the vector, an mbarrier and an abort flag
+        unsigned char *wb = smem_raw + (size_t)w * lf_warp_bytes<R>(mul);
+        R *S = reinterpret_cast<R *>(wb);
         R *vs = S + wsz;
+        const uint32_t bar = tc::su32(wb + sizeof(R) * (wsz + 64));
+        volatile int *wabort = reinterpret_cast<volatile int *>(wb + sizeof(R) * (wsz + 64) + 8);
+        const long long off = blk * 64;
         if (mul) {                                      // the factor, stored full: XOR-permuted image
             const R *Lb = L + blk * 4096;
             for (int e = lane; e < 64 * NP; e += 32) {
                 const int r = e / NP, pc = e % NP;
                 cp_async16(S + r * 64 + ((pc ^ (r & (NP - 1))) * PER), Lb + r * 64 + pc * PER);
             }
-        } else {                                        // its inverse, packed, copied as it is stored
-            const R *Lb = Li + blk * tri_block_elems<R>();
-            for (int e = lane; e < tri_row_start<R>(64); e += 32) cp_async16(S + e * PER, Lb + e * PER);
+            vs[lane] = in[off + lane];
+            vs[lane + 32] = in[off + lane + 32];
+            cp_async_wait_all();
+        } else {                                        // its inverse, packed: one bulk copy as it is stored
+            constexpr uint32_t bytes = (uint32_t)(sizeof(R) * tri_block_elems<R>());
+            if (lane == 0) {
+                *wabort = 0;
+                tc::mbar_init(bar, 1);
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                tc::mbar_expect_tx(bar, bytes);
+                tc::bulk_g2s(tc::su32(S), Li + blk * tri_block_elems<R>(), bytes, bar);
+            }
+            vs[lane] = in[off + lane];
+            vs[lane + 32] = in[off + lane + 32];
+            __syncwarp();
+            if (!tc::mbar_wait_ab(bar, 0u, wabort)) {
+                if (lane == 0) atomicExch(status, (int)FM_ERR_TIMEOUT);
+                return;
+            }
         }
-        const long long off = blk * 64;
-        vs[lane] = in[off + lane];
-        vs[lane + 32] = in[off + lane + 32];
-        cp_async_wait_all();
         __syncwarp();
         if (mul) {
             R y0, y1;
@@ -1000,7 +1024,7 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
     if (bs > 1) {
         const long long nb = c.n_sky / bs;
         const int ng = 2 * c.A * c.NG;
-        const size_t smem = sizeof(R) * (size_t)LF_WARPS * ((mul ? 4096 : tri_block_elems<R>()) + 64);
+        const size_t smem = (size_t)LF_WARPS * lf_warp_bytes<R>(mul);
         FM_CK(smem_opt_in(k_lf_tri<R>));
         const long long grid = (nb + LF_WARPS - 1) / LF_WARPS;
         // the gain block runs as extra warps of the same launch: one FP64 product with L_g (mul),
@@ -1016,7 +1040,7 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
         if (dn.M) dn.nctas = cdiv(ng, LF_WARPS);
         const long long gtot = grid + dn.nctas;
         k_lf_tri<R><<<(unsigned)gtot, LF_WARPS * 32, smem, st>>>(nb, (const R *)c.pc_linv, L, in, fwd, bwd, mul, q,
-                                                                peps, out, kin_out ? part : nullptr, dn);
+                                                                peps, out, kin_out ? part : nullptr, dn, c.status);
         FM_CK_LAUNCH();
         if (ng > 0 && !dn.M && fwd && bwd) {     // both solves with the kinetic energy: two products
             const long long base = c.n_sky;
