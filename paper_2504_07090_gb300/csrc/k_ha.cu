@@ -75,6 +75,14 @@ struct HaLayout {
     size_t smem;
 };
 
+// 8-byte shared-memory load at a 32-bit shared address
+__device__ __forceinline__ float2 lds_f2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
 // first work unit of CTA g when Q units are cut into G contiguous ranges
 __host__ __device__ __forceinline__ long long range_lo(long long Q, int G, int g) { return Q * g / G; }
 
@@ -806,8 +814,12 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + misc + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the groups' table rows as byte offsets within an E chunk
     int2 *suij = reinterpret_cast<int2 *>(gbase + L.v_off + ((size_t)2 * 32 * (128 + 64 * h.k + 1) + 4 * 128) * 4);
-    for (int e = tid; e < 32 * h.nkq; e += blockDim.x) suij[e] = h.uij[e];
+    for (int e = tid; e < 32 * h.nkq; e += blockDim.x) {
+        const int2 ij = h.uij[e];
+        suij[e] = make_int2(ij.x * (HA_EW * 8), ij.y * (HA_EW * 8));
+    }
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
             mbar_init(full0 + 8 * s, HA_PROD_WARPS);
@@ -845,8 +857,9 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
                 mbar_wait_ab(efull0 + 8 * se, eph, abort_flag);
                 __syncwarp();
                 if (*abort_flag) goto done;
-                const uint8_t *es = gbase + L.e_off + (size_t)se * L.eslot_bytes + (size_t)(n >> 6) * echunk +
-                                    (size_t)(n & 63) * 8;
+                // shared address of this row's cell in the slot's first table row
+                const uint32_t es = base + L.e_off + (uint32_t)se * L.eslot_bytes + (uint32_t)(n >> 6) * echunk +
+                                    (uint32_t)(n & 63) * 8u;
                 for (int kq = 0; kq < h.nkq; ++kq) {
                     if (lane == 0 && wrapped) mbar_wait_ab(empty0 + 8 * s, ph ^ 1u, abort_flag);
                     __syncwarp();
@@ -855,9 +868,8 @@ k_adj_ha(HaDev h, HaLayout L, const uint8_t *__restrict__ qimg, const float *__r
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int2 ij = suij[32 * kq + 8 * qq + q];
-                        const float2 a = *reinterpret_cast<const float2 *>(es + (size_t)ij.x * (HA_EW * 8));
-                        const float2 b = *reinterpret_cast<const float2 *>(es + (size_t)ij.y * (HA_EW * 8));
-                        Elem<ET>::split(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y), hw[q], lw[q]);
+                        const float2 a = lds_f2(es + (uint32_t)ij.x), b = lds_f2(es + (uint32_t)ij.y);
+                        Elem<ET>::split2(make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y)), hw[q], lw[q]);
                     }
                     // TMEM lane n (= 32 (warp & 3) + lane), columns 8 qq .. 8 qq + 7 of stage s
                     const uint32_t ta = tmem_d + ((uint32_t)(32 * (warp & 3)) << 16) +
