@@ -260,27 +260,25 @@ template <int ET>
 __global__ void k_ha_yprep(HaDev h, const float *__restrict__ x, const unsigned *__restrict__ xmax,
                            uint16_t *__restrict__ ys_hi, uint16_t *__restrict__ ys_lo)
 {
-    // one strip (channel, declination) per block iteration, its element pairs over the threads
-    const int half = h.Ly / 2, nrow = h.F * h.D, off0 = h.nhp - 1 - (h.R - 1) * h.q;
-    for (int fd = blockIdx.x; fd < nrow; fd += gridDim.x) {
-        const float sc = pow2_scale(__uint_as_float(xmax[fd / h.D]));
-        const float *xr = x + (size_t)fd * h.R;
-        uint32_t *oh = reinterpret_cast<uint32_t *>(ys_hi) + (size_t)fd * half;
-        uint32_t *ol = reinterpret_cast<uint32_t *>(ys_lo) + (size_t)fd * half;
-        for (int jh = threadIdx.x; jh < half; jh += blockDim.x) {
-            float v[2];
+    const long long total = (long long)h.F * h.D * (h.Ly / 2);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int jp = 2 * (int)(e % (h.Ly / 2));
+        const long long fd = e / (h.Ly / 2);
+        const int f = (int)(fd / h.D);
+        const float sc = pow2_scale(__uint_as_float(xmax[f]));
+        float v[2];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                // element j holds pixel r when j - (nhp - 1 - (R - 1) qc) = r qc (qc cells per pixel)
-                const int rr = 2 * jh + q - off0;
-                const int r = h.q == 1 ? rr : (rr >= 0 && rr % h.q == 0 ? rr / h.q : -1);
-                v[q] = (r >= 0 && r < h.R) ? sc * xr[r] : 0.f;
-            }
-            uint32_t hi, lo;
-            Elem<ET>::split(v[0], v[1], hi, lo);
-            oh[jh] = hi;
-            ol[jh] = lo;
+        for (int q = 0; q < 2; ++q) {
+            // element j holds pixel r when j - (nhp - 1 - (R - 1) qc) = r qc (qc cells per pixel)
+            const int rr = jp + q - (h.nhp - 1 - (h.R - 1) * h.q);
+            const int r = h.q == 1 ? rr : (rr >= 0 && rr % h.q == 0 ? rr / h.q : -1);
+            v[q] = (r >= 0 && r < h.R) ? sc * x[fd * h.R + r] : 0.f;
         }
+        uint32_t hi, lo;
+        Elem<ET>::split(v[0], v[1], hi, lo);
+        reinterpret_cast<uint32_t *>(ys_hi)[e] = hi;
+        reinterpret_cast<uint32_t *>(ys_lo)[e] = lo;
     }
 }
 
