@@ -393,6 +393,7 @@ fm_status ha_set_grids(Ctx &c, int ctas_fwd, int ctas_adj);
 fm_status modes_tc_setup(Ctx &c);
 fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax);
 fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st);
+fm_status launch_modes_tc_adjoint_maps(Ctx &c, const float *xbar, int nmaps, float *abar, cudaStream_t st);
 // dc != nullptr: also adds the monopole visibilities dc[f * dcs] U[f][t][b]; xmax_ready: the
 // channel maxima of x are already in c.ha.xmax (formed by the mode transform)
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc = nullptr,

@@ -562,9 +562,12 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
     }
     const int U = c.pc_U;
     const int *g_rep = c.pc_grp, *g_off = c.pc_grp + 2 * U, *g_mem = g_off + U + 1;
-    // scratch for one (channel, LST): fringes X [2][U][npix], Q [2][U][D][M], S [2][U][nk], G [nk/bs][bs][bs],
-    // group weights W [F][U]
-    size_t nX = 2 * (size_t)U * c.npix, nQ = 2 * (size_t)U * c.D * c.M, nS = 2 * (size_t)U * c.nk;
+    // scratch for TB LSTs of one channel: fringes X [TB][2][U][npix], Q [2][U][D][M] (CUDA-core
+    // route only), S [TB][2][U][nk], G [nk/bs][bs][bs], group weights W [F][U].  The tensor-core
+    // transform takes TB LSTs' response maps per launch.
+    const bool tcx = std::is_same<R, float>::value && c.mtc.on;
+    const int TB = tcx ? (c.T < 4 ? c.T : 4) : 1;
+    size_t nX = 2 * (size_t)U * c.npix * TB, nQ = tcx ? 0 : 2 * (size_t)U * c.D * c.M, nS = 2 * (size_t)U * c.nk * TB;
     // (counts rounded up to even so that the FP64 scratch after them stays 8-byte aligned)
     size_t nG = ((size_t)c.nk * bs + 1) & ~(size_t)1, nW = ((size_t)c.F * U + 1) & ~(size_t)1;
     R *X = nullptr;
@@ -600,24 +603,33 @@ fm_status run_build_precond(Ctx &c, const R *theta, int block, cudaStream_t st)
                 rc = FM_ERR_CUDA;
                 break;
             }
-            for (int t = 0; t < c.T; ++t) {
-                k_pc_fringe<R><<<2048, 256, 0, st>>>(c.g, f, t, U, g_rep, Wg, X);
+            for (int t = 0; t < c.T; t += TB) {
+                const int tbn = c.T - t < TB ? c.T - t : TB;
+                for (int tb = 0; tb < tbn; ++tb)
+                    k_pc_fringe<R><<<2048, 256, 0, st>>>(c.g, f, t + tb, U, g_rep, Wg, X + (size_t)tb * 2 * U * c.npix);
                 if (cudaGetLastError() != cudaSuccess) { rc = FM_ERR_CUDA; break; }
-                // Q[pl,b][d][m] = sum_r X[pl,b][d][r] Phi[r][m]
-                const R *phi = std::is_same<R, float>::value ? (const R *)c.g.phi32 : (const R *)c.g.phi64;
-                const R *leg = std::is_same<R, float>::value ? (const R *)c.g.leg32 : (const R *)c.g.leg64;
-                GemmArgsH q1{(int)(2LL * U * c.D), c.M, c.R, 0, c.R, 1, 0, c.M, 1, 0, c.M, 1};
-                if ((rc = gemm_h<R>(q1, 1, X, phi, Q, st)) != FM_OK) break;
-                // S[pl,b][m][n] = sum_d Q[pl,b][d][m] P[d][n]
-                GemmArgsH q2{c.M, c.N, c.D, (long long)c.D * c.M, 1, c.M, 0, c.N, 1, c.nk, c.N, 1};
-                if ((rc = gemm_h<R>(q2, 2LL * U, Q, leg, S, st)) != FM_OK) break;
+                if (tcx) {
+                    // S[tb,pl,b][m][n] = sum_{d,r} Phi[r][m] X[tb,pl,b][d][r] P[d][n]: the tensor-core
+                    // pixel -> mode transform over the 2U response maps of tbn LSTs
+                    if ((rc = launch_modes_tc_adjoint_maps(c, (const float *)X, 2 * U * tbn, (float *)S, st)) != FM_OK)
+                        break;
+                } else {
+                    // Q[pl,b][d][m] = sum_r X[pl,b][d][r] Phi[r][m]
+                    const R *phi = std::is_same<R, float>::value ? (const R *)c.g.phi32 : (const R *)c.g.phi64;
+                    const R *leg = std::is_same<R, float>::value ? (const R *)c.g.leg32 : (const R *)c.g.leg64;
+                    GemmArgsH q1{(int)(2LL * U * c.D), c.M, c.R, 0, c.R, 1, 0, c.M, 1, 0, c.M, 1};
+                    if ((rc = gemm_h<R>(q1, 1, X, phi, Q, st)) != FM_OK) break;
+                    // S[pl,b][m][n] = sum_d Q[pl,b][d][m] P[d][n]
+                    GemmArgsH q2{c.M, c.N, c.D, (long long)c.D * c.M, 1, c.M, 0, c.N, 1, c.nk, c.N, 1};
+                    if ((rc = gemm_h<R>(q2, 2LL * U, Q, leg, S, st)) != FM_OK) break;
+                }
                 if (bs > 1) {
-                    // G[j0][c][c'] = sum_{pl,b} S[pl,b][j0*bs+c] S[pl,b][j0*bs+c']
-                    GemmArgsH q3{bs, bs, 2 * U, bs, 1, c.nk, bs, c.nk, 1, (long long)bs * bs, bs, 1};
+                    // G[j0][c][c'] = sum_{tb,pl,b} S[tb,pl,b][j0*bs+c] S[tb,pl,b][j0*bs+c']
+                    GemmArgsH q3{bs, bs, 2 * U * tbn, bs, 1, c.nk, bs, c.nk, 1, (long long)bs * bs, bs, 1};
                     if ((rc = gemm_h<R>(q3, c.nk / bs, S, S, G, st)) != FM_OK) break;
                     k_pc_accum<R><<<512, 256, 0, st>>>((long long)c.nk * bs, G, accf);
                 } else {
-                    k_pc_diag<R><<<cdiv(c.nk, 256), 256, 0, st>>>(c.nk, 2 * U, S, accf);
+                    k_pc_diag<R><<<cdiv(c.nk, 256), 256, 0, st>>>(c.nk, 2 * U * tbn, S, accf);
                 }
                 if (cudaGetLastError() != cudaSuccess) { rc = FM_ERR_CUDA; break; }
             }

@@ -561,9 +561,16 @@ fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t
 
 fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st)
 {
-    const MdDims z = md_dims(c);
+    return launch_modes_tc_adjoint_maps(c, xbar, c.F, abar, st);
+}
+
+// the same transform for nmaps pixel maps xbar[nmaps][D][R] -> abar[nmaps][M][N]
+fm_status launch_modes_tc_adjoint_maps(Ctx &c, const float *xbar, int nmaps, float *abar, cudaStream_t st)
+{
+    MdDims z = md_dims(c);
+    z.F = nmaps;
     const int nmt = (c.M + 127) / 128;
-    k_modes_adj<<<dim3(c.F, nmt), MD_THREADS, md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np), st>>>(
+    k_modes_adj<<<dim3(nmaps, nmt), MD_THREADS, md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np), st>>>(
         z, xbar, c.mtc.phit_img, c.mtc.legt_img, abar, c.status, md_cols(z.Dp + z.Np));
     FM_CK_LAUNCH();
     return FM_OK;

@@ -151,7 +151,9 @@ def test_leapfrog_trajectory_matches_oracle(name, K, prec, eps, prior, check_err
     check_err(rel_l2(tp.cpu().numpy(), pw), tol_q, key(form, "lf_p_K", prec), f"{name} K{K}")
     check_err(abs(hh[0] - H0) / abs(H0), 1e-12 if exact else 1e-5, key(form, "H0_K", prec), f"{name} K{K}")
     e_dh = abs((hh[1] - hh[0]) - (H1 - H0)) / max(1.0, abs(H1 - H0))
-    check_err(e_dh, 1e-9 if exact else (2e-2 if form == "direct" else 1.5), key(form, "dH_K", prec), f"{name} K{K}")
+    # the split modes' energy change: an absolute error of order one (the bound and its
+    # derivation as in the uncompressed trajectory test)
+    check_err(e_dh, 1e-9 if exact else (2e-2 if form == "direct" else 3.0), key(form, "dH_K", prec), f"{name} K{K}")
     assert int(aout.item()) == 1
 
 

@@ -100,8 +100,8 @@ def test_leapfrog_trajectory_matches_oracle(name, prec, form, eps, prior, check_
     hh = hout.cpu().numpy()
     exact = prec == "fp64"
     # the trajectory integrates 20 gradients in FP32 state: held to the FP32 gradient target,
-    # except ha37m (1.3e-4 in both split modes, so from the FP32 state and mass-matrix
-    # solves, not the contraction): 2e-4
+    # except ha37m (6.5e-5 fp16x3, 7.1e-5 bf16x3, up to 1.3e-4 with other builds of the mass
+    # matrix: from the FP32 state and mass-matrix solves, not the contraction): 2e-4
     tol_q = 1e-9 if exact else LF_Q_BOUND[name]
     e_q = rel_l2(tq.cpu().numpy() - q0, qw - q0)
     e_p = rel_l2(tp.cpu().numpy(), pw)
@@ -115,10 +115,12 @@ def test_leapfrog_trajectory_matches_oracle(name, prec, form, eps, prior, check_
     # H0 = U(q0) + z.z/2: U carries the chi^2 error that the visibility bound implies
     check_err(e_h0, 1e-12 if exact else 1e-5, key(form, "H0", prec), name)
     # H1 - H0: U falls by about 1e4 along this trajectory (q0 is 0.5 % off the truth), and the
-    # model's visibility error (about 1e-6 of |m|, times |m| / |m - d| ~ 100 in U) moves with
-    # it, so the split modes' energy change carries an absolute error of order one (measured
-    # 0.73 fp16x3, 0.97 bf16x3); the direct FP32 form's 2e-4
-    check_err(e_dh, 1e-9 if exact else (2e-2 if form == "direct" else 1.5), key(form, "dH", prec), name)
+    # model's visibility error dm = eps_V |m| moves U by up to |m - d| |dm| / sigma^2 =
+    # eps_V (|m| / sigma) (|m - d| / sigma), about 2.4e-6 x 1.4e4 x 1.4e2 = 4.8 here, less as the
+    # error's direction is not the residual's: an absolute error of order one in the split modes'
+    # energy change (measured 0.76 fp16x3, 1.65 bf16x3 with the mass matrix built through the
+    # FP16-split mode transform); the direct FP32 form's 2e-4
+    check_err(e_dh, 1e-9 if exact else (2e-2 if form == "direct" else 3.0), key(form, "dH", prec), name)
     assert int(aout.item()) == 1
     # rejection restores q0: u just above the acceptance probability
     a = math.exp(min(0.0, H0 - H1))
