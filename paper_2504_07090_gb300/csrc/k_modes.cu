@@ -272,31 +272,58 @@ __device__ __forceinline__ void md_tmem_to_atom(uint32_t tmem, int c0, int ka, f
 }
 
 // Result rows (TMEM lanes) to a row-major array out[row * ld + col], times `inv`: each warp
-// passes its 32 rows x 16 columns through a padded shared-memory tile (32 x 17 floats) so
-// that one store instruction writes 16 consecutive columns of two rows; rows >= nrows and
-// columns >= ncols are skipped.  Returns the largest |value| this thread stored.
+// passes its 32 rows x 16 columns through a shared-memory tile (32 rows of 20 floats: 16-byte
+// pieces, conflict-free for the row-wise writes) so that one store instruction writes 16
+// consecutive columns of eight rows (16 bytes a lane when the rows are 16-byte aligned, one
+// float otherwise, two rows an instruction); rows >= nrows and columns >= ncols are skipped.
+// Returns the largest |value| this thread stored.
 __device__ __forceinline__ float md_store_rows(uint32_t tmem, int c0, int cols_pad, int row_base, int nrows, int ncols,
                                                float inv, float *__restrict__ out, size_t ld, float *tile)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = w & 3, half = w >> 2;
     const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
     const int row0 = row_base + 32 * quarter;
-    float *t = tile + (size_t)w * (32 * 17);
+    float *t = tile + (size_t)w * (32 * 20);
+    const bool vec = (ld & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
     float mx = 0.f;
     for (int cg = 16 * half; cg < cols_pad; cg += 32) {
         float v[16];
         tmem_ld16(taddr + (uint32_t)cg, v);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) t[lane * 17 + q] = v[q] * inv;
+        for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<float4 *>(t + lane * 20 + 4 * k) =
+                make_float4(v[4 * k] * inv, v[4 * k + 1] * inv, v[4 * k + 2] * inv, v[4 * k + 3] * inv);
         __syncwarp();
+        if (vec) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rr = 8 * i + (lane >> 2), cc = 4 * (lane & 3);
+                const int row = row0 + rr, col = cg + cc;
+                const float4 a = *reinterpret_cast<const float4 *>(t + rr * 20 + cc);
+                if (row < nrows) {
+                    if (col + 3 < ncols) {
+                        *reinterpret_cast<float4 *>(out + (size_t)row * ld + col) = a;
+                        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+                    } else {
+                        const float e[4] = {a.x, a.y, a.z, a.w};
+                        for (int q = 0; q < 4; ++q)
+                            if (col + q < ncols) {
+                                out[(size_t)row * ld + col + q] = e[q];
+                                mx = fmaxf(mx, fabsf(e[q]));
+                            }
+                    }
+                }
+            }
+        } else {
 #pragma unroll 4
-        for (int i = 0; i < 16; ++i) {
-            const int rr = 2 * i + (lane >> 4), cc = lane & 15;
-            const int row = row0 + rr, col = cg + cc;
-            const float xv = t[rr * 17 + cc];
-            if (row < nrows && col < ncols) {
-                out[(size_t)row * ld + col] = xv;
-                mx = fmaxf(mx, fabsf(xv));
+            for (int i = 0; i < 16; ++i) {
+                const int rr = 2 * i + (lane >> 4), cc = lane & 15;
+                const int row = row0 + rr, col = cg + cc;
+                const float xv = t[rr * 20 + cc];
+                if (row < nrows && col < ncols) {
+                    out[(size_t)row * ld + col] = xv;
+                    mx = fmaxf(mx, fabsf(xv));
+                }
             }
         }
         __syncwarp();
