@@ -279,11 +279,11 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 // (inside the last kernel of the hour-angle form, as a separate pass otherwise)
 template <typename R>
 static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st, const R *dc = nullptr, long long dcs = 0,
-                         bool xmax_ready = false)
+                         bool xmax_ready = false, bool strips_ready = false)
 {
     // the tensor-core launchers time their main kernel themselves
     if constexpr (std::is_same<R, float>::value) {
-        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs, xmax_ready);
+        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs, xmax_ready, strips_ready);
         if (c.prec >= FM_PREC_BF16X1) {
             FM_TRY(launch_vis_tc(c, x, vis, st));
             return dc ? launch_add_dc<R>(c, dc, dcs, vis, st) : FM_OK;
@@ -307,19 +307,19 @@ template <typename R>
 fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st)
 {
     // hour-angle form after the tensor-core transform: the transform forms the channel maxima
-    // of x that scale the sky strip
+    // of x that scale the sky strip, and with one CTA per channel the strips themselves
     unsigned *xmax = nullptr;
+    StripArgs sa;
+    bool strips = false;
     if constexpr (std::is_same<R, float>::value)
         if (c.ha.on && c.mtc.on) {
-            FM_CK(cudaMemsetAsync(c.ha.xmax, 0, sizeof(unsigned) * c.F, st));
+            strips = ha_strip_args(c, sa);
+            if (!strips) FM_CK(cudaMemsetAsync(c.ha.xmax, 0, sizeof(unsigned) * c.F, st));
             xmax = c.ha.xmax;
         }
-    if (c.dc_split) {
-        FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 1, xmax));
-        return run_vis<R>(c, xbuf, vis, st, a, c.nk, xmax != nullptr);
-    }
-    FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, 0, xmax));
-    return run_vis<R>(c, xbuf, vis, st, nullptr, 0, xmax != nullptr);
+    const bool dc = c.dc_split;
+    FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, dc ? 1 : 0, xmax, strips ? &sa : nullptr));
+    return run_vis<R>(c, xbuf, vis, st, dc ? a : nullptr, dc ? c.nk : 0, xmax != nullptr, strips);
 }
 template fm_status vis_of_modes<float>(Ctx &, const float *, float *, float *, cudaStream_t);
 template fm_status vis_of_modes<double>(Ctx &, const double *, double *, double *, cudaStream_t);

@@ -329,10 +329,24 @@ fm_status profiled(Ctx &c, int cls, cudaStream_t st, F fn)
 // (each defined in the .cu file that owns the kernels; all enqueue on `st`)
 fm_status launch_precompute(Ctx &c, cudaStream_t st);
 
+// Sky strips of the hour-angle forward written by the tensor-core mode transform: element
+// j = off + r q of the strip of (channel f, declination d), at hi/lo + (f D + d) Ly + j, holds
+// sc x[f][d][r] split into 16-bit hi / lo parts (FP16 or BF16), sc = 2^(14 - e) for the
+// channel's largest |x| in [2^(e-1), 2^e); the other elements stay zero.
+struct StripArgs {
+    uint16_t *hi = nullptr, *lo = nullptr;
+    int Ly = 0, off = 0, q = 1, bf16 = 0;
+};
+// the hour-angle form's strips as a StripArgs when the transform can write them (one CTA
+// per channel: at most 128 declinations)
+bool ha_strip_args(const Ctx &c, StripArgs &sa);
+
 template <typename R>
-// a -> x; xmax != NULL (tensor-core transform only): also atomicMax of each channel's largest
-// |x| (as float bits) into xmax[f], which the caller has zeroed
-fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc = 0, unsigned *xmax = nullptr);
+// a -> x; xmax != NULL (tensor-core transform only): also each channel's largest |x| (as
+// float bits) into xmax[f] (atomicMax into a zeroed xmax; with strips, a plain store and the
+// strips of the hour-angle forward as well)
+fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc = 0, unsigned *xmax = nullptr,
+                               const StripArgs *strips = nullptr);
 template <typename R>
 fm_status launch_modes_adjoint(Ctx &c, const R *xbar, R *abar, cudaStream_t st);  // xbar -> abar
 template <typename R>
@@ -391,13 +405,15 @@ fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st);
 fm_status ha_set_grids(Ctx &c, int ctas_fwd, int ctas_adj);
 // tensor-core mode transforms (float handles of the split precisions)
 fm_status modes_tc_setup(Ctx &c);
-fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax);
+fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax,
+                                  const StripArgs *strips = nullptr);
 fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaStream_t st);
 fm_status launch_modes_tc_adjoint_maps(Ctx &c, const float *xbar, int nmaps, float *abar, cudaStream_t st);
 // dc != nullptr: also adds the monopole visibilities dc[f * dcs] U[f][t][b]; xmax_ready: the
-// channel maxima of x are already in c.ha.xmax (formed by the mode transform)
+// channel maxima of x are already in c.ha.xmax (formed by the mode transform); strips_ready:
+// so are the sky strips of x (written by the mode transform)
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc = nullptr,
-                        long long dcs = 0, bool xmax_ready = false);
+                        long long dcs = 0, bool xmax_ready = false, bool strips_ready = false);
 // q_ready: the group sums q32 / qmax_ft were already formed from omega (by the chi^2 epilogue)
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready = false);
 

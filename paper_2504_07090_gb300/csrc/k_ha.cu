@@ -1188,7 +1188,7 @@ bool make_layout_adj(const Ctx &c, bool x3, HaLayout &L)
 
 template <int ET, bool X3>
 fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cudaStream_t st, const float *dc,
-                        long long dcs, bool xmax_ready)
+                        long long dcs, bool xmax_ready, bool strips_ready)
 {
     HaState &s = c.ha;
     HaLayout L;
@@ -1202,8 +1202,10 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
         k_ha_xmax<<<dim3(cdiv(c.npix, 256 * 8), c.F), 256, 0, st>>>(c.npix, x, s.xmax);
         FM_CK_LAUNCH();
     }
-    k_ha_yprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, ys_hi, ys_lo);
-    FM_CK_LAUNCH();
+    if (!strips_ready) {
+        k_ha_yprep<ET><<<1024, 256, 0, st>>>(h, x, s.xmax, ys_hi, ys_lo);
+        FM_CK_LAUNCH();
+    }
     FM_CK(smem_opt_in(k_vis_ha<ET, X3>));
     // one pass per chunk of at most HA_TCHUNK LSTs (the partial sums are reused)
     for (int t0 = 0; t0 < c.T; t0 += HA_TCHUNK) {
@@ -1486,6 +1488,7 @@ fm_status ha_setup(Ctx &c)
     FM_TRY(ha_alloc(c, &s.mem, (size_t)c.B));
     FM_TRY(ha_alloc(c, &s.ncontrib, ncontrib.size()));
     FM_TRY(ha_alloc(c, &s.ys, ys_n));
+    FM_CK(cudaMemset(s.ys, 0, ys_n * sizeof(uint16_t)));     // strip elements outside the pixels stay zero
     FM_TRY(ha_alloc(c, &s.xmax, (size_t)c.F));
     FM_TRY(ha_alloc(c, &s.vpart, vp_n));
     s.J_alloc = s.J;
@@ -1578,15 +1581,30 @@ fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st)
 }
 
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc, long long dcs,
-                        bool xmax_ready)
+                        bool xmax_ready, bool strips_ready)
 {
     const HaDev h = make_dev(c);
     const bool x3 = x3_of(c.prec);
     if (f16_of(c.prec))
-        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs, xmax_ready)
-                  : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs, xmax_ready);
-    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs, xmax_ready)
-              : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs, xmax_ready);
+        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready)
+                  : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready);
+    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready)
+              : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready);
+}
+
+bool ha_strip_args(const Ctx &c, StripArgs &sa)
+{
+    if (!c.ha.on || c.D > 128) return false;
+    if (const char *e = getenv("FM_MODES_STRIPS"))      // 0: strips from their own kernel
+        if (atoi(e) == 0) return false;
+    const HaState &s = c.ha;
+    sa.hi = s.ys;
+    sa.lo = s.ys + (size_t)c.F * c.D * s.Ly;
+    sa.Ly = s.Ly;
+    sa.q = s.q;
+    sa.off = s.nhp - 1 - (c.R - 1) * s.q;       // element of pixel 0 (k_ha_yprep)
+    sa.bf16 = f16_of(c.prec) ? 0 : 1;
+    return true;
 }
 
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready)

@@ -9,9 +9,10 @@
 // the modes a and the pixel gradient xbar are converted tile by tile.  Products use the
 // three-term split hi*hi + hi*lo + lo*hi with FP32 accumulation.
 //
-// K is processed one 64-wide atom at a time with single-buffered tiles: fill (bulk copy
-// of an image atom, conversion of the other operand), fence, one thread issues 4 x 3 MMAs
-// and commits to an mbarrier that all threads wait on (bounded) before the next atom.
+// K is processed one 64-wide atom at a time through one or two operand slots: the image
+// atom arrives by bulk copy, the other operand is converted by all threads, and one thread
+// issues 4 x 3 MMAs per atom and commits them to the slot's mbarrier; a slot is refilled
+// once the barrier shows its MMAs complete (bounded waits throughout).
 #include <cmath>
 #include <cstdlib>
 
@@ -102,41 +103,45 @@ __device__ __forceinline__ void issue_atom(uint32_t tmem, uint32_t a_s, uint32_t
     }
 }
 
-// Shared state of both kernels.
+// Shared state of both kernels: one or two operand slots, each an A atom (128 rows) and a B
+// atom (up to b_rows_max rows), hi rows then lo rows; per slot one mbarrier for the bulk copy
+// of its basis-image atom and one for the MMAs that read it.
 struct MdSmem {
-    uint8_t *a, *b;            // operand atoms
-    uint32_t a_s, b_s;         // their shared addresses
-    uint32_t bar;              // MMA completion barrier
+    uint8_t *g;                // slot 0's A atom; its B atom follows at +32 KB
+    uint32_t base;             // its shared address
+    uint32_t stride;           // bytes from slot 0 to slot 1 (0 with one slot)
+    uint32_t bars;             // bar_img(s) = bars + 8 s, bar_mma(s) = bars + 16 + 8 s
     uint32_t *tmem_slot;
     volatile int *abort_flag;
     float *red;
+    __device__ __forceinline__ uint8_t *a(int s) const { return g + (uint32_t)s * stride; }
+    __device__ __forceinline__ uint8_t *b(int s) const { return g + (uint32_t)s * stride + 2 * 128 * 128; }
+    __device__ __forceinline__ uint32_t a_s(int s) const { return base + (uint32_t)s * stride; }
+    __device__ __forceinline__ uint32_t b_s(int s) const { return base + (uint32_t)s * stride + 2u * 128u * 128u; }
+    __device__ __forceinline__ uint32_t bar_img(int s) const { return bars + 8u * (uint32_t)s; }
+    __device__ __forceinline__ uint32_t bar_mma(int s) const { return bars + 16u + 8u * (uint32_t)s; }
 };
 
-__device__ __forceinline__ MdSmem md_smem(int b_rows_max)
+__host__ __device__ constexpr uint32_t md_slot_bytes(int b_rows_max)
+{
+    return 2u * 128u * 128u + 2u * (uint32_t)b_rows_max * 128u;
+}
+
+__device__ __forceinline__ MdSmem md_smem(int b_rows_max, int ns)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    uint8_t *g = smem_raw + (base - raw);
+    const uint32_t slot = md_slot_bytes(b_rows_max), tail = (uint32_t)ns * slot;
     MdSmem m;
-    m.a = g;
-    m.a_s = base;
-    m.b = g + 2 * 128 * 128;
-    m.b_s = base + 2u * 128u * 128u;
-    const uint32_t tail = 2u * 128u * 128u + 2u * (uint32_t)b_rows_max * 128u;
-    m.bar = base + tail;
-    m.tmem_slot = reinterpret_cast<uint32_t *>(g + tail + 8);
-    m.abort_flag = reinterpret_cast<volatile int *>(g + tail + 12);
-    m.red = reinterpret_cast<float *>(g + tail + 16);
+    m.g = smem_raw + (base - raw);
+    m.base = base;
+    m.stride = ns == 2 ? slot : 0u;
+    m.bars = base + tail;
+    m.tmem_slot = reinterpret_cast<uint32_t *>(m.g + tail + 32);
+    m.abort_flag = reinterpret_cast<volatile int *>(m.g + tail + 36);
+    m.red = reinterpret_cast<float *>(m.g + tail + 64);
     return m;
-}
-
-// wait for the atom's MMAs (phase `ph`), all threads; returns false after a timeout
-__device__ __forceinline__ bool md_wait(const MdSmem &m, uint32_t ph)
-{
-    mbar_wait_ab<32>(m.bar, ph, m.abort_flag);
-    __syncthreads();
-    return *m.abort_flag == 0;
 }
 
 // after an atom is filled: make the generic-proxy writes visible to the tensor core
@@ -144,28 +149,6 @@ __device__ __forceinline__ void md_filled()
 {
     fence_async_smem();
     __syncthreads();
-}
-
-// copy a 2 x rows x 128-byte image atom into shared memory (all threads, 16-byte pieces,
-// eight loads in flight per thread)
-__device__ __forceinline__ void md_copy_atom(uint8_t *dst, const uint8_t *src, int rows)
-{
-    const int n = rows * 2 * 128 / 16;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-    for (int e0 = threadIdx.x; e0 < n; e0 += 8 * blockDim.x) {
-        uint4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n) v[u] = __ldg(s4 + e);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n) d4[e] = v[u];
-        }
-    }
 }
 
 // largest |v| over a row-major [rows][cols] array (16-byte loads when rows are 16-byte
@@ -271,14 +254,57 @@ __device__ __forceinline__ void md_tmem_to_atom(uint32_t tmem, int c0, int ka, f
     }
 }
 
+// Sky strips written beside the pixels (forward, hour-angle form): value v of pixel (d, r) goes
+// to hi/lo[d Ly + r q] as the 16-bit hi / lo parts of sc v; hi == nullptr: none.
+struct StripOut {
+    uint16_t *hi, *lo;         // channel's strips, offset to the element of pixel 0
+    int Ly, q, bf16;
+    int vec4;                  // q == 1 and every row's element of pixel 0 8-byte aligned
+    float sc;
+};
+
+__device__ __forceinline__ uint32_t strip_split(const StripOut &so, float v, uint32_t &lo)
+{
+    const float y = so.sc * v;
+    if (so.bf16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(y);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(y - __bfloat162float(h)));
+        return __bfloat16_as_ushort(h);
+    }
+    const __half h = __float2half_rn(y);
+    lo = __half_as_ushort(__float2half_rn(y - __half2float(h)));
+    return __half_as_ushort(h);
+}
+
+__device__ __forceinline__ void strip_put(const StripOut &so, int row, int col, float v)
+{
+    const size_t e = (size_t)row * so.Ly + (size_t)col * so.q;
+    uint32_t lo;
+    so.hi[e] = (uint16_t)strip_split(so, v, lo);
+    so.lo[e] = (uint16_t)lo;
+}
+
+// four consecutive pixels of a row (vec4 strips): one 8-byte store per part
+__device__ __forceinline__ void strip_put4(const StripOut &so, int row, int col, const float *v)
+{
+    const size_t e = (size_t)row * so.Ly + (size_t)col;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = strip_split(so, v[q], l[q]);
+    *reinterpret_cast<uint2 *>(so.hi + e) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    *reinterpret_cast<uint2 *>(so.lo + e) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+}
+
 // Result rows (TMEM lanes) to a row-major array out[row * ld + col], times `inv`: each warp
 // passes its 32 rows x 16 columns through a shared-memory tile (32 rows of 20 floats: 16-byte
 // pieces, conflict-free for the row-wise writes) so that one store instruction writes 16
 // consecutive columns of eight rows (16 bytes a lane when the rows are 16-byte aligned, one
 // float otherwise, two rows an instruction); rows >= nrows and columns >= ncols are skipped.
-// Returns the largest |value| this thread stored.
+// Every stored value also goes to the strips `so` when so.hi != nullptr.  Returns the largest
+// |value| this thread stored.
 __device__ __forceinline__ float md_store_rows(uint32_t tmem, int c0, int cols_pad, int row_base, int nrows, int ncols,
-                                               float inv, float *__restrict__ out, size_t ld, float *tile)
+                                               float inv, float *__restrict__ out, size_t ld, float *tile,
+                                               const StripOut &so)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, quarter = w & 3, half = w >> 2;
     const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
@@ -301,15 +327,24 @@ __device__ __forceinline__ float md_store_rows(uint32_t tmem, int c0, int cols_p
                 const int row = row0 + rr, col = cg + cc;
                 const float4 a = *reinterpret_cast<const float4 *>(t + rr * 20 + cc);
                 if (row < nrows) {
+                    const float e[4] = {a.x, a.y, a.z, a.w};
                     if (col + 3 < ncols) {
                         *reinterpret_cast<float4 *>(out + (size_t)row * ld + col) = a;
                         mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+                        if (so.hi) {
+                            if (so.vec4) {
+                                strip_put4(so, row, col, e);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) strip_put(so, row, col + q, e[q]);
+                            }
+                        }
                     } else {
-                        const float e[4] = {a.x, a.y, a.z, a.w};
                         for (int q = 0; q < 4; ++q)
                             if (col + q < ncols) {
                                 out[(size_t)row * ld + col + q] = e[q];
                                 mx = fmaxf(mx, fabsf(e[q]));
+                                if (so.hi) strip_put(so, row, col + q, e[q]);
                             }
                     }
                 }
@@ -323,6 +358,7 @@ __device__ __forceinline__ float md_store_rows(uint32_t tmem, int c0, int cols_p
                 if (row < nrows && col < ncols) {
                     out[(size_t)row * ld + col] = xv;
                     mx = fmaxf(mx, fabsf(xv));
+                    if (so.hi) strip_put(so, row, col, xv);
                 }
             }
         }
@@ -346,170 +382,219 @@ __device__ __forceinline__ float md_tmem_max(uint32_t tmem, int c0, int ncols, f
     return block_max(m, red);
 }
 
-// ---------------------------------------------------------------- forward
-// CTA (f, d tile): stage 1 D1[d][m] (TMEM columns 0 .. Mp) = Leg_tile a_f^T over n;
-// stage 2 D2[d][r] (columns Mp .. Mp + Rp) = W Phi^T over m; x[f][d][r] = D2 / scales.
-// xmax != NULL: the largest |x| the CTA wrote goes to xmax[f] by atomicMax on its float bits
-// (non-negative floats order like their bit patterns, so the result is independent of order).
-__global__ void __launch_bounds__(MD_THREADS, 1)
-k_modes_fwd(MdDims z, const float *__restrict__ a_all, int skip_dc, const uint8_t *__restrict__ leg_img,
-            const uint8_t *__restrict__ phi_img, float *__restrict__ x_all, int *__restrict__ status, int ncols,
-            unsigned *__restrict__ xmax)
+// Operands of one direction's two chained products (the kernels below say which is which).
+struct MdPlan {
+    const uint8_t *img1;    // stage-1 A image atoms (2 x 128 rows x 128 bytes each)
+    const uint8_t *img2;    // stage-2 B image atoms (2 x nb2 rows x 128 bytes each)
+    const float *src;       // stage-1 B operand, row-major [src_rows][src_cols]
+    int src_rows, src_cols;
+    int n1;                 // stage-1 K atoms
+    int nb1;                // stage-1 N (rows of its B atoms, padded) = stage-2 K
+    int nb2;                // stage-2 N
+    bool skip_dc;           // read src[0][0] as zero
+};
+
+__device__ __forceinline__ uint32_t md_setup(const MdSmem &m, int ncols)
 {
-    const int f = blockIdx.x, dt = blockIdx.y;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    MdSmem m = md_smem(z.Mp > z.Rp ? z.Mp : z.Rp);
-    if (tid == 0) {
-        mbar_init(m.bar, 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(m.bar_img(s), 1);
+            mbar_init(m.bar_mma(s), 1);
+        }
         *m.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(su32(m.tmem_slot), (uint32_t)ncols);
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(su32(m.tmem_slot), (uint32_t)ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *m.tmem_slot;
-    const float *a = a_all + (size_t)f * z.M * z.N;
-    uint32_t ph = 0;
+    return *m.tmem_slot;
+}
+
+// Both products of one CTA through `ns` operand slots.  Atom i (stage 1 for i < n1, stage 2
+// after) uses slot i % ns.  Its basis-image part arrives by one bulk copy, issued by thread 0
+// as soon as the slot's previous atom (i - ns) has been read by its MMAs (the first ns at
+// once, while the CTA scans the FP32 operand for its scale); its other part is written by
+// all threads: in stage 1 the FP32 operand split into FP16 hi/lo, in stage 2 the first
+// product read from TMEM, scaled and split.  Thread 0 issues each atom's 12 MMAs and commits
+// them to the slot's barrier without waiting, so that filling atom i + 1 overlaps the MMAs
+// of atom i.  The first product occupies TMEM columns 0 .. nb1, the second nb1 .. nb1 + nb2.
+// sa and g are the power-of-two scales of the two products' B and A operands.  Returns false
+// after a timeout (abort flag raised; the copies and MMAs in flight drained).
+__device__ __forceinline__ bool md_two_stage(const MdSmem &m, int ns, uint32_t tmem, const MdPlan &p, float &sa,
+                                             float &g)
+{
+    const int tid = threadIdx.x;
+    const int n = p.n1 + p.nb1 / 64;
+    auto slot = [&](int j) { return ns == 2 ? (j & 1) : 0; };
+    auto par = [&](int j) { return (uint32_t)((j / ns) & 1); };   // phase of atom j on its slot's barriers
+    const uint32_t b2_bytes = 2u * (uint32_t)p.nb2 * 128u;
+    auto img_issue = [&](int i) {
+        const int s = slot(i);
+        if (i < p.n1) {
+            mbar_expect_tx(m.bar_img(s), 2u * 128u * 128u);
+            bulk_g2s(m.a_s(s), p.img1 + (size_t)i * 2 * 128 * 128, 2u * 128u * 128u, m.bar_img(s));
+        } else {
+            mbar_expect_tx(m.bar_img(s), b2_bytes);
+            bulk_g2s(m.b_s(s), p.img2 + (size_t)(i - p.n1) * b2_bytes, b2_bytes, m.bar_img(s));
+        }
+    };
+    // thread 0: the last atom whose image copy / MMAs it issued, per slot
+    int last_img0 = -1, last_img1 = -1, last_mma0 = -1, last_mma1 = -1;
+    if (tid == 0)
+        for (int i = 0; i < ns && i < n; ++i) {
+            img_issue(i);
+            (i == 0 ? last_img0 : last_img1) = i;
+        }
+    sa = pow2_below(md_absmax(p.src, p.src_rows, p.src_cols, p.skip_dc, m.red));
+    g = 1.f;
+    const uint32_t idesc1 = idesc_f16(128, p.nb1, 0), idesc2 = idesc_f16(128, p.nb2, 0);
     bool ok = true;
-
-    // scale of the modes
-    const float sa = pow2_below(md_absmax(a, z.M, z.N, skip_dc != 0, m.red));
-
-    // stage 1: K = n, A = Leg tile image, B = a_f rows m
-    const uint32_t idesc1 = idesc_f16(128, z.Mp, 0);
-    for (int ka = 0; ka < z.Np / 64 && ok; ++ka) {
-        md_copy_atom(m.a, leg_img + ((size_t)dt * (z.Np / 64) + ka) * 2 * 128 * 128, 128);
-        md_convert_atom(a, z.M, z.N, z.Mp, ka, sa, skip_dc != 0, m.b);
-        md_filled();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_atom(tmem, m.a_s, m.b_s, z.Mp, ka == 0, idesc1);
-            mma_commit(m.bar);
+    for (int i = 0; i < n; ++i) {
+        const int s = slot(i);
+        if (i >= ns) {                          // the slot's previous atom is consumed
+            mbar_wait_ab<32>(m.bar_mma(s), par(i - ns), m.abort_flag);
+            if (tid == 0 && *m.abort_flag == 0) {
+                img_issue(i);
+                (s == 0 ? last_img0 : last_img1) = i;
+            }
         }
-        ok = md_wait(m, ph);
-        ph ^= 1u;
-    }
-    tc_fence_after();
-
-    // stage 2: K = m, A = scaled W from TMEM, B = Phi image
-    const float g = ok ? pow2_below(md_tmem_max(tmem, 0, z.Mp, m.red)) : 1.f;
-    const uint32_t idesc2 = idesc_f16(128, z.Rp, 0);
-    for (int ka = 0; ka < z.Mp / 64 && ok; ++ka) {
-        md_tmem_to_atom(tmem, 0, ka, g, m.a);
-        md_copy_atom(m.b, phi_img + (size_t)ka * 2 * z.Rp * 128, z.Rp);
-        tc_fence_before();
-        md_filled();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_atom(tmem + (uint32_t)z.Mp, m.a_s, m.b_s, z.Rp, ka == 0, idesc2);
-            mma_commit(m.bar);
+        if (i == p.n1)                          // the first product is complete
+            mbar_wait_ab<32>(m.bar_mma(slot(p.n1 - 1)), par(p.n1 - 1), m.abort_flag);
+        __syncthreads();
+        if (*m.abort_flag) {
+            ok = false;
+            break;
         }
-        ok = md_wait(m, ph);
-        ph ^= 1u;
+        if (i < p.n1) {
+            md_convert_atom(p.src, p.src_rows, p.src_cols, p.nb1, i, sa, p.skip_dc, m.b(s));
+        } else {
+            if (i == p.n1) {
+                tc_fence_after();
+                g = pow2_below(md_tmem_max(tmem, 0, p.nb1, m.red));
+            }
+            md_tmem_to_atom(tmem, 0, i - p.n1, g, m.a(s));
+            tc_fence_before();
+        }
+        md_filled();
+        if (tid == 0 && mbar_wait_ab<32>(m.bar_img(s), par(i), m.abort_flag)) {
+            tc_fence_after();
+            if (i < p.n1) issue_atom(tmem, m.a_s(s), m.b_s(s), p.nb1, i == 0, idesc1);
+            else issue_atom(tmem + (uint32_t)p.nb1, m.a_s(s), m.b_s(s), p.nb2, i == p.n1, idesc2);
+            mma_commit(m.bar_mma(s));
+            (s == 0 ? last_mma0 : last_mma1) = i;
+        }
     }
+    if (ok) mbar_wait_ab<32>(m.bar_mma(slot(n - 1)), par(n - 1), m.abort_flag);   // all MMAs
     tc_fence_after();
+    __syncthreads();
+    if (*m.abort_flag) {
+        ok = false;
+        if (tid == 0) {
+            if (last_img0 >= 0) mbar_drain(m.bar_img(0), par(last_img0));
+            if (last_img1 >= 0) mbar_drain(m.bar_img(1), par(last_img1));
+            if (last_mma0 >= 0) mbar_drain(m.bar_mma(0), par(last_mma0));
+            if (last_mma1 >= 0) mbar_drain(m.bar_mma(1), par(last_mma1));
+        }
+        __syncthreads();
+    }
+    return ok;
+}
 
-    // x = D2 / (g 2^28 sa), through the A atom's space (free once the last MMAs are complete)
-    float xm = 0.f;
-    if (ok) {
-        const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sa);
-        xm = md_store_rows(tmem, z.Mp, z.Rp, 128 * dt, z.D, z.R, inv, x_all + (size_t)f * z.D * z.R, (size_t)z.R,
-                           reinterpret_cast<float *>(m.a));
-    }
-    if (xmax) {                                 // uniform: every thread takes part
-        const float bm = block_max(xm, m.red);
-        if (tid == 0 && ok) atomicMax(xmax + f, __float_as_uint(bm));
-    }
+__device__ __forceinline__ void md_finish(const MdSmem &m, bool ok, int *status, uint32_t tmem, int ncols)
+{
     tc_fence_before();
     __syncthreads();
-    if (*m.abort_flag && tid == 0) {
-        mbar_drain(m.bar, ph ^ 1u);            // the atom whose wait gave up
-        atomicExch(status, (int)FM_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    if (warp == 0) {
+    if (!ok && threadIdx.x == 0) atomicExch(status, (int)FM_ERR_TIMEOUT);
+    if ((threadIdx.x >> 5) == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, (uint32_t)ncols);
     }
 }
 
-// ---------------------------------------------------------------- adjoint
-// CTA (f, m tile): stage 1 D1[m][d] (columns 0 .. Dp) = PhiT_tile xbar_f^T over r;
-// stage 2 D2[m][n] (columns Dp .. Dp + Np) = U LegT^T over d; abar = D2 / scales.
+// ---------------------------------------------------------------- forward
+// CTA (f, d tile): stage 1 D1[d][m] = Leg_tile a_f^T over n (A = Leg tile image, B = a_f
+// rows m); stage 2 D2[d][r] = W Phi^T over m (A = scaled W from TMEM, B = Phi image);
+// x[f][d][r] = D2 / scales.  xmax != NULL: the largest |x| the CTA wrote goes to xmax[f] by
+// atomicMax on its float bits (non-negative floats order like their bit patterns, so the
+// result is independent of order).
 __global__ void __launch_bounds__(MD_THREADS, 1)
-k_modes_adj(MdDims z, const float *__restrict__ xb_all, const uint8_t *__restrict__ phit_img,
+k_modes_fwd(MdDims z, int ns, const float *__restrict__ a_all, int skip_dc, const uint8_t *__restrict__ leg_img,
+            const uint8_t *__restrict__ phi_img, float *__restrict__ x_all, int *__restrict__ status, int ncols,
+            unsigned *__restrict__ xmax, StripArgs sp)
+{
+    const int f = blockIdx.x, dt = blockIdx.y;
+    const MdSmem m = md_smem(z.Mp > z.Rp ? z.Mp : z.Rp, ns);
+    const uint32_t tmem = md_setup(m, ncols);
+    MdPlan p;
+    p.img1 = leg_img + (size_t)dt * (z.Np / 64) * 2 * 128 * 128;
+    p.img2 = phi_img;
+    p.src = a_all + (size_t)f * z.M * z.N;
+    p.src_rows = z.M;
+    p.src_cols = z.N;
+    p.n1 = z.Np / 64;
+    p.nb1 = z.Mp;
+    p.nb2 = z.Rp;
+    p.skip_dc = skip_dc != 0;
+    float sa, g;
+    const bool ok = md_two_stage(m, ns, tmem, p, sa, g);
+    // x = D2 / (g 2^28 sa), through slot 0's A atom (free once the last MMAs are complete);
+    // with strips (one CTA per channel) the channel's largest |x| is read from TMEM first
+    // (inv is a power of two, so it is the largest stored |x| exactly) and sets their scale
+    const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sa);
+    StripOut so{nullptr, nullptr, 0, 1, 0, 0, 1.f};
+    if (sp.hi && ok) {                          // uniform
+        const float cm = md_tmem_max(tmem, z.Mp, z.Rp, m.red) * inv;
+        so.hi = sp.hi + (size_t)f * z.D * sp.Ly + sp.off;
+        so.lo = sp.lo + (size_t)f * z.D * sp.Ly + sp.off;
+        so.Ly = sp.Ly;
+        so.q = sp.q;
+        so.bf16 = sp.bf16;
+        so.vec4 = sp.q == 1 && (sp.off & 3) == 0 && (sp.Ly & 3) == 0 &&
+                  ((reinterpret_cast<uintptr_t>(sp.hi) | reinterpret_cast<uintptr_t>(sp.lo)) & 7) == 0;
+        so.sc = pow2_below(cm);
+        if (threadIdx.x == 0) xmax[f] = __float_as_uint(cm);
+    }
+    float xm = 0.f;
+    if (ok)
+        xm = md_store_rows(tmem, z.Mp, z.Rp, 128 * dt, z.D, z.R, inv, x_all + (size_t)f * z.D * z.R, (size_t)z.R,
+                           reinterpret_cast<float *>(m.a(0)), so);
+    if (xmax && !sp.hi) {                       // uniform: every thread takes part
+        const float bm = block_max(xm, m.red);
+        if (threadIdx.x == 0 && ok) atomicMax(xmax + f, __float_as_uint(bm));
+    }
+    md_finish(m, ok, status, tmem, ncols);
+}
+
+// ---------------------------------------------------------------- adjoint
+// CTA (f, m tile): stage 1 D1[m][d] = PhiT_tile xbar_f^T over r (A = PhiT tile image, B =
+// xbar_f rows d); stage 2 D2[m][n] = U LegT^T over d (A = scaled U from TMEM, B = LegT
+// image); abar = D2 / scales.
+__global__ void __launch_bounds__(MD_THREADS, 1)
+k_modes_adj(MdDims z, int ns, const float *__restrict__ xb_all, const uint8_t *__restrict__ phit_img,
             const uint8_t *__restrict__ legt_img, float *__restrict__ abar_all, int *__restrict__ status, int ncols)
 {
     const int f = blockIdx.x, mtile = blockIdx.y;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    MdSmem m = md_smem(z.Dp > z.Np ? z.Dp : z.Np);
-    if (tid == 0) {
-        mbar_init(m.bar, 1);
-        *m.abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) tmem_alloc(su32(m.tmem_slot), (uint32_t)ncols);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *m.tmem_slot;
-    const float *xb = xb_all + (size_t)f * z.D * z.R;
-    uint32_t ph = 0;
-    bool ok = true;
-
-    const float sx = pow2_below(md_absmax(xb, z.D, z.R, false, m.red));
-
-    // stage 1: K = r, A = PhiT tile image, B = xbar_f rows d
-    const uint32_t idesc1 = idesc_f16(128, z.Dp, 0);
-    for (int ka = 0; ka < z.Rp / 64 && ok; ++ka) {
-        md_copy_atom(m.a, phit_img + ((size_t)mtile * (z.Rp / 64) + ka) * 2 * 128 * 128, 128);
-        md_convert_atom(xb, z.D, z.R, z.Dp, ka, sx, false, m.b);
-        md_filled();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_atom(tmem, m.a_s, m.b_s, z.Dp, ka == 0, idesc1);
-            mma_commit(m.bar);
-        }
-        ok = md_wait(m, ph);
-        ph ^= 1u;
-    }
-    tc_fence_after();
-
-    // stage 2: K = d, A = scaled U from TMEM, B = LegT image
-    const float g = ok ? pow2_below(md_tmem_max(tmem, 0, z.Dp, m.red)) : 1.f;
-    const uint32_t idesc2 = idesc_f16(128, z.Np, 0);
-    for (int ka = 0; ka < z.Dp / 64 && ok; ++ka) {
-        md_tmem_to_atom(tmem, 0, ka, g, m.a);
-        md_copy_atom(m.b, legt_img + (size_t)ka * 2 * z.Np * 128, z.Np);
-        tc_fence_before();
-        md_filled();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_atom(tmem + (uint32_t)z.Dp, m.a_s, m.b_s, z.Np, ka == 0, idesc2);
-            mma_commit(m.bar);
-        }
-        ok = md_wait(m, ph);
-        ph ^= 1u;
-    }
-    tc_fence_after();
-
+    const MdSmem m = md_smem(z.Dp > z.Np ? z.Dp : z.Np, ns);
+    const uint32_t tmem = md_setup(m, ncols);
+    MdPlan p;
+    p.img1 = phit_img + (size_t)mtile * (z.Rp / 64) * 2 * 128 * 128;
+    p.img2 = legt_img;
+    p.src = xb_all + (size_t)f * z.D * z.R;
+    p.src_rows = z.D;
+    p.src_cols = z.R;
+    p.n1 = z.Rp / 64;
+    p.nb1 = z.Dp;
+    p.nb2 = z.Np;
+    p.skip_dc = false;
+    float sx, g;
+    const bool ok = md_two_stage(m, ns, tmem, p, sx, g);
     if (ok) {
         const float inv = 1.f / (g * MD_CSCALE * MD_CSCALE * sx);
         md_store_rows(tmem, z.Dp, z.Np, 128 * mtile, z.M, z.N, inv, abar_all + (size_t)f * z.M * z.N, (size_t)z.N,
-                      reinterpret_cast<float *>(m.a));
+                      reinterpret_cast<float *>(m.a(0)), StripOut{nullptr, nullptr, 0, 1, 0, 0, 1.f});
     }
-    tc_fence_before();
-    __syncthreads();
-    if (*m.abort_flag && tid == 0) {
-        mbar_drain(m.bar, ph ^ 1u);            // the atom whose wait gave up
-        atomicExch(status, (int)FM_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, (uint32_t)ncols);
-    }
+    md_finish(m, ok, status, tmem, ncols);
 }
 
 MdDims md_dims(const Ctx &c)
@@ -521,7 +606,21 @@ MdDims md_dims(const Ctx &c)
     return z;
 }
 
-size_t md_smem_bytes(int b_rows_max) { return 1024 + 2 * 128 * 128 + 2 * (size_t)b_rows_max * 128 + 64 + 64; }
+size_t md_smem_bytes(int b_rows_max, int ns) { return 1024 + (size_t)ns * md_slot_bytes(b_rows_max) + 128; }
+
+// two operand slots when the grid fills at most one wave of one CTA per SM; one otherwise
+// (smaller CTAs: two can share an SM where TMEM allows)
+int md_slots(int grid)
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return grid <= sms ? 2 : 1;
+}
 
 int md_cols(int n)
 {
@@ -568,7 +667,6 @@ fm_status modes_tc_setup(Ctx &c)
     }
     k_md_image<<<256, 256>>>(c.g.leg64, c.D, c.N, 1, 0, z.Np, z.Dp, MD_CSCALE, s.legt_img);
     FM_CK_LAUNCH();
-    const size_t sf = md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp), sa = md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np);
     FM_CK(smem_opt_in(k_modes_fwd));
     FM_CK(smem_opt_in(k_modes_adj));
     FM_CK(cudaDeviceSynchronize());
@@ -576,12 +674,18 @@ fm_status modes_tc_setup(Ctx &c)
     return FM_OK;
 }
 
-fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax)
+fm_status launch_modes_tc_forward(Ctx &c, const float *a, float *x, cudaStream_t st, int skip_dc, unsigned *xmax,
+                                  const StripArgs *strips)
 {
     const MdDims z = md_dims(c);
-    const int ndt = (c.D + 127) / 128;
-    k_modes_fwd<<<dim3(c.F, ndt), MD_THREADS, md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp), st>>>(
-        z, a, skip_dc, c.mtc.leg_img, c.mtc.phi_img, x, c.status, md_cols(z.Mp + z.Rp), xmax);
+    const int ndt = (c.D + 127) / 128, ns = md_slots(c.F * ndt);
+    if (strips && (ndt != 1 || !xmax)) {
+        set_error("sky strips need one CTA per channel and the channel maxima");
+        return FM_ERR_STATE;
+    }
+    k_modes_fwd<<<dim3(c.F, ndt), MD_THREADS, md_smem_bytes(z.Mp > z.Rp ? z.Mp : z.Rp, ns), st>>>(
+        z, ns, a, skip_dc, c.mtc.leg_img, c.mtc.phi_img, x, c.status, md_cols(z.Mp + z.Rp), xmax,
+        strips ? *strips : StripArgs{});
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -596,9 +700,9 @@ fm_status launch_modes_tc_adjoint_maps(Ctx &c, const float *xbar, int nmaps, flo
 {
     MdDims z = md_dims(c);
     z.F = nmaps;
-    const int nmt = (c.M + 127) / 128;
-    k_modes_adj<<<dim3(nmaps, nmt), MD_THREADS, md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np), st>>>(
-        z, xbar, c.mtc.phit_img, c.mtc.legt_img, abar, c.status, md_cols(z.Dp + z.Np));
+    const int nmt = (c.M + 127) / 128, ns = md_slots(nmaps * nmt);
+    k_modes_adj<<<dim3(nmaps, nmt), MD_THREADS, md_smem_bytes(z.Dp > z.Np ? z.Dp : z.Np, ns), st>>>(
+        z, ns, xbar, c.mtc.phit_img, c.mtc.legt_img, abar, c.status, md_cols(z.Dp + z.Np));
     FM_CK_LAUNCH();
     return FM_OK;
 }

@@ -159,11 +159,12 @@ template <> const float *tab_leg<float>(const Ctx &c) { return c.g.leg32; }
 
 // x[f][d][r] = sum_n P[d][n] sum_m Phi[r][m] a[f][m][n]   (Eq. fg_separable)
 template <typename R>
-fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc, unsigned *xmax)
+fm_status launch_modes_forward(Ctx &c, const R *a, R *x, cudaStream_t st, int skip_dc, unsigned *xmax,
+                               const StripArgs *strips)
 {
     if constexpr (std::is_same<R, float>::value)
-        if (c.mtc.on) return launch_modes_tc_forward(c, a, x, st, skip_dc, xmax);
-    if (xmax) {
+        if (c.mtc.on) return launch_modes_tc_forward(c, a, x, st, skip_dc, xmax, strips);
+    if (xmax || strips) {
         set_error("channel maxima are formed only by the tensor-core mode transform");
         return FM_ERR_STATE;
     }
@@ -1088,7 +1089,8 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
 #define FM_INST(R)                                                                                       \
     template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t, const R *); \
     template fm_status launch_gain_reduce_chan<R>(Ctx &, const R *, R *, cudaStream_t);                 \
-    template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int, unsigned *);    \
+    template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int, unsigned *,        \
+                                               const StripArgs *);                                           \
     template fm_status launch_modes_adjoint<R>(Ctx &, const R *, R *, cudaStream_t);                     \
     template fm_status launch_gains<R>(Ctx &, const R *, R *, cudaStream_t);                             \
     template fm_status launch_vis<R>(Ctx &, const R *, R *, cudaStream_t);                               \
