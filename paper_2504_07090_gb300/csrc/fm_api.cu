@@ -279,11 +279,11 @@ static fm_status create_impl(const fm_config *cfg, Ctx *c)
 // (inside the last kernel of the hour-angle form, as a separate pass otherwise)
 template <typename R>
 static fm_status run_vis(Ctx &c, const R *x, R *vis, cudaStream_t st, const R *dc = nullptr, long long dcs = 0,
-                         bool xmax_ready = false, bool strips_ready = false)
+                         bool xmax_ready = false, bool strips_ready = false, bool partials_only = false)
 {
     // the tensor-core launchers time their main kernel themselves
     if constexpr (std::is_same<R, float>::value) {
-        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs, xmax_ready, strips_ready);
+        if (c.ha.on) return launch_vis_ha(c, x, vis, st, dc, dcs, xmax_ready, strips_ready, partials_only);
         if (c.prec >= FM_PREC_BF16X1) {
             FM_TRY(launch_vis_tc(c, x, vis, st));
             return dc ? launch_add_dc<R>(c, dc, dcs, vis, st) : FM_OK;
@@ -304,8 +304,12 @@ static fm_status run_adjoint(Ctx &c, const R *omega, R *xbar, cudaStream_t st, b
 }
 
 template <typename R>
-fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st)
+fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st, bool partials_only)
 {
+    if (partials_only && !(std::is_same<R, float>::value && c.ha.on)) {
+        set_error("unfinished visibilities exist only in the hour-angle form");
+        return FM_ERR_STATE;
+    }
     // hour-angle form after the tensor-core transform: the transform forms the channel maxima
     // of x that scale the sky strip, and with one CTA per channel the strips themselves
     unsigned *xmax = nullptr;
@@ -319,10 +323,10 @@ fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st)
         }
     const bool dc = c.dc_split;
     FM_TRY(launch_modes_forward<R>(c, a, xbuf, st, dc ? 1 : 0, xmax, strips ? &sa : nullptr));
-    return run_vis<R>(c, xbuf, vis, st, dc ? a : nullptr, dc ? c.nk : 0, xmax != nullptr, strips);
+    return run_vis<R>(c, xbuf, vis, st, dc ? a : nullptr, dc ? c.nk : 0, xmax != nullptr, strips, partials_only);
 }
-template fm_status vis_of_modes<float>(Ctx &, const float *, float *, float *, cudaStream_t);
-template fm_status vis_of_modes<double>(Ctx &, const double *, double *, double *, cudaStream_t);
+template fm_status vis_of_modes<float>(Ctx &, const float *, float *, float *, cudaStream_t, bool);
+template fm_status vis_of_modes<double>(Ctx &, const double *, double *, double *, cudaStream_t, bool);
 
 template <typename R>
 fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out, R *grad, cudaStream_t st,
@@ -335,10 +339,17 @@ fm_status run_chi2_grad(Ctx &c, const R *theta, double *chi2_out, double *u_out,
         FM_TRY(launch_freq_expand<R>(c, theta, (R *)c.ax, st));
         sky = (const R *)c.ax;
     }
-    FM_TRY(vis_of_modes<R>(c, sky, x, vis, st));
-    // hour-angle form: the epilogue forms the group sums of omega itself
+    // hour-angle form: the epilogue forms the group sums of omega itself, and without the
+    // delay filter (one LST pass) also V from the forward's partial sums
     const bool groups = std::is_same<R, float>::value && c.ha.on;
-    if (c.df_on) {
+    HaVSrc hv;
+    bool fused = false;
+    if constexpr (std::is_same<R, float>::value)
+        if (groups && !c.df_on) fused = ha_vsrc(c, c.dc_split ? sky : nullptr, c.nk, hv);
+    FM_TRY(vis_of_modes<R>(c, sky, x, vis, st, fused));
+    if (fused) {
+        FM_TRY(launch_chi2_chan<R>(c, nullptr, theta + c.n_sky, om, zp, c.chi2p, groups, st, nullptr, &hv));
+    } else if (c.df_on) {
         // delay filter: the filtered chi^2 and the residual weights sigma^2 F^T W F r, which the
         // epilogue then uses in place of m - d (its own chi^2 partials are not used)
         FM_TRY(launch_delay_filter<R>(c, vis, theta + c.n_sky, st));

@@ -151,6 +151,7 @@ struct HaState {
     int *ncontrib = nullptr;   // [nmt * F] forward CTAs contributing to each segment
     uint16_t *ys = nullptr;    // [2][F][D][Ly] scaled sky strips in the forward's cell order, hi then lo
     unsigned *xmax = nullptr;  // [F] max |x| of the centred sky per channel, as float bits
+    float *ug = nullptr;       // [F][T][U][2] monopole visibility of each group (k_ha_monopole)
     float *vpart = nullptr;    // [nmt * F][J][128][npad] forward partial sums
     float *q32 = nullptr;      // [F][T][U][2] residual weights summed per group
     float *qmax_ft = nullptr;  // [F][T] max |Re Q|, |Im Q| per (channel, LST)
@@ -368,9 +369,29 @@ fm_status launch_gain_reduce(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t 
 // per-(channel, LST) form of the chi^2 epilogue (gradient path): chi2p[f][t], the gain
 // partials zpart[f][t][a][2], omega, or (groups) the hour-angle group sums of omega; the
 // gains are formed inside from the coefficients gamma [A][NG][2]
+// The hour-angle forward's unfinished output (one pass over the LSTs), from which the chi^2
+// epilogue forms V itself: V_b = sc (S[2u], s S[2u+1]) + c_f (Ug_re[u], s Ug_im[u]) for member
+// b of group u (s = -1 when reversed), S = the sum over the segment's contributors of the
+// partial rows at the CTA's LST, sc = 1 / (sp 2^(14-e)) for the channel maximum xmax[f] in
+// [2^(e-1), 2^e), c_f = dc[f dcs] (0 without the monopole split).
+struct HaVSrc {
+    const float *vpart = nullptr;    // [nmt F][J][npad][128]
+    const int *ncontrib = nullptr;   // [nmt F]
+    const int *bmap = nullptr;       // [B] 2 u + reversed
+    const unsigned *xmax = nullptr;  // [F]
+    const float *dc = nullptr;
+    long long dcs = 0;
+    const float *ug = nullptr;       // [F][T][U][2]
+    float sp = 1.f;
+    int J = 0, npad = 0, nmt = 0, F = 0;
+};
+// fills v when the epilogue can form V from the partials (hour-angle form on, one LST pass,
+// the groups' monopole visibilities present when dc != nullptr)
+bool ha_vsrc(const Ctx &c, const float *dc, long long dcs, HaVSrc &v);
+
 template <typename R>
 fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zpart, double *chi2p, bool groups,
-                           cudaStream_t st, const R *rin = nullptr);
+                           cudaStream_t st, const R *rin = nullptr, const HaVSrc *hv = nullptr);
 // grad_gain from zpart in one pass over (channel, LST)
 template <typename R>
 fm_status launch_gain_reduce_chan(Ctx &c, const R *zpart, R *grad_gain, cudaStream_t st);
@@ -389,7 +410,7 @@ fm_status launch_center(Ctx &c, const R *x, R *xc, R *mean, cudaStream_t st);
 // on the FP32 paths, V(x) directly on the FP64 path; x is left in `xbuf`
 fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st);
 template <typename R>
-fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st);
+fm_status vis_of_modes(Ctx &c, const R *a, R *xbuf, R *vis, cudaStream_t st, bool partials_only = false);
 
 // tensor-core contraction (sm_103a tcgen05); returns FM_ERR_UNSUPPORTED when the
 // shape does not fit its tiles
@@ -411,9 +432,11 @@ fm_status launch_modes_tc_adjoint(Ctx &c, const float *xbar, float *abar, cudaSt
 fm_status launch_modes_tc_adjoint_maps(Ctx &c, const float *xbar, int nmaps, float *abar, cudaStream_t st);
 // dc != nullptr: also adds the monopole visibilities dc[f * dcs] U[f][t][b]; xmax_ready: the
 // channel maxima of x are already in c.ha.xmax (formed by the mode transform); strips_ready:
-// so are the sky strips of x (written by the mode transform)
+// so are the sky strips of x (written by the mode transform); partials_only: V is not
+// finished (the forward's partial sums stay in c.ha.vpart for the chi^2 epilogue, HaVSrc)
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc = nullptr,
-                        long long dcs = 0, bool xmax_ready = false, bool strips_ready = false);
+                        long long dcs = 0, bool xmax_ready = false, bool strips_ready = false,
+                        bool partials_only = false);
 // q_ready: the group sums q32 / qmax_ft were already formed from omega (by the chi^2 epilogue)
 fm_status launch_adjoint_ha(Ctx &c, const float *omega, float *xbar, cudaStream_t st, bool q_ready = false);
 

@@ -192,6 +192,7 @@ struct HaMonoArgs {
     const double *freq;
     const int *rep;                       // [U][2] antennas of each group's representative pair
     const int *moff, *mem;                // CSR members, b * 2 + reversed
+    float *ug;                            // [F][T][U][2] the group's value (nullptr: not kept)
 };
 
 __global__ void __launch_bounds__(256) k_ha_monopole(HaMonoArgs a, float *__restrict__ U)
@@ -244,6 +245,9 @@ __global__ void __launch_bounds__(256) k_ha_monopole(HaMonoArgs a, float *__rest
     }
     __syncthreads();
     const int m0 = a.moff[u], m1 = a.moff[u + 1];
+    if (a.ug)
+        for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+            reinterpret_cast<float2 *>(a.ug)[((size_t)f * a.T + t) * a.U + u] = make_float2((float)ar[t], (float)ai[t]);
     for (int e = threadIdx.x; e < (m1 - m0) * a.T; e += blockDim.x) {
         const int m = m0 + e / a.T, t = e % a.T;
         const int code = a.mem[m], b = code >> 1;
@@ -355,7 +359,7 @@ __device__ __forceinline__ void build_image_any(const uint32_t *strip, int Ly, i
 // Work units q in [0, Q), q = (mt F + f) nchunk + d nbc + c (c: 64-cell chunk in m order);
 // CTA g takes the contiguous range [Q g / G, Q (g+1) / G).  A segment is the part of one
 // (M-tile, channel) pair inside a CTA's range; its partial sum goes to
-// vpart[segment][j] with j the CTA's rank among the segment's contributors.
+// vpart[segment][j][t][row] with j the CTA's rank among the segment's contributors.
 //   load warp (21): per unit, the E chunk [A][HA_EW] (cells paired) (and, at the first unit of a
 //     (channel, declination) group, the two sky strips) by bulk copies;  efull[se] (tx)
 //   producers (warps 0-15): four groups of four warps take turns by unit; warp w fills TMEM
@@ -610,7 +614,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
             float *dst = nullptr;
             if (seg_last) {
                 const int jrank = blockIdx.x - cta_of((long long)seg * h.nchunk, h.Q, G);
-                dst = vpart + (((size_t)seg * h.J + jrank) * 128 + row) * h.npad;
+                dst = vpart + ((size_t)seg * h.J + jrank) * h.npad * 128 + row;
             }
             for (int c16 = 0; c16 < h.npad; c16 += 16) {
                 float v[16], a[16];
@@ -621,7 +625,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
                 if (seg_last) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        if (c16 + j < h.T) dst[c16 + j] = a[j];
+                        if (c16 + j < h.T) dst[(size_t)(c16 + j) * 128] = a[j];
                         a[j] = 0.f;
                     }
                 }
@@ -660,10 +664,10 @@ __global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float 
     const int t0 = blockIdx.y * HA_VF_T, tn = min(HA_VF_T, h.T - t0);
     const int nc = ncontrib[seg];
     for (int e = threadIdx.x; e < 128 * HA_VF_T; e += blockDim.x) {
-        const int row = e / HA_VF_T, tl = e % HA_VF_T;
+        const int row = e % 128, tl = e / 128;
         float a = 0.f;
         if (tl < tn)
-            for (int j = 0; j < nc; ++j) a += vpart[(((size_t)seg * h.J + j) * 128 + row) * h.npad + t0 + tl];
+            for (int j = 0; j < nc; ++j) a += vpart[(((size_t)seg * h.J + j) * h.npad + t0 + tl) * 128 + row];
         sv[row][tl] = a;
     }
     __syncthreads();
@@ -676,11 +680,12 @@ __global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float 
         const float sgn = (code & 1) ? -1.f : 1.f;
         for (int tl = 0; tl < tn; ++tl) {
             const size_t e = ((size_t)f * h.Tt + h.t0 + t0 + tl) * B + b;
-            float2 v = make_float2(sv[row][tl] * sc, sgn * sv[row + 1][tl] * sc);
+            // explicit roundings: the chi^2 epilogue forms the same values (HaVSrc)
+            float2 v = make_float2(__fmul_rn(sv[row][tl], sc), __fmul_rn(sgn * sv[row + 1][tl], sc));
             if (dc) {
                 const float2 u2 = reinterpret_cast<const float2 *>(U)[e];
-                v.x += cf * u2.x;
-                v.y += cf * u2.y;
+                v.x = __fmaf_rn(cf, u2.x, v.x);
+                v.y = __fmaf_rn(cf, u2.y, v.y);
             }
             reinterpret_cast<float2 *>(vis)[e] = v;
         }
@@ -1188,7 +1193,7 @@ bool make_layout_adj(const Ctx &c, bool x3, HaLayout &L)
 
 template <int ET, bool X3>
 fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cudaStream_t st, const float *dc,
-                        long long dcs, bool xmax_ready, bool strips_ready)
+                        long long dcs, bool xmax_ready, bool strips_ready, bool partials_only)
 {
     HaState &s = c.ha;
     HaLayout L;
@@ -1217,6 +1222,13 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
             FM_CK_LAUNCH();
             return FM_OK;
         }));
+        if (partials_only) {
+            if (c.T > HA_TCHUNK) {
+                set_error("the forward's partial sums hold one pass of at most %d LSTs", HA_TCHUNK);
+                return FM_ERR_STATE;
+            }
+            continue;
+        }
         k_ha_vfinish<<<dim3(s.nmt * c.F, cdiv(hc.T, HA_VF_T)), 256, 0, st>>>(hc, c.B, s.vpart, s.ncontrib, s.bmap,
                                                                              s.xmax, s.sp, dc, dcs, c.dc_u, vis);
         FM_CK_LAUNCH();
@@ -1568,7 +1580,18 @@ fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st)
     a.kap64 = c.g.kap64; a.bcoef64 = c.g.bcoef64; a.domega64 = c.g.domega64;
     a.airy = c.g.beam32 != nullptr; a.dew = c.g.dish_ew; a.dns = c.g.dish_ns; a.freq = c.g.freq64;
     a.rep = rep; a.moff = s.moff; a.mem = s.mem;
+    a.ug = nullptr;
     fm_status rc = FM_OK;
+    if (!c.ha.ug) {
+        void *q = nullptr;
+        if ((e = cudaMalloc(&q, sizeof(float) * 2 * (size_t)c.F * c.T * s.U)) != cudaSuccess) {
+            cudaFree(rep);
+            return cuda_fail(e, "cudaMalloc (group monopoles)", __FILE__, __LINE__);
+        }
+        c.allocs.push_back(q);
+        c.ha.ug = reinterpret_cast<float *>(q);
+    }
+    a.ug = c.ha.ug;
     if ((e = smem_opt_in(k_ha_monopole)) != cudaSuccess) rc = cuda_fail(e, "smem_opt_in", __FILE__, __LINE__);
     if (rc == FM_OK) {
         k_ha_monopole<<<(unsigned)((long long)c.F * s.U), 256, smem, st>>>(a, U);
@@ -1581,15 +1604,36 @@ fm_status ha_monopole(Ctx &c, float *U, cudaStream_t st)
 }
 
 fm_status launch_vis_ha(Ctx &c, const float *x, float *vis, cudaStream_t st, const float *dc, long long dcs,
-                        bool xmax_ready, bool strips_ready)
+                        bool xmax_ready, bool strips_ready, bool partials_only)
 {
     const HaDev h = make_dev(c);
-    const bool x3 = x3_of(c.prec);
+    const bool x3 = x3_of(c.prec), po = partials_only;
     if (f16_of(c.prec))
-        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready)
-                  : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready);
-    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready)
-              : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready);
+        return x3 ? vis_ha_launch<1, true>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready, po)
+                  : vis_ha_launch<1, false>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready, po);
+    return x3 ? vis_ha_launch<0, true>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready, po)
+              : vis_ha_launch<0, false>(c, h, x, vis, st, dc, dcs, xmax_ready, strips_ready, po);
+}
+
+bool ha_vsrc(const Ctx &c, const float *dc, long long dcs, HaVSrc &v)
+{
+    const HaState &s = c.ha;
+    if (!s.on || c.T > HA_TCHUNK || (dc && !s.ug)) return false;
+    if (const char *e = getenv("FM_HA_FUSED_CHI2"))      // 0: V finished by its own kernel
+        if (atoi(e) == 0) return false;
+    v.vpart = s.vpart;
+    v.ncontrib = s.ncontrib;
+    v.bmap = s.bmap;
+    v.xmax = s.xmax;
+    v.dc = dc;
+    v.dcs = dcs;
+    v.ug = s.ug;
+    v.sp = s.sp;
+    v.J = s.J;
+    v.npad = s.npad;
+    v.nmt = s.nmt;
+    v.F = c.F;
+    return true;
 }
 
 bool ha_strip_args(const Ctx &c, StripArgs &sa)

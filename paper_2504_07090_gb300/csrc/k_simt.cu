@@ -486,7 +486,9 @@ __global__ void __launch_bounds__(256) k_chi2_mid(DevGeom g, const R *__restrict
 // in CF_THREADS / A interleaved chunks (one thread each) and adds the chunks in order.  The
 // gains g_i(nu_f) = sum_k X_k(nu_f) gamma_ik are formed from the coefficients gamma in the
 // prologue.  With q32 != NULL (hour-angle form) omega is not written: its sums over the
-// baseline groups go to q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].  Needs
+// baseline groups go to q32[f][t][u] and their largest |Re|, |Im| to qmax_ft[f][t].  With
+// hv.vpart != NULL (hour-angle form, one LST pass) V is formed here from the forward's partial
+// sums and the groups' monopole visibilities (HaVSrc) instead of being read from vis.  Needs
 // A <= CF_THREADS.
 constexpr int CF_THREADS = 256;
 template <typename R>
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
                                                         R *__restrict__ zpart, double *__restrict__ chi2p, int U,
                                                         const int *__restrict__ moff, const int *__restrict__ mem,
                                                         float *__restrict__ q32, float *__restrict__ qmax_ft,
-                                                        const R *__restrict__ rin)
+                                                        const R *__restrict__ rin, HaVSrc hv)
 {
     using C2 = typename V2<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -503,6 +505,7 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
     C2 *sTi = sG + g.A;                                    // [B] term of baseline (i, j) in Z_i
     C2 *sTj = sTi + g.B;                                   // [B] term of baseline (i, j) in Z_j
     C2 *sW = sTj + g.B;                                    // [B] omega (hour-angle form)
+    float *sS = reinterpret_cast<float *>(sW + g.B);       // [nmt][128] forward partial sums (hv)
     __shared__ C2 sZ[CF_THREADS];                          // chunk sums of Z_a
     __shared__ double dred[CF_THREADS / 32];
     __shared__ float fred[CF_THREADS / 32];
@@ -519,9 +522,28 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
             sG[i].y = im;
         }
     }
+    float hsc = 0.f, hcf = 0.f;
+    if (hv.vpart) {     // the partial rows of every M-tile at this LST, summed in rank order
+        const int t = ft - f * g.T;
+        for (int e = tid; e < hv.nmt * 128; e += CF_THREADS) {
+            const int seg = (e >> 7) * hv.F + f, row = e & 127, nc = hv.ncontrib[seg];
+            float a = 0.f;
+            for (int j = 0; j < nc; ++j) a += hv.vpart[(((size_t)seg * hv.J + j) * hv.npad + t) * 128 + row];
+            sS[e] = a;
+        }
+        const float mx = __uint_as_float(hv.xmax[f]);
+        float s2 = 1.f;
+        if (mx > 0.f && isfinite(mx)) {
+            int ex;
+            frexpf(mx, &ex);
+            s2 = ldexpf(1.f, 14 - ex);
+        }
+        hsc = 1.f / (hv.sp * s2);
+        hcf = hv.dc ? hv.dc[(size_t)f * hv.dcs] : 0.f;
+    }
     __syncthreads();
     const R is2 = (R)g.inv_sigma2;
-    const C2 *vrow = reinterpret_cast<const C2 *>(vis) + (size_t)ft * g.B;
+    const C2 *vrow = vis ? reinterpret_cast<const C2 *>(vis) + (size_t)ft * g.B : nullptr;
     const C2 *drow = reinterpret_cast<const C2 *>(data) + (size_t)ft * g.B;
     // rin != NULL (delay filter): the residual weights come in precomputed, sigma^2 F^T W F r
     const C2 *rrow = rin ? reinterpret_cast<const C2 *>(rin) + (size_t)ft * g.B : nullptr;
@@ -529,7 +551,23 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
     R c2 = 0;   // a warp's terms in the working type; FP64 across warps
     for (int b = tid; b < g.B; b += CF_THREADS) {
         const int i = g.bl_i[b], j = g.bl_j[b];
-        const C2 V = vrow[b], d = drow[b], gi = sG[i], gj = sG[j];
+        C2 V;
+        if (hv.vpart) {
+            const int code = hv.bmap[b], u = code >> 1, row = 128 * (u >> 6) + 2 * (u & 63);
+            const float sgn = (code & 1) ? -1.f : 1.f;
+            // the roundings of k_ha_vfinish, so that V equals the finished forward's bitwise
+            float vx = __fmul_rn(sS[row], hsc), vy = __fmul_rn(sgn * sS[row + 1], hsc);
+            if (hv.dc) {
+                const float2 u2 = reinterpret_cast<const float2 *>(hv.ug)[(size_t)ft * U + u];
+                vx = __fmaf_rn(hcf, u2.x, vx);
+                vy = __fmaf_rn(hcf, sgn * u2.y, vy);
+            }
+            V.x = (R)vx;
+            V.y = (R)vy;
+        } else {
+            V = vrow[b];
+        }
+        const C2 d = drow[b], gi = sG[i], gj = sG[j];
         const R ggr = gi.x * gj.x + gi.y * gj.y, ggi = gi.y * gj.x - gi.x * gj.y;     // g_i conj(g_j)
         C2 r, om, ti, tj;
         if (rrow) {
@@ -664,16 +702,21 @@ __global__ void __launch_bounds__(GR_THREADS) k_gain_reduce_ft(DevGeom g, const 
 
 template <typename R>
 fm_status launch_chi2_chan(Ctx &c, const R *vis, const R *gamma, R *omega, R *zpart, double *chi2p, bool groups,
-                           cudaStream_t st, const R *rin)
+                           cudaStream_t st, const R *rin, const HaVSrc *hv)
 {
-    const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R);
+    if (hv && (!std::is_same<R, float>::value || !groups || rin)) {
+        set_error("V from the forward's partial sums: hour-angle form, FP32, no delay filter");
+        return FM_ERR_STATE;
+    }
+    const size_t smem = (c.A + 3 * (size_t)c.B) * 2 * sizeof(R) + (hv ? sizeof(float) * 128 * (size_t)hv->nmt : 0);
     if (smem > 227 * 1024 || c.A > CF_THREADS) {
         set_error("chi^2 epilogue: %d antennas (at most %d, %zu bytes of shared memory)", c.A, CF_THREADS, smem);
         return FM_ERR_UNSUPPORTED;
     }
     FM_CK(smem_opt_in(k_chi2_ft<R>));
     k_chi2_ft<R><<<c.F * c.T, CF_THREADS, smem, st>>>(c.g, vis, (const R *)c.data, gamma, omega, zpart, chi2p, c.ha.U,
-                                                c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft, rin);
+                                                c.ha.moff, c.ha.mem, groups ? c.ha.q32 : nullptr, c.ha.qmax_ft, rin,
+                                                hv ? *hv : HaVSrc{});
     FM_CK_LAUNCH();
     return FM_OK;
 }
@@ -1087,7 +1130,8 @@ fm_status launch_d2f(long long n, const double *a, float *b, cudaStream_t st)
 }
 
 #define FM_INST(R)                                                                                       \
-    template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t, const R *); \
+    template fm_status launch_chi2_chan<R>(Ctx &, const R *, const R *, R *, R *, double *, bool, cudaStream_t, const R *, \
+                                           const HaVSrc *);                                              \
     template fm_status launch_gain_reduce_chan<R>(Ctx &, const R *, R *, cudaStream_t);                 \
     template fm_status launch_modes_forward<R>(Ctx &, const R *, R *, cudaStream_t, int, unsigned *,        \
                                                const StripArgs *);                                           \

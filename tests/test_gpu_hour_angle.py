@@ -115,6 +115,29 @@ def test_repeat_runs_are_bitwise_identical():
     assert bool((s1 == s2).all()) and bool((g1 == g2).all())
 
 
+# With one pass over the LSTs the chi^2 epilogue forms V itself from the forward's partial
+# sums, with the roundings of the kernel that otherwise finishes V (FM_HA_FUSED_CHI2=0): the
+# two routes give the same bits, and the fused one launches one kernel fewer.  harand has two
+# forward M-tiles, hafrac2 cells of half a pixel.
+@pytest.mark.parametrize("name", ["ha37", "harand", "hafrac2"])
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+def test_fused_chi2_epilogue_equals_the_finished_forward(name, prec, monkeypatch):
+    from paper_2504_07090_gb300 import fm
+    p, o, th, d, mu, lam = make_case(name)
+    d, mu, lam = quant(prec, d, mu, lam)
+    h = handle(p, prec, d, mu, lam)
+    t = _t(quant(prec, perturbed(o, th, 0.01, 2)), h)
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("FM_HA_FUSED_CHI2", fused)
+        n0 = fm.kernel_launches()
+        s, g = h.chi2_grad(t)
+        out[fused] = (s.clone(), g.clone(), fm.kernel_launches() - n0)
+    (s1, g1, n1), (s0, g0, n0) = out["1"], out["0"]
+    assert bool((s1 == s0).all()) and bool((g1 == g0).all())
+    assert n1 == n0 - 1
+
+
 def test_antenna_form_is_used_when_disabled(monkeypatch, check_err):
     monkeypatch.setenv("FM_HA", "0")
     p, o, th, d, mu, lam = make_case("ha37")
