@@ -986,14 +986,26 @@ __global__ void __launch_bounds__(256) k_lf_solve_diag(long long n, const R *__r
     if (threadIdx.x == 0 && kin) kin[blockIdx.x] = red[0];
 }
 
-__global__ void __launch_bounds__(256) k_sum_to(int n, const double *__restrict__ part, double *__restrict__ out)
+// out = half the sum of part[0 .. n) in a fixed order: thread t adds the elements t + 1024 j in
+// four interleaved running sums (four loads in flight), then the threads' sums pairwise
+constexpr int SUM_THREADS = 1024;
+__global__ void __launch_bounds__(SUM_THREADS) k_sum_to(int n, const double *__restrict__ part, double *__restrict__ out)
 {
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
-    red[threadIdx.x] = s;
+    __shared__ double red[SUM_THREADS];
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * SUM_THREADS) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * SUM_THREADS;
+            v[u] = i < n ? part[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += v[u];
+    }
+    red[threadIdx.x] = (s[0] + s[1]) + (s[2] + s[3]);
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    for (int w = SUM_THREADS / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
@@ -1065,14 +1077,14 @@ static fm_status lf_blocks(Ctx &c, const R *in, int fwd, int bwd, int mul, R *q,
             FM_CK_LAUNCH();
         }
         if (kin_out) {
-            k_sum_to<<<1, 256, 0, st>>>((int)(nb + ng), part, kin_out);
+            k_sum_to<<<1, SUM_THREADS, 0, st>>>((int)(nb + ng), part, kin_out);
             FM_CK_LAUNCH();
         }
     } else {
         k_lf_solve_diag<R><<<512, 256, 0, st>>>(c.n_par, L, in, fwd, bwd, mul, q, peps, out, kin_out ? part : nullptr);
         FM_CK_LAUNCH();
         if (kin_out) {
-            k_sum_to<<<1, 256, 0, st>>>(512, part, kin_out);
+            k_sum_to<<<1, SUM_THREADS, 0, st>>>(512, part, kin_out);
             FM_CK_LAUNCH();
         }
     }

@@ -972,23 +972,40 @@ __global__ void __launch_bounds__(PT_THREADS) k_prior_total(long long n, int vec
             const Pack16<R> *lp = reinterpret_cast<const Pack16<R> *>(lam);
             Pack16<R> *gp = reinterpret_cast<Pack16<R> *>(grad);
             Pack16<R> *pp = reinterpret_cast<Pack16<R> *>(p);
-            for (long long k = gtid; k < np; k += gstride) {
-                Pack16<R> gr = gp[k];
-                if (lam) {
-                    const Pack16<R> t = th[k], m = mp[k], l = lp[k];
+            // two packs a thread at a time (k and k + gstride), all their loads issued first;
+            // the terms still go into acc in the order of k
+            for (long long k0 = gtid; k0 < np; k0 += 2 * gstride) {
+                const long long kk[2] = {k0, k0 + gstride};
+                const bool has1 = kk[1] < np;
+                Pack16<R> gr[2], t[2], m[2], l[2], pv[2];
 #pragma unroll
-                    for (int e = 0; e < W; ++e) {
-                        const R dv = t.v[e] - m.v[e], ld = l.v[e] * dv;
-                        gr.v[e] += ld;
-                        acc += ld * dv;
+                for (int u = 0; u < 2; ++u) {
+                    if (u == 1 && !has1) break;
+                    gr[u] = gp[kk[u]];
+                    if (lam) {
+                        t[u] = th[kk[u]];
+                        m[u] = mp[kk[u]];
+                        l[u] = lp[kk[u]];
                     }
-                    gp[k] = gr;
+                    if (p) pv[u] = pp[kk[u]];
                 }
-                if (p) {
-                    Pack16<R> pv = pp[k];
 #pragma unroll
-                    for (int e = 0; e < W; ++e) pv.v[e] += ak * gr.v[e];
-                    pp[k] = pv;
+                for (int u = 0; u < 2; ++u) {
+                    if (u == 1 && !has1) break;
+                    if (lam) {
+#pragma unroll
+                        for (int e = 0; e < W; ++e) {
+                            const R dv = t[u].v[e] - m[u].v[e], ld = l[u].v[e] * dv;
+                            gr[u].v[e] += ld;
+                            acc += ld * dv;
+                        }
+                        gp[kk[u]] = gr[u];
+                    }
+                    if (p) {
+#pragma unroll
+                        for (int e = 0; e < W; ++e) pv[u].v[e] += ak * gr[u].v[e];
+                        pp[kk[u]] = pv[u];
+                    }
                 }
             }
         }
