@@ -419,23 +419,29 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
     if (warp < HA_PROD_WARPS) {
         // ------------------------------------------------------------ producers
         // four groups of four warps; group pg builds the units l = q - q0 = pg, pg + 4, ...,
-        // its warp (pg, quarter) the 32 TMEM lanes of that quarter over all 64 cells
+        // its warp (pg, quarter) the 32 TMEM lanes of that quarter over all 64 cells, as two
+        // 16-lane blocks b: lanes 0-7 of a block hold the Re rows and lanes 8-15 the Im rows of
+        // groups 16 quarter + 8 b + (0 .. 7) (the drain warps put the rows back in the order
+        // 2 u + (Re, Im)).  A thread forms both rows of group 16 quarter + 8 b + lane / 4 on
+        // columns 2 (lane % 4) + {0, 1} of every 8 (tcgen05.st.16x256b): one complex product
+        // per cell pair for both rows
         const int quarter = warp & 3, pg = warp / 4, gt = 32 * quarter + lane;
-        const int ul = 16 * quarter + (lane >> 1);               // group within the M-tile
-        const bool im_row = lane & 1;
+        const int ul = 16 * quarter + (lane >> 2);               // block 0's group; block 1's is ul + 8
+        const int ccb = 2 * (lane & 3);
         const uint32_t ta_row = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)L.abase;
         const int c0 = (int)(q0 % h.nbc);
         const long long per_mt = (long long)h.F * h.nchunk;
         int mt = (int)((q0 + pg) / per_mt);
         long long next_mt = (long long)(mt + 1) * per_mt;
         int c = (int)((q0 + pg) % h.nbc);
-        int2 ij = h.uij[mt * 64 + ul];
+        int2 ij0 = h.uij[mt * 64 + ul], ij1 = h.uij[mt * 64 + ul + 8];
         for (long long l = pg; q0 + l < q1; l += HA_PGROUPS) {
             const long long q = q0 + l;
             if (q >= next_mt) {
                 mt = (int)(q / per_mt);
                 next_mt = (long long)(mt + 1) * per_mt;
-                ij = h.uij[mt * 64 + ul];
+                ij0 = h.uij[mt * 64 + ul];
+                ij1 = h.uij[mt * 64 + ul + 8];
             }
             const int se = (int)(l % L.neslot), s = (int)(l % L.nstage);
             const uint32_t eph = (uint32_t)((l / L.neslot) & 1), ph = (uint32_t)((l / L.nstage) & 1);
@@ -462,30 +468,39 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
                 else build_image_any<NT>(strip, h.Lyc, h.Jc, h.k, L.img_bytes, img, gt, 128);
             }
             {
-                const uint8_t *ei = eslot + (size_t)ij.x * (HA_EW * 8), *ej = eslot + (size_t)ij.y * (HA_EW * 8);
                 const uint32_t ta = ta_row + (uint32_t)(s * L.acols);
 #pragma unroll 1
-                for (int kq = 0; kq < 4; ++kq) {
-                    // column 8 kq + cc holds cells m = 16 kq + 2 cc (low half) and + 1, i.e.
-                    // table cells n + 1 and n with n = 62 - 16 kq - 2 cc: the row's cell pair n / 2
-                    uint32_t hw[8], lw[8];
+                for (int b = 0; b < 2; ++b) {
+                    const int2 ij = b ? ij1 : ij0;
+                    const uint8_t *ei = eslot + (size_t)ij.x * (HA_EW * 8), *ej = eslot + (size_t)ij.y * (HA_EW * 8);
+                    const uint32_t tb = ta + ((uint32_t)(16 * b) << 16);
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) {
-                        const int pc = 31 - 8 * kq - cc;
-                        const float4 a = *reinterpret_cast<const float4 *>(ei + pc * 16);
-                        const float4 b = *reinterpret_cast<const float4 *>(ej + pc * 16);
-                        // P = E_i conj(E_j) on the cell pair (n, n + 1), packed: .x cell n (odd m),
-                        // .y cell n + 1 (even m)
-                        const float2 xa = make_float2(a.x, a.y), ya = make_float2(a.z, a.w);
-                        const float2 xb = make_float2(b.x, b.y), yb = make_float2(b.z, b.w);
-                        const float2 re = __ffma2_rn(xa, xb, __fmul2_rn(ya, yb));
-                        const float2 mxy = __fmul2_rn(xa, yb);
-                        const float2 im = __ffma2_rn(ya, xb, make_float2(-mxy.x, -mxy.y));
-                        const float2 v = im_row ? im : re;
-                        Elem<ET>::split2(make_float2(v.y, v.x), hw[cc], lw[cc]);
+                    for (int kh = 0; kh < 2; ++kh) {
+                        // column 8 kq + cc holds cells m = 16 kq + 2 cc (low half) and + 1, i.e.
+                        // table cells n + 1 and n with n = 62 - 16 kq - 2 cc: the row's cell pair n / 2
+                        uint32_t hw[8], lw[8];
+#pragma unroll
+                        for (int jr = 0; jr < 2; ++jr) {
+                            const int kq = 2 * kh + jr;
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const int pc = 31 - 8 * kq - (ccb + e);
+                                const float4 a = *reinterpret_cast<const float4 *>(ei + pc * 16);
+                                const float4 bq = *reinterpret_cast<const float4 *>(ej + pc * 16);
+                                // P = E_i conj(E_j) on the cell pair (n, n + 1), packed: .x cell n
+                                // (odd m), .y cell n + 1 (even m)
+                                const float2 xa = make_float2(a.x, a.y), ya = make_float2(a.z, a.w);
+                                const float2 xb = make_float2(bq.x, bq.y), yb = make_float2(bq.z, bq.w);
+                                const float2 re = __ffma2_rn(xa, xb, __fmul2_rn(ya, yb));
+                                const float2 mxy = __fmul2_rn(xa, yb);
+                                const float2 im = __ffma2_rn(ya, xb, make_float2(-mxy.x, -mxy.y));
+                                Elem<ET>::split2(make_float2(re.y, re.x), hw[4 * jr + e], lw[4 * jr + e]);
+                                Elem<ET>::split2(make_float2(im.y, im.x), hw[4 * jr + 2 + e], lw[4 * jr + 2 + e]);
+                            }
+                        }
+                        tmem_st_16x256b_x2(tb + 16u * kh, hw);
+                        if (X3) tmem_st_16x256b_x2(tb + 32u + 16u * kh, lw);
                     }
-                    tmem_st8(ta + 8u * kq, hw);
-                    if (X3) tmem_st8(ta + 32u + 8u * kq, lw);
                 }
                 tmem_wait_st();
             }
@@ -588,7 +603,10 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
         }
     } else {
         // ------------------------------------------------------------ epilogue (warps 16-19)
-        const int quarter = warp & 3, row = 32 * quarter + lane;
+        // TMEM lane 32 quarter + 16 b + 8 part + j holds row 2 u + part of group
+        // u = 16 quarter + 8 b + j (the producers' 16-lane blocks)
+        const int quarter = warp & 3, lb = lane & 15;
+        const int row = 32 * quarter + 16 * (lane >> 4) + 2 * (lb & 7) + (lb >> 3);
         // the running sum of the segment lives in TMEM columns [2 npad, 3 npad)
         const uint32_t tsum = tmem_d + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(2 * h.npad);
         {

@@ -185,6 +185,16 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r)
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 16 lanes x 16 columns, register -> TMEM (completion: tmem_wait_st): thread t writes lanes
+// t / 4 (r[0], r[1], r[4], r[5]) and t / 4 + 8 (r[2], r[3], r[6], r[7]) of the 16 starting at
+// taddr's lane, columns 2 (t % 4) + {0, 1} (r[0..3]) and 8 + 2 (t % 4) + {0, 1} (r[4..7])
+__device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, const uint32_t *r)
+{
+    asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor, K-major without swizzle: 8 x 16-byte core matrices stored
 // as 128 contiguous bytes; `lbo` = byte step between core matrices adjacent in K, `sbo` =
 // byte step between 8-row groups (both multiples of 16).
