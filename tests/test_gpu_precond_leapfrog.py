@@ -118,8 +118,8 @@ def test_leapfrog_trajectory_matches_oracle(name, prec, form, eps, prior, check_
     # model's visibility error dm = eps_V |m| moves U by up to |m - d| |dm| / sigma^2 =
     # eps_V (|m| / sigma) (|m - d| / sigma), about 2.4e-6 x 1.4e4 x 1.4e2 = 4.8 here, less as the
     # error's direction is not the residual's: an absolute error of order one in the split modes'
-    # energy change (measured 0.76 fp16x3, 1.65 bf16x3 with the mass matrix built through the
-    # FP16-split mode transform); the direct FP32 form's 2e-4
+    # energy change (measured 0.58 fp16x3, 1.04 bf16x3; 0.76 and 1.65 with builds that rounded
+    # the same visibilities differently); the direct FP32 form's 2e-4
     check_err(e_dh, 1e-9 if exact else (2e-2 if form == "direct" else 3.0), key(form, "dH", prec), name)
     assert int(aout.item()) == 1
     # rejection restores q0: u just above the acceptance probability
