@@ -684,8 +684,18 @@ __global__ void __launch_bounds__(256) k_ha_vfinish(HaDev h, int B, const float 
     for (int e = threadIdx.x; e < 128 * HA_VF_T; e += blockDim.x) {
         const int row = e % 128, tl = e / 128;
         float a = 0.f;
-        if (tl < tn)
-            for (int j = 0; j < nc; ++j) a += vpart[(((size_t)seg * h.J + j) * h.npad + t0 + tl) * 128 + row];
+        if (tl < tn) {      // the contributors' rows in rank order, four loads ahead
+            const float *src = vpart + ((size_t)seg * h.J * h.npad + t0 + tl) * 128 + row;
+            const size_t js = (size_t)h.npad * 128;
+            for (int j0 = 0; j0 < nc; j0 += 4) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = j0 + u < nc ? src[(size_t)(j0 + u) * js] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u < nc) a += v[u];
+            }
+        }
         sv[row][tl] = a;
     }
     __syncthreads();

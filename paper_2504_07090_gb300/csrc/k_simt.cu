@@ -527,8 +527,18 @@ __global__ void __launch_bounds__(CF_THREADS, sizeof(R) == 4 ? 8 : 1) k_chi2_ft(
         const int t = ft - f * g.T;
         for (int e = tid; e < hv.nmt * 128; e += CF_THREADS) {
             const int seg = (e >> 7) * hv.F + f, row = e & 127, nc = hv.ncontrib[seg];
+            // the contributors' rows in rank order, four loads ahead
+            const float *src = hv.vpart + ((size_t)seg * hv.J * hv.npad + t) * 128 + row;
+            const size_t js = (size_t)hv.npad * 128;
             float a = 0.f;
-            for (int j = 0; j < nc; ++j) a += hv.vpart[(((size_t)seg * hv.J + j) * hv.npad + t) * 128 + row];
+            for (int j0 = 0; j0 < nc; j0 += 4) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = j0 + u < nc ? src[(size_t)(j0 + u) * js] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u < nc) a += v[u];
+            }
             sS[e] = a;
         }
         const float mx = __uint_as_float(hv.xmax[f]);
