@@ -782,7 +782,7 @@ static fm_status vis_tc_launch(Ctx &c, const FwdLayout &L, int rch, int sub, siz
 fm_status launch_vis_tc(Ctx &c, const float *x, float *vis, cudaStream_t st)
 {
     if (2 * c.A > 128) {
-        set_error("tensor-core contraction supports at most 64 antennas in this build");
+        set_error("the antenna-form tensor-core contraction supports at most 64 antennas");
         return FM_ERR_UNSUPPORTED;
     }
     const bool x3 = c.prec == FM_PREC_BF16X3 || c.prec == FM_PREC_FP16X3;
@@ -849,7 +849,7 @@ static fm_status adj_tc_launch(Ctx &c, const AdjLayout &L, size_t smem, int grid
 fm_status launch_adjoint_tc(Ctx &c, const float *omega, float *xbar, cudaStream_t st)
 {
     if (2 * c.A > 128) {
-        set_error("tensor-core adjoint supports at most 64 antennas in this build");
+        set_error("the antenna-form tensor-core adjoint supports at most 64 antennas");
         return FM_ERR_UNSUPPORTED;
     }
     if (!c.tc_wbar) {
