@@ -42,12 +42,12 @@ namespace {
 
 using namespace tc;
 
+// the adjoint's roles (the forward's are the HF_ constants below)
 constexpr int HA_PROD_WARPS = 16;
 constexpr int HA_EPI_WARP0 = 16;          // warps 16..19 drain TMEM (lane quarter = warp & 3)
 constexpr int HA_MMA_WARP = 20;
 constexpr int HA_LOAD_WARP = 21;          // bulk copies of the phasor table (and sky strips)
 constexpr int HA_QLOAD_WARP = 22;         // adjoint only: bulk copies of the residual tiles
-constexpr int HA_THREADS = 22 * 32;       // forward
 constexpr int HA_EPI2_WARP0 = 23;         // adjoint only: warps 23..26, the second epilogue set
 constexpr int HA_ADJ_THREADS = 27 * 32;   // adjoint
 constexpr int HA_SUB = 4;                 // 64-cell K chunks per TMEM accumulation chain (shorter chains: less FP32 accumulation bias)
@@ -56,7 +56,15 @@ constexpr int HA_EW = 66;                 // float2 entries per table row: 64 ce
 constexpr int HA_NSTAGE = 4;              // adjoint operand stages (A in TMEM, B in shared memory)
 constexpr int HA_TCHUNK = 64;             // LSTs per pass (the GEMM's N); more run as several passes
 constexpr int HA_NSTAGE_FWD = 5;          // forward A stages in TMEM
-constexpr int HA_PGROUPS = 4;             // forward producer groups of HA_PROD_WARPS / 4 warps, one unit each
+// the forward's roles: HF_PROD_WARPS producer warps in HF_PGROUPS groups of four (one unit each),
+// then four TMEM-drain warps, the MMA warp and the bulk-copy warp
+constexpr int HF_PROD_WARPS = 12;
+constexpr int HF_PGROUPS = HF_PROD_WARPS / 4;
+constexpr int HF_EPI_WARP0 = HF_PROD_WARPS;
+constexpr int HF_MMA_WARP = HF_PROD_WARPS + 4;
+constexpr int HF_LOAD_WARP = HF_PROD_WARPS + 5;
+constexpr int HF_THREADS = (HF_PROD_WARPS + 6) * 32;
+static_assert((HF_MMA_WARP & 3) == 0 && HF_EPI_WARP0 + 4 == HF_MMA_WARP, "the MMA warp on the first sub-partition");
 
 // kernel parameters, by value
 struct HaDev {
@@ -371,7 +379,7 @@ __device__ __forceinline__ void build_image_any(const uint32_t *strip, int Ly, i
 //   epilogue (16-19): adds the chain into the segment's running sum in TMEM columns
 //     [2 npad, 3 npad), writes it at the end of a segment;  acce[q] (4 arrivals)
 template <int ET, bool X3>
-__global__ void __launch_bounds__(HA_THREADS, 1)
+__global__ void __launch_bounds__(HF_THREADS, 1)
 k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t *__restrict__ ys_lo,
          float *__restrict__ vpart, int *__restrict__ status)
 {
@@ -390,12 +398,12 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < L.nstage; ++s) {
-            mbar_init(full0 + 8 * s, HA_PROD_WARPS / HA_PGROUPS);
+            mbar_init(full0 + 8 * s, HF_PROD_WARPS / HF_PGROUPS);
             mbar_init(empty0 + 8 * s, 1);
         }
         for (int s = 0; s < L.neslot; ++s) {
             mbar_init(efull0 + 8 * s, 1);
-            mbar_init(eempty0 + 8 * s, HA_PROD_WARPS / HA_PGROUPS);
+            mbar_init(eempty0 + 8 * s, HF_PROD_WARPS / HF_PGROUPS);
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(accf0 + 8 * q, 1);
@@ -405,7 +413,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == HA_MMA_WARP) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
+    if (warp == HF_MMA_WARP) tmem_alloc(su32(tmem_slot), (uint32_t)L.ncols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -416,9 +424,9 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
     const uint32_t eb = (uint32_t)h.A * (uint32_t)(HA_EW * 8);    // E chunk bytes
     const uint32_t sb = (uint32_t)h.Lyc * 2u;                     // bytes of one strip part (this chunk)
 
-    if (warp < HA_PROD_WARPS) {
+    if (warp < HF_PROD_WARPS) {
         // ------------------------------------------------------------ producers
-        // four groups of four warps; group pg builds the units l = q - q0 = pg, pg + 4, ...,
+        // HF_PGROUPS groups of four warps; group pg builds the units l = q - q0 = pg, pg + HF_PGROUPS, ...,
         // its warp (pg, quarter) the 32 TMEM lanes of that quarter over all 64 cells, as two
         // 16-lane blocks b: lanes 0-7 of a block hold the Re rows and lanes 8-15 the Im rows of
         // groups 16 quarter + 8 b + (0 .. 7) (the drain warps put the rows back in the order
@@ -435,7 +443,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
         long long next_mt = (long long)(mt + 1) * per_mt;
         int c = (int)((q0 + pg) % h.nbc);
         int2 ij0 = h.uij[mt * 64 + ul], ij1 = h.uij[mt * 64 + ul + 8];
-        for (long long l = pg; q0 + l < q1; l += HA_PGROUPS) {
+        for (long long l = pg; q0 + l < q1; l += HF_PGROUPS) {
             const long long q = q0 + l;
             if (q >= next_mt) {
                 mt = (int)(q / per_mt);
@@ -510,9 +518,9 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(full0 + 8 * s);
-            c = (c + HA_PGROUPS) % h.nbc;
+            c = (c + HF_PGROUPS) % h.nbc;
         }
-    } else if (warp == HA_LOAD_WARP) {
+    } else if (warp == HF_LOAD_WARP) {
         // ------------------------------------------------------------ bulk loads of E chunks
         if (lane == 0) {
             int se = 0, last_se = -1;
@@ -552,7 +560,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
                 }
             }
         }
-    } else if (warp == HA_MMA_WARP) {
+    } else if (warp == HF_MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(128, h.npad, Elem<ET>::kFmt);
@@ -602,7 +610,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
             if (*abort_flag && last_s >= 0) mbar_drain(empty0 + 8 * last_s, last_ph);
         }
     } else {
-        // ------------------------------------------------------------ epilogue (warps 16-19)
+        // ------------------------------------------------------------ epilogue (warps HF_EPI_WARP0 ..)
         // TMEM lane 32 quarter + 16 b + 8 part + j holds row 2 u + part of group
         // u = 16 quarter + 8 b + j (the producers' 16-lane blocks)
         const int quarter = warp & 3, lb = lane & 15;
@@ -658,7 +666,7 @@ k_vis_ha(HaDev h, HaLayout L, const uint16_t *__restrict__ ys_hi, const uint16_t
 done:
     __syncthreads();
     if (*abort_flag && tid == 0) atomicExch(status, (int)FM_ERR_TIMEOUT);
-    if (warp == HA_MMA_WARP) {
+    if (warp == HF_MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tmem_d, (uint32_t)L.ncols);
     }
@@ -1246,7 +1254,7 @@ fm_status vis_ha_launch(Ctx &c, const HaDev &h, const float *x, float *vis, cuda
         hc.t0 = t0;
         hc.T = c.T - t0 < HA_TCHUNK ? c.T - t0 : HA_TCHUNK;
         FM_TRY(profiled(c, 0, st, [&]() -> fm_status {
-            k_vis_ha<ET, X3><<<s.grid, HA_THREADS, L.smem, st>>>(hc, L, ys_hi, ys_lo, s.vpart, c.status);
+            k_vis_ha<ET, X3><<<s.grid, HF_THREADS, L.smem, st>>>(hc, L, ys_hi, ys_lo, s.vpart, c.status);
             FM_CK_LAUNCH();
             return FM_OK;
         }));
